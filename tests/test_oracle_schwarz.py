@@ -1,0 +1,134 @@
+"""Pins for the oracle's operator, schedules and multiplicative Schwarz step
+(Section 3.1.1).
+
+Independent references: the explicit Kronecker matrix (numpy), a brute-force
+coupling check of every colour class, and the paper's product formula
+prod_j (I - V_j^T A_j^{-1} V_j A) for the error propagation, built densely
+with numpy on tiny grids.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+
+def _dense_A(oracle_mod, dim, p, m):
+    K, M = oracle_mod.assemble_1d(p, m)
+    if dim == 2:
+        return np.kron(K, M) + np.kron(M, K), K, M
+    return (np.kron(K, np.kron(M, M)) + np.kron(M, np.kron(K, M))
+            + np.kron(M, np.kron(M, K))), K, M
+
+
+def _block(dim, n, c, r):
+    """Grid indices of the s^d box around centre index c, clipped, x fastest."""
+    cz, cy, cx = (c // (n * n), (c // n) % n, c % n) if dim == 3 else (0, c // n, c % n)
+    out = []
+    zr = range(cz - r, cz + r + 1) if dim == 3 else [0]
+    for z in zr:
+        for y in range(cy - r, cy + r + 1):
+            for x in range(cx - r, cx + r + 1):
+                if 0 <= x < n and 0 <= y < n and 0 <= z < (n if dim == 3 else 1):
+                    out.append(x + n * (y + n * z))
+    return np.array(out)
+
+
+@pytest.mark.parametrize("dim,p,m", [(2, 2, 5), (2, 5, 4), (3, 2, 4), (3, 3, 3)])
+def test_apply_A_matches_kronecker(oracle_mod, dim, p, m):
+    A, K, M = _dense_A(oracle_mod, dim, p, m)
+    u = np.random.default_rng(0).standard_normal(A.shape[0])
+    assert np.allclose(oracle_mod.apply_A(dim, K, M, u, p), A @ u, atol=1e-12)
+
+
+SCHED_CASES = [
+    # dim, p, m, kind, tile, period, stride
+    (2, 2, 14, 1, 0, 5, 2),
+    (2, 3, 14, 1, 0, 7, 2),
+    (2, 4, 12, 2, 7, 7, 2),
+    (2, 2, 20, 2, 5, 5, 2),
+    (2, 5, 15, 2, 10, 10, 3),
+    (3, 2, 8, 1, 0, 5, 2),
+    (3, 3, 9, 2, 7, 7, 2),
+]
+
+
+@pytest.mark.parametrize("dim,p,m,kind,tile,period,stride", SCHED_CASES)
+def test_schedule_colours_are_coupling_free(oracle_mod, dim, p, m, kind, tile, period, stride):
+    """Within a colour no block shares a DOF with, or reads a DOF written by, another."""
+    A, _, _ = _dense_A(oracle_mod, dim, p, m)
+    n = m + p - 2
+    s = oracle_mod.block_size(p)
+    r = (s - 1) // 2
+    colour, order, ncol = oracle_mod.schedule(dim, n, s, p, kind, tile, period, stride)
+    nz = A != 0
+    assert sorted(order.tolist()) == list(range(n ** dim))
+    assert np.all(np.diff(colour[order]) >= 0)
+    for col in np.unique(colour):
+        cent = np.nonzero(colour == col)[0]
+        blocks = [_block(dim, n, c, r) for c in cent]
+        reads = [np.nonzero(nz[b].any(axis=0))[0] for b in blocks]
+        for a, b in itertools.combinations(range(len(cent)), 2):
+            assert not np.intersect1d(blocks[a], blocks[b]).size
+            assert not np.intersect1d(blocks[a], reads[b]).size
+            assert not np.intersect1d(blocks[b], reads[a]).size
+
+
+def test_schedule_rejects_short_period(oracle_mod):
+    with pytest.raises(ValueError):
+        oracle_mod.schedule(2, 20, 3, 2, 1, 0, 4, 1)  # q < s + p
+    with pytest.raises(ValueError):
+        oracle_mod.schedule(2, 20, 3, 2, 1, 0, 6, 2)  # gcd(g, q) != 1
+    with pytest.raises(ValueError):
+        oracle_mod.schedule(2, 20, 3, 2, 2, 4, 5, 2)  # tile < q
+
+
+@pytest.mark.parametrize("dim,p,m,kind,tile", [(2, 2, 6, 0, 0), (2, 2, 8, 1, 0), (2, 3, 9, 2, 7),
+                                               (2, 5, 5, 1, 0), (3, 2, 4, 1, 0), (3, 3, 3, 0, 0)])
+def test_schwarz_matches_product_formula(oracle_mod, dim, p, m, kind, tile):
+    """u_new - u* = prod_j (I - V_j^T A_j^{-1} V_j A) (u - u*), blocks in schedule order."""
+    A, K, M = _dense_A(oracle_mod, dim, p, m)
+    n = m + p - 2
+    N = n ** dim
+    s = oracle_mod.block_size(p)
+    r = (s - 1) // 2
+    _, order, _ = oracle_mod.schedule(dim, n, s, p, kind, tile)
+    rng = np.random.default_rng(11)
+    b = rng.standard_normal(N)
+    u = rng.standard_normal(N)
+    ustar = np.linalg.solve(A, b)
+    E = np.eye(N)
+    for c in order:
+        B = _block(dim, n, c, r)
+        V = np.zeros((len(B), N))
+        V[np.arange(len(B)), B] = 1.0
+        E = (np.eye(N) - V.T @ np.linalg.solve(V @ A @ V.T, V @ A)) @ E
+    got = oracle_mod.schwarz_sweep(dim, K, M, p, s, order, b, u)
+    ref = ustar + E @ (u - ustar)
+    assert np.allclose(got, ref, atol=1e-11 * np.abs(ref).max())
+
+
+def test_order_within_colour_is_irrelevant(oracle_mod):
+    dim, p, m = 2, 3, 24
+    n = m + p - 2
+    s = 3
+    K, M = oracle_mod.assemble_1d(p, m)
+    colour, order, _ = oracle_mod.schedule(dim, n, s, p, 1)
+    rng = np.random.default_rng(3)
+    b = rng.standard_normal(n * n)
+    u = rng.standard_normal(n * n)
+    # reverse the order inside every colour class
+    perm = np.lexsort((-order, colour[order]))
+    order2 = order[perm].astype(np.int32)
+    assert not np.array_equal(order, order2)
+    a1 = oracle_mod.schwarz_sweep(dim, K, M, p, s, order, b, u)
+    a2 = oracle_mod.schwarz_sweep(dim, K, M, p, s, order2, b, u)
+    assert np.array_equal(a1, a2)
+
+
+def test_block_size_table(oracle_mod):
+    import json, os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_tables.json")))
+    for p, s in gold["block_size"].items():
+        if p.startswith("_"):
+            continue
+        assert oracle_mod.block_size(int(p)) == s
