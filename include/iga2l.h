@@ -1,0 +1,155 @@
+/*
+ * iga2l.h -- C ABI of the GB300 two-level solver for B-spline isogeometric
+ * Poisson problems (de la Riva, Rodrigo, Gaspar, "A two level method for
+ * isogeometric discretizations", arXiv 2009.01499).
+ *
+ * Problem (Section 2): -Laplace(u) = f on (0,1)^d, u = 0 on the boundary,
+ * Galerkin discretisation with degree-p, C^{p-1} B-splines on a uniform mesh
+ * of m elements per axis.  Unknowns are the control points u_p of
+ * A_p u_p = b_p (Section 2, A_p = (a(phi_j, phi_i)), b_p = (f, phi_i)).
+ *
+ * Conventions for every entry point
+ *   - Vectors are caller-owned DEVICE pointers to contiguous float64 arrays of
+ *     n^d entries, n = m + p - 2 DOFs per axis (the Dirichlet-restricted spline
+ *     space of eq. (splinespace)), laid out C-order with x fastest:
+ *     index = i + n*(j + n*k).  Second-level vectors have nc^d entries,
+ *     nc = m/2 - 1 (degree 1 on the 2h mesh, Section 3.3).
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *     enqueued on it; entry points that return a host scalar synchronise it.
+ *   - The handle owns its device tables and workspace, allocated in
+ *     iga2l_assemble and released by iga2l_destroy.  No other entry point
+ *     allocates device memory.  A handle must not be used from two host
+ *     threads at once, and two calls on one handle must not overlap on the GPU
+ *     (they share workspace).
+ *   - Return codes: IGA2L_OK, IGA2L_NOT_CONVERGED or a negative error code
+ *     (iga2l_strerror; iga2l_last_error gives detail for the calling thread).
+ *     Argument checks happen before any work is enqueued.
+ */
+#ifndef IGA2L_H
+#define IGA2L_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define IGA2L_OK 0
+#define IGA2L_NOT_CONVERGED 1
+#define IGA2L_ERR_INVALID_ARG (-1)
+#define IGA2L_ERR_CUDA (-2)
+#define IGA2L_ERR_DEVICE_TIMEOUT (-3)
+#define IGA2L_ERR_NONFINITE (-4)
+#define IGA2L_ERR_UNSUPPORTED (-5)
+
+/* precision */
+#define IGA2L_FP64 0
+/* schedule: colour classes of the multiplicative Schwarz step */
+#define IGA2L_SCHED_LATTICE 1
+#define IGA2L_SCHED_TILE 2
+/* second-level solver */
+#define IGA2L_COARSE_EXACT 0
+#define IGA2L_COARSE_VCYCLE 1
+
+typedef struct iga2l_solver *iga2l_handle;
+
+typedef struct {
+    int precision;   /* IGA2L_FP64 */
+    int schedule;    /* IGA2L_SCHED_LATTICE or IGA2L_SCHED_TILE */
+    int tile;        /* TILE side T >= period (0 = library default) */
+    int period;      /* colour period q >= s + p (0 = library default for p) */
+    int stride;      /* colour stride g, gcd(g, q) = 1 (0 = library default) */
+    int coarse;      /* IGA2L_COARSE_VCYCLE (Section 3.2) or IGA2L_COARSE_EXACT */
+    int block_side;  /* Schwarz block side s (0 = the paper's choice for p, Section 4.3) */
+    int max_cycles;  /* default cap for iga2l_solve when its max_cycles <= 0 */
+} iga2l_options;
+
+/* Fills the defaults: FP64, LATTICE, V(1,1), the paper's block side, 100 cycles. */
+void iga2l_default_options(iga2l_options *opt);
+
+/* Builds the solver for degree p (2..5), m elements per axis, dimension dim (2).
+ * Host work: 1D B-spline Galerkin tables (Section 2.1), the Schwarz block
+ * inverses of every block class (Section 3.1.1), the lumped L2-projection
+ * restriction composed with h->2h (Sections 3.1.2, 3.3), the degree-1
+ * hierarchy (Section 3.2) and the dense inverse of its coarsest level; then one
+ * upload.  m must be even and large enough that interior blocks exist
+ * (m >= 4p + 4); the colouring must satisfy q >= s+p, gcd(g,q) = 1, T >= q.
+ * *out receives the handle (NULL on error).  opt may be NULL (defaults). */
+int iga2l_assemble(int p, int m, int dim, const iga2l_options *opt, iga2l_handle *out);
+
+/* Sizes: total fine DOFs, DOFs per axis, total and per-axis second-level DOFs.
+ * Any output pointer may be NULL. */
+int iga2l_num_dofs(iga2l_handle h, long long *n_total, int *n_axis,
+                   long long *nc_total, int *nc_axis);
+
+/* y = A_p u, A_p = K(x)M + M(x)K (Section 2, tensor-product stiffness). */
+int iga2l_apply_A(iga2l_handle h, const double *u, double *y, void *stream);
+
+/* Defect d = b - A_p u (Algorithm 1).  d may be NULL (norm only).  If norm is
+ * not NULL it receives ||d||_2 on the host (the stream is synchronised). */
+int iga2l_residual(iga2l_handle h, const double *u, const double *b, double *d,
+                   double *norm, void *stream);
+
+/* One multiplicative Schwarz step u <- u + S_p(b - A_p u) (Section 3.1.1): for
+ * every grid point, in the order of the handle's colour schedule, the s^d block
+ * around it (clipped to the grid) is corrected by u_B += A_B^{-1} (b - A u)_B. */
+int iga2l_schwarz_sweep(iga2l_handle h, double *u, const double *b, void *stream);
+
+/* Same step with the colour order reversed (the transpose of the Schwarz
+ * approximate inverse; used by the adjoint cycle). */
+int iga2l_schwarz_sweep_reverse(iga2l_handle h, double *u, const double *b, void *stream);
+
+/* d_c = I_{p,h}^{1,2h} d (Sections 3.1.2 and 3.3): lumped L2 projection onto
+ * the degree-1 space followed by the degree-1 h -> 2h restriction.  dc has nc^d entries. */
+int iga2l_restrict(iga2l_handle h, const double *d, double *dc, void *stream);
+
+/* u += I_{1,2h}^{p,h} e_c, the adjoint of iga2l_restrict (Section 3.1.2). */
+int iga2l_prolong_add(iga2l_handle h, const double *ec, double *u, void *stream);
+
+/* e_c ~= A_1^{-1} d_c on the second level: one V(1,1) cycle with red-black
+ * Gauss-Seidel from e_c = 0 (Section 3.2), or the exact solve (Algorithm 1). */
+int iga2l_coarse_solve(iga2l_handle h, const double *dc, double *ec, void *stream);
+
+/* One cycle of Algorithm 1 in place: Schwarz step, defect, restriction,
+ * second-level solve, prolongation and update. */
+int iga2l_cycle(iga2l_handle h, double *u, const double *b, void *stream);
+
+/* One transposed cycle: second-level correction first, then the reversed
+ * Schwarz step.  Its approximate inverse is the transpose of iga2l_cycle's. */
+int iga2l_cycle_adjoint(iga2l_handle h, double *u, const double *b, void *stream);
+
+/* Cycles from the guess in u until ||b - A u||_2 <= tol ||b - A u_0||_2
+ * (Section 5 stopping rule) or max_cycles (<= 0: the handle's default).
+ * Writes the cycle count, the final relative residual and, if hist is not
+ * NULL, the relative residual after every cycle (host array of max_cycles).
+ * Returns IGA2L_OK, IGA2L_NOT_CONVERGED or an error (IGA2L_ERR_NONFINITE if a
+ * residual norm is not finite).  Synchronises the stream once per cycle. */
+int iga2l_solve(iga2l_handle h, const double *b, double tol, int max_cycles, double *u,
+                int *cycles, double *relres, double *hist, void *stream);
+
+/* Solve of A_p lambda = g with the transposed cycle (A_p is symmetric, so the
+ * limit is A_p^{-1} g; the iterates are those of the adjoint iteration). */
+int iga2l_adjoint_solve(iga2l_handle h, const double *g, double tol, int max_cycles,
+                        double *lambda, int *cycles, double *relres, void *stream);
+
+/* b = (M(x)M) f: load vector of f = sum_i f_i phi_i given by its B-spline
+ * coefficients (b_p = (f, phi_i), Section 2). */
+int iga2l_rhs_from_coeffs(iga2l_handle h, const double *f, double *b, void *stream);
+
+/* Host copies of the handle's 1D band tables, rows of width 2p+1 (entry a of
+ * row i is the coefficient of DOF i + a - p), for tests: K then M, n*(2p+1) each. */
+int iga2l_get_bands(iga2l_handle h, double *K, double *M);
+
+/* Host-only helpers (no GPU needed), for checking the library's setup code:
+ * the 1D band rows of the degree-p space with m elements (n*(2p+1) each, as in
+ * iga2l_get_bands) and the dense 1D aggressive restriction (m/2-1) x n. */
+int iga2l_host_bands(int p, int m, double *K, double *M);
+int iga2l_host_restriction(int p, int m, double *R);
+
+void iga2l_destroy(iga2l_handle h);
+const char *iga2l_strerror(int code);
+/* Detail of the last error on the calling host thread ("" if none). */
+const char *iga2l_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IGA2L_H */

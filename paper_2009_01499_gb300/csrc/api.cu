@@ -1,0 +1,508 @@
+// api.cu -- the C ABI of include/iga2l.h: handle construction, table upload,
+// per-step entry points, Algorithm 1 and the solver loop.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace iga2l;
+
+struct iga2l_solver : public Solver {
+    double *host_norm = nullptr;   // pinned scalar for norm readback
+    double *dev_norm = nullptr;
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string &msg)
+{
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *where)
+{
+    return fail(IGA2L_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+template <typename T>
+cudaError_t upload(iga2l_solver *S, T **dst, const std::vector<T> &src)
+{
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, sizeof(T) * (src.empty() ? 1 : src.size()));
+    if (e != cudaSuccess) return e;
+    S->allocs.push_back(p);
+    *dst = static_cast<T *>(p);
+    if (src.empty()) return cudaSuccess;
+    return cudaMemcpy(p, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice);
+}
+
+cudaError_t alloc(iga2l_solver *S, double **dst, size_t count)
+{
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, sizeof(double) * (count ? count : 1));
+    if (e != cudaSuccess) return e;
+    S->allocs.push_back(p);
+    *dst = static_cast<double *>(p);
+    return cudaSuccess;
+}
+
+void release(iga2l_solver *S)
+{
+    if (!S) return;
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != S->device) cudaSetDevice(S->device);
+    for (void *p : S->allocs) cudaFree(p);
+    S->allocs.clear();
+    if (S->host_norm) cudaFreeHost(S->host_norm);
+    if (cur >= 0 && cur != S->device) cudaSetDevice(cur);
+    delete S;
+}
+
+int gcd_int(int a, int b)
+{
+    while (b) { int t = a % b; a = b; b = t; }
+    return a;
+}
+
+// Kronecker-structured entry A[(x1,y1)][(x2,y2)] from the band rows.
+double band(const std::vector<double> &B, int p, int i, int j)
+{
+    const int off = j - i;
+    if (off < -p || off > p) return 0.0;
+    return B[(size_t)i * (2 * p + 1) + off + p];
+}
+
+int check_handle(iga2l_handle h)
+{
+    if (!h) return fail(IGA2L_ERR_INVALID_ARG, "null handle");
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) return fail(IGA2L_ERR_CUDA, "cudaGetDevice failed");
+    if (cur != h->device) {
+        cudaError_t e = cudaSetDevice(h->device);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    }
+    return IGA2L_OK;
+}
+
+cudaStream_t as_stream(void *s) { return static_cast<cudaStream_t>(s); }
+
+int finish(cudaError_t e, const char *where)
+{
+    if (e != cudaSuccess) return cuda_fail(e, where);
+    return IGA2L_OK;
+}
+
+// ||b - A u||_2^2 (or ||A u||^2 when b is null) into h->host_norm; synchronises.
+int residual_norm2(iga2l_handle h, const double *u, const double *b, double *d, cudaStream_t st,
+                   double *out)
+{
+    cudaError_t e = launch_residual(*h, u, b, d, h->part, st);
+    if (e == cudaSuccess) e = launch_norm_finish(*h, h->part, h->dev_norm, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->host_norm, h->dev_norm, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "residual norm");
+    *out = *h->host_norm;
+    return IGA2L_OK;
+}
+
+int coarse_correction(iga2l_handle h, double *u, const double *b, cudaStream_t st)
+{
+    cudaError_t e = launch_residual(*h, u, b, h->d, nullptr, st);
+    if (e == cudaSuccess) e = launch_restrict(*h, h->d, h->dc, st);
+    if (e == cudaSuccess) e = launch_coarse_solve(*h, h->dc, h->ec, st);
+    if (e == cudaSuccess) e = launch_prolong_add(*h, h->ec, u, st);
+    return finish(e, "coarse correction");
+}
+
+int run_cycle(iga2l_handle h, double *u, const double *b, cudaStream_t st, bool adjoint)
+{
+    if (!adjoint) {
+        cudaError_t e = launch_schwarz(*h, u, b, false, st);
+        if (e != cudaSuccess) return cuda_fail(e, "schwarz sweep");
+        return coarse_correction(h, u, b, st);
+    }
+    int rc = coarse_correction(h, u, b, st);
+    if (rc != IGA2L_OK) return rc;
+    return finish(launch_schwarz(*h, u, b, true, st), "reverse schwarz sweep");
+}
+
+int solve_impl(iga2l_handle h, const double *b, double tol, int max_cycles, double *u, int *cycles,
+               double *relres, double *hist, void *stream, bool adjoint)
+{
+    if (!b || !u) return fail(IGA2L_ERR_INVALID_ARG, "null vector");
+    if (!(tol >= 0.0)) return fail(IGA2L_ERR_INVALID_ARG, "tol must be >= 0");
+    if (max_cycles <= 0) max_cycles = h->opt.max_cycles;
+    cudaStream_t st = as_stream(stream);
+    double r0sq = 0.0;
+    int rc = residual_norm2(h, u, b, nullptr, st, &r0sq);
+    if (rc != IGA2L_OK) return rc;
+    if (!std::isfinite(r0sq)) return fail(IGA2L_ERR_NONFINITE, "initial residual is not finite");
+    const double r0 = std::sqrt(r0sq);
+    int k = 0;
+    double rel = 0.0;
+    int status = r0 == 0.0 ? IGA2L_OK : IGA2L_NOT_CONVERGED;
+    while (status != IGA2L_OK && k < max_cycles) {
+        rc = run_cycle(h, u, b, st, adjoint);
+        if (rc != IGA2L_OK) return rc;
+        ++k;
+        double rsq = 0.0;
+        rc = residual_norm2(h, u, b, nullptr, st, &rsq);
+        if (rc != IGA2L_OK) return rc;
+        if (!std::isfinite(rsq)) {
+            if (cycles) *cycles = k;
+            return fail(IGA2L_ERR_NONFINITE, "residual norm is not finite");
+        }
+        rel = std::sqrt(rsq) / r0;
+        if (hist) hist[k - 1] = rel;
+        if (rel <= tol) status = IGA2L_OK;
+    }
+    if (cycles) *cycles = k;
+    if (relres) *relres = rel;
+    if (status != IGA2L_OK) g_last_error = "cycle cap reached";
+    return status;
+}
+
+}  // namespace
+
+extern "C" {
+
+void iga2l_default_options(iga2l_options *opt)
+{
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->precision = IGA2L_FP64;
+    opt->schedule = IGA2L_SCHED_LATTICE;
+    opt->coarse = IGA2L_COARSE_VCYCLE;
+    opt->max_cycles = 100;
+}
+
+int iga2l_assemble(int p, int m, int dim, const iga2l_options *opt_in, iga2l_handle *out)
+{
+    if (!out) return fail(IGA2L_ERR_INVALID_ARG, "null output handle");
+    *out = nullptr;
+    iga2l_options opt;
+    if (opt_in) opt = *opt_in; else iga2l_default_options(&opt);
+    if (opt.max_cycles <= 0) opt.max_cycles = 100;
+    if (dim != 2) return fail(IGA2L_ERR_UNSUPPORTED, "only dim = 2 is compiled");
+    if (p < 2 || p > kMaxP) return fail(IGA2L_ERR_INVALID_ARG, "p must be in 2..5");
+    if (m < 4 * p + 4 || (m % 2) != 0)
+        return fail(IGA2L_ERR_INVALID_ARG, "m must be even and >= 4p+4 (aggressive 2h coarsening)");
+    if (opt.precision != IGA2L_FP64) return fail(IGA2L_ERR_UNSUPPORTED, "precision not available");
+    if (opt.schedule != IGA2L_SCHED_LATTICE)
+        return fail(IGA2L_ERR_UNSUPPORTED, "schedule not available");
+    if (opt.coarse != IGA2L_COARSE_VCYCLE && opt.coarse != IGA2L_COARSE_EXACT)
+        return fail(IGA2L_ERR_INVALID_ARG, "unknown coarse solver");
+    const int s = opt.block_side > 0 ? opt.block_side : default_block_side(p);
+    if (!((s == 3 && p <= 4) || (s == 5 && p == 5)))
+        return fail(IGA2L_ERR_UNSUPPORTED, "block side not compiled for this degree");
+    int q = opt.period, g = opt.stride;
+    if (q <= 0) default_colouring(p, s, q, g);
+    if (g <= 0) g = 1;
+    if (q < s + p) return fail(IGA2L_ERR_INVALID_ARG, "colour period must be >= s + p");
+    if (gcd_int(g % q, q) != 1) return fail(IGA2L_ERR_INVALID_ARG, "colour stride must be coprime to the period");
+
+    iga2l_solver *S = new (std::nothrow) iga2l_solver();
+    if (!S) return fail(IGA2L_ERR_CUDA, "host allocation failed");
+    S->dim = dim; S->p = p; S->m = m; S->s = s; S->r = (s - 1) / 2;
+    S->n = m + p - 2;
+    S->N = (long long)S->n * S->n;
+    S->opt = opt;
+    S->q = q; S->g = g % q; S->tile = opt.tile;
+    cudaError_t ce = cudaGetDevice(&S->device);
+    if (ce != cudaSuccess) { release(S); return cuda_fail(ce, "cudaGetDevice"); }
+
+    std::string err;
+    int rc = build_host_tables(p, m, s, S->ht, err);
+    if (rc != IGA2L_OK) { release(S); return fail(rc, err); }
+    const HostTables &ht = S->ht;
+    const int n = S->n, W = 2 * p + 1, SS = s * s;
+
+    // residual stencils per (row-class of y, row-class of x)
+    std::vector<double> stencil((size_t)ht.npc * ht.npc * W * W);
+    for (int cy = 0; cy < ht.npc; ++cy)
+        for (int cx = 0; cx < ht.npc; ++cx) {
+            const int xr = ht.pc_rep[cx], yr = ht.pc_rep[cy];
+            double *st = &stencil[(size_t)(cy * ht.npc + cx) * W * W];
+            for (int b = 0; b < W; ++b)
+                for (int a = 0; a < W; ++a)
+                    st[b * W + a] = ht.Kb[(size_t)xr * W + a] * ht.Mb[(size_t)yr * W + b]
+                                  + ht.Mb[(size_t)xr * W + a] * ht.Kb[(size_t)yr * W + b];
+        }
+    std::vector<int> pcls(n), bcls(n);
+    for (int x = 0; x < n; ++x) {
+        pcls[x] = x < 2 * p - 1 ? x : (x > n - 2 * p ? x - n + 4 * p - 1 : 2 * p - 1);
+        bcls[x] = x < ht.L ? x : (x > n - 1 - ht.L ? 2 * ht.L - (n - 1 - x) : ht.L);
+    }
+    // Schwarz block inverses per (block class of cy, block class of cx); block DOF
+    // e = ex + s*ey is (c_x - r + ex, c_y - r + ey); DOFs outside the grid get zero rows
+    std::vector<double> binv((size_t)ht.nbc * ht.nbc * SS * SS, 0.0);
+    for (int by = 0; by < ht.nbc; ++by)
+        for (int bx = 0; bx < ht.nbc; ++bx) {
+            const int cx = ht.bc_rep[bx], cy = ht.bc_rep[by];
+            std::vector<double> A((size_t)SS * SS, 0.0);
+            std::vector<int> valid(SS);
+            for (int a = 0; a < SS; ++a) {
+                const int xa = cx - S->r + a % s, ya = cy - S->r + a / s;
+                valid[a] = xa >= 0 && xa < n && ya >= 0 && ya < n;
+            }
+            for (int a = 0; a < SS; ++a)
+                for (int c = 0; c < SS; ++c) {
+                    if (!valid[a] || !valid[c]) { A[(size_t)a * SS + c] = (a == c) ? 1.0 : 0.0; continue; }
+                    const int xa = cx - S->r + a % s, ya = cy - S->r + a / s;
+                    const int xc = cx - S->r + c % s, yc = cy - S->r + c / s;
+                    A[(size_t)a * SS + c] = band(ht.Kb, p, xa, xc) * band(ht.Mb, p, ya, yc)
+                                          + band(ht.Mb, p, xa, xc) * band(ht.Kb, p, ya, yc);
+                }
+            if (!cholesky_inverse(SS, A)) { release(S); return fail(IGA2L_ERR_INVALID_ARG, "block matrix not SPD"); }
+            double *dst = &binv[(size_t)(by * ht.nbc + bx) * SS * SS];
+            for (int a = 0; a < SS; ++a)
+                for (int c = 0; c < SS; ++c)
+                    dst[(size_t)a * SS + c] = (valid[a] && valid[c]) ? A[(size_t)a * SS + c] : 0.0;
+        }
+
+    // second-level hierarchy (degree 1 on the 2h mesh, then 4h, ...)
+    S->nc = ht.nc;
+    S->Nc = (long long)ht.nc * ht.nc;
+    for (int ml = m / 2;;) {
+        Level L;
+        L.m = ml;
+        L.n = ml - 1;
+        L.N = (long long)L.n * L.n;
+        L.k[0] = -(double)ml; L.k[1] = 2.0 * ml; L.k[2] = -(double)ml;
+        L.mm[0] = 1.0 / (6.0 * ml); L.mm[1] = 4.0 / (6.0 * ml); L.mm[2] = 1.0 / (6.0 * ml);
+        S->lev.push_back(L);
+        if (opt.coarse == IGA2L_COARSE_EXACT || ml <= 8 || (ml % 2) != 0 || (int)S->lev.size() >= kMaxLevels)
+            break;
+        ml /= 2;
+    }
+    const Level &D = S->lev.back();
+    S->ndirect = (int)D.N;
+    if (S->ndirect > 2048) { release(S); return fail(IGA2L_ERR_UNSUPPORTED, "exact second-level solve too large"); }
+    std::vector<double> Ad((size_t)S->ndirect * S->ndirect, 0.0);
+    for (int y = 0; y < D.n; ++y)
+        for (int x = 0; x < D.n; ++x)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int x2 = x + dx, y2 = y + dy;
+                    if (x2 < 0 || x2 >= D.n || y2 < 0 || y2 >= D.n) continue;
+                    Ad[(size_t)(y * D.n + x) * S->ndirect + (y2 * D.n + x2)] =
+                        D.k[dx + 1] * D.mm[dy + 1] + D.mm[dx + 1] * D.k[dy + 1];
+                }
+    if (!cholesky_inverse(S->ndirect, Ad)) { release(S); return fail(IGA2L_ERR_INVALID_ARG, "coarsest matrix not SPD"); }
+
+    // upload
+    if ((ce = upload(S, &S->Kb, ht.Kb)) != cudaSuccess ||
+        (ce = upload(S, &S->Mb, ht.Mb)) != cudaSuccess ||
+        (ce = upload(S, &S->stencil, stencil)) != cudaSuccess ||
+        (ce = upload(S, &S->binv, binv)) != cudaSuccess ||
+        (ce = upload(S, &S->pcls, pcls)) != cudaSuccess ||
+        (ce = upload(S, &S->bcls, bcls)) != cudaSuccess ||
+        (ce = upload(S, &S->Rb, ht.Rb)) != cudaSuccess ||
+        (ce = upload(S, &S->Cb, ht.Cb)) != cudaSuccess ||
+        (ce = upload(S, &S->Rlo, ht.Rlo)) != cudaSuccess ||
+        (ce = upload(S, &S->Clo, ht.Clo)) != cudaSuccess ||
+        (ce = upload(S, &S->dinv, Ad)) != cudaSuccess) {
+        release(S);
+        return cuda_fail(ce, "table upload");
+    }
+    S->npart = residual_partials(*S);
+    if ((ce = alloc(S, &S->d, S->N)) != cudaSuccess || (ce = alloc(S, &S->bwork, S->N)) != cudaSuccess ||
+        (ce = alloc(S, &S->t, (size_t)n * S->nc)) != cudaSuccess ||
+        (ce = alloc(S, &S->t2, (size_t)n * S->nc)) != cudaSuccess ||
+        (ce = alloc(S, &S->dc, S->Nc)) != cudaSuccess || (ce = alloc(S, &S->ec, S->Nc)) != cudaSuccess ||
+        (ce = alloc(S, &S->part, S->npart)) != cudaSuccess || (ce = alloc(S, &S->dev_norm, 1)) != cudaSuccess) {
+        release(S);
+        return cuda_fail(ce, "workspace allocation");
+    }
+    for (Level &L : S->lev)
+        if ((ce = alloc(S, &L.e, L.N)) != cudaSuccess || (ce = alloc(S, &L.rhs, L.N)) != cudaSuccess ||
+            (ce = alloc(S, &L.r, L.N)) != cudaSuccess) {
+            release(S);
+            return cuda_fail(ce, "level allocation");
+        }
+    if ((ce = cudaMallocHost(&S->host_norm, sizeof(double))) != cudaSuccess) {
+        release(S);
+        return cuda_fail(ce, "pinned host scalar");
+    }
+    *out = S;
+    g_last_error.clear();
+    return IGA2L_OK;
+}
+
+int iga2l_num_dofs(iga2l_handle h, long long *n_total, int *n_axis, long long *nc_total, int *nc_axis)
+{
+    if (!h) return fail(IGA2L_ERR_INVALID_ARG, "null handle");
+    if (n_total) *n_total = h->N;
+    if (n_axis) *n_axis = h->n;
+    if (nc_total) *nc_total = h->Nc;
+    if (nc_axis) *nc_axis = h->nc;
+    return IGA2L_OK;
+}
+
+int iga2l_apply_A(iga2l_handle h, const double *u, double *y, void *stream)
+{
+    int rc = check_handle(h);
+    if (rc != IGA2L_OK) return rc;
+    if (!u || !y) return fail(IGA2L_ERR_INVALID_ARG, "null vector");
+    return finish(launch_apply_A(*h, u, y, as_stream(stream)), "apply_A");
+}
+
+int iga2l_residual(iga2l_handle h, const double *u, const double *b, double *d, double *norm, void *stream)
+{
+    int rc = check_handle(h);
+    if (rc != IGA2L_OK) return rc;
+    if (!u || !b) return fail(IGA2L_ERR_INVALID_ARG, "null vector");
+    cudaStream_t st = as_stream(stream);
+    if (!norm) return finish(launch_residual(*h, u, b, d, nullptr, st), "residual");
+    double sq = 0.0;
+    rc = residual_norm2(h, u, b, d, st, &sq);
+    if (rc != IGA2L_OK) return rc;
+    *norm = std::sqrt(sq);
+    return IGA2L_OK;
+}
+
+int iga2l_schwarz_sweep(iga2l_handle h, double *u, const double *b, void *stream)
+{
+    int rc = check_handle(h);
+    if (rc != IGA2L_OK) return rc;
+    if (!u || !b) return fail(IGA2L_ERR_INVALID_ARG, "null vector");
+    return finish(launch_schwarz(*h, u, b, false, as_stream(stream)), "schwarz sweep");
+}
+
+int iga2l_schwarz_sweep_reverse(iga2l_handle h, double *u, const double *b, void *stream)
+{
+    int rc = check_handle(h);
+    if (rc != IGA2L_OK) return rc;
+    if (!u || !b) return fail(IGA2L_ERR_INVALID_ARG, "null vector");
+    return finish(launch_schwarz(*h, u, b, true, as_stream(stream)), "reverse schwarz sweep");
+}
+
+int iga2l_restrict(iga2l_handle h, const double *d, double *dc, void *stream)
+{
+    int rc = check_handle(h);
+    if (rc != IGA2L_OK) return rc;
+    if (!d || !dc) return fail(IGA2L_ERR_INVALID_ARG, "null vector");
+    return finish(launch_restrict(*h, d, dc, as_stream(stream)), "restrict");
+}
+
+int iga2l_prolong_add(iga2l_handle h, const double *ec, double *u, void *stream)
+{
+    int rc = check_handle(h);
+    if (rc != IGA2L_OK) return rc;
+    if (!ec || !u) return fail(IGA2L_ERR_INVALID_ARG, "null vector");
+    return finish(launch_prolong_add(*h, ec, u, as_stream(stream)), "prolong_add");
+}
+
+int iga2l_coarse_solve(iga2l_handle h, const double *dc, double *ec, void *stream)
+{
+    int rc = check_handle(h);
+    if (rc != IGA2L_OK) return rc;
+    if (!dc || !ec) return fail(IGA2L_ERR_INVALID_ARG, "null vector");
+    return finish(launch_coarse_solve(*h, dc, ec, as_stream(stream)), "coarse solve");
+}
+
+int iga2l_cycle(iga2l_handle h, double *u, const double *b, void *stream)
+{
+    int rc = check_handle(h);
+    if (rc != IGA2L_OK) return rc;
+    if (!u || !b) return fail(IGA2L_ERR_INVALID_ARG, "null vector");
+    return run_cycle(h, u, b, as_stream(stream), false);
+}
+
+int iga2l_cycle_adjoint(iga2l_handle h, double *u, const double *b, void *stream)
+{
+    int rc = check_handle(h);
+    if (rc != IGA2L_OK) return rc;
+    if (!u || !b) return fail(IGA2L_ERR_INVALID_ARG, "null vector");
+    return run_cycle(h, u, b, as_stream(stream), true);
+}
+
+int iga2l_solve(iga2l_handle h, const double *b, double tol, int max_cycles, double *u, int *cycles,
+                double *relres, double *hist, void *stream)
+{
+    int rc = check_handle(h);
+    if (rc != IGA2L_OK) return rc;
+    return solve_impl(h, b, tol, max_cycles, u, cycles, relres, hist, stream, false);
+}
+
+int iga2l_adjoint_solve(iga2l_handle h, const double *g, double tol, int max_cycles, double *lambda,
+                        int *cycles, double *relres, void *stream)
+{
+    int rc = check_handle(h);
+    if (rc != IGA2L_OK) return rc;
+    return solve_impl(h, g, tol, max_cycles, lambda, cycles, relres, nullptr, stream, true);
+}
+
+int iga2l_rhs_from_coeffs(iga2l_handle h, const double *f, double *b, void *stream)
+{
+    int rc = check_handle(h);
+    if (rc != IGA2L_OK) return rc;
+    if (!f || !b || f == b) return fail(IGA2L_ERR_INVALID_ARG, "null or aliased vector");
+    return finish(launch_mass2(*h, f, b, as_stream(stream)), "rhs_from_coeffs");
+}
+
+int iga2l_get_bands(iga2l_handle h, double *K, double *M)
+{
+    if (!h || !K || !M) return fail(IGA2L_ERR_INVALID_ARG, "null argument");
+    std::memcpy(K, h->ht.Kb.data(), sizeof(double) * h->ht.Kb.size());
+    std::memcpy(M, h->ht.Mb.data(), sizeof(double) * h->ht.Mb.size());
+    return IGA2L_OK;
+}
+
+int iga2l_host_bands(int p, int m, double *K, double *M)
+{
+    if (p < 1 || p > kMaxP || m < 1 || !K || !M) return fail(IGA2L_ERR_INVALID_ARG, "bad arguments");
+    std::vector<double> Kb, Mb;
+    bspline_band_1d(p, m, Kb, Mb);
+    std::memcpy(K, Kb.data(), sizeof(double) * Kb.size());
+    std::memcpy(M, Mb.data(), sizeof(double) * Mb.size());
+    return IGA2L_OK;
+}
+
+int iga2l_host_restriction(int p, int m, double *R)
+{
+    if (p < 2 || p > kMaxP || m < 4 || (m % 2) != 0 || !R) return fail(IGA2L_ERR_INVALID_ARG, "bad arguments");
+    HostTables ht;
+    std::string err;
+    const int s = default_block_side(p);
+    int rc = build_host_tables(p, m, s, ht, err);
+    if (rc != IGA2L_OK) return fail(rc, err);
+    const int n = ht.n, nc = ht.nc;
+    std::memset(R, 0, sizeof(double) * (size_t)nc * n);
+    for (int I = 0; I < nc; ++I)
+        for (int t = 0; t < ht.wr; ++t) {
+            const int j = ht.Rlo[I] + t;
+            if (j < n) R[(size_t)I * n + j] = ht.Rb[(size_t)I * ht.wr + t];
+        }
+    return IGA2L_OK;
+}
+
+void iga2l_destroy(iga2l_handle h) { release(h); }
+
+const char *iga2l_strerror(int code)
+{
+    switch (code) {
+    case IGA2L_OK: return "ok";
+    case IGA2L_NOT_CONVERGED: return "not converged";
+    case IGA2L_ERR_INVALID_ARG: return "invalid argument";
+    case IGA2L_ERR_CUDA: return "CUDA error";
+    case IGA2L_ERR_DEVICE_TIMEOUT: return "device wait timed out";
+    case IGA2L_ERR_NONFINITE: return "non-finite value";
+    case IGA2L_ERR_UNSUPPORTED: return "unsupported configuration";
+    default: return "unknown error";
+    }
+}
+
+const char *iga2l_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,91 @@
+// internal.h -- solver state shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/iga2l.h"
+
+namespace iga2l {
+
+constexpr int kMaxP = 5;       // degrees with compiled kernels: 2..5
+constexpr int kMaxLevels = 24;
+
+// Host-side tables built once per handle (setup.cpp); uploaded by api.cu.
+struct HostTables {
+    int p = 0, m = 0, n = 0, s = 0, r = 0;
+    // 1D band rows, n x (2p+1): entry a of row i couples DOF i with DOF i+a-p
+    std::vector<double> Kb, Mb;
+    // point classes of the residual stencil: rows closer than 2p-1 to a
+    // boundary have their own class, the others share the Toeplitz row
+    int npc = 0;                       // classes per axis (4p - 1)
+    std::vector<int> pc_rep;           // representative row of each class
+    // block classes of the Schwarz step: blocks touching the non-uniform
+    // boundary functions have their own class
+    int L = 0, nbc = 0;                // nbc = 2L + 1 classes per axis
+    std::vector<int> bc_rep;           // representative centre of each class
+    // aggressive restriction R = S^T D^{-1} M_p^1 as a row band and a column band
+    int nc = 0, wr = 0, wc = 0;
+    std::vector<double> Rb, Cb;        // nc x wr, n x wc
+    std::vector<int> Rlo, Clo;
+};
+
+struct Level {                 // degree-1 level of the second-level hierarchy
+    int m = 0, n = 0;          // elements, DOFs per axis
+    long long N = 0;
+    double k[3] = {0, 0, 0};   // 1D stiffness row  (-1, 2, -1)/H
+    double mm[3] = {0, 0, 0};  // 1D mass row (1, 4, 1) H/6
+    double *e = nullptr, *rhs = nullptr, *r = nullptr;   // device
+};
+
+struct Solver {
+    int dim = 2, p = 2, m = 0, n = 0, s = 3, r = 1;
+    long long N = 0;
+    iga2l_options opt{};
+    int device = 0;
+    int q = 5, g = 1, tile = 0;
+    HostTables ht;
+    // device tables
+    double *Kb = nullptr, *Mb = nullptr;
+    double *stencil = nullptr;   // npc^dim classes x (2p+1)^dim coefficients
+    double *binv = nullptr;      // nbc^dim classes x S*S, S = s^dim
+    int *pcls = nullptr;         // point class of every row index (n)
+    int *bcls = nullptr;         // block class of every centre index (n)
+    double *Rb = nullptr, *Cb = nullptr;
+    int *Rlo = nullptr, *Clo = nullptr;
+    int nc = 0;
+    long long Nc = 0;
+    std::vector<Level> lev;      // lev[0] is the second level (nc per axis)
+    int ndirect = 0;             // size of the directly solved level
+    double *dinv = nullptr;      // dense inverse of the direct level
+    // workspace
+    double *d = nullptr, *t = nullptr, *dc = nullptr, *ec = nullptr, *t2 = nullptr;
+    double *part = nullptr;      // per-CTA partial sums of squares
+    int npart = 0;
+    double *bwork = nullptr;     // b built from coefficients in solve paths
+    std::vector<void *> allocs;
+};
+
+// setup.cpp
+int build_host_tables(int p, int m, int s, HostTables &ht, std::string &err);
+void bspline_band_1d(int p, int m, std::vector<double> &K, std::vector<double> &M);
+bool cholesky_inverse(int N, std::vector<double> &A);   // in place, SPD
+int default_block_side(int p);
+void default_colouring(int p, int s, int &q, int &g);
+
+// kernels (kernels_fine.cu, kernels_coarse.cu); all enqueue on `st`
+cudaError_t launch_residual(const Solver &S, const double *u, const double *b, double *d,
+                            double *part, cudaStream_t st);
+cudaError_t launch_apply_A(const Solver &S, const double *u, double *y, cudaStream_t st);
+cudaError_t launch_norm_finish(const Solver &S, const double *part, double *out, cudaStream_t st);
+cudaError_t launch_schwarz(const Solver &S, double *u, const double *b, bool reverse,
+                           cudaStream_t st);
+cudaError_t launch_restrict(const Solver &S, const double *d, double *dc, cudaStream_t st);
+cudaError_t launch_prolong_add(const Solver &S, const double *ec, double *u, cudaStream_t st);
+cudaError_t launch_coarse_solve(const Solver &S, const double *dc, double *ec, cudaStream_t st);
+cudaError_t launch_mass2(const Solver &S, const double *f, double *b, cudaStream_t st);
+int residual_partials(const Solver &S);
+
+}  // namespace iga2l

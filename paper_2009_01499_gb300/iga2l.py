@@ -1,0 +1,239 @@
+"""Thin ctypes binding of the C ABI in include/iga2l.h.
+
+Argument marshalling only: every step of the solver runs in libiga2l.so's CUDA
+kernels.  Vectors are torch float64 CUDA tensors (contiguous, x fastest);
+streams default to torch's current stream.  If the library cannot be loaded
+the binding raises: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+OK, NOT_CONVERGED = 0, 1
+ERR_INVALID_ARG, ERR_CUDA, ERR_DEVICE_TIMEOUT, ERR_NONFINITE, ERR_UNSUPPORTED = -1, -2, -3, -4, -5
+FP64 = 0
+SCHED_LATTICE, SCHED_TILE = 1, 2
+COARSE_EXACT, COARSE_VCYCLE = 0, 1
+
+# Every exported symbol of include/iga2l.h.
+EXPORTS = (
+    "iga2l_default_options", "iga2l_assemble", "iga2l_num_dofs", "iga2l_apply_A",
+    "iga2l_residual", "iga2l_schwarz_sweep", "iga2l_schwarz_sweep_reverse", "iga2l_restrict",
+    "iga2l_prolong_add", "iga2l_coarse_solve", "iga2l_cycle", "iga2l_cycle_adjoint",
+    "iga2l_solve", "iga2l_adjoint_solve", "iga2l_rhs_from_coeffs", "iga2l_get_bands",
+    "iga2l_host_bands", "iga2l_host_restriction", "iga2l_destroy", "iga2l_strerror",
+    "iga2l_last_error",
+)
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("schedule", ctypes.c_int), ("tile", ctypes.c_int),
+                ("period", ctypes.c_int), ("stride", ctypes.c_int), ("coarse", ctypes.c_int),
+                ("block_side", ctypes.c_int), ("max_cycles", ctypes.c_int)]
+
+
+class IgaError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"iga2l error {code}: {msg}")
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+_vp, _dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
+_ip, _llp = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong)
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libiga2l.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build() if build_if_missing else _build.LIB
+        if not os.path.exists(path):
+            raise ImportError(f"libiga2l.so not found at {path}; run __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        sig = {
+            "iga2l_default_options": (None, [ctypes.POINTER(Options)]),
+            "iga2l_assemble": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                              ctypes.POINTER(Options), ctypes.POINTER(_vp)]),
+            "iga2l_num_dofs": (ctypes.c_int, [_vp, _llp, _ip, _llp, _ip]),
+            "iga2l_apply_A": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+            "iga2l_residual": (ctypes.c_int, [_vp, _vp, _vp, _vp, _dp, _vp]),
+            "iga2l_schwarz_sweep": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+            "iga2l_schwarz_sweep_reverse": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+            "iga2l_restrict": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+            "iga2l_prolong_add": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+            "iga2l_coarse_solve": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+            "iga2l_cycle": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+            "iga2l_cycle_adjoint": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+            "iga2l_solve": (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.c_int, _vp, _ip, _dp,
+                                           _dp, _vp]),
+            "iga2l_adjoint_solve": (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.c_int, _vp,
+                                                   _ip, _dp, _vp]),
+            "iga2l_rhs_from_coeffs": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+            "iga2l_get_bands": (ctypes.c_int, [_vp, _dp, _dp]),
+            "iga2l_host_bands": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _dp, _dp]),
+            "iga2l_host_restriction": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _dp]),
+            "iga2l_destroy": (None, [_vp]),
+            "iga2l_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+            "iga2l_last_error": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(rc, allow_not_converged=False):
+    if rc == OK or (allow_not_converged and rc == NOT_CONVERGED):
+        return rc
+    lib = load()
+    raise IgaError(rc, f"{lib.iga2l_strerror(rc).decode()}: {lib.iga2l_last_error().decode()}")
+
+
+def _ptr(t, dtype="float64", numel=None):
+    import torch
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if t.dtype != getattr(torch, dtype) or not t.is_contiguous():
+        raise TypeError(f"expected a contiguous {dtype} tensor")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"expected {numel} entries, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    load().iga2l_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, int(v))
+    return o
+
+
+def host_bands(p: int, m: int):
+    """Library's 1D band rows (host setup code, no GPU): K, M as n x (2p+1)."""
+    n, w = m + p - 2, 2 * p + 1
+    K = np.zeros(n * w)
+    M = np.zeros(n * w)
+    _check(load().iga2l_host_bands(p, m, K.ctypes.data_as(_dp), M.ctypes.data_as(_dp)))
+    return K.reshape(n, w), M.reshape(n, w)
+
+
+def host_restriction(p: int, m: int):
+    """Library's dense 1D aggressive restriction (host setup code, no GPU)."""
+    n, nc = m + p - 2, m // 2 - 1
+    R = np.zeros(nc * n)
+    _check(load().iga2l_host_restriction(p, m, R.ctypes.data_as(_dp)))
+    return R.reshape(nc, n)
+
+
+class Solver:
+    """Handle of one assembled problem (degree p, m elements per axis, dimension dim)."""
+
+    def __init__(self, p: int, m: int, dim: int = 2, **options):
+        self._lib = load()
+        self.options = default_options(**options)
+        h = _vp()
+        _check(self._lib.iga2l_assemble(p, m, dim, ctypes.byref(self.options), ctypes.byref(h)))
+        self._h = h
+        self.p, self.m, self.dim = p, m, dim
+        nt, na, nct, nca = ctypes.c_longlong(), ctypes.c_int(), ctypes.c_longlong(), ctypes.c_int()
+        _check(self._lib.iga2l_num_dofs(h, ctypes.byref(nt), ctypes.byref(na), ctypes.byref(nct),
+                                        ctypes.byref(nca)))
+        self.N, self.n, self.Nc, self.nc = nt.value, na.value, nct.value, nca.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.iga2l_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # --- single steps -------------------------------------------------------
+    def apply_A(self, u, y, stream=None):
+        _check(self._lib.iga2l_apply_A(self._h, _ptr(u, numel=self.N), _ptr(y, numel=self.N),
+                                       _stream(stream)))
+
+    def residual(self, u, b, d=None, want_norm=False, stream=None):
+        nrm = ctypes.c_double(0.0)
+        _check(self._lib.iga2l_residual(self._h, _ptr(u, numel=self.N), _ptr(b, numel=self.N),
+                                        _ptr(d, numel=self.N) if d is not None else None,
+                                        ctypes.byref(nrm) if want_norm else None, _stream(stream)))
+        return nrm.value if want_norm else None
+
+    def schwarz_sweep(self, u, b, reverse=False, stream=None):
+        fn = self._lib.iga2l_schwarz_sweep_reverse if reverse else self._lib.iga2l_schwarz_sweep
+        _check(fn(self._h, _ptr(u, numel=self.N), _ptr(b, numel=self.N), _stream(stream)))
+
+    def restrict(self, d, dc, stream=None):
+        _check(self._lib.iga2l_restrict(self._h, _ptr(d, numel=self.N), _ptr(dc, numel=self.Nc),
+                                        _stream(stream)))
+
+    def prolong_add(self, ec, u, stream=None):
+        _check(self._lib.iga2l_prolong_add(self._h, _ptr(ec, numel=self.Nc), _ptr(u, numel=self.N),
+                                           _stream(stream)))
+
+    def coarse_solve(self, dc, ec, stream=None):
+        _check(self._lib.iga2l_coarse_solve(self._h, _ptr(dc, numel=self.Nc), _ptr(ec, numel=self.Nc),
+                                            _stream(stream)))
+
+    def cycle(self, u, b, adjoint=False, stream=None):
+        fn = self._lib.iga2l_cycle_adjoint if adjoint else self._lib.iga2l_cycle
+        _check(fn(self._h, _ptr(u, numel=self.N), _ptr(b, numel=self.N), _stream(stream)))
+
+    def rhs_from_coeffs(self, f, b, stream=None):
+        _check(self._lib.iga2l_rhs_from_coeffs(self._h, _ptr(f, numel=self.N), _ptr(b, numel=self.N),
+                                               _stream(stream)))
+
+    # --- solves -------------------------------------------------------------
+    def solve(self, b, u, tol=1e-8, max_cycles=0, stream=None):
+        """Cycles in place on u; returns (cycles, relres, history, converged)."""
+        cap = max_cycles if max_cycles > 0 else self.options.max_cycles
+        hist = np.zeros(cap)
+        cyc, rel = ctypes.c_int(0), ctypes.c_double(0.0)
+        rc = _check(self._lib.iga2l_solve(self._h, _ptr(b, numel=self.N), float(tol), cap,
+                                          _ptr(u, numel=self.N), ctypes.byref(cyc), ctypes.byref(rel),
+                                          hist.ctypes.data_as(_dp), _stream(stream)),
+                    allow_not_converged=True)
+        return cyc.value, rel.value, hist[: cyc.value].copy(), rc == OK
+
+    def adjoint_solve(self, g, lam, tol=1e-8, max_cycles=0, stream=None):
+        cyc, rel = ctypes.c_int(0), ctypes.c_double(0.0)
+        rc = _check(self._lib.iga2l_adjoint_solve(self._h, _ptr(g, numel=self.N), float(tol),
+                                                  int(max_cycles), _ptr(lam, numel=self.N),
+                                                  ctypes.byref(cyc), ctypes.byref(rel), _stream(stream)),
+                    allow_not_converged=True)
+        return cyc.value, rel.value, rc == OK
+
+    def bands(self):
+        w = 2 * self.p + 1
+        K = np.zeros(self.n * w)
+        M = np.zeros(self.n * w)
+        _check(self._lib.iga2l_get_bands(self._h, K.ctypes.data_as(_dp), M.ctypes.data_as(_dp)))
+        return K.reshape(self.n, w), M.reshape(self.n, w)

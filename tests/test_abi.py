@@ -1,0 +1,74 @@
+"""CPU checks of the C ABI library: it loads, exports every symbol declared in
+include/iga2l.h, and its host-side setup tables agree with the oracle's."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2009_01499_gb300 import iga2l
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    hdr = open(os.path.join(ROOT, "include", "iga2l.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    return sorted(set(re.findall(r"\b(iga2l_[A-Za-z0-9_]+)\s*\(", hdr)))
+
+
+def test_library_loads_and_exports_every_declared_symbol():
+    lib = iga2l.load()
+    declared = _declared_symbols()
+    assert len(declared) >= 15
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert sorted(iga2l.EXPORTS) == declared
+
+
+def test_error_strings_and_options():
+    lib = iga2l.load()
+    assert lib.iga2l_strerror(0) == b"ok"
+    assert b"invalid" in lib.iga2l_strerror(-1)
+    o = iga2l.default_options()
+    assert o.precision == iga2l.FP64 and o.schedule == iga2l.SCHED_LATTICE
+    assert o.coarse == iga2l.COARSE_VCYCLE and o.max_cycles == 100
+
+
+def test_assemble_rejects_bad_arguments_before_touching_the_gpu():
+    lib = iga2l.load()
+    h = ctypes.c_void_p()
+    for p, m, dim in [(1, 32, 2), (9, 64, 2), (2, 31, 2), (2, 8, 2), (2, 32, 4)]:
+        rc = lib.iga2l_assemble(p, m, dim, None, ctypes.byref(h))
+        assert rc in (iga2l.ERR_INVALID_ARG, iga2l.ERR_UNSUPPORTED)
+        assert not h.value
+    bad = iga2l.default_options(period=4)   # q < s + p
+    assert lib.iga2l_assemble(2, 32, 2, ctypes.byref(bad), ctypes.byref(h)) == iga2l.ERR_INVALID_ARG
+    bad = iga2l.default_options(period=6, stride=2)   # gcd(g, q) != 1
+    assert lib.iga2l_assemble(2, 32, 2, ctypes.byref(bad), ctypes.byref(h)) == iga2l.ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("m", [12, 33])
+def test_library_bands_match_oracle(oracle_mod, p, m):
+    K, M = oracle_mod.assemble_1d(p, m)
+    Kb, Mb = iga2l.host_bands(p, m)
+    n = m + p - 2
+    for i in range(n):
+        for a in range(2 * p + 1):
+            j = i + a - p
+            ref_k = K[i, j] if 0 <= j < n else 0.0
+            ref_m = M[i, j] if 0 <= j < n else 0.0
+            # independent assemblies: rounding-level agreement (1e-13 relative to the row scale)
+            assert abs(Kb[i, a] - ref_k) <= 1e-13 * m
+            assert abs(Mb[i, a] - ref_m) <= 1e-13 / m
+
+
+@pytest.mark.parametrize("p", [2, 3, 4, 5])
+@pytest.mark.parametrize("m", [24, 40])
+def test_library_restriction_matches_oracle(oracle_mod, p, m):
+    R = oracle_mod.restriction_1d(p, m, aggressive=True)
+    Rl = iga2l.host_restriction(p, m)
+    assert np.array_equal(Rl == 0, R == 0)              # same band
+    assert np.allclose(Rl, R, atol=1e-14, rtol=0)        # rounding-level agreement
