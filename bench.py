@@ -1,0 +1,445 @@
+#!/usr/bin/env python3
+"""Benchmark: DOF/s to a 1e-8 relative residual on the paper's square-domain workload.
+
+Workload (one step): the two-level solver of Algorithm 1 (LATTICE-coloured
+multiplicative Schwarz, aggressive 2h degree-1 second level with one V(1,1)
+cycle) run to ||b - A u|| <= 1e-8 ||b - A u_0|| on the 2D Poisson problem with
+1024 x 1024 elements for each of p = 2, 3, 4, 5 (block sides 3, 3, 3, 5), FP64.
+Inputs are synthetic and seeded: f has i.i.d. uniform[-1,1] B-spline
+coefficients, b = (M (x) M) f, u_0 is i.i.d. uniform[-1,1] (SplitMix64).
+
+value  = sum_p N_p / step time, inputs resident in HBM, L2 flushed before every solve.
+e2e    = the same through the public API with host buffers: H2D of f and u_0,
+         b = (M (x) M) f, solve, D2H of u, all inside the timed region.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+N > 1 runs as one process per GPU under torchrun; every rank solves the same
+workload independently (replicas, weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+M_ELEM = 1024
+DEGREES = (2, 3, 4, 5)
+TOL = 1e-8
+COLOURING = {2: (5, 2), 3: (7, 2), 4: (7, 2), 5: (10, 3)}
+METRIC = "DOF/s to 1e-8 rel. residual, mixed vs FP64; Schwarz sweep % of roofline"
+WORKLOAD = ("2D Poisson on the unit square, B-splines p=2,3,4,5 (C^{p-1}), 1024x1024 elements "
+            "(~1.05M DOFs each), seeded uniform[-1,1] coefficients of f, LATTICE-coloured "
+            "multiplicative Schwarz + aggressive 2h linear second level with V(1,1), FP64, to 1e-8")
+L2_BYTES = 129 * 1024 * 1024
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.json")
+ORACLE_CYCLES = os.path.join(ROOT, "tests", "golden", "oracle_cycles_m1024.json")
+# FP64 pipe of GB300: 2 FP64 FMA per clock per SM, 152 SMs, 2070 MHz maximum SM clock
+FP64_PEAK_GFLOPS = 2 * 2 * 152 * 2.070
+
+
+def seeds(p):
+    from paper_2009_01499_gb300 import synth
+    base = synth.BASE_SEED + 1
+    return base + p, base + 10 + p
+
+
+def schwarz_flops_per_dof(p, s, dim=2):
+    """Algorithmic FP64 flops of one Schwarz block (one per DOF): the block residual
+    (s^d rows of (2p+1)^d multiply-adds and one subtraction), the block solve with the
+    precomputed inverse (s^{2d} multiply-adds) and the update (s^d adds)."""
+    sd = s ** dim
+    return 2 * sd * (2 * p + 1) ** dim + sd + 2 * sd * sd + sd
+
+
+def block_side(p):
+    return 3 if p <= 4 else 5
+
+
+# ---------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples during the timed region (read-only queries)."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------- dist
+def dist_setup(backend):
+    import torch.distributed as dist
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend)
+    return rank, local, ws
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(x, ws, device):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------- oracle
+def oracle_cycle_sample(degrees, cycles_per_p):
+    """Times one full-size oracle cycle plus one stopping-rule residual per degree and
+    scales by the cycle counts: seconds the oracle needs to reach 1e-8."""
+    import oracle
+    from paper_2009_01499_gb300 import synth
+    total = 0.0
+    per = {}
+    for p in degrees:
+        q, g = COLOURING[p]
+        O = oracle.Problem(2, p, M_ELEM, sched=oracle.LATTICE, coarse=oracle.VCYCLE, period=q, stride=g)
+        sf, su = seeds(p)
+        f = synth.coefficients(O.N, sf)
+        u0 = synth.initial_guess(O.N, su)
+        _, Mm = oracle.assemble_1d(p, M_ELEM)
+        b = (Mm @ f.reshape(O.n, O.n) @ Mm.T).ravel()
+        t0 = time.perf_counter()
+        d = O.residual(u0, b)
+        np.linalg.norm(d)
+        t1 = time.perf_counter()
+        O.cycle(u0, b)
+        t2 = time.perf_counter()
+        t_res, t_cyc = t1 - t0, t2 - t1
+        est = t_res + cycles_per_p[p] * (t_cyc + t_res)
+        per[p] = {"cycle_s": t_cyc, "residual_s": t_res, "cycles": cycles_per_p[p], "solve_s_est": est}
+        total += est
+    return total, per
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle on the host cores, same workload and metric."""
+    if int(os.environ.get("RANK", "0")) != 0:
+        return                      # under torchrun only rank 0 runs the reference
+    import oracle
+    from paper_2009_01499_gb300 import synth
+    oracle.build()
+    counts = {int(k): int(v) for k, v in json.load(open(ORACLE_CYCLES))["cycles"].items()}
+    probs = {}
+    for p in DEGREES:
+        q, g = COLOURING[p]
+        O = oracle.Problem(2, p, M_ELEM, sched=oracle.LATTICE, coarse=oracle.VCYCLE, period=q, stride=g)
+        sf, su = seeds(p)
+        f = synth.coefficients(O.N, sf)
+        _, Mm = oracle.assemble_1d(p, M_ELEM)
+        b = (Mm @ f.reshape(O.n, O.n) @ Mm.T).ravel()
+        probs[p] = (O, b, synth.initial_guess(O.N, su))
+    t_cyc = {p: [] for p in DEGREES}
+    t_res = {p: [] for p in DEGREES}
+    step_s = []
+
+    def sample(p):
+        O, b, u0 = probs[p]
+        t0 = time.perf_counter()
+        u1 = O.cycle(u0, b)
+        t1 = time.perf_counter()
+        np.linalg.norm(O.residual(u1, b))
+        t2 = time.perf_counter()
+        return t1 - t0, t2 - t1
+
+    for k in range(args.warmup + args.steps):
+        p = DEGREES[k % len(DEGREES)]
+        tc, tr = sample(p)
+        if k >= args.warmup:
+            t_cyc[p].append(tc)
+            t_res[p].append(tr)
+            step_s.append(tc + tr)
+    total = 0.0
+    for p in DEGREES:
+        if not t_cyc[p]:            # degree not reached by the timed steps: one extra sample
+            tc, tr = sample(p)
+            t_cyc[p].append(tc)
+            t_res[p].append(tr)
+        tc, tr = statistics.mean(t_cyc[p]), statistics.mean(t_res[p])
+        total += tr + counts[p] * (tc + tr)
+    ndofs = sum(probs[p][0].N for p in DEGREES)
+    value = ndofs / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(step_s),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "m": M_ELEM, "degrees": list(DEGREES),
+                                        "tol": TOL, "dofs_per_step": ndofs},
+        "cpu_baseline": {"value": value, "unit": "DOF/s", "cores": 1, "kind": "oracle",
+                         "sample": "each step: one full-size oracle cycle + stopping residual of one "
+                                   "degree (p rotating 2,3,4,5); DOF/s = sum N_p / sum_p (t_res + "
+                                   "cycles_p (t_cycle + t_res)), cycles_p = the oracle's own counts "
+                                   "(tests/golden/oracle_cycles_m1024.json)"},
+        "e2e": {"value": value, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------- gpu arm
+def run_gpu(args):
+    import torch
+
+    rank, local, ws = dist_setup("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2009_01499_gb300 import iga2l, synth
+
+    iga2l.load()
+    solvers, bs, u0s, us, fhost, u0host, uhost = {}, {}, {}, {}, {}, {}, {}
+    for p in DEGREES:
+        q, g = COLOURING[p]
+        S = iga2l.Solver(p, M_ELEM, period=q, stride=g)
+        sf, su = seeds(p)
+        f = torch.tensor(synth.coefficients(S.N, sf), device=dev)
+        b = torch.empty_like(f)
+        S.rhs_from_coeffs(f, b)
+        solvers[p], bs[p] = S, b
+        u0s[p] = torch.tensor(synth.initial_guess(S.N, su), device=dev)
+        us[p] = torch.empty_like(u0s[p])
+        fhost[p] = torch.tensor(synth.coefficients(S.N, sf)).pin_memory()
+        u0host[p] = torch.tensor(synth.initial_guess(S.N, su)).pin_memory()
+        uhost[p] = torch.empty(S.N, dtype=torch.float64).pin_memory()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ndofs = sum(solvers[p].N for p in DEGREES)
+
+    def step(timed):
+        tot_ms, cyc = 0.0, {}
+        for p in DEGREES:
+            flush.fill_(1.0)                       # evict L2 before every solve
+            us[p].copy_(u0s[p])
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            c, rel, _, ok = solvers[p].solve(bs[p], us[p], tol=TOL)
+            e1.record(stream)
+            e1.synchronize()
+            if not ok:
+                raise RuntimeError(f"p={p} did not converge (rel {rel:.3e})")
+            tot_ms += e0.elapsed_time(e1)
+            cyc[p] = c
+        return tot_ms, cyc
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clocks = ClockSampler(local)
+    clocks.start()
+    torch.cuda.synchronize()
+    barrier(ws)
+    l0 = iga2l.kernel_launches()
+    step_ms, cycles = [], None
+    for _ in range(args.steps):
+        ms, cycles = step(True)
+        step_ms.append(ms)
+    launches = iga2l.kernel_launches() - l0
+    torch.cuda.synchronize()
+    barrier(ws)
+    clk = clocks.stop()
+    ms_step = allmax(statistics.mean(step_ms), ws, dev)
+    value = ws * ndofs / (ms_step * 1e-3)
+
+    # end to end through the public API with host buffers (H2D, rhs, solve, D2H)
+    h2d = d2h = 0
+    e2e_ms = []
+    for it in range(args.warmup + args.steps):
+        tot = 0.0
+        for p in DEGREES:
+            S = solvers[p]
+            flush.fill_(1.0)
+            f_dev = torch.empty(S.N, dtype=torch.float64, device=dev)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            f_dev.copy_(fhost[p], non_blocking=True)
+            us[p].copy_(u0host[p], non_blocking=True)
+            S.rhs_from_coeffs(f_dev, bs[p])
+            S.solve(bs[p], us[p], tol=TOL)
+            uhost[p].copy_(us[p], non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+            if it == 0:
+                h2d += fhost[p].numel() * 8 + u0host[p].numel() * 8
+                d2h += uhost[p].numel() * 8
+        if it >= args.warmup:
+            e2e_ms.append(tot)
+    e2e_step = allmax(statistics.mean(e2e_ms), ws, dev)
+
+    # roofline of the dominant kernel, the Schwarz colour-phase kernel (FP64 pipe bound)
+    sweep_flops, sweep_ms, per_p = 0.0, 0.0, {}
+    for p in DEGREES:
+        S = solvers[p]
+        u = us[p]
+        u.copy_(u0s[p])
+        S.schwarz_sweep(u, bs[p])
+        reps = 3
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            S.schwarz_sweep(u, bs[p])
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        q = COLOURING[p][0]
+        fl = schwarz_flops_per_dof(p, block_side(p)) * S.N
+        per_p[str(p)] = {"sweep_ms": round(ms, 4), "launches_per_sweep": q * q,
+                         "gflops": round(fl / ms / 1e6, 1), "cycles": cycles[p]}
+        sweep_flops += cycles[p] * fl
+        sweep_ms += cycles[p] * ms
+    achieved = sweep_flops / sweep_ms / 1e6   # GFLOP/s
+    traffic = None
+    if os.path.exists(TRAFFIC_FILE):
+        rec = json.load(open(TRAFFIC_FILE))
+        src = os.path.join(ROOT, "paper_2009_01499_gb300", "csrc", "kernels_fine.cu")
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if rec.get("source_sha256_16") == digest:
+            traffic = rec.get("bytes_per_launch")
+    roofline = {"bound": "alu", "achieved": round(achieved, 1), "peak": round(FP64_PEAK_GFLOPS, 1),
+                "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4), "traffic": traffic,
+                "kernel": "k_schwarz_lattice2d (one colour phase per launch)",
+                "peak_source": "FP64 FMA pipe: 2 FMA/clk/SM x 152 SMs x 2070 MHz (derived; a "
+                               "dependent-free FMA loop measured 1256 GFLOP/s on this GB300)",
+                "per_degree": per_p}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "m": M_ELEM, "degrees": list(DEGREES), "tol": TOL,
+                   "dofs_per_step": ndofs, "cycles": {str(p): cycles[p] for p in DEGREES},
+                   "l2": "flushed (256 MiB write) before every solve", "schedule": "LATTICE",
+                   "colouring": {str(p): list(COLOURING[p]) for p in DEGREES},
+                   "parallelism": f"replicas x{ws}"},
+        "e2e": {"value": ws * ndofs / (e2e_step * 1e-3), "unit": "DOF/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "roofline": roofline,
+        "clocks": clk,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        total_s, per = oracle_cycle_sample(DEGREES, {p: cycles[p] for p in DEGREES})
+        line["cpu_baseline"] = {
+            "value": ndofs / total_s, "unit": "DOF/s", "cores": 1, "kind": "oracle",
+            "sample": "one full-size oracle cycle + one stopping residual per degree, scaled by the "
+                      "GPU run's cycle counts (identical iterates): "
+                      + ", ".join(f"p={p}: {v['cycle_s']:.2f}s/cycle" for p, v in per.items())}
+    elif rank == 0:
+        line["cpu_baseline"] = None
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_profile_step(args):
+    """For ncu: --warmup solves per degree, then one solve per degree, nothing else."""
+    import torch
+    from paper_2009_01499_gb300 import iga2l, synth
+    dev = torch.device("cuda", 0)
+    degrees = (args.profile_p,) if args.profile_p else DEGREES
+    for p in degrees:
+        q, g = COLOURING[p]
+        S = iga2l.Solver(p, args.profile_m, period=q, stride=g)
+        sf, su = seeds(p)
+        f = torch.tensor(synth.coefficients(S.N, sf), device=dev)
+        b = torch.empty_like(f)
+        S.rhs_from_coeffs(f, b)
+        u0 = torch.tensor(synth.initial_guess(S.N, su), device=dev)
+        u = torch.empty_like(u0)
+        for _ in range(args.warmup + 1):
+            u.copy_(u0)
+            cyc, rel, _, ok = S.solve(b, u, tol=TOL)
+        torch.cuda.synchronize()
+        print(f"p={p} m={args.profile_m}: {cyc} cycles, rel {rel:.3e}, converged {ok}", flush=True)
+        S.close()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="profiling aid: warm-up solves then one solve per degree, no timing")
+    ap.add_argument("--profile-m", type=int, default=M_ELEM)
+    ap.add_argument("--profile-p", type=int, default=0)
+    args = ap.parse_args()
+    if args.profile_step:
+        run_profile_step(args)
+        return
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

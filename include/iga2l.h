@@ -149,6 +149,10 @@ const char *iga2l_strerror(int code);
 /* Detail of the last error on the calling host thread ("" if none). */
 const char *iga2l_last_error(void);
 
+/* Number of CUDA kernels this library has launched in this process so far
+ * (all handles and threads).  For benchmarks; no GPU work. */
+long long iga2l_kernel_launches(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -2,6 +2,7 @@
 // per-step entry points, Algorithm 1 and the solver loop.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -11,6 +12,12 @@
 #include "internal.h"
 
 using namespace iga2l;
+
+namespace iga2l {
+static std::atomic<long long> g_launches{0};
+void count_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace iga2l
 
 struct iga2l_solver : public Solver {
     double *host_norm = nullptr;   // pinned scalar for norm readback
@@ -504,5 +511,7 @@ const char *iga2l_strerror(int code)
 }
 
 const char *iga2l_last_error(void) { return g_last_error.c_str(); }
+
+long long iga2l_kernel_launches(void) { return launches_so_far(); }
 
 }  // extern "C"

@@ -68,6 +68,11 @@ struct Solver {
     std::vector<void *> allocs;
 };
 
+// Number of kernels this library has launched (process-wide), for benchmarks
+// that report how many of the timed region's kernels are this library's.
+void count_launches(long long k);
+long long launches_so_far();
+
 // setup.cpp
 int build_host_tables(int p, int m, int s, HostTables &ht, std::string &err);
 void bspline_band_1d(int p, int m, std::vector<double> &K, std::vector<double> &M);

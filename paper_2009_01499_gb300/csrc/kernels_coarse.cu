@@ -142,6 +142,7 @@ cudaError_t gs_pass(const Level &L, const Stencil9 &st, const double *rhs, doubl
     for (int t = 0; t < 4; ++t) {
         const int c = forward ? t : 3 - t;
         k_gs_sublattice<<<grid2(half, half, blk), blk, 0, s>>>(L.n, kGsSeq[c][0], kGsSeq[c][1], st, rhs, e);
+        count_launches(1);
     }
     return cudaGetLastError();
 }
@@ -153,6 +154,7 @@ cudaError_t vcycle(const Solver &S, int l, const double *rhs, double *e, cudaStr
     if (l == last) {
         const int N = S.ndirect;
         k_dense_matvec<<<(N * 32 + 255) / 256, 256, 0, s>>>(N, S.dinv, rhs, e);
+        count_launches(1);
         return cudaGetLastError();
     }
     const Level &C = S.lev[l + 1];
@@ -162,10 +164,13 @@ cudaError_t vcycle(const Solver &S, int l, const double *rhs, double *e, cudaStr
     if (err != cudaSuccess) return err;
     if ((err = gs_pass(L, st, rhs, e, true, s)) != cudaSuccess) return err;
     k_level_residual<<<grid2(L.n, L.n, blk), blk, 0, s>>>(L.n, st, rhs, e, L.r);
+    count_launches(1);
     k_level_restrict<<<grid2(C.n, C.n, blk), blk, 0, s>>>(L.n, C.n, L.r, C.rhs);
+    count_launches(1);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     if ((err = vcycle(S, l + 1, C.rhs, C.e, s)) != cudaSuccess) return err;
     k_level_prolong_add<<<grid2(L.n, L.n, blk), blk, 0, s>>>(L.n, C.n, C.e, e);
+    count_launches(1);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     return gs_pass(L, st, rhs, e, false, s);
 }

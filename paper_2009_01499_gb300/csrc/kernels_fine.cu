@@ -229,6 +229,7 @@ cudaError_t residual_p(const Solver &S, const double *u, const double *b, double
 {
     dim3 blk(kResTX, kResTY), grd((S.n + kResTX - 1) / kResTX, (S.n + kResTY - 1) / kResTY);
     k_residual2d<P><<<grd, blk, 0, st>>>(S.n, S.ht.npc, S.stencil, S.pcls, u, b, d, part);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -248,6 +249,7 @@ cudaError_t schwarz_p(const Solver &S, double *u, const double *b, bool reverse,
         k_schwarz_lattice2d<P, SB><<<grid, 256, 0, st>>>(S.n, S.ht.npc, S.ht.nbc, q, ox, oy, nbx,
                                                           nblocks, S.stencil, S.pcls, S.binv,
                                                           S.bcls, u, b);
+        count_launches(1);
         cudaError_t err = cudaGetLastError();
         if (err != cudaSuccess) return err;
     }
@@ -281,6 +283,7 @@ cudaError_t launch_apply_A(const Solver &S, const double *u, double *y, cudaStre
 cudaError_t launch_norm_finish(const Solver &S, const double *part, double *out, cudaStream_t st)
 {
     k_sum_partials<<<1, 1024, 0, st>>>(part, residual_partials(S), out);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -304,7 +307,9 @@ cudaError_t launch_restrict(const Solver &S, const double *d, double *dc, cudaSt
 {
     const int nc = S.nc, n = S.n;
     k_restrict_x<<<dim3((nc + 127) / 128, n), 128, 0, st>>>(n, nc, S.ht.wr, S.Rb, S.Rlo, d, S.t);
+    count_launches(1);
     k_restrict_y<<<dim3((nc + 127) / 128, nc), 128, 0, st>>>(n, nc, S.ht.wr, S.Rb, S.Rlo, S.t, dc);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -312,7 +317,9 @@ cudaError_t launch_prolong_add(const Solver &S, const double *ec, double *u, cud
 {
     const int nc = S.nc, n = S.n;
     k_prolong_x<<<dim3((n + 127) / 128, nc), 128, 0, st>>>(n, nc, S.ht.wc, S.Cb, S.Clo, ec, S.t2);
+    count_launches(1);
     k_prolong_y<<<dim3((n + 127) / 128, n), 128, 0, st>>>(n, nc, S.ht.wc, S.Cb, S.Clo, S.t2, u);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -321,9 +328,13 @@ cudaError_t launch_mass2(const Solver &S, const double *f, double *b, cudaStream
     dim3 grd((S.n + 127) / 128, S.n);
     switch (S.p) {
     case 2: k_mass2d<2><<<grd, 128, 0, st>>>(S.n, S.Mb, f, b); break;
+    count_launches(1);
     case 3: k_mass2d<3><<<grd, 128, 0, st>>>(S.n, S.Mb, f, b); break;
+    count_launches(1);
     case 4: k_mass2d<4><<<grd, 128, 0, st>>>(S.n, S.Mb, f, b); break;
+    count_launches(1);
     case 5: k_mass2d<5><<<grd, 128, 0, st>>>(S.n, S.Mb, f, b); break;
+    count_launches(1);
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

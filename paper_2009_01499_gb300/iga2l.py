@@ -28,7 +28,7 @@ EXPORTS = (
     "iga2l_prolong_add", "iga2l_coarse_solve", "iga2l_cycle", "iga2l_cycle_adjoint",
     "iga2l_solve", "iga2l_adjoint_solve", "iga2l_rhs_from_coeffs", "iga2l_get_bands",
     "iga2l_host_bands", "iga2l_host_restriction", "iga2l_destroy", "iga2l_strerror",
-    "iga2l_last_error",
+    "iga2l_last_error", "iga2l_kernel_launches",
 )
 
 
@@ -89,6 +89,7 @@ def load(build_if_missing: bool = True):
             "iga2l_destroy": (None, [_vp]),
             "iga2l_strerror": (ctypes.c_char_p, [ctypes.c_int]),
             "iga2l_last_error": (ctypes.c_char_p, []),
+            "iga2l_kernel_launches": (ctypes.c_longlong, []),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -122,6 +123,11 @@ def _stream(stream):
     import torch
     s = torch.cuda.current_stream() if stream is None else stream
     return ctypes.c_void_p(s.cuda_stream)
+
+
+def kernel_launches() -> int:
+    """Kernels launched by libiga2l.so in this process so far."""
+    return int(load().iga2l_kernel_launches())
 
 
 def default_options(**kw) -> Options:
