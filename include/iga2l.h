@@ -144,6 +144,30 @@ int iga2l_get_bands(iga2l_handle h, double *K, double *M);
 int iga2l_host_bands(int p, int m, double *K, double *M);
 int iga2l_host_restriction(int p, int m, double *R);
 
+/* Defect and its squared norm for callers that cannot allocate device memory.
+ * (The paper has no counterpart: this is a deployment aid.)  Some callers may
+ * not call cudaMalloc at all -- code where the CUDA allocator is off limits, or
+ * a host runtime that owns every device allocation and only lends out its own
+ * buffers -- so they cannot create a handle (iga2l_assemble allocates).  This
+ * entry point needs no handle and allocates nothing: it writes
+ * d = b - A_p u (if d is not NULL) and *norm2 = ||d||_2^2, where A_p =
+ * K(x)M + M(x)K is given by the caller's DEVICE copies of the 1D band rows Kb, Mb
+ * (n x (2p+1) each, the layout of iga2l_host_bands / iga2l_get_bands; n = m+p-2).
+ * u, b, d are device vectors of n*n doubles; norm2 is one device double.  All
+ * buffers belong to the caller; work is enqueued on `stream`, nothing is
+ * synchronised.  p must be 2..5 and n at most 4096 (IGA2L_ERR_INVALID_ARG with
+ * a message in iga2l_last_error otherwise).
+ * Its only scratch (one partial sum per thread block) is a fixed 512 KiB array
+ * inside the library, held by every GPU that loads the library until the
+ * process exits.  The first call on each device looks up that array's address
+ * (cudaGetSymbolAddress) with the device current; make that first call before
+ * any stream capture.  Every call shares the array: each call overwrites the
+ * partials it reads, so nothing has to be cleared, but calls that overlap on the
+ * GPU (other streams, other threads) race on it. */
+int iga2l_residual_norm2_noalloc(int p, int n, const double *Kb, const double *Mb,
+                                 const double *u, const double *b, double *d,
+                                 double *norm2, void *stream);
+
 void iga2l_destroy(iga2l_handle h);
 const char *iga2l_strerror(int code);
 /* Detail of the last error on the calling host thread ("" if none). */

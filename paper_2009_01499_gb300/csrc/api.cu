@@ -181,6 +181,8 @@ int solve_impl(iga2l_handle h, const double *b, double tol, int max_cycles, doub
 
 }  // namespace
 
+void iga2l::set_last_error(const std::string &msg) { g_last_error = msg; }
+
 extern "C" {
 
 void iga2l_default_options(iga2l_options *opt)

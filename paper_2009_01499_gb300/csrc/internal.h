@@ -73,6 +73,9 @@ struct Solver {
 void count_launches(long long k);
 long long launches_so_far();
 
+// Sets the text returned by iga2l_last_error on the calling thread (api.cu).
+void set_last_error(const std::string &msg);
+
 // setup.cpp
 int build_host_tables(int p, int m, int s, HostTables &ht, std::string &err);
 void bspline_band_1d(int p, int m, std::vector<double> &K, std::vector<double> &M);

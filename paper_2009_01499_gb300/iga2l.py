@@ -28,7 +28,7 @@ EXPORTS = (
     "iga2l_prolong_add", "iga2l_coarse_solve", "iga2l_cycle", "iga2l_cycle_adjoint",
     "iga2l_solve", "iga2l_adjoint_solve", "iga2l_rhs_from_coeffs", "iga2l_get_bands",
     "iga2l_host_bands", "iga2l_host_restriction", "iga2l_destroy", "iga2l_strerror",
-    "iga2l_last_error", "iga2l_kernel_launches",
+    "iga2l_last_error", "iga2l_kernel_launches", "iga2l_residual_norm2_noalloc",
 )
 
 
@@ -90,6 +90,8 @@ def load(build_if_missing: bool = True):
             "iga2l_strerror": (ctypes.c_char_p, [ctypes.c_int]),
             "iga2l_last_error": (ctypes.c_char_p, []),
             "iga2l_kernel_launches": (ctypes.c_longlong, []),
+            "iga2l_residual_norm2_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _vp, _vp, _vp,
+                                                            _vp, _vp, _vp, _vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -153,6 +155,16 @@ def host_restriction(p: int, m: int):
     R = np.zeros(nc * n)
     _check(load().iga2l_host_restriction(p, m, R.ctypes.data_as(_dp)))
     return R.reshape(nc, n)
+
+
+def residual_norm2_noalloc(p, n, Kb, Mb, u, b, d, norm2, stream=None):
+    """Handle-free defect d = b - A u and ||d||^2 (device scalar) for callers that
+    cannot allocate device memory; Kb, Mb are device copies of the 1D band rows.
+    The library allocates nothing for this call (see include/iga2l.h)."""
+    _check(load().iga2l_residual_norm2_noalloc(
+        int(p), int(n), _ptr(Kb, numel=n * (2 * p + 1)), _ptr(Mb, numel=n * (2 * p + 1)),
+        _ptr(u, numel=n * n), _ptr(b, numel=n * n), _ptr(d, numel=n * n) if d is not None else None,
+        _ptr(norm2, numel=1), _stream(stream)))
 
 
 class Solver:
