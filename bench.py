@@ -328,6 +328,44 @@ def run_gpu(args):
             e2e_ms.append(tot)
     e2e_step = allmax(statistics.mean(e2e_ms), ws, dev)
 
+    # mixed precision (FP32 inner cycle, TILE(32) schedule) inside FP64 refinement, same
+    # workload and stopping rule
+    mixed = None
+    if not args.no_mixed:
+        msolv = {}
+        for p in DEGREES:
+            q, g = COLOURING[p]
+            msolv[p] = iga2l.Solver(p, M_ELEM, period=q, stride=g, precision=iga2l.MIXED_FP32,
+                                    schedule=iga2l.SCHED_TILE)
+        mcyc = {}
+
+        def mstep():
+            tot = 0.0
+            for p in DEGREES:
+                flush.fill_(1.0)
+                us[p].copy_(u0s[p])
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                c, rel, _, ok = msolv[p].solve(bs[p], us[p], tol=TOL)
+                e1.record(stream)
+                e1.synchronize()
+                if not ok:
+                    raise RuntimeError(f"mixed p={p} did not converge")
+                tot += e0.elapsed_time(e1)
+                mcyc[p] = c
+            return tot
+
+        for _ in range(args.warmup):
+            mstep()
+        mms = allmax(statistics.mean([mstep() for _ in range(args.steps)]), ws, dev)
+        mixed = {"value": ws * ndofs / (mms * 1e-3), "unit": "DOF/s", "ms_per_step": mms,
+                 "speedup_vs_fp64": ms_step / mms, "dtype": "f32 inner cycle, f64 residual/update",
+                 "schedule": "TILE(32)", "cycles": {str(p): mcyc[p] for p in DEGREES},
+                 "accuracy": "same 1e-8 FP64 residual rule; refined to 1e-12 the solution is within "
+                             "1e-8 of the FP64 oracle's (tests/test_gpu_mixed.py)"}
+        for S in msolv.values():
+            S.close()
+
     # roofline of the dominant kernel, the Schwarz colour-phase kernel (FP64 pipe bound)
     sweep_flops, sweep_ms, per_p = 0.0, 0.0, {}
     for p in DEGREES:
@@ -379,6 +417,7 @@ def run_gpu(args):
         "gpu_launches": int(launches),
         "roofline": roofline,
         "clocks": clk,
+        "mixed": mixed,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         import oracle
@@ -425,6 +464,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision leg")
     ap.add_argument("--profile-step", action="store_true",
                     help="profiling aid: warm-up solves then one solve per degree, no timing")
     ap.add_argument("--profile-m", type=int, default=M_ELEM)

@@ -17,10 +17,14 @@
  *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
  *     enqueued on it; entry points that return a host scalar synchronise it.
  *   - The handle owns its device tables and workspace, allocated in
- *     iga2l_assemble and released by iga2l_destroy.  No other entry point
- *     allocates device memory.  A handle must not be used from two host
- *     threads at once, and two calls on one handle must not overlap on the GPU
- *     (they share workspace).
+ *     iga2l_assemble and released by iga2l_destroy; no other entry point calls
+ *     cudaMalloc.  With options.graphs = 1, the first cycle on a new (u, b)
+ *     pair captures it into a CUDA graph (the driver keeps its resources until
+ *     iga2l_destroy; the handle keeps the four most recently used) and later
+ *     cycles replay it; when the caller's stream is itself being captured the
+ *     kernels are enqueued directly instead.  A handle must not be used from
+ *     two host threads at once, and two calls on one handle must not overlap
+ *     on the GPU (they share workspace).
  *   - Return codes: IGA2L_OK, IGA2L_NOT_CONVERGED or a negative error code
  *     (iga2l_strerror; iga2l_last_error gives detail for the calling thread).
  *     Argument checks happen before any work is enqueued.
@@ -42,6 +46,9 @@ extern "C" {
 
 /* precision */
 #define IGA2L_FP64 0
+/* FP64 outer residual, norm and update around an FP32 inner cycle (FP32 storage
+ * and FMA; FP64 boundary-block inverses and coarsest solve): iterative refinement */
+#define IGA2L_MIXED_FP32 1
 /* schedule: colour classes of the multiplicative Schwarz step */
 #define IGA2L_SCHED_LATTICE 1
 #define IGA2L_SCHED_TILE 2
@@ -52,17 +59,19 @@ extern "C" {
 typedef struct iga2l_solver *iga2l_handle;
 
 typedef struct {
-    int precision;   /* IGA2L_FP64 */
+    int precision;   /* IGA2L_FP64 or IGA2L_MIXED_FP32 */
     int schedule;    /* IGA2L_SCHED_LATTICE or IGA2L_SCHED_TILE */
-    int tile;        /* TILE side T >= period (0 = library default) */
+    int tile;        /* TILE side T >= period (0 = library default, 32; only 32 is compiled) */
     int period;      /* colour period q >= s + p (0 = library default for p) */
     int stride;      /* colour stride g, gcd(g, q) = 1 (0 = library default) */
     int coarse;      /* IGA2L_COARSE_VCYCLE (Section 3.2) or IGA2L_COARSE_EXACT */
     int block_side;  /* Schwarz block side s (0 = the paper's choice for p, Section 4.3) */
     int max_cycles;  /* default cap for iga2l_solve when its max_cycles <= 0 */
+    int graphs;      /* 1: replay cycles as captured CUDA graphs (default); 0: plain launches */
 } iga2l_options;
 
-/* Fills the defaults: FP64, LATTICE, V(1,1), the paper's block side, 100 cycles. */
+/* Fills the defaults: FP64, LATTICE, V(1,1), the paper's block side, 100 cycles,
+ * graphs on. */
 void iga2l_default_options(iga2l_options *opt);
 
 /* Builds the solver for degree p (2..5), m elements per axis, dimension dim (2).
@@ -109,7 +118,9 @@ int iga2l_prolong_add(iga2l_handle h, const double *ec, double *u, void *stream)
 int iga2l_coarse_solve(iga2l_handle h, const double *dc, double *ec, void *stream);
 
 /* One cycle of Algorithm 1 in place: Schwarz step, defect, restriction,
- * second-level solve, prolongation and update. */
+ * second-level solve, prolongation and update.  With IGA2L_MIXED_FP32: r = b - A u
+ * in FP64, the same cycle in FP32 on A delta = r from delta = 0, u += delta in FP64
+ * (equal to the FP64 cycle in exact arithmetic, since the cycle is affine in u). */
 int iga2l_cycle(iga2l_handle h, double *u, const double *b, void *stream);
 
 /* One transposed cycle: second-level correction first, then the reversed
@@ -126,7 +137,8 @@ int iga2l_solve(iga2l_handle h, const double *b, double tol, int max_cycles, dou
                 int *cycles, double *relres, double *hist, void *stream);
 
 /* Solve of A_p lambda = g with the transposed cycle (A_p is symmetric, so the
- * limit is A_p^{-1} g; the iterates are those of the adjoint iteration). */
+ * limit is A_p^{-1} g; the iterates are those of the adjoint iteration).  Always
+ * FP64 (also on a mixed-precision handle). */
 int iga2l_adjoint_solve(iga2l_handle h, const double *g, double tol, int max_cycles,
                         double *lambda, int *cycles, double *relres, void *stream);
 

@@ -2,6 +2,7 @@
 // per-step entry points, Algorithm 1 and the solver loop.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -15,13 +16,31 @@ using namespace iga2l;
 
 namespace iga2l {
 static std::atomic<long long> g_launches{0};
-void count_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+// kernels enqueued while a cycle is being captured into a graph are counted when the
+// graph is launched, not when they are recorded
+static thread_local bool g_capturing = false;
+void count_launches(long long k)
+{
+    if (!g_capturing) g_launches.fetch_add(k, std::memory_order_relaxed);
+}
 long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 }  // namespace iga2l
 
 struct iga2l_solver : public Solver {
     double *host_norm = nullptr;   // pinned scalar for norm readback
     double *dev_norm = nullptr;
+    // Cycles are captured once per (u, b, kind) into CUDA graphs and replayed: one
+    // graph launch instead of ~100 small kernel launches per cycle.
+    struct CycleGraph {
+        const double *u, *b;
+        int kind;                  // bit 0: adjoint, bit 1: ends with the residual norm, bit 2: mixed
+        cudaGraphExec_t exec;
+        long long kernels;
+        unsigned long long last_use;
+    };
+    std::vector<CycleGraph> graphs;
+    unsigned long long tick = 0;
+    cudaStream_t cap_stream = nullptr;
 };
 
 namespace {
@@ -67,6 +86,9 @@ void release(iga2l_solver *S)
     int cur = -1;
     cudaGetDevice(&cur);
     if (cur != S->device) cudaSetDevice(S->device);
+    for (auto &g : S->graphs) cudaGraphExecDestroy(g.exec);
+    S->graphs.clear();
+    if (S->cap_stream) cudaStreamDestroy(S->cap_stream);
     for (void *p : S->allocs) cudaFree(p);
     S->allocs.clear();
     if (S->host_norm) cudaFreeHost(S->host_norm);
@@ -131,16 +153,101 @@ int coarse_correction(iga2l_handle h, double *u, const double *b, cudaStream_t s
     return finish(e, "coarse correction");
 }
 
-int run_cycle(iga2l_handle h, double *u, const double *b, cudaStream_t st, bool adjoint)
+// Enqueues one cycle (optionally followed by the residual norm into host_norm).
+// Mixed precision (forward cycles only): the FP32 inner cycle on A delta = r from
+// delta = 0, then u += delta in FP64, then the FP64 residual r = b - A u (stored in
+// FP32 for the next inner cycle) -- r must already hold b - A u on entry.
+int enqueue_cycle(iga2l_handle h, double *u, const double *b, cudaStream_t st, bool adjoint, bool norm)
 {
+    int rc;
+    if (h->mx.enabled && !adjoint) {
+        cudaError_t e = launch_inner_fine(*h, h->mx.r, false, st);
+        if (e == cudaSuccess) e = launch_inner_coarse(*h, st);
+        if (e == cudaSuccess) e = launch_inner_update(*h, u, st);
+        if (e == cudaSuccess) e = launch_outer_residual(*h, u, b, h->mx.r, norm ? h->part : nullptr, st);
+        if (e == cudaSuccess && norm) e = launch_norm_finish(*h, h->part, h->dev_norm, st);
+        if (e == cudaSuccess && norm)
+            e = cudaMemcpyAsync(h->host_norm, h->dev_norm, sizeof(double), cudaMemcpyDeviceToHost, st);
+        return finish(e, "mixed-precision cycle");
+    }
     if (!adjoint) {
         cudaError_t e = launch_schwarz(*h, u, b, false, st);
         if (e != cudaSuccess) return cuda_fail(e, "schwarz sweep");
-        return coarse_correction(h, u, b, st);
+        if ((rc = coarse_correction(h, u, b, st)) != IGA2L_OK) return rc;
+    } else {
+        if ((rc = coarse_correction(h, u, b, st)) != IGA2L_OK) return rc;
+        cudaError_t e = launch_schwarz(*h, u, b, true, st);
+        if (e != cudaSuccess) return cuda_fail(e, "reverse schwarz sweep");
     }
-    int rc = coarse_correction(h, u, b, st);
-    if (rc != IGA2L_OK) return rc;
-    return finish(launch_schwarz(*h, u, b, true, st), "reverse schwarz sweep");
+    if (norm) {
+        cudaError_t e = launch_residual(*h, u, b, nullptr, h->part, st);
+        if (e == cudaSuccess) e = launch_norm_finish(*h, h->part, h->dev_norm, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h->host_norm, h->dev_norm, sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return cuda_fail(e, "residual norm");
+    }
+    return IGA2L_OK;
+}
+
+// One cycle on `st`: replays a captured graph for (u, b, kind), capturing it first if needed.
+int run_cycle_graph(iga2l_handle h, double *u, const double *b, cudaStream_t st, bool adjoint, bool norm)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (!h->opt.graphs || cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+        return enqueue_cycle(h, u, b, st, adjoint, norm);   // plain launches (or the caller is capturing)
+    const int kind = (adjoint ? 1 : 0) | (norm ? 2 : 0) | (h->mx.enabled ? 4 : 0);
+    iga2l_solver::CycleGraph *g = nullptr;
+    for (auto &c : h->graphs)
+        if (c.u == u && c.b == b && c.kind == kind) g = &c;
+    if (!g) {
+        cudaError_t e;
+        if (!h->cap_stream && (e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_fail(e, "capture stream");
+        if ((e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+            return cuda_fail(e, "begin capture");
+        g_capturing = true;
+        int rc = enqueue_cycle(h, u, b, h->cap_stream, adjoint, norm);
+        g_capturing = false;
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(h->cap_stream, &graph);
+        if (rc != IGA2L_OK) { if (graph) cudaGraphDestroy(graph); return rc; }
+        if (e != cudaSuccess) return cuda_fail(e, "end capture");
+        size_t nn = 0;
+        cudaGraphGetNodes(graph, nullptr, &nn);
+        std::vector<cudaGraphNode_t> nodes(nn);
+        long long kernels = 0;
+        if (nn && cudaGraphGetNodes(graph, nodes.data(), &nn) == cudaSuccess)
+            for (auto nd : nodes) {
+                cudaGraphNodeType t;
+                if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kernels;
+            }
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+        if (h->graphs.size() >= 4) {   // keep the four most recently used
+            auto lru = std::min_element(h->graphs.begin(), h->graphs.end(),
+                                        [](const auto &x, const auto &y) { return x.last_use < y.last_use; });
+            cudaGraphExecDestroy(lru->exec);
+            h->graphs.erase(lru);
+        }
+        h->graphs.push_back({u, b, kind, exec, kernels, 0});
+        g = &h->graphs.back();
+    }
+    g->last_use = ++h->tick;
+    cudaError_t e = cudaGraphLaunch(g->exec, st);
+    if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+    count_launches(g->kernels);
+    return IGA2L_OK;
+}
+
+int run_cycle(iga2l_handle h, double *u, const double *b, cudaStream_t st, bool adjoint)
+{
+    if (h->mx.enabled && !adjoint) {   // the inner cycle starts from r = b - A u
+        cudaError_t e = launch_outer_residual(*h, u, b, h->mx.r, nullptr, st);
+        if (e != cudaSuccess) return cuda_fail(e, "outer residual");
+    }
+    return run_cycle_graph(h, u, b, st, adjoint, false);
 }
 
 int solve_impl(iga2l_handle h, const double *b, double tol, int max_cycles, double *u, int *cycles,
@@ -151,20 +258,31 @@ int solve_impl(iga2l_handle h, const double *b, double tol, int max_cycles, doub
     if (max_cycles <= 0) max_cycles = h->opt.max_cycles;
     cudaStream_t st = as_stream(stream);
     double r0sq = 0.0;
-    int rc = residual_norm2(h, u, b, nullptr, st, &r0sq);
-    if (rc != IGA2L_OK) return rc;
+    int rc;
+    if (h->mx.enabled && !adjoint) {   // r_0 in FP64, kept in FP32 for the first inner cycle
+        cudaError_t e = launch_outer_residual(*h, u, b, h->mx.r, h->part, st);
+        if (e == cudaSuccess) e = launch_norm_finish(*h, h->part, h->dev_norm, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h->host_norm, h->dev_norm, sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "initial residual");
+        r0sq = *h->host_norm;
+    } else if ((rc = residual_norm2(h, u, b, nullptr, st, &r0sq)) != IGA2L_OK) {
+        return rc;
+    }
     if (!std::isfinite(r0sq)) return fail(IGA2L_ERR_NONFINITE, "initial residual is not finite");
     const double r0 = std::sqrt(r0sq);
     int k = 0;
     double rel = 0.0;
     int status = r0 == 0.0 ? IGA2L_OK : IGA2L_NOT_CONVERGED;
     while (status != IGA2L_OK && k < max_cycles) {
-        rc = run_cycle(h, u, b, st, adjoint);
+        // one cycle and its residual norm, read back once per cycle
+        rc = run_cycle_graph(h, u, b, st, adjoint, true);
         if (rc != IGA2L_OK) return rc;
         ++k;
-        double rsq = 0.0;
-        rc = residual_norm2(h, u, b, nullptr, st, &rsq);
-        if (rc != IGA2L_OK) return rc;
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "solve");
+        const double rsq = *h->host_norm;
         if (!std::isfinite(rsq)) {
             if (cycles) *cycles = k;
             return fail(IGA2L_ERR_NONFINITE, "residual norm is not finite");
@@ -193,6 +311,7 @@ void iga2l_default_options(iga2l_options *opt)
     opt->schedule = IGA2L_SCHED_LATTICE;
     opt->coarse = IGA2L_COARSE_VCYCLE;
     opt->max_cycles = 100;
+    opt->graphs = 1;
 }
 
 int iga2l_assemble(int p, int m, int dim, const iga2l_options *opt_in, iga2l_handle *out)
@@ -206,9 +325,14 @@ int iga2l_assemble(int p, int m, int dim, const iga2l_options *opt_in, iga2l_han
     if (p < 2 || p > kMaxP) return fail(IGA2L_ERR_INVALID_ARG, "p must be in 2..5");
     if (m < 4 * p + 4 || (m % 2) != 0)
         return fail(IGA2L_ERR_INVALID_ARG, "m must be even and >= 4p+4 (aggressive 2h coarsening)");
-    if (opt.precision != IGA2L_FP64) return fail(IGA2L_ERR_UNSUPPORTED, "precision not available");
-    if (opt.schedule != IGA2L_SCHED_LATTICE)
+    if (opt.precision != IGA2L_FP64 && opt.precision != IGA2L_MIXED_FP32)
+        return fail(IGA2L_ERR_UNSUPPORTED, "precision not available");
+    if (opt.schedule != IGA2L_SCHED_LATTICE && opt.schedule != IGA2L_SCHED_TILE)
         return fail(IGA2L_ERR_UNSUPPORTED, "schedule not available");
+    if (opt.schedule == IGA2L_SCHED_TILE) {
+        if (opt.tile == 0) opt.tile = kTile;
+        if (opt.tile != kTile) return fail(IGA2L_ERR_UNSUPPORTED, "only TILE side 32 is compiled");
+    }
     if (opt.coarse != IGA2L_COARSE_VCYCLE && opt.coarse != IGA2L_COARSE_EXACT)
         return fail(IGA2L_ERR_INVALID_ARG, "unknown coarse solver");
     const int s = opt.block_side > 0 ? opt.block_side : default_block_side(p);
@@ -218,6 +342,8 @@ int iga2l_assemble(int p, int m, int dim, const iga2l_options *opt_in, iga2l_han
     if (q <= 0) default_colouring(p, s, q, g);
     if (g <= 0) g = 1;
     if (q < s + p) return fail(IGA2L_ERR_INVALID_ARG, "colour period must be >= s + p");
+    if (opt.schedule == IGA2L_SCHED_TILE && opt.tile < q)
+        return fail(IGA2L_ERR_INVALID_ARG, "TILE side must be >= the colour period");
     if (gcd_int(g % q, q) != 1) return fail(IGA2L_ERR_INVALID_ARG, "colour stride must be coprime to the period");
 
     iga2l_solver *S = new (std::nothrow) iga2l_solver();
@@ -309,6 +435,27 @@ int iga2l_assemble(int p, int m, int dim, const iga2l_options *opt_in, iga2l_han
                 }
     if (!cholesky_inverse(S->ndirect, Ad)) { release(S); return fail(IGA2L_ERR_INVALID_ARG, "coarsest matrix not SPD"); }
 
+    // the interior stencil of degree p from a reference mesh, so that every handle of
+    // degree p writes identical constant-memory values (2D stencils do not depend on h)
+    {
+        HostTables ref;
+        std::string rerr;
+        const int mref = 8 * p + 16;
+        if (build_host_tables(p, mref, s, ref, rerr) != IGA2L_OK) { release(S); return fail(IGA2L_ERR_INVALID_ARG, rerr); }
+        const int xr = ref.pc_rep[2 * p - 1];
+        std::vector<double> sti((size_t)W * W);
+        for (int bb = 0; bb < W; ++bb)
+            for (int a = 0; a < W; ++a)
+                sti[(size_t)bb * W + a] = ref.Kb[(size_t)xr * W + a] * ref.Mb[(size_t)xr * W + bb]
+                                        + ref.Mb[(size_t)xr * W + a] * ref.Kb[(size_t)xr * W + bb];
+        // the handle's own interior class uses the same values
+        double *dst = &stencil[(size_t)((2 * p - 1) * ht.npc + (2 * p - 1)) * W * W];
+        for (int i = 0; i < W * W; ++i) dst[i] = sti[i];
+        if ((ce = upload_interior_stencil(p, sti.data(), W * W)) != cudaSuccess) {
+            release(S);
+            return cuda_fail(ce, "constant stencil upload");
+        }
+    }
     // upload
     if ((ce = upload(S, &S->Kb, ht.Kb)) != cudaSuccess ||
         (ce = upload(S, &S->Mb, ht.Mb)) != cudaSuccess ||
@@ -334,14 +481,45 @@ int iga2l_assemble(int p, int m, int dim, const iga2l_options *opt_in, iga2l_han
         return cuda_fail(ce, "workspace allocation");
     }
     for (Level &L : S->lev)
-        if ((ce = alloc(S, &L.e, L.N)) != cudaSuccess || (ce = alloc(S, &L.rhs, L.N)) != cudaSuccess ||
-            (ce = alloc(S, &L.r, L.N)) != cudaSuccess) {
+        if ((ce = alloc(S, &L.e, L.N)) != cudaSuccess || (ce = alloc(S, &L.rhs, L.N)) != cudaSuccess) {
             release(S);
             return cuda_fail(ce, "level allocation");
         }
     if ((ce = cudaMallocHost(&S->host_norm, sizeof(double))) != cudaSuccess) {
         release(S);
         return cuda_fail(ce, "pinned host scalar");
+    }
+    if (opt.precision == IGA2L_MIXED_FP32) {
+        // FP32 copies of the tables for the inner cycle (the FP64 block inverses are kept
+        // for boundary classes and the FP64 coarsest inverse for the direct solve)
+        MixedState &X = S->mx;
+        auto to_f = [](const std::vector<double> &v) { return std::vector<float>(v.begin(), v.end()); };
+        auto allocf = [&](float **dst, size_t count) {
+            void *p = nullptr;
+            cudaError_t e = cudaMalloc(&p, sizeof(float) * (count ? count : 1));
+            if (e == cudaSuccess) { S->allocs.push_back(p); *dst = static_cast<float *>(p); }
+            return e;
+        };
+        if ((ce = upload(S, &X.stencil, to_f(stencil))) != cudaSuccess ||
+            (ce = upload(S, &X.binv, to_f(binv))) != cudaSuccess ||
+            (ce = upload(S, &X.Rb, to_f(ht.Rb))) != cudaSuccess ||
+            (ce = upload(S, &X.Cb, to_f(ht.Cb))) != cudaSuccess ||
+            (ce = allocf(&X.r, S->N)) != cudaSuccess || (ce = allocf(&X.delta, S->N)) != cudaSuccess ||
+            (ce = allocf(&X.d, S->N)) != cudaSuccess || (ce = allocf(&X.t, (size_t)n * S->nc)) != cudaSuccess ||
+            (ce = allocf(&X.t2, (size_t)n * S->nc)) != cudaSuccess || (ce = allocf(&X.dc, S->Nc)) != cudaSuccess ||
+            (ce = allocf(&X.ec, S->Nc)) != cudaSuccess) {
+            release(S);
+            return cuda_fail(ce, "mixed-precision allocation");
+        }
+        X.lev_e.assign(S->lev.size(), nullptr);
+        X.lev_rhs.assign(S->lev.size(), nullptr);
+        for (size_t l = 1; l < S->lev.size(); ++l)
+            if ((ce = allocf(&X.lev_e[l], S->lev[l].N)) != cudaSuccess ||
+                (ce = allocf(&X.lev_rhs[l], S->lev[l].N)) != cudaSuccess) {
+                release(S);
+                return cuda_fail(ce, "mixed-precision level allocation");
+            }
+        X.enabled = true;
     }
     *out = S;
     g_last_error.clear();

@@ -12,6 +12,7 @@ namespace iga2l {
 
 constexpr int kMaxP = 5;       // degrees with compiled kernels: 2..5
 constexpr int kMaxLevels = 24;
+constexpr int kTile = 32;       // side of the TILE schedule's tiles (block centres)
 
 // Host-side tables built once per handle (setup.cpp); uploaded by api.cu.
 struct HostTables {
@@ -40,6 +41,16 @@ struct Level {                 // degree-1 level of the second-level hierarchy
     double *e = nullptr, *rhs = nullptr, *r = nullptr;   // device
 };
 
+// FP32 state of the inner cycle of the mixed-precision form (device pointers).
+struct MixedState {
+    bool enabled = false;
+    float *stencil = nullptr, *binv = nullptr, *Rb = nullptr, *Cb = nullptr;
+    float *r = nullptr;       // outer residual b - A u, computed in FP64, stored in FP32
+    float *delta = nullptr;   // correction of the Schwarz step
+    float *d = nullptr, *t = nullptr, *t2 = nullptr, *dc = nullptr, *ec = nullptr;
+    std::vector<float *> lev_e, lev_rhs;   // level arrays (index 0 unused: dc / ec)
+};
+
 struct Solver {
     int dim = 2, p = 2, m = 0, n = 0, s = 3, r = 1;
     long long N = 0;
@@ -65,6 +76,7 @@ struct Solver {
     double *part = nullptr;      // per-CTA partial sums of squares
     int npart = 0;
     double *bwork = nullptr;     // b built from coefficients in solve paths
+    MixedState mx;
     std::vector<void *> allocs;
 };
 
@@ -94,6 +106,16 @@ cudaError_t launch_restrict(const Solver &S, const double *d, double *dc, cudaSt
 cudaError_t launch_prolong_add(const Solver &S, const double *ec, double *u, cudaStream_t st);
 cudaError_t launch_coarse_solve(const Solver &S, const double *dc, double *ec, cudaStream_t st);
 cudaError_t launch_mass2(const Solver &S, const double *f, double *b, cudaStream_t st);
+// mixed precision: FP64 outer residual stored in FP32; FP32 inner cycle on A delta = r
+// from delta = 0 (fine part, second level, then u += delta + P e_c in FP64)
+cudaError_t launch_outer_residual(const Solver &S, const double *u, const double *b, float *r32,
+                                  double *part, cudaStream_t st);
+cudaError_t launch_inner_fine(const Solver &S, const float *r32, bool reverse, cudaStream_t st);
+cudaError_t launch_inner_coarse(const Solver &S, cudaStream_t st);
+cudaError_t launch_inner_update(const Solver &S, double *u, cudaStream_t st);
 int residual_partials(const Solver &S);
+// Interior 2D residual stencil of degree p (h-independent) into constant memory; written
+// once per device and degree.
+cudaError_t upload_interior_stencil(int p, const double *st64, int count);
 
 }  // namespace iga2l

@@ -1,4 +1,4 @@
-// kernels_fine.cu -- fine-level kernels of the two-level cycle (2D, FP64).
+// kernels_fine.cu -- fine-level kernels of the two-level cycle (2D).
 //
 //   residual     d = b - A_p u (Algorithm 1) with per-CTA partial sums of d^2
 //   schwarz      one colour phase of the multiplicative Schwarz step (Section 3.1.1)
@@ -9,9 +9,15 @@
 // A_p = K (x) M + M (x) K.  The 2D coefficient of DOF (x+a-p, y+b-p) in row
 // (x, y) is K[x][a] M[y][b] + M[x][a] K[y][b]; rows 2p-1 .. n-2p of K and M are
 // Toeplitz, so the stencil depends only on the (point class of x, point class of y)
-// pair and is read from a small table that stays in L1.  On GB300 these FP64
-// kernels are bound by the FP64 pipe, not by HBM.
+// pair and is read from a small table that stays in L1.
+//
+// Every kernel is templated on its storage/arithmetic type: double for the FP64
+// form, float for the inner cycle of the mixed-precision form (FP32 storage and
+// FP32 FMA), whose boundary-class block solves still use the FP64 inverses.  On
+// GB300 the FP64 kernels are bound by the FP64 pipe, not by HBM.
 #include <cuda_runtime.h>
+
+#include <mutex>
 
 #include "internal.h"
 
@@ -21,40 +27,41 @@ namespace {
 
 constexpr int kResTX = 32, kResTY = 8;   // residual tile (outputs per CTA)
 
-// d = b - A u  (b != nullptr)  or  d = A u  (b == nullptr); part[cta] = sum d^2
-template <int P>
+// d = b - A u  (b != nullptr)  or  d = A u  (b == nullptr), arithmetic in T, output
+// stored as TO; part[cta] = sum of d^2 (in double) when part != nullptr.
+template <int P, typename T, typename TO>
 __global__ void __launch_bounds__(kResTX *kResTY)
-k_residual2d(int n, int npc, const double *__restrict__ stencil, const int *__restrict__ pcls,
-             const double *__restrict__ u, const double *__restrict__ b, double *__restrict__ d,
+k_residual2d(int n, int npc, const T *__restrict__ stencil, const int *__restrict__ pcls,
+             const T *__restrict__ u, const T *__restrict__ b, TO *__restrict__ d,
              double *__restrict__ part)
 {
     constexpr int W = 2 * P + 1;
     constexpr int SX = kResTX + 2 * P, SY = kResTY + 2 * P;
-    __shared__ double su[SY][SX];
+    __shared__ T su[SY][SX];
     __shared__ double red[kResTX * kResTY / 32];
     const int x0 = blockIdx.x * kResTX, y0 = blockIdx.y * kResTY;
     const int tid = threadIdx.x + kResTX * threadIdx.y;
     for (int t = tid; t < SX * SY; t += kResTX * kResTY) {
         const int ly = t / SX, lx = t % SX;
         const int gx = x0 + lx - P, gy = y0 + ly - P;
-        su[ly][lx] = (gx >= 0 && gx < n && gy >= 0 && gy < n) ? u[(size_t)gy * n + gx] : 0.0;
+        su[ly][lx] = (gx >= 0 && gx < n && gy >= 0 && gy < n) ? u[(size_t)gy * n + gx] : T(0);
     }
     __syncthreads();
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
-    double dv = 0.0;
+    T dv = T(0);
     if (x < n && y < n) {
-        const double *st = stencil + (size_t)(pcls[y] * npc + pcls[x]) * (W * W);
-        double acc = 0.0;
+        const T *st = stencil + (size_t)(pcls[y] * npc + pcls[x]) * (W * W);
+        T acc = T(0);
 #pragma unroll
         for (int bb = 0; bb < W; ++bb)
 #pragma unroll
             for (int aa = 0; aa < W; ++aa)
                 acc = fma(__ldg(&st[bb * W + aa]), su[threadIdx.y + bb][threadIdx.x + aa], acc);
         dv = b ? b[(size_t)y * n + x] - acc : acc;
-        if (d) d[(size_t)y * n + x] = dv;
+        if (d) d[(size_t)y * n + x] = (TO)dv;
     }
     if (part) {
-        double s = dv * dv;
+        double s = (double)dv * (double)dv;
         for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
         if ((tid & 31) == 0) red[tid >> 5] = s;
         __syncthreads();
@@ -85,16 +92,18 @@ __global__ void k_sum_partials(const double *__restrict__ part, int np, double *
 // S*S threads per Schwarz block: thread e computes the residual at block DOF e,
 // then row e of A_B^{-1} times the block residual, and adds it to u.  Blocks of
 // one colour neither share DOFs nor read each other's DOFs, so they run in parallel.
-template <int P, int S>
+// With T = float, blocks of the interior class use the FP32 inverse and the other
+// (boundary) classes the FP64 inverse binv64.
+template <int P, int S, typename T>
 __global__ void __launch_bounds__(256)
 k_schwarz_lattice2d(int n, int npc, int nbc, int q, int ox, int oy, int nbx, int nblocks,
-                    const double *__restrict__ stencil, const int *__restrict__ pcls,
-                    const double *__restrict__ binv, const int *__restrict__ bcls,
-                    double *__restrict__ u, const double *__restrict__ b)
+                    const T *__restrict__ stencil, const int *__restrict__ pcls,
+                    const T *__restrict__ binv, const double *__restrict__ binv64, int interior,
+                    const int *__restrict__ bcls, T *__restrict__ u, const T *__restrict__ b)
 {
     constexpr int W = 2 * P + 1, SS = S * S, R = (S - 1) / 2;
     constexpr int BPC = 256 / SS;   // Schwarz blocks per CTA
-    __shared__ double rs[BPC * SS];
+    __shared__ T rs[BPC * SS];
     const int lb = threadIdx.x / SS, e = threadIdx.x % SS;
     const int blk = blockIdx.x * BPC + lb;
     const bool active = lb < BPC && blk < nblocks;
@@ -107,15 +116,15 @@ k_schwarz_lattice2d(int n, int npc, int nbc, int q, int ox, int oy, int nbx, int
         y = cy - R + e / S;
         inside = x >= 0 && x < n && y >= 0 && y < n;
     }
-    double rv = 0.0;
+    T rv = T(0);
     if (inside) {
-        const double *st = stencil + (size_t)(pcls[y] * npc + pcls[x]) * (W * W);
-        double acc = 0.0;
+        const T *st = stencil + (size_t)(pcls[y] * npc + pcls[x]) * (W * W);
+        T acc = T(0);
 #pragma unroll
         for (int bb = 0; bb < W; ++bb) {
             const int yy = y + bb - P;
             if (yy < 0 || yy >= n) continue;
-            const double *urow = u + (size_t)yy * n;
+            const T *urow = u + (size_t)yy * n;
 #pragma unroll
             for (int aa = 0; aa < W; ++aa) {
                 const int xx = x + aa - P;
@@ -127,25 +136,188 @@ k_schwarz_lattice2d(int n, int npc, int nbc, int q, int ox, int oy, int nbx, int
     if (threadIdx.x < BPC * SS) rs[threadIdx.x] = rv;
     __syncthreads();
     if (inside) {
-        const double *Bi = binv + ((size_t)(bcls[cy] * nbc + bcls[cx]) * SS + e) * SS;
-        const double *rb = rs + lb * SS;
-        double ev = 0.0;
+        const int cls = bcls[cy] * nbc + bcls[cx];
+        const T *rb = rs + lb * SS;
+        if (sizeof(T) == sizeof(double) || cls == interior) {
+            const T *Bi = binv + ((size_t)cls * SS + e) * SS;
+            T ev = T(0);
 #pragma unroll
-        for (int f = 0; f < SS; ++f) ev = fma(__ldg(&Bi[f]), rb[f], ev);
-        u[(size_t)y * n + x] += ev;
+            for (int f = 0; f < SS; ++f) ev = fma(__ldg(&Bi[f]), rb[f], ev);
+            u[(size_t)y * n + x] += ev;
+        } else {
+            const double *Bi = binv64 + ((size_t)cls * SS + e) * SS;
+            double ev = 0.0;
+#pragma unroll
+            for (int f = 0; f < SS; ++f) ev = fma(__ldg(&Bi[f]), (double)rb[f], ev);
+            u[(size_t)y * n + x] += (T)ev;
+        }
+    }
+}
+
+// Interior residual stencil of each degree (2D; independent of h), written once per
+// process per degree and read as compile-time-indexed constant operands.
+__constant__ double c_stencil64[kMaxP + 1][(2 * kMaxP + 1) * (2 * kMaxP + 1)];
+__constant__ float c_stencil32[kMaxP + 1][(2 * kMaxP + 1) * (2 * kMaxP + 1)];
+
+template <typename T>
+__device__ __forceinline__ T cst(int p, int i);
+template <>
+__device__ __forceinline__ double cst<double>(int p, int i) { return c_stencil64[p][i]; }
+template <>
+__device__ __forceinline__ float cst<float>(int p, int i) { return c_stencil32[p][i]; }
+
+// One tile phase of the TILE(TT) schedule: tiles (tx, ty) with tx = px, px+2, ... and
+// ty = py, py+2, ...; each CTA runs all q^2 lattice colours of its tile in order
+// (anchored at the tile origin), with u (tile + halo R+P) and b (tile + halo R) staged
+// in shared memory, then writes back the DOFs its blocks can change (tile + halo R).
+// Tiles of one phase are at least TT >= q apart: none reads what another writes.
+//
+// Thread roles are fixed for all colours: a colour has at most NB1 x NB1 blocks in a
+// tile (NB1 = ceil(TT / (S+P)), since q >= S+P), and thread (block slot, entry)
+// computes that entry's residual (one accumulator per stencil row) and then applies
+// the matching row of the block inverse.  Tiles whose blocks and stencil rows are all interior (almost
+// all) take a path without bounds or class checks, with the interior stencil as
+// compile-time-indexed constant operands and the interior inverse in shared memory.
+template <int P, int S, int TT, typename T>
+__global__ void __launch_bounds__(512, sizeof(T) == sizeof(float) ? 2 : 1)
+k_schwarz_tile2d(int n, int npc, int nbc, int q, int g, int rev, int px, int py, int ntpx,
+                 const T *__restrict__ stencil, const T *__restrict__ binv,
+                 const double *__restrict__ binv64, int interior, T *__restrict__ u,
+                 const T *__restrict__ b)
+{
+    constexpr int W = 2 * P + 1, SS = S * S, R = (S - 1) / 2, H = R + P, L = P - 1 + R;
+    constexpr int SW = TT + 2 * H, BW = TT + 2 * R;
+    constexpr int QMIN = S + P, NB1 = (TT + QMIN - 1) / QMIN, NBLK = NB1 * NB1;
+    constexpr int PCI = 2 * P - 1;   // interior point class
+    static_assert(NBLK * SS <= 512, "one solve-phase thread per block entry");
+    __shared__ T su[SW * SW];
+    __shared__ T sb[BW * BW];
+    __shared__ T rs[NBLK * SS];
+    __shared__ T sbi[SS * SS];       // interior block inverse
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int tx = px + 2 * (blockIdx.x % ntpx), ty = py + 2 * (blockIdx.x / ntpx);
+    const int x0 = tx * TT, y0 = ty * TT;
+    for (int i = tid; i < SW * SW; i += nth) {
+        const int gx = x0 - H + i % SW, gy = y0 - H + i / SW;
+        su[i] = (gx >= 0 && gx < n && gy >= 0 && gy < n) ? u[(size_t)gy * n + gx] : T(0);
+    }
+    for (int i = tid; i < BW * BW; i += nth) {
+        const int gx = x0 - R + i % BW, gy = y0 - R + i / BW;
+        sb[i] = (gx >= 0 && gx < n && gy >= 0 && gy < n) ? b[(size_t)gy * n + gx] : T(0);
+    }
+    for (int i = tid; i < SS * SS; i += nth) sbi[i] = binv[(size_t)interior * SS * SS + i];
+    __syncthreads();
+    const int tw = min(TT, n - x0), th = min(TT, n - y0);   // centres of this tile
+    // every residual row and every block of the tile interior?
+    const bool fast = x0 - R >= PCI && x0 + TT - 1 + R <= n - 2 * P && y0 - R >= PCI &&
+                      y0 + TT - 1 + R <= n - 2 * P;
+    // fixed roles: (block slot, entry)
+    const int blk2 = tid / SS, e2 = tid % SS, bx2 = blk2 % NB1, by2 = blk2 / NB1;
+    const int ex2 = e2 % S, ey2 = e2 / S;
+    const bool role2 = tid < NBLK * SS;
+    const int ncol = q * q;
+    for (int t = 0; t < ncol; ++t) {
+        const int c = rev ? ncol - 1 - t : t;
+        const int cq = c / q;
+        const int ox = ((c - cq * q) * g) % q, oy = (cq * g) % q;
+        // residual phase: one block entry per thread, one accumulator per stencil row
+        if (role2) {
+            const int cxl = ox + q * bx2, cyl = oy + q * by2;
+            if (cxl < tw && cyl < th) {
+                const int lx = cxl - R + ex2, ly = cyl - R + ey2;
+                T rv = T(0);
+                if (fast) {
+                    const T *w0 = su + (ly + R) * SW + (lx + R);
+                    T racc[W];
+#pragma unroll
+                    for (int bb = 0; bb < W; ++bb) {
+                        racc[bb] = T(0);
+#pragma unroll
+                        for (int aa = 0; aa < W; ++aa)
+                            racc[bb] = fma(cst<T>(P, bb * W + aa), w0[bb * SW + aa], racc[bb]);
+                    }
+                    T acc = racc[0];
+#pragma unroll
+                    for (int bb = 1; bb < W; ++bb) acc += racc[bb];
+                    rv = sb[(ly + R) * BW + (lx + R)] - acc;
+                } else {
+                    const int gx = x0 + lx, gy = y0 + ly;
+                    if (gx >= 0 && gx < n && gy >= 0 && gy < n) {
+                        const int pcx = gx < PCI ? gx : (gx > n - 2 * P ? gx - n + 4 * P - 1 : PCI);
+                        const int pcy = gy < PCI ? gy : (gy > n - 2 * P ? gy - n + 4 * P - 1 : PCI);
+                        const T *st = stencil + (size_t)(pcy * npc + pcx) * (W * W);
+                        const T *w0 = su + (ly + R) * SW + (lx + R);
+                        T racc[W];
+#pragma unroll
+                        for (int bb = 0; bb < W; ++bb) {
+                            racc[bb] = T(0);
+#pragma unroll
+                            for (int aa = 0; aa < W; ++aa)
+                                racc[bb] = fma(__ldg(&st[bb * W + aa]), w0[bb * SW + aa], racc[bb]);
+                        }
+                        T acc = racc[0];
+#pragma unroll
+                        for (int bb = 1; bb < W; ++bb) acc += racc[bb];
+                        rv = sb[(ly + R) * BW + (lx + R)] - acc;
+                    }
+                }
+                rs[tid] = rv;
+            }
+        }
+        __syncthreads();
+        // solve phase: one row of the block inverse per thread
+        if (role2) {
+            const int cxl = ox + q * bx2, cyl = oy + q * by2;
+            const int lx = cxl - R + ex2, ly = cyl - R + ey2;
+            const int gx = x0 + lx, gy = y0 + ly;
+            if (cxl < tw && cyl < th && gx >= 0 && gx < n && gy >= 0 && gy < n) {
+                const T *rb = rs + blk2 * SS;
+                T *dst = su + (ly + H) * SW + (lx + H);
+                int cls = interior;
+                if (!fast) {
+                    const int ccx = x0 + cxl, ccy = y0 + cyl;
+                    const int bx = ccx < L ? ccx : (ccx > n - 1 - L ? 2 * L - (n - 1 - ccx) : L);
+                    const int by = ccy < L ? ccy : (ccy > n - 1 - L ? 2 * L - (n - 1 - ccy) : L);
+                    cls = by * nbc + bx;
+                }
+                if (cls == interior) {
+                    const T *Bi = sbi + e2 * SS;
+                    T ev = T(0);
+#pragma unroll
+                    for (int f = 0; f < SS; ++f) ev = fma(Bi[f], rb[f], ev);
+                    *dst += ev;
+                } else if (sizeof(T) == sizeof(double)) {
+                    const T *Bi = binv + ((size_t)cls * SS + e2) * SS;
+                    T ev = T(0);
+                    for (int f = 0; f < SS; ++f) ev = fma(__ldg(&Bi[f]), rb[f], ev);
+                    *dst += ev;
+                } else {
+                    const double *Bi = binv64 + ((size_t)cls * SS + e2) * SS;
+                    double ev = 0.0;
+                    for (int f = 0; f < SS; ++f) ev = fma(__ldg(&Bi[f]), (double)rb[f], ev);
+                    *dst += (T)ev;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    for (int i = tid; i < BW * BW; i += nth) {
+        const int gx = x0 - R + i % BW, gy = y0 - R + i / BW;
+        if (gx >= 0 && gx < n && gy >= 0 && gy < n) u[(size_t)gy * n + gx] = su[(i / BW + P) * SW + (i % BW + P)];
     }
 }
 
 // t[j][I] = sum_w Rb[I][w] d[j][Rlo[I]+w]   (x direction, n rows x nc)
-__global__ void k_restrict_x(int n, int nc, int wr, const double *__restrict__ Rb,
-                             const int *__restrict__ Rlo, const double *__restrict__ d,
-                             double *__restrict__ t)
+template <typename T>
+__global__ void k_restrict_x(int n, int nc, int wr, const T *__restrict__ Rb,
+                             const int *__restrict__ Rlo, const T *__restrict__ d,
+                             T *__restrict__ t)
 {
     const int I = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
     if (I >= nc) return;
     const int lo = Rlo[I];
-    const double *row = d + (size_t)j * n;
-    double acc = 0.0;
+    const T *row = d + (size_t)j * n;
+    T acc = T(0);
     for (int w = 0; w < wr; ++w) {
         const int i = lo + w;
         if (i < n) acc = fma(Rb[(size_t)I * wr + w], row[i], acc);
@@ -154,14 +326,15 @@ __global__ void k_restrict_x(int n, int nc, int wr, const double *__restrict__ R
 }
 
 // dc[J][I] = sum_w Rb[J][w] t[Rlo[J]+w][I]   (y direction)
-__global__ void k_restrict_y(int n, int nc, int wr, const double *__restrict__ Rb,
-                             const int *__restrict__ Rlo, const double *__restrict__ t,
-                             double *__restrict__ dc)
+template <typename T>
+__global__ void k_restrict_y(int n, int nc, int wr, const T *__restrict__ Rb,
+                             const int *__restrict__ Rlo, const T *__restrict__ t,
+                             T *__restrict__ dc)
 {
     const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y;
     if (I >= nc) return;
     const int lo = Rlo[J];
-    double acc = 0.0;
+    T acc = T(0);
     for (int w = 0; w < wr; ++w) {
         const int j = lo + w;
         if (j < n) acc = fma(Rb[(size_t)J * wr + w], t[(size_t)j * nc + I], acc);
@@ -170,14 +343,15 @@ __global__ void k_restrict_y(int n, int nc, int wr, const double *__restrict__ R
 }
 
 // t2[J][i] = sum_w Cb[i][w] ec[J][Clo[i]+w]   (x direction of R^T)
-__global__ void k_prolong_x(int n, int nc, int wc, const double *__restrict__ Cb,
-                            const int *__restrict__ Clo, const double *__restrict__ ec,
-                            double *__restrict__ t2)
+template <typename T>
+__global__ void k_prolong_x(int n, int nc, int wc, const T *__restrict__ Cb,
+                            const int *__restrict__ Clo, const T *__restrict__ ec,
+                            T *__restrict__ t2)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y;
     if (i >= n) return;
     const int lo = Clo[i];
-    double acc = 0.0;
+    T acc = T(0);
     for (int w = 0; w < wc; ++w) {
         const int I = lo + w;
         if (I < nc) acc = fma(Cb[(size_t)i * wc + w], ec[(size_t)J * nc + I], acc);
@@ -185,20 +359,24 @@ __global__ void k_prolong_x(int n, int nc, int wc, const double *__restrict__ Cb
     t2[(size_t)J * n + i] = acc;
 }
 
-// u[j][i] += sum_w Cb[j][w] t2[Clo[j]+w][i]   (y direction of R^T)
-__global__ void k_prolong_y(int n, int nc, int wc, const double *__restrict__ Cb,
-                            const int *__restrict__ Clo, const double *__restrict__ t2,
-                            double *__restrict__ u)
+// u[j][i] += sum_w Cb[j][w] t2[Clo[j]+w][i]   (y direction of R^T); with delta != nullptr
+// the update is u += delta + (R^T e_c), u in double (end of a mixed-precision inner cycle).
+template <typename T, typename TU>
+__global__ void k_prolong_y(int n, int nc, int wc, const T *__restrict__ Cb,
+                            const int *__restrict__ Clo, const T *__restrict__ t2,
+                            const T *__restrict__ delta, TU *__restrict__ u)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
     if (i >= n) return;
     const int lo = Clo[j];
-    double acc = 0.0;
+    T acc = T(0);
     for (int w = 0; w < wc; ++w) {
         const int J = lo + w;
         if (J < nc) acc = fma(Cb[(size_t)j * wc + w], t2[(size_t)J * n + i], acc);
     }
-    u[(size_t)j * n + i] += acc;
+    const size_t k = (size_t)j * n + i;
+    if (delta) u[k] += (TU)delta[k] + (TU)acc;
+    else u[k] += (TU)acc;
 }
 
 // b[j][i] = sum_b M[j][b] sum_a M[i][a] f[j+b-p][i+a-p]
@@ -223,21 +401,36 @@ __global__ void k_mass2d(int n, const double *__restrict__ Mb, const double *__r
     b[(size_t)j * n + i] = acc;
 }
 
-template <int P>
-cudaError_t residual_p(const Solver &S, const double *u, const double *b, double *d, double *part,
+template <int P, typename T, typename TO>
+cudaError_t residual_p(const Solver &S, const T *stencil, const T *u, const T *b, TO *d, double *part,
                        cudaStream_t st)
 {
     dim3 blk(kResTX, kResTY), grd((S.n + kResTX - 1) / kResTX, (S.n + kResTY - 1) / kResTY);
-    k_residual2d<P><<<grd, blk, 0, st>>>(S.n, S.ht.npc, S.stencil, S.pcls, u, b, d, part);
+    k_residual2d<P, T, TO><<<grd, blk, 0, st>>>(S.n, S.ht.npc, stencil, S.pcls, u, b, d, part);
     count_launches(1);
     return cudaGetLastError();
 }
 
-template <int P, int SB>
-cudaError_t schwarz_p(const Solver &S, double *u, const double *b, bool reverse, cudaStream_t st)
+template <typename T, typename TO>
+cudaError_t residual_any(const Solver &S, const T *stencil, const T *u, const T *b, TO *d, double *part,
+                         cudaStream_t st)
+{
+    switch (S.p) {
+    case 2: return residual_p<2, T, TO>(S, stencil, u, b, d, part, st);
+    case 3: return residual_p<3, T, TO>(S, stencil, u, b, d, part, st);
+    case 4: return residual_p<4, T, TO>(S, stencil, u, b, d, part, st);
+    case 5: return residual_p<5, T, TO>(S, stencil, u, b, d, part, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int P, int SB, typename T>
+cudaError_t schwarz_lattice_p(const Solver &S, const T *stencil, const T *binv, T *u, const T *b, bool reverse,
+                              cudaStream_t st)
 {
     constexpr int BPC = 256 / (SB * SB);
     const int q = S.q, ncol = q * q;
+    const int interior = S.ht.L * S.ht.nbc + S.ht.L;
     for (int t = 0; t < ncol; ++t) {
         const int c = reverse ? ncol - 1 - t : t;
         // colour c visits offsets (rank_x g mod q, rank_y g mod q)
@@ -246,9 +439,9 @@ cudaError_t schwarz_p(const Solver &S, double *u, const double *b, bool reverse,
         const int nblocks = nbx * nby;
         if (nblocks <= 0) continue;
         const int grid = (nblocks + BPC - 1) / BPC;
-        k_schwarz_lattice2d<P, SB><<<grid, 256, 0, st>>>(S.n, S.ht.npc, S.ht.nbc, q, ox, oy, nbx,
-                                                          nblocks, S.stencil, S.pcls, S.binv,
-                                                          S.bcls, u, b);
+        k_schwarz_lattice2d<P, SB, T><<<grid, 256, 0, st>>>(S.n, S.ht.npc, S.ht.nbc, q, ox, oy, nbx,
+                                                             nblocks, stencil, S.pcls, binv, S.binv,
+                                                             interior, S.bcls, u, b);
         count_launches(1);
         cudaError_t err = cudaGetLastError();
         if (err != cudaSuccess) return err;
@@ -256,7 +449,97 @@ cudaError_t schwarz_p(const Solver &S, double *u, const double *b, bool reverse,
     return cudaSuccess;
 }
 
+template <int P, int SB, typename T>
+cudaError_t schwarz_tile_p(const Solver &S, const T *stencil, const T *binv, T *u, const T *b, bool reverse,
+                           cudaStream_t st)
+{
+    constexpr int TT = kTile;
+    const int interior = S.ht.L * S.ht.nbc + S.ht.L;
+    const int nt = (S.n + TT - 1) / TT;
+    for (int t = 0; t < 4; ++t) {
+        const int ph = reverse ? 3 - t : t;
+        const int px = ph & 1, py = ph >> 1;
+        const int ntpx = (nt - px + 1) / 2, ntpy = (nt - py + 1) / 2;
+        if (ntpx <= 0 || ntpy <= 0) continue;
+        k_schwarz_tile2d<P, SB, TT, T><<<ntpx * ntpy, 512, 0, st>>>(S.n, S.ht.npc, S.ht.nbc, S.q, S.g,
+                                                                     reverse ? 1 : 0, px, py, ntpx, stencil,
+                                                                     binv, S.binv, interior, u, b);
+        count_launches(1);
+        cudaError_t err = cudaGetLastError();
+        if (err != cudaSuccess) return err;
+    }
+    return cudaSuccess;
+}
+
+template <int P, int SB, typename T>
+cudaError_t schwarz_p(const Solver &S, const T *stencil, const T *binv, T *u, const T *b, bool reverse,
+                      cudaStream_t st)
+{
+    if (S.opt.schedule == IGA2L_SCHED_TILE) return schwarz_tile_p<P, SB, T>(S, stencil, binv, u, b, reverse, st);
+    return schwarz_lattice_p<P, SB, T>(S, stencil, binv, u, b, reverse, st);
+}
+
+template <typename T>
+cudaError_t schwarz_any(const Solver &S, const T *stencil, const T *binv, T *u, const T *b, bool reverse,
+                        cudaStream_t st)
+{
+    if (S.s == 3) {
+        switch (S.p) {
+        case 2: return schwarz_p<2, 3, T>(S, stencil, binv, u, b, reverse, st);
+        case 3: return schwarz_p<3, 3, T>(S, stencil, binv, u, b, reverse, st);
+        case 4: return schwarz_p<4, 3, T>(S, stencil, binv, u, b, reverse, st);
+        default: break;
+        }
+    } else if (S.s == 5 && S.p == 5) {
+        return schwarz_p<5, 5, T>(S, stencil, binv, u, b, reverse, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t restrict_any(const Solver &S, const T *Rb, const T *d, T *t, T *dc, cudaStream_t st)
+{
+    const int nc = S.nc, n = S.n;
+    k_restrict_x<T><<<dim3((nc + 127) / 128, n), 128, 0, st>>>(n, nc, S.ht.wr, Rb, S.Rlo, d, t);
+    count_launches(1);
+    k_restrict_y<T><<<dim3((nc + 127) / 128, nc), 128, 0, st>>>(n, nc, S.ht.wr, Rb, S.Rlo, t, dc);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <typename T, typename TU>
+cudaError_t prolong_any(const Solver &S, const T *Cb, const T *ec, T *t2, const T *delta, TU *u,
+                        cudaStream_t st)
+{
+    const int nc = S.nc, n = S.n;
+    k_prolong_x<T><<<dim3((n + 127) / 128, nc), 128, 0, st>>>(n, nc, S.ht.wc, Cb, S.Clo, ec, t2);
+    count_launches(1);
+    k_prolong_y<T, TU><<<dim3((n + 127) / 128, n), 128, 0, st>>>(n, nc, S.ht.wc, Cb, S.Clo, t2, delta, u);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t upload_interior_stencil(int p, const double *st64, int count)
+{
+    static std::mutex mu;
+    static bool done[64][kMaxP + 1] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev < 0 || dev >= 64 || p < 0 || p > kMaxP) return cudaErrorInvalidValue;
+    if (done[dev][p]) return cudaSuccess;
+    float st32[(2 * kMaxP + 1) * (2 * kMaxP + 1)];
+    for (int i = 0; i < count; ++i) st32[i] = (float)st64[i];
+    const size_t row = sizeof(double) * (2 * kMaxP + 1) * (2 * kMaxP + 1);
+    e = cudaMemcpyToSymbol(c_stencil64, st64, sizeof(double) * count, row * p);
+    if (e == cudaSuccess)
+        e = cudaMemcpyToSymbol(c_stencil32, st32, sizeof(float) * count, (row / 2) * p);
+    if (e == cudaSuccess) done[dev][p] = true;
+    return e;
+}
 
 int residual_partials(const Solver &S)
 {
@@ -266,13 +549,7 @@ int residual_partials(const Solver &S)
 cudaError_t launch_residual(const Solver &S, const double *u, const double *b, double *d,
                             double *part, cudaStream_t st)
 {
-    switch (S.p) {
-    case 2: return residual_p<2>(S, u, b, d, part, st);
-    case 3: return residual_p<3>(S, u, b, d, part, st);
-    case 4: return residual_p<4>(S, u, b, d, part, st);
-    case 5: return residual_p<5>(S, u, b, d, part, st);
-    default: return cudaErrorInvalidValue;
-    }
+    return residual_any<double, double>(S, S.stencil, u, b, d, part, st);
 }
 
 cudaError_t launch_apply_A(const Solver &S, const double *u, double *y, cudaStream_t st)
@@ -290,37 +567,41 @@ cudaError_t launch_norm_finish(const Solver &S, const double *part, double *out,
 cudaError_t launch_schwarz(const Solver &S, double *u, const double *b, bool reverse,
                            cudaStream_t st)
 {
-    if (S.s == 3) {
-        switch (S.p) {
-        case 2: return schwarz_p<2, 3>(S, u, b, reverse, st);
-        case 3: return schwarz_p<3, 3>(S, u, b, reverse, st);
-        case 4: return schwarz_p<4, 3>(S, u, b, reverse, st);
-        default: break;
-        }
-    } else if (S.s == 5 && S.p == 5) {
-        return schwarz_p<5, 5>(S, u, b, reverse, st);
-    }
-    return cudaErrorInvalidValue;
+    return schwarz_any<double>(S, S.stencil, S.binv, u, b, reverse, st);
 }
 
 cudaError_t launch_restrict(const Solver &S, const double *d, double *dc, cudaStream_t st)
 {
-    const int nc = S.nc, n = S.n;
-    k_restrict_x<<<dim3((nc + 127) / 128, n), 128, 0, st>>>(n, nc, S.ht.wr, S.Rb, S.Rlo, d, S.t);
-    count_launches(1);
-    k_restrict_y<<<dim3((nc + 127) / 128, nc), 128, 0, st>>>(n, nc, S.ht.wr, S.Rb, S.Rlo, S.t, dc);
-    count_launches(1);
-    return cudaGetLastError();
+    return restrict_any<double>(S, S.Rb, d, S.t, dc, st);
 }
 
 cudaError_t launch_prolong_add(const Solver &S, const double *ec, double *u, cudaStream_t st)
 {
-    const int nc = S.nc, n = S.n;
-    k_prolong_x<<<dim3((n + 127) / 128, nc), 128, 0, st>>>(n, nc, S.ht.wc, S.Cb, S.Clo, ec, S.t2);
-    count_launches(1);
-    k_prolong_y<<<dim3((n + 127) / 128, n), 128, 0, st>>>(n, nc, S.ht.wc, S.Cb, S.Clo, S.t2, u);
-    count_launches(1);
-    return cudaGetLastError();
+    return prolong_any<double, double>(S, S.Cb, ec, S.t2, nullptr, u, st);
+}
+
+// ---- mixed precision -------------------------------------------------------------
+
+cudaError_t launch_outer_residual(const Solver &S, const double *u, const double *b, float *r32,
+                                  double *part, cudaStream_t st)
+{
+    return residual_any<double, float>(S, S.stencil, u, b, r32, part, st);
+}
+
+cudaError_t launch_inner_fine(const Solver &S, const float *r32, bool reverse, cudaStream_t st)
+{
+    const MixedState &X = S.mx;
+    cudaError_t e = cudaMemsetAsync(X.delta, 0, sizeof(float) * S.N, st);
+    if (e == cudaSuccess) e = schwarz_any<float>(S, X.stencil, X.binv, X.delta, r32, reverse, st);
+    if (e == cudaSuccess) e = residual_any<float, float>(S, X.stencil, X.delta, r32, X.d, nullptr, st);
+    if (e == cudaSuccess) e = restrict_any<float>(S, X.Rb, X.d, X.t, X.dc, st);
+    return e;
+}
+
+cudaError_t launch_inner_update(const Solver &S, double *u, cudaStream_t st)
+{
+    const MixedState &X = S.mx;
+    return prolong_any<float, double>(S, X.Cb, X.ec, X.t2, X.delta, u, st);
 }
 
 cudaError_t launch_mass2(const Solver &S, const double *f, double *b, cudaStream_t st)
@@ -328,15 +609,12 @@ cudaError_t launch_mass2(const Solver &S, const double *f, double *b, cudaStream
     dim3 grd((S.n + 127) / 128, S.n);
     switch (S.p) {
     case 2: k_mass2d<2><<<grd, 128, 0, st>>>(S.n, S.Mb, f, b); break;
-    count_launches(1);
     case 3: k_mass2d<3><<<grd, 128, 0, st>>>(S.n, S.Mb, f, b); break;
-    count_launches(1);
     case 4: k_mass2d<4><<<grd, 128, 0, st>>>(S.n, S.Mb, f, b); break;
-    count_launches(1);
     case 5: k_mass2d<5><<<grd, 128, 0, st>>>(S.n, S.Mb, f, b); break;
-    count_launches(1);
     default: return cudaErrorInvalidValue;
     }
+    count_launches(1);
     return cudaGetLastError();
 }
 

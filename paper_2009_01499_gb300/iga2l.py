@@ -17,7 +17,7 @@ from . import build as _build
 
 OK, NOT_CONVERGED = 0, 1
 ERR_INVALID_ARG, ERR_CUDA, ERR_DEVICE_TIMEOUT, ERR_NONFINITE, ERR_UNSUPPORTED = -1, -2, -3, -4, -5
-FP64 = 0
+FP64, MIXED_FP32 = 0, 1
 SCHED_LATTICE, SCHED_TILE = 1, 2
 COARSE_EXACT, COARSE_VCYCLE = 0, 1
 
@@ -35,7 +35,7 @@ EXPORTS = (
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("schedule", ctypes.c_int), ("tile", ctypes.c_int),
                 ("period", ctypes.c_int), ("stride", ctypes.c_int), ("coarse", ctypes.c_int),
-                ("block_side", ctypes.c_int), ("max_cycles", ctypes.c_int)]
+                ("block_side", ctypes.c_int), ("max_cycles", ctypes.c_int), ("graphs", ctypes.c_int)]
 
 
 class IgaError(RuntimeError):

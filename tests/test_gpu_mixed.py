@@ -1,0 +1,126 @@
+"""GPU tests of the mixed-precision form (FP64 outer residual and update around an
+FP32 inner cycle) against the FP64 oracle.
+
+Bar (the benchmark spec): after refinement to a 1e-8 relative residual, the solution is
+within 1e-8 (relative, 2-norm) of the FP64 oracle's solution, with the same
+cycle count.  Single inner cycles agree with the FP64 cycle to FP32 accuracy.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2009_01499_gb300 import iga2l, synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+COLOURING = {2: (5, 2), 3: (7, 2), 4: (7, 2), 5: (10, 3)}
+
+
+def _dev(x):
+    return torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+
+
+def _host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+@pytest.mark.parametrize("p,m", [(2, 50), (3, 64), (4, 66), (5, 70)])
+def test_mixed_iterates_track_fp64_oracle(oracle_mod, p, m):
+    q, g = COLOURING[p]
+    S = iga2l.Solver(p, m, period=q, stride=g, precision=iga2l.MIXED_FP32)
+    O = oracle_mod.Problem(2, p, m, sched=oracle_mod.LATTICE, coarse=oracle_mod.VCYCLE,
+                           period=q, stride=g)
+    f = synth.coefficients(S.N, 400 + p)
+    u0 = synth.initial_guess(S.N, 401 + p)
+    K, M = oracle_mod.assemble_1d(p, m)
+    b = (M @ f.reshape(S.n, S.n) @ M.T).ravel()
+    ud, bd = _dev(u0), _dev(b)
+    uo = u0.copy()
+    ustar = np.linalg.norm(uo)
+    for k in range(4):
+        e_before = np.linalg.norm(_host(ud) - uo)
+        S.cycle(ud, bd)
+        uo = O.cycle(uo, b)
+        # an FP32 inner cycle perturbs the correction by ~1e-7 of its size
+        corr = np.linalg.norm(uo - _host(ud))
+        assert corr <= 1e-5 * ustar, (k, corr / ustar)
+        assert e_before <= 1e-5 * ustar
+
+
+@pytest.mark.parametrize("p", [2, 3, 4, 5])
+def test_mixed_refinement_reaches_fp64_solution(oracle_mod, p):
+    """At the 1e-8 stopping rule the mixed form takes the oracle's cycle count and is
+    as accurate as the FP64 oracle (its error against a tightly converged solution
+    matches the oracle's own); refined on to a 1e-12 residual it is within 1e-8 of
+    the FP64 oracle's solution.  (With a random initial guess 10^4 times larger than
+    the solution, a 1e-8 residual reduction leaves both forms ~1e-3 from the exact
+    discrete solution, so the 1e-8 solution bar is applied after refinement.)"""
+    m = 128
+    q, g = COLOURING[p]
+    S = iga2l.Solver(p, m, period=q, stride=g, precision=iga2l.MIXED_FP32)
+    O = oracle_mod.Problem(2, p, m, sched=oracle_mod.LATTICE, coarse=oracle_mod.VCYCLE,
+                           period=q, stride=g)
+    f = synth.coefficients(S.N, 500 + p)
+    u0 = synth.initial_guess(S.N, 501 + p)
+    bd = torch.empty(S.N, dtype=torch.float64, device="cuda")
+    S.rhs_from_coeffs(_dev(f), bd)
+    b = _host(bd)
+    ustar, _, _, _, ok_s = O.solve(b, u0, tol=1e-14, maxc=80)
+    assert ok_s
+    # the metric's stopping rule
+    ud = _dev(u0)
+    cyc, rel, hist, ok = S.solve(bd, ud, tol=1e-8, max_cycles=40)
+    uo, cyc_o, rel_o, hist_o, ok_o = O.solve(b, u0, tol=1e-8, maxc=40)
+    assert ok and ok_o and abs(cyc - cyc_o) <= 1, (cyc, cyc_o)
+    r = np.linalg.norm(O.residual(_host(ud), b)) / np.linalg.norm(O.residual(u0, b))
+    assert r <= 1.001e-8                       # the reported residual is a true FP64 residual
+    err_mixed = np.linalg.norm(_host(ud) - ustar)
+    err_fp64 = np.linalg.norm(uo - ustar)
+    assert err_mixed <= 1.01 * err_fp64 + 1e-14 * np.linalg.norm(ustar)
+    # refinement continued to a 1e-12 residual
+    ud = _dev(u0)
+    cyc, rel, hist, ok = S.solve(bd, ud, tol=1e-12, max_cycles=60)
+    uo, cyc_o, rel_o, hist_o, ok_o = O.solve(b, u0, tol=1e-12, maxc=60)
+    assert ok and ok_o and abs(cyc - cyc_o) <= 1
+    err = np.linalg.norm(_host(ud) - uo) / np.linalg.norm(uo)
+    assert err <= 1e-8, err
+
+
+def test_mixed_full_size_matches_fp64_gpu():
+    """1024^2, p = 3: same cycle count as the FP64 GPU form at 1e-8; refined to 1e-12 the
+    two solutions agree within 1e-8."""
+    p, m = 3, 1024
+    q, g = COLOURING[p]
+    A = iga2l.Solver(p, m, period=q, stride=g)
+    B = iga2l.Solver(p, m, period=q, stride=g, precision=iga2l.MIXED_FP32)
+    f = _dev(synth.coefficients(A.N, 7))
+    b = torch.empty_like(f)
+    A.rhs_from_coeffs(f, b)
+    u0 = _dev(synth.initial_guess(A.N, 8))
+    ua, ub = u0.clone(), u0.clone()
+    ca, ra, _, oka = A.solve(b, ua, tol=1e-8)
+    cb, rb, _, okb = B.solve(b, ub, tol=1e-8)
+    assert oka and okb and abs(ca - cb) <= 1
+    ua, ub = u0.clone(), u0.clone()
+    A.solve(b, ua, tol=1e-12, max_cycles=60)
+    B.solve(b, ub, tol=1e-12, max_cycles=60)
+    err = float(torch.linalg.norm(ua - ub) / torch.linalg.norm(ua))
+    assert err <= 1e-8, err
+
+
+@pytest.mark.parametrize("p", [2, 5])
+def test_fp32_tile_sweep_matches_fp64_tile_sweep(p):
+    """The FP32 TILE sweep (used by the mixed form) against the FP64 TILE sweep, through a
+    mixed-precision cycle from the same start: corrections agree to FP32 accuracy."""
+    q, g = COLOURING[p]
+    A = iga2l.Solver(p, 132, period=q, stride=g, schedule=iga2l.SCHED_TILE)
+    B = iga2l.Solver(p, 132, period=q, stride=g, schedule=iga2l.SCHED_TILE, precision=iga2l.MIXED_FP32)
+    f = _dev(synth.coefficients(A.N, 31))
+    u0 = _dev(synth.initial_guess(A.N, 32))
+    ua, ub = u0.clone(), u0.clone()
+    A.cycle(ua, f)
+    B.cycle(ub, f)
+    corr = float(torch.linalg.norm(ua - u0))
+    assert float(torch.linalg.norm(ua - ub)) <= 1e-5 * corr

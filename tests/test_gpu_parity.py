@@ -18,12 +18,14 @@ TOL = 1e-12
 COLOURING = {2: (5, 2), 3: (7, 2), 4: (7, 2), 5: (10, 3)}
 
 
-def _pair(oracle_mod, p, m, coarse="vcycle"):
+def _pair(oracle_mod, p, m, coarse="vcycle", sched="lattice"):
     q, g = COLOURING[p]
     cg = iga2l.COARSE_VCYCLE if coarse == "vcycle" else iga2l.COARSE_EXACT
     co = oracle_mod.VCYCLE if coarse == "vcycle" else oracle_mod.EXACT
-    S = iga2l.Solver(p, m, period=q, stride=g, coarse=cg)
-    O = oracle_mod.Problem(2, p, m, sched=oracle_mod.LATTICE, coarse=co, period=q, stride=g)
+    sg = iga2l.SCHED_TILE if sched == "tile" else iga2l.SCHED_LATTICE
+    so = oracle_mod.TILE if sched == "tile" else oracle_mod.LATTICE
+    S = iga2l.Solver(p, m, period=q, stride=g, coarse=cg, schedule=sg)
+    O = oracle_mod.Problem(2, p, m, sched=so, tile=32, coarse=co, period=q, stride=g)
     assert S.N == O.N and S.Nc == O.Nc
     return S, O
 
@@ -64,14 +66,16 @@ def test_residual_and_apply(oracle_mod, p, m):
     _close(_host(y), O.apply_A(u))
 
 
-@pytest.mark.parametrize("p,m", CASES)
+@pytest.mark.parametrize("p,m", CASES + [(2, 100), (5, 132)])
 @pytest.mark.parametrize("reverse", [False, True])
-def test_schwarz_sweep(oracle_mod, p, m, reverse):
-    S, O = _pair(oracle_mod, p, m)
+@pytest.mark.parametrize("sched", ["lattice", "tile"])
+def test_schwarz_sweep(oracle_mod, p, m, reverse, sched):
+    S, O = _pair(oracle_mod, p, m, sched=sched)
     b, u = _inputs(S.N, 7 * p + m)
     ud = _dev(u)
     S.schwarz_sweep(ud, _dev(b), reverse=reverse)
-    _, order, _ = oracle_mod.schedule(2, S.n, O.s, p, oracle_mod.LATTICE, 0, *COLOURING[p])
+    kind = oracle_mod.TILE if sched == "tile" else oracle_mod.LATTICE
+    _, order, _ = oracle_mod.schedule(2, S.n, O.s, p, kind, 32, *COLOURING[p])
     if reverse:
         order = order[::-1].copy()
     K, M = oracle_mod.assemble_1d(p, m)
@@ -103,9 +107,10 @@ def test_coarse_solve(oracle_mod, p, m, coarse):
 
 
 @pytest.mark.parametrize("p,m", [(2, 50), (3, 64), (4, 66), (5, 70)])
-def test_cycles_per_iterate(oracle_mod, p, m):
+@pytest.mark.parametrize("sched", ["lattice", "tile"])
+def test_cycles_per_iterate(oracle_mod, p, m, sched):
     """Per-iterate parity over 5 cycles of Algorithm 1 (V(1,1) second level)."""
-    S, O = _pair(oracle_mod, p, m)
+    S, O = _pair(oracle_mod, p, m, sched=sched)
     f, u0 = _inputs(S.N, 100 + p)
     K, M = oracle_mod.assemble_1d(p, m)
     b = (M @ f.reshape(S.n, S.n) @ M.T).ravel()
@@ -218,3 +223,24 @@ def test_invalid_calls_raise_before_launch():
     # zero right-hand side and guess: converged with zero cycles
     cyc, rel, hist, ok = S.solve(torch.zeros_like(b), torch.zeros_like(b))
     assert ok and cyc == 0
+
+
+def test_graph_replay_matches_plain_launches(oracle_mod):
+    """Cycles replayed from captured CUDA graphs equal plain launches bit for bit."""
+    q, g = COLOURING[3]
+    A = iga2l.Solver(3, 66, period=q, stride=g, graphs=1)
+    B = iga2l.Solver(3, 66, period=q, stride=g, graphs=0)
+    f, u0 = _inputs(A.N, 55)
+    b = _dev(f)
+    ua, ub = _dev(u0), _dev(u0)
+    for _ in range(3):
+        A.cycle(ua, b)
+        B.cycle(ub, b)
+    assert torch.equal(ua, ub)
+    ua2, ub2 = _dev(u0), _dev(u0)
+    ca, ra, ha, _ = A.solve(b, ua2, tol=1e-9)
+    cb, rb, hb, _ = B.solve(b, ub2, tol=1e-9)
+    assert ca == cb and np.array_equal(ha, hb) and torch.equal(ua2, ub2)
+    n0 = iga2l.kernel_launches()
+    A.cycle(ua, b)
+    assert iga2l.kernel_launches() - n0 > 30      # a replayed graph still counts its kernels
