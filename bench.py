@@ -135,12 +135,13 @@ def barrier(ws):
         dist.barrier()
 
 
-def allmax(x, ws, device):
+def allmax(x, ws, device=None):
+    """Maximum of a per-rank scalar over all ranks (the step time the job is charged)."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device=device)
+    t = torch.tensor([x], dtype=torch.float64, device=device if device is not None else "cpu")
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 

@@ -74,7 +74,8 @@ typedef struct {
  * graphs on. */
 void iga2l_default_options(iga2l_options *opt);
 
-/* Builds the solver for degree p (2..5), m elements per axis, dimension dim (2).
+/* Builds the solver for degree p (2..5 in 2D, 2..4 in 3D), m elements per axis,
+ * dimension dim (2 or 3; 3D uses the LATTICE schedule).
  * Host work: 1D B-spline Galerkin tables (Section 2.1), the Schwarz block
  * inverses of every block class (Section 3.1.1), the lumped L2-projection
  * restriction composed with h->2h (Sections 3.1.2, 3.3), the degree-1
@@ -142,8 +143,8 @@ int iga2l_solve(iga2l_handle h, const double *b, double tol, int max_cycles, dou
 int iga2l_adjoint_solve(iga2l_handle h, const double *g, double tol, int max_cycles,
                         double *lambda, int *cycles, double *relres, void *stream);
 
-/* b = (M(x)M) f: load vector of f = sum_i f_i phi_i given by its B-spline
- * coefficients (b_p = (f, phi_i), Section 2). */
+/* b = (M(x)M) f (3D: M(x)M(x)M): load vector of f = sum_i f_i phi_i given by its
+ * B-spline coefficients (b_p = (f, phi_i), Section 2). */
 int iga2l_rhs_from_coeffs(iga2l_handle h, const double *f, double *b, void *stream);
 
 /* Host copies of the handle's 1D band tables, rows of width 2p+1 (entry a of

@@ -321,14 +321,17 @@ int iga2l_assemble(int p, int m, int dim, const iga2l_options *opt_in, iga2l_han
     iga2l_options opt;
     if (opt_in) opt = *opt_in; else iga2l_default_options(&opt);
     if (opt.max_cycles <= 0) opt.max_cycles = 100;
-    if (dim != 2) return fail(IGA2L_ERR_UNSUPPORTED, "only dim = 2 is compiled");
+    if (dim != 2 && dim != 3) return fail(IGA2L_ERR_INVALID_ARG, "dim must be 2 or 3");
     if (p < 2 || p > kMaxP) return fail(IGA2L_ERR_INVALID_ARG, "p must be in 2..5");
+    if (dim == 3 && p > 4) return fail(IGA2L_ERR_UNSUPPORTED, "3D kernels are compiled for p = 2..4");
     if (m < 4 * p + 4 || (m % 2) != 0)
         return fail(IGA2L_ERR_INVALID_ARG, "m must be even and >= 4p+4 (aggressive 2h coarsening)");
     if (opt.precision != IGA2L_FP64 && opt.precision != IGA2L_MIXED_FP32)
         return fail(IGA2L_ERR_UNSUPPORTED, "precision not available");
     if (opt.schedule != IGA2L_SCHED_LATTICE && opt.schedule != IGA2L_SCHED_TILE)
         return fail(IGA2L_ERR_UNSUPPORTED, "schedule not available");
+    if (dim == 3 && opt.schedule != IGA2L_SCHED_LATTICE)
+        return fail(IGA2L_ERR_UNSUPPORTED, "3D uses the LATTICE schedule");
     if (opt.schedule == IGA2L_SCHED_TILE) {
         if (opt.tile == 0) opt.tile = kTile;
         if (opt.tile != kTile) return fail(IGA2L_ERR_UNSUPPORTED, "only TILE side 32 is compiled");
@@ -350,7 +353,7 @@ int iga2l_assemble(int p, int m, int dim, const iga2l_options *opt_in, iga2l_han
     if (!S) return fail(IGA2L_ERR_CUDA, "host allocation failed");
     S->dim = dim; S->p = p; S->m = m; S->s = s; S->r = (s - 1) / 2;
     S->n = m + p - 2;
-    S->N = (long long)S->n * S->n;
+    S->N = (long long)S->n * S->n * (dim == 3 ? S->n : 1);
     S->opt = opt;
     S->q = q; S->g = g % q; S->tile = opt.tile;
     cudaError_t ce = cudaGetDevice(&S->device);
@@ -362,9 +365,9 @@ int iga2l_assemble(int p, int m, int dim, const iga2l_options *opt_in, iga2l_han
     const HostTables &ht = S->ht;
     const int n = S->n, W = 2 * p + 1, SS = s * s;
 
-    // residual stencils per (row-class of y, row-class of x)
-    std::vector<double> stencil((size_t)ht.npc * ht.npc * W * W);
-    for (int cy = 0; cy < ht.npc; ++cy)
+    // residual stencils per (row-class of y, row-class of x) (2D kernels)
+    std::vector<double> stencil(dim == 2 ? (size_t)ht.npc * ht.npc * W * W : 1, 0.0);
+    for (int cy = 0; dim == 2 && cy < ht.npc; ++cy)
         for (int cx = 0; cx < ht.npc; ++cx) {
             const int xr = ht.pc_rep[cx], yr = ht.pc_rep[cy];
             double *st = &stencil[(size_t)(cy * ht.npc + cx) * W * W];
@@ -378,41 +381,49 @@ int iga2l_assemble(int p, int m, int dim, const iga2l_options *opt_in, iga2l_han
         pcls[x] = x < 2 * p - 1 ? x : (x > n - 2 * p ? x - n + 4 * p - 1 : 2 * p - 1);
         bcls[x] = x < ht.L ? x : (x > n - 1 - ht.L ? 2 * ht.L - (n - 1 - x) : ht.L);
     }
-    // Schwarz block inverses per (block class of cy, block class of cx); block DOF
-    // e = ex + s*ey is (c_x - r + ex, c_y - r + ey); DOFs outside the grid get zero rows
-    std::vector<double> binv((size_t)ht.nbc * ht.nbc * SS * SS, 0.0);
-    for (int by = 0; by < ht.nbc; ++by)
-        for (int bx = 0; bx < ht.nbc; ++bx) {
-            const int cx = ht.bc_rep[bx], cy = ht.bc_rep[by];
-            std::vector<double> A((size_t)SS * SS, 0.0);
-            std::vector<int> valid(SS);
-            for (int a = 0; a < SS; ++a) {
-                const int xa = cx - S->r + a % s, ya = cy - S->r + a / s;
-                valid[a] = xa >= 0 && xa < n && ya >= 0 && ya < n;
-            }
-            for (int a = 0; a < SS; ++a)
-                for (int c = 0; c < SS; ++c) {
-                    if (!valid[a] || !valid[c]) { A[(size_t)a * SS + c] = (a == c) ? 1.0 : 0.0; continue; }
-                    const int xa = cx - S->r + a % s, ya = cy - S->r + a / s;
-                    const int xc = cx - S->r + c % s, yc = cy - S->r + c / s;
-                    A[(size_t)a * SS + c] = band(ht.Kb, p, xa, xc) * band(ht.Mb, p, ya, yc)
-                                          + band(ht.Mb, p, xa, xc) * band(ht.Kb, p, ya, yc);
-                }
-            if (!cholesky_inverse(SS, A)) { release(S); return fail(IGA2L_ERR_INVALID_ARG, "block matrix not SPD"); }
-            double *dst = &binv[(size_t)(by * ht.nbc + bx) * SS * SS];
-            for (int a = 0; a < SS; ++a)
-                for (int c = 0; c < SS; ++c)
-                    dst[(size_t)a * SS + c] = (valid[a] && valid[c]) ? A[(size_t)a * SS + c] : 0.0;
+    // Schwarz block inverses per block class (cz,) cy, cx; block DOF e = ex + s*(ey + s*ez) is
+    // (c_x - r + ex, c_y - r + ey, c_z - r + ez); DOFs outside the grid get zero rows
+    const int SD = dim == 3 ? s * s * s : s * s;
+    const int ncls = dim == 3 ? ht.nbc * ht.nbc * ht.nbc : ht.nbc * ht.nbc;
+    std::vector<double> binv((size_t)ncls * SD * SD, 0.0);
+    for (int cls = 0; cls < ncls; ++cls) {
+        const int bx = cls % ht.nbc, by = (cls / ht.nbc) % ht.nbc, bz = cls / (ht.nbc * ht.nbc);
+        const int cx = ht.bc_rep[bx], cy = ht.bc_rep[by], cz = dim == 3 ? ht.bc_rep[bz] : 0;
+        std::vector<double> A((size_t)SD * SD, 0.0);
+        std::vector<int> valid(SD), X(SD), Y(SD), Z(SD);
+        for (int a = 0; a < SD; ++a) {
+            X[a] = cx - S->r + a % s;
+            Y[a] = cy - S->r + (a / s) % s;
+            Z[a] = dim == 3 ? cz - S->r + a / (s * s) : 0;
+            valid[a] = X[a] >= 0 && X[a] < n && Y[a] >= 0 && Y[a] < n && (dim == 2 || (Z[a] >= 0 && Z[a] < n));
         }
+        for (int a = 0; a < SD; ++a)
+            for (int c = 0; c < SD; ++c) {
+                if (!valid[a] || !valid[c]) { A[(size_t)a * SD + c] = (a == c) ? 1.0 : 0.0; continue; }
+                const double kx = band(ht.Kb, p, X[a], X[c]), mx = band(ht.Mb, p, X[a], X[c]);
+                const double ky = band(ht.Kb, p, Y[a], Y[c]), my = band(ht.Mb, p, Y[a], Y[c]);
+                if (dim == 2) {
+                    A[(size_t)a * SD + c] = kx * my + mx * ky;
+                } else {
+                    const double kz = band(ht.Kb, p, Z[a], Z[c]), mz = band(ht.Mb, p, Z[a], Z[c]);
+                    A[(size_t)a * SD + c] = kx * my * mz + mx * ky * mz + mx * my * kz;
+                }
+            }
+        if (!cholesky_inverse(SD, A)) { release(S); return fail(IGA2L_ERR_INVALID_ARG, "block matrix not SPD"); }
+        double *dst = &binv[(size_t)cls * SD * SD];
+        for (int a = 0; a < SD; ++a)
+            for (int c = 0; c < SD; ++c)
+                dst[(size_t)a * SD + c] = (valid[a] && valid[c]) ? A[(size_t)a * SD + c] : 0.0;
+    }
 
     // second-level hierarchy (degree 1 on the 2h mesh, then 4h, ...)
     S->nc = ht.nc;
-    S->Nc = (long long)ht.nc * ht.nc;
+    S->Nc = (long long)ht.nc * ht.nc * (dim == 3 ? ht.nc : 1);
     for (int ml = m / 2;;) {
         Level L;
         L.m = ml;
         L.n = ml - 1;
-        L.N = (long long)L.n * L.n;
+        L.N = (long long)L.n * L.n * (dim == 3 ? L.n : 1);
         L.k[0] = -(double)ml; L.k[1] = 2.0 * ml; L.k[2] = -(double)ml;
         L.mm[0] = 1.0 / (6.0 * ml); L.mm[1] = 4.0 / (6.0 * ml); L.mm[2] = 1.0 / (6.0 * ml);
         S->lev.push_back(L);
@@ -424,20 +435,30 @@ int iga2l_assemble(int p, int m, int dim, const iga2l_options *opt_in, iga2l_han
     S->ndirect = (int)D.N;
     if (S->ndirect > 2048) { release(S); return fail(IGA2L_ERR_UNSUPPORTED, "exact second-level solve too large"); }
     std::vector<double> Ad((size_t)S->ndirect * S->ndirect, 0.0);
-    for (int y = 0; y < D.n; ++y)
-        for (int x = 0; x < D.n; ++x)
-            for (int dy = -1; dy <= 1; ++dy)
-                for (int dx = -1; dx <= 1; ++dx) {
-                    const int x2 = x + dx, y2 = y + dy;
-                    if (x2 < 0 || x2 >= D.n || y2 < 0 || y2 >= D.n) continue;
-                    Ad[(size_t)(y * D.n + x) * S->ndirect + (y2 * D.n + x2)] =
-                        D.k[dx + 1] * D.mm[dy + 1] + D.mm[dx + 1] * D.k[dy + 1];
-                }
+    {
+        const int nd = D.n, nz = dim == 3 ? nd : 1;
+        for (int z = 0; z < nz; ++z)
+            for (int y = 0; y < nd; ++y)
+                for (int x = 0; x < nd; ++x)
+                    for (int dz = (dim == 3 ? -1 : 0); dz <= (dim == 3 ? 1 : 0); ++dz)
+                        for (int dy = -1; dy <= 1; ++dy)
+                            for (int dx = -1; dx <= 1; ++dx) {
+                                const int x2 = x + dx, y2 = y + dy, z2 = z + dz;
+                                if (x2 < 0 || x2 >= nd || y2 < 0 || y2 >= nd || z2 < 0 || z2 >= nz) continue;
+                                const size_t row = ((size_t)z * nd + y) * nd + x, col = ((size_t)z2 * nd + y2) * nd + x2;
+                                double v;
+                                if (dim == 2) v = D.k[dx + 1] * D.mm[dy + 1] + D.mm[dx + 1] * D.k[dy + 1];
+                                else
+                                    v = D.k[dx + 1] * D.mm[dy + 1] * D.mm[dz + 1] + D.mm[dx + 1] * D.k[dy + 1] * D.mm[dz + 1] +
+                                        D.mm[dx + 1] * D.mm[dy + 1] * D.k[dz + 1];
+                                Ad[row * S->ndirect + col] = v;
+                            }
+    }
     if (!cholesky_inverse(S->ndirect, Ad)) { release(S); return fail(IGA2L_ERR_INVALID_ARG, "coarsest matrix not SPD"); }
 
     // the interior stencil of degree p from a reference mesh, so that every handle of
     // degree p writes identical constant-memory values (2D stencils do not depend on h)
-    {
+    if (dim == 2) {
         HostTables ref;
         std::string rerr;
         const int mref = 8 * p + 16;
@@ -473,15 +494,21 @@ int iga2l_assemble(int p, int m, int dim, const iga2l_options *opt_in, iga2l_han
     }
     S->npart = residual_partials(*S);
     if ((ce = alloc(S, &S->d, S->N)) != cudaSuccess || (ce = alloc(S, &S->bwork, S->N)) != cudaSuccess ||
-        (ce = alloc(S, &S->t, (size_t)n * S->nc)) != cudaSuccess ||
-        (ce = alloc(S, &S->t2, (size_t)n * S->nc)) != cudaSuccess ||
+        (ce = alloc(S, &S->t, dim == 3 ? (size_t)n * n * S->nc : (size_t)n * S->nc)) != cudaSuccess ||
+        (ce = alloc(S, &S->t2, dim == 3 ? (size_t)n * S->nc * S->nc : (size_t)n * S->nc)) != cudaSuccess ||
         (ce = alloc(S, &S->dc, S->Nc)) != cudaSuccess || (ce = alloc(S, &S->ec, S->Nc)) != cudaSuccess ||
         (ce = alloc(S, &S->part, S->npart)) != cudaSuccess || (ce = alloc(S, &S->dev_norm, 1)) != cudaSuccess) {
         release(S);
         return cuda_fail(ce, "workspace allocation");
     }
+    {
+        std::vector<int> mlo(n);
+        for (int i = 0; i < n; ++i) mlo[i] = i - p;
+        if ((ce = upload(S, &S->Mlo, mlo)) != cudaSuccess) { release(S); return cuda_fail(ce, "mass band"); }
+    }
     for (Level &L : S->lev)
-        if ((ce = alloc(S, &L.e, L.N)) != cudaSuccess || (ce = alloc(S, &L.rhs, L.N)) != cudaSuccess) {
+        if ((ce = alloc(S, &L.e, L.N)) != cudaSuccess || (ce = alloc(S, &L.rhs, L.N)) != cudaSuccess ||
+            (dim == 3 && (ce = alloc(S, &L.r, L.N)) != cudaSuccess)) {
             release(S);
             return cuda_fail(ce, "level allocation");
         }
@@ -505,17 +532,22 @@ int iga2l_assemble(int p, int m, int dim, const iga2l_options *opt_in, iga2l_han
             (ce = upload(S, &X.Rb, to_f(ht.Rb))) != cudaSuccess ||
             (ce = upload(S, &X.Cb, to_f(ht.Cb))) != cudaSuccess ||
             (ce = allocf(&X.r, S->N)) != cudaSuccess || (ce = allocf(&X.delta, S->N)) != cudaSuccess ||
-            (ce = allocf(&X.d, S->N)) != cudaSuccess || (ce = allocf(&X.t, (size_t)n * S->nc)) != cudaSuccess ||
-            (ce = allocf(&X.t2, (size_t)n * S->nc)) != cudaSuccess || (ce = allocf(&X.dc, S->Nc)) != cudaSuccess ||
+            (ce = upload(S, &X.Kb, to_f(ht.Kb))) != cudaSuccess || (ce = upload(S, &X.Mb, to_f(ht.Mb))) != cudaSuccess ||
+            (ce = allocf(&X.d, S->N)) != cudaSuccess ||
+            (ce = allocf(&X.t, dim == 3 ? (size_t)n * n * S->nc : (size_t)n * S->nc)) != cudaSuccess ||
+            (ce = allocf(&X.t2, dim == 3 ? (size_t)n * S->nc * S->nc : (size_t)n * S->nc)) != cudaSuccess ||
+            (ce = allocf(&X.dc, S->Nc)) != cudaSuccess ||
             (ce = allocf(&X.ec, S->Nc)) != cudaSuccess) {
             release(S);
             return cuda_fail(ce, "mixed-precision allocation");
         }
         X.lev_e.assign(S->lev.size(), nullptr);
         X.lev_rhs.assign(S->lev.size(), nullptr);
-        for (size_t l = 1; l < S->lev.size(); ++l)
-            if ((ce = allocf(&X.lev_e[l], S->lev[l].N)) != cudaSuccess ||
-                (ce = allocf(&X.lev_rhs[l], S->lev[l].N)) != cudaSuccess) {
+        X.lev_r.assign(S->lev.size(), nullptr);
+        for (size_t l = 0; l < S->lev.size(); ++l)
+            if ((l > 0 && (ce = allocf(&X.lev_e[l], S->lev[l].N)) != cudaSuccess) ||
+                (l > 0 && (ce = allocf(&X.lev_rhs[l], S->lev[l].N)) != cudaSuccess) ||
+                (dim == 3 && (ce = allocf(&X.lev_r[l], S->lev[l].N)) != cudaSuccess)) {
                 release(S);
                 return cuda_fail(ce, "mixed-precision level allocation");
             }

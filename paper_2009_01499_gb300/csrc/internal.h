@@ -45,10 +45,12 @@ struct Level {                 // degree-1 level of the second-level hierarchy
 struct MixedState {
     bool enabled = false;
     float *stencil = nullptr, *binv = nullptr, *Rb = nullptr, *Cb = nullptr;
+    float *Kb = nullptr, *Mb = nullptr;   // FP32 band rows (3D kernels)
     float *r = nullptr;       // outer residual b - A u, computed in FP64, stored in FP32
     float *delta = nullptr;   // correction of the Schwarz step
     float *d = nullptr, *t = nullptr, *t2 = nullptr, *dc = nullptr, *ec = nullptr;
     std::vector<float *> lev_e, lev_rhs;   // level arrays (index 0 unused: dc / ec)
+    std::vector<float *> lev_r;            // level residuals (3D)
 };
 
 struct Solver {
@@ -66,6 +68,7 @@ struct Solver {
     int *bcls = nullptr;         // block class of every centre index (n)
     double *Rb = nullptr, *Cb = nullptr;
     int *Rlo = nullptr, *Clo = nullptr;
+    int *Mlo = nullptr;          // row starts i - p of the mass band (3D mass apply)
     int nc = 0;
     long long Nc = 0;
     std::vector<Level> lev;      // lev[0] is the second level (nc per axis)
@@ -114,6 +117,20 @@ cudaError_t launch_inner_fine(const Solver &S, const float *r32, bool reverse, c
 cudaError_t launch_inner_coarse(const Solver &S, cudaStream_t st);
 cudaError_t launch_inner_update(const Solver &S, double *u, cudaStream_t st);
 int residual_partials(const Solver &S);
+// 3D (kernels_3d.cu)
+int residual3d_partials(const Solver &S);
+cudaError_t launch3d_residual(const Solver &S, const double *u, const double *b, double *d, double *part,
+                              cudaStream_t st);
+cudaError_t launch3d_schwarz(const Solver &S, double *u, const double *b, bool reverse, cudaStream_t st);
+cudaError_t launch3d_restrict(const Solver &S, const double *d, double *dc, cudaStream_t st);
+cudaError_t launch3d_prolong_add(const Solver &S, const double *ec, double *u, cudaStream_t st);
+cudaError_t launch3d_coarse_solve(const Solver &S, const double *dc, double *ec, cudaStream_t st);
+cudaError_t launch3d_mass(const Solver &S, const double *f, double *b, cudaStream_t st);
+cudaError_t launch3d_outer_residual(const Solver &S, const double *u, const double *b, float *r32, double *part,
+                                    cudaStream_t st);
+cudaError_t launch3d_inner_fine(const Solver &S, const float *r32, cudaStream_t st);
+cudaError_t launch3d_inner_coarse(const Solver &S, cudaStream_t st);
+cudaError_t launch3d_inner_update(const Solver &S, double *u, cudaStream_t st);
 // Interior 2D residual stencil of degree p (h-independent) into constant memory; written
 // once per device and degree.
 cudaError_t upload_interior_stencil(int p, const double *st64, int count);

@@ -1,0 +1,609 @@
+// kernels_3d.cu -- the two-level cycle in 3D (the paper's method on (0,1)^3).
+//
+// A_p = K(x)M(x)M + M(x)K(x)M + M(x)M(x)K.  Every application of A_p is sum-
+// factorised with the exact 1D band rows (row x of K, M couples DOF x with x+a-p):
+//   tK = K_x u, tM = M_x u;   S1 = M_y tK + K_y tM, MM = M_y tM;   A u = M_z S1 + K_z MM,
+// i.e. 2 + 3 + 2 band passes of width 2p+1 instead of (2p+1)^3 taps per row.
+//
+//   residual    d = b - A u (+ per-CTA partial sums of d^2), tiles in shared memory
+//   schwarz     one LATTICE colour: per block, the patch (s+2p)^3 of u, three band
+//               passes, the block residual, the block inverse of its class
+//   band_axis   one 1D band along one axis of a 3D array (restriction, prolongation, mass)
+//   level_*     degree-1 hierarchy: 27-point stencil, red-black Gauss-Seidel on the 8
+//               parity sub-lattices, trilinear transfers, dense coarsest inverse
+// Templated on the storage type (double: FP64 form; float: inner cycle of the mixed form).
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "internal.h"
+
+namespace iga2l {
+
+namespace {
+
+constexpr int kR3X = 16, kR3Y = 8, kR3Z = 4;   // residual tile (outputs per CTA)
+
+template <int P>
+constexpr int res3d_smem_elems()
+{
+    return (kR3Z + 2 * P) * (kR3Y + 2 * P) * (kR3X + 2 * P)      // u tile
+           + 2 * (kR3Z + 2 * P) * (kR3Y + 2 * P) * kR3X          // tK, tM
+           + 2 * (kR3Z + 2 * P) * kR3Y * kR3X;                   // S1, MM
+}
+
+// d = b - A u (b != nullptr) or d = A u, arithmetic in T, output TO; part = sum d^2
+template <int P, typename T, typename TO>
+__global__ void __launch_bounds__(256)
+k_residual3d(int n, const T *__restrict__ Kb, const T *__restrict__ Mb, const T *__restrict__ u,
+             const T *__restrict__ b, TO *__restrict__ d, double *__restrict__ part)
+{
+    constexpr int W = 2 * P + 1;
+    constexpr int UZ = kR3Z + 2 * P, UY = kR3Y + 2 * P, UX = kR3X + 2 * P;
+    extern __shared__ __align__(16) unsigned char smem3[];
+    T *su = reinterpret_cast<T *>(smem3);
+    T *tK = su + UZ * UY * UX;
+    T *tM = tK + UZ * UY * kR3X;
+    T *S1 = tM + UZ * UY * kR3X;
+    T *MM = S1 + UZ * kR3Y * kR3X;
+    __shared__ double red[8];
+    const int x0 = blockIdx.x * kR3X, y0 = blockIdx.y * kR3Y, z0 = blockIdx.z * kR3Z;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    for (int i = tid; i < UZ * UY * UX; i += nth) {
+        const int lx = i % UX, ly = (i / UX) % UY, lz = i / (UX * UY);
+        const int gx = x0 + lx - P, gy = y0 + ly - P, gz = z0 + lz - P;
+        su[i] = (gx >= 0 && gx < n && gy >= 0 && gy < n && gz >= 0 && gz < n)
+                    ? u[((size_t)gz * n + gy) * n + gx] : T(0);
+    }
+    __syncthreads();
+    // x pass on (UZ, UY, kR3X)
+    for (int i = tid; i < UZ * UY * kR3X; i += nth) {
+        const int lx = i % kR3X, r = i / kR3X;   // r = lz * UY + ly
+        const int gx = x0 + lx;
+        T k = T(0), m = T(0);
+        if (gx < n) {
+            const T *kr = Kb + (size_t)gx * W, *mr = Mb + (size_t)gx * W;
+            const T *ur = su + r * UX + lx;
+#pragma unroll
+            for (int a = 0; a < W; ++a) {
+                k = fma(kr[a], ur[a], k);
+                m = fma(mr[a], ur[a], m);
+            }
+        }
+        tK[i] = k;
+        tM[i] = m;
+    }
+    __syncthreads();
+    // y pass on (UZ, kR3Y, kR3X)
+    for (int i = tid; i < UZ * kR3Y * kR3X; i += nth) {
+        const int lx = i % kR3X, ly = (i / kR3X) % kR3Y, lz = i / (kR3X * kR3Y);
+        const int gy = y0 + ly;
+        T s1 = T(0), mm = T(0);
+        if (gy < n) {
+            const T *kr = Kb + (size_t)gy * W, *mr = Mb + (size_t)gy * W;
+#pragma unroll
+            for (int bb = 0; bb < W; ++bb) {
+                const int j = (lz * UY + ly + bb) * kR3X + lx;
+                s1 = fma(mr[bb], tK[j], s1);
+                s1 = fma(kr[bb], tM[j], s1);
+                mm = fma(mr[bb], tM[j], mm);
+            }
+        }
+        S1[i] = s1;
+        MM[i] = mm;
+    }
+    __syncthreads();
+    // z pass and output, one thread per output (kR3X * kR3Y * kR3Z = 512 outputs, 2 per thread)
+    double sq = 0.0;
+    for (int i = tid; i < kR3Z * kR3Y * kR3X; i += nth) {
+        const int lx = i % kR3X, ly = (i / kR3X) % kR3Y, lz = i / (kR3X * kR3Y);
+        const int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
+        if (gx >= n || gy >= n || gz >= n) continue;
+        const T *kr = Kb + (size_t)gz * W, *mr = Mb + (size_t)gz * W;
+        T acc = T(0);
+#pragma unroll
+        for (int c = 0; c < W; ++c) {
+            const int j = ((lz + c) * kR3Y + ly) * kR3X + lx;
+            acc = fma(mr[c], S1[j], acc);
+            acc = fma(kr[c], MM[j], acc);
+        }
+        const size_t gi = ((size_t)gz * n + gy) * n + gx;
+        const T dv = b ? b[gi] - acc : acc;
+        if (d) d[gi] = (TO)dv;
+        sq += (double)dv * (double)dv;
+    }
+    if (part) {
+        for (int off = 16; off > 0; off >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, off);
+        if ((tid & 31) == 0) red[tid >> 5] = sq;
+        __syncthreads();
+        if (tid == 0) {
+            double tot = 0.0;
+            for (int w = 0; w < nth / 32; ++w) tot += red[w];
+            part[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = tot;
+        }
+    }
+}
+
+// One LATTICE colour in 3D, one Schwarz block per CTA (128 threads), block side S = 3.
+template <int P, typename T>
+__global__ void __launch_bounds__(128)
+k_schwarz_lattice3d(int n, int nbc, int q, int ox, int oy, int oz, int nbx, int nby,
+                    const T *__restrict__ Kb, const T *__restrict__ Mb, const T *__restrict__ binv,
+                    const double *__restrict__ binv64, int interior, const int *__restrict__ bcls,
+                    T *__restrict__ u, const T *__restrict__ b)
+{
+    constexpr int S = 3, R = 1, W = 2 * P + 1, SS = S * S * S, PW = S + 2 * P;   // patch side
+    __shared__ T pu[PW * PW * PW];
+    __shared__ T tK[PW * PW * S], tM[PW * PW * S];
+    __shared__ T S1[PW * S * S], MM[PW * S * S];
+    __shared__ T rs[SS];
+    const int blk = blockIdx.x;
+    const int cx = ox + q * (blk % nbx), cy = oy + q * ((blk / nbx) % nby), cz = oz + q * (blk / (nbx * nby));
+    const int px0 = cx - R - P, py0 = cy - R - P, pz0 = cz - R - P;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    for (int i = tid; i < PW * PW * PW; i += nth) {
+        const int gx = px0 + i % PW, gy = py0 + (i / PW) % PW, gz = pz0 + i / (PW * PW);
+        pu[i] = (gx >= 0 && gx < n && gy >= 0 && gy < n && gz >= 0 && gz < n)
+                    ? u[((size_t)gz * n + gy) * n + gx] : T(0);
+    }
+    __syncthreads();
+    for (int i = tid; i < PW * PW * S; i += nth) {   // x pass: (z, y) patch rows, 3 x outputs
+        const int ex = i % S, r = i / S;
+        const int gx = cx - R + ex;
+        T k = T(0), m = T(0);
+        if (gx >= 0 && gx < n) {
+            const T *kr = Kb + (size_t)gx * W, *mr = Mb + (size_t)gx * W;
+            const T *ur = pu + r * PW + ex;
+#pragma unroll
+            for (int a = 0; a < W; ++a) {
+                k = fma(kr[a], ur[a], k);
+                m = fma(mr[a], ur[a], m);
+            }
+        }
+        tK[i] = k;
+        tM[i] = m;
+    }
+    __syncthreads();
+    for (int i = tid; i < PW * S * S; i += nth) {    // y pass: z patch rows, 3 y x 3 x outputs
+        const int ex = i % S, ey = (i / S) % S, z = i / (S * S);
+        const int gy = cy - R + ey;
+        T s1 = T(0), mm = T(0);
+        if (gy >= 0 && gy < n) {
+            const T *kr = Kb + (size_t)gy * W, *mr = Mb + (size_t)gy * W;
+#pragma unroll
+            for (int bb = 0; bb < W; ++bb) {
+                const int j = (z * PW + ey + bb) * S + ex;
+                s1 = fma(mr[bb], tK[j], s1);
+                s1 = fma(kr[bb], tM[j], s1);
+                mm = fma(mr[bb], tM[j], mm);
+            }
+        }
+        S1[i] = s1;
+        MM[i] = mm;
+    }
+    __syncthreads();
+    if (tid < SS) {                                  // z pass and block residual
+        const int ex = tid % S, ey = (tid / S) % S, ez = tid / (S * S);
+        const int gx = cx - R + ex, gy = cy - R + ey, gz = cz - R + ez;
+        T rv = T(0);
+        if (gx >= 0 && gx < n && gy >= 0 && gy < n && gz >= 0 && gz < n) {
+            const T *kr = Kb + (size_t)gz * W, *mr = Mb + (size_t)gz * W;
+            T acc = T(0);
+#pragma unroll
+            for (int c = 0; c < W; ++c) {
+                const int j = ((ez + c) * S + ey) * S + ex;
+                acc = fma(mr[c], S1[j], acc);
+                acc = fma(kr[c], MM[j], acc);
+            }
+            rv = b[((size_t)gz * n + gy) * n + gx] - acc;
+        }
+        rs[tid] = rv;
+    }
+    __syncthreads();
+    if (tid < SS) {                                  // block solve and update
+        const int ex = tid % S, ey = (tid / S) % S, ez = tid / (S * S);
+        const int gx = cx - R + ex, gy = cy - R + ey, gz = cz - R + ez;
+        if (gx >= 0 && gx < n && gy >= 0 && gy < n && gz >= 0 && gz < n) {
+            const int cls = (bcls[cz] * nbc + bcls[cy]) * nbc + bcls[cx];
+            if (sizeof(T) == sizeof(double) || cls == interior) {
+                const T *Bi = binv + ((size_t)cls * SS + tid) * SS;
+                T ev = T(0);
+#pragma unroll
+                for (int f = 0; f < SS; ++f) ev = fma(__ldg(&Bi[f]), rs[f], ev);
+                u[((size_t)gz * n + gy) * n + gx] += ev;
+            } else {
+                const double *Bi = binv64 + ((size_t)cls * SS + tid) * SS;
+                double ev = 0.0;
+#pragma unroll
+                for (int f = 0; f < SS; ++f) ev = fma(__ldg(&Bi[f]), (double)rs[f], ev);
+                u[((size_t)gz * n + gy) * n + gx] += (T)ev;
+            }
+        }
+    }
+}
+
+// out[z][y][x'] = sum_w B[x'][w] in[z][y][lo[x'] + w] along axis `ax` (0 = x, 1 = y, 2 = z):
+// in has dims (nx, ny, nz), out the same with the axis length replaced by nout.  With
+// accumulate = 1 the result is added to out (TU) after adding delta (if not null).
+template <typename T, typename TU>
+__global__ void k_band_axis(int ax, int nx, int ny, int nz, int nout, int nin_axis, int wb,
+                            const T *__restrict__ B, const int *__restrict__ lo, const T *__restrict__ in,
+                            TU *__restrict__ out, const T *__restrict__ delta, int accumulate)
+{
+    const long long total = (ax == 0 ? (long long)nout * ny * nz : ax == 1 ? (long long)nx * nout * nz
+                                                                            : (long long)nx * ny * nout);
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const int ox_ = ax == 0 ? nout : nx, oy_ = ax == 1 ? nout : ny;
+    const int x = (int)(i % ox_), y = (int)((i / ox_) % oy_), z = (int)(i / ((long long)ox_ * oy_));
+    const int o = ax == 0 ? x : ax == 1 ? y : z;    // output index along the axis
+    const long long stride = ax == 0 ? 1 : ax == 1 ? nx : (long long)nx * ny;
+    const long long base = (long long)(ax == 0 ? 0 : x) + (long long)(ax == 1 ? 0 : y) * nx +
+                           (long long)(ax == 2 ? 0 : z) * nx * ny;
+    const int l0 = lo[o];
+    T acc = T(0);
+    for (int w = 0; w < wb; ++w) {
+        const int j = l0 + w;
+        if (j >= 0 && j < nin_axis) acc = fma(B[(size_t)o * wb + w], in[base + j * stride], acc);
+    }
+    if (accumulate) {
+        if (delta) out[i] += (TU)delta[i] + (TU)acc;
+        else out[i] += (TU)acc;
+    } else {
+        out[i] = (TU)acc;
+    }
+}
+
+// ---- degree-1 hierarchy in 3D -----------------------------------------------------
+template <typename T>
+struct Stencil27 {
+    T c[27];   // c[(dz*3 + dy)*3 + dx]
+};
+
+template <typename T>
+Stencil27<T> level_stencil27(const Level &L)
+{
+    Stencil27<T> s;
+    for (int dz = 0; dz < 3; ++dz)
+        for (int dy = 0; dy < 3; ++dy)
+            for (int dx = 0; dx < 3; ++dx)
+                s.c[(dz * 3 + dy) * 3 + dx] = (T)(L.k[dx] * L.mm[dy] * L.mm[dz] + L.mm[dx] * L.k[dy] * L.mm[dz] +
+                                                  L.mm[dx] * L.mm[dy] * L.k[dz]);
+    return s;
+}
+
+template <typename T>
+__device__ __forceinline__ T apply27(int n, const Stencil27<T> &st, const T *e, int x, int y, int z)
+{
+    T acc = T(0);
+#pragma unroll
+    for (int dz = 0; dz < 3; ++dz) {
+        const int zz = z + dz - 1;
+        if (zz < 0 || zz >= n) continue;
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy) {
+            const int yy = y + dy - 1;
+            if (yy < 0 || yy >= n) continue;
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx) {
+                const int xx = x + dx - 1;
+                if (xx >= 0 && xx < n) acc = fma(st.c[(dz * 3 + dy) * 3 + dx], e[((size_t)zz * n + yy) * n + xx], acc);
+            }
+        }
+    }
+    return acc;
+}
+
+// relax the parity sub-lattice (px, py, pz); first = the first pass from e = 0
+template <typename T>
+__global__ void k_gs3d(int n, int px, int py, int pz, int first, Stencil27<T> st, const T *__restrict__ rhs,
+                       T *__restrict__ e)
+{
+    const int half = (n + 1) / 2;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (first) {
+        if (i >= (long long)n * n * n) return;
+        const int x = (int)(i % n), y = (int)((i / n) % n), z = (int)(i / ((long long)n * n));
+        e[i] = ((x | y | z) & 1) ? T(0) : (rhs[i] - T(0)) / st.c[13];
+        return;
+    }
+    if (i >= (long long)half * half * half) return;
+    const int x = 2 * (int)(i % half) + px, y = 2 * (int)((i / half) % half) + py,
+              z = 2 * (int)(i / ((long long)half * half)) + pz;
+    if (x >= n || y >= n || z >= n) return;
+    const size_t gi = ((size_t)z * n + y) * n + x;
+    e[gi] += (rhs[gi] - apply27<T>(n, st, e, x, y, z)) / st.c[13];
+}
+
+template <typename T>
+__global__ void k_level_residual3d(int n, Stencil27<T> st, const T *__restrict__ rhs, const T *__restrict__ e,
+                                   T *__restrict__ r)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)n * n * n) return;
+    const int x = (int)(i % n), y = (int)((i / n) % n), z = (int)(i / ((long long)n * n));
+    r[i] = rhs[i] - apply27<T>(n, st, e, x, y, z);
+}
+
+// rc[K][J][I] = sum w_dz w_dy w_dx r[2K+dz][2J+dy][2I+dx], w = (1/2, 1, 1/2)
+template <typename T>
+__global__ void k_level_restrict3d(int nf, int nc, const T *__restrict__ r, T *__restrict__ rc)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)nc * nc * nc) return;
+    const int I = (int)(i % nc), J = (int)((i / nc) % nc), K = (int)(i / ((long long)nc * nc));
+    const T w[3] = {T(0.5), T(1), T(0.5)};
+    T acc = T(0);
+#pragma unroll
+    for (int dz = 0; dz < 3; ++dz) {
+        T sy = T(0);
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy) {
+            const T *row = r + ((size_t)(2 * K + dz) * nf + (2 * J + dy)) * nf + 2 * I;
+            T sx = T(0);
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx) sx = fma(w[dx], row[dx], sx);
+            sy = fma(w[dy], sx, sy);
+        }
+        acc = fma(w[dz], sy, acc);
+    }
+    rc[i] = acc;
+}
+
+template <typename T>
+__global__ void k_level_prolong3d(int nf, int nc, const T *__restrict__ ec, T *__restrict__ e)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)nf * nf * nf) return;
+    const int c3[3] = {(int)(i % nf), (int)((i / nf) % nf), (int)(i / ((long long)nf * nf))};
+    int I[3][2], cnt[3];
+    T w[3][2];
+    for (int k = 0; k < 3; ++k) {
+        const int x = c3[k];
+        if (x & 1) { I[k][0] = (x - 1) / 2; w[k][0] = T(1); cnt[k] = 1; }
+        else { I[k][0] = x / 2 - 1; I[k][1] = x / 2; w[k][0] = T(0.5); w[k][1] = T(0.5); cnt[k] = 2; }
+    }
+    T acc = T(0);
+    for (int cz = 0; cz < cnt[2]; ++cz) {
+        if (I[2][cz] < 0 || I[2][cz] >= nc) continue;
+        T sy = T(0);
+        for (int cy = 0; cy < cnt[1]; ++cy) {
+            if (I[1][cy] < 0 || I[1][cy] >= nc) continue;
+            T sx = T(0);
+            for (int cx = 0; cx < cnt[0]; ++cx) {
+                if (I[0][cx] < 0 || I[0][cx] >= nc) continue;
+                sx = fma(w[0][cx], ec[((size_t)I[2][cz] * nc + I[1][cy]) * nc + I[0][cx]], sx);
+            }
+            sy = fma(w[1][cy], sx, sy);
+        }
+        acc = fma(w[2][cz], sy, acc);
+    }
+    e[i] += acc;
+}
+
+template <typename T>
+__global__ void k_dense_matvec3(int N, const double *__restrict__ Ainv, const T *__restrict__ rhs, T *__restrict__ x)
+{
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= N) return;
+    const double *row = Ainv + (size_t)warp * N;
+    double s = 0.0;
+    for (int j = lane; j < N; j += 32) s = fma(row[j], (double)rhs[j], s);
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (lane == 0) x[warp] = (T)s;
+}
+
+inline int blocks_for(long long n, int t) { return (int)((n + t - 1) / t); }
+
+// red-black order in 3D: red (0,0,0),(1,1,0),(1,0,1),(0,1,1), black (1,0,0),(0,1,0),(0,0,1),(1,1,1)
+constexpr int kGs3Seq[8][3] = {{0, 0, 0}, {1, 1, 0}, {1, 0, 1}, {0, 1, 1},
+                               {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {1, 1, 1}};
+
+template <typename T>
+cudaError_t vcycle3d(const Solver &S, int l, const T *rhs, T *e, T *const *levE, T *const *levR, T *const *levT,
+                     cudaStream_t s)
+{
+    const Level &L = S.lev[l];
+    const int last = (int)S.lev.size() - 1;
+    if (l == last) {
+        const int N = S.ndirect;
+        k_dense_matvec3<T><<<(N * 32 + 255) / 256, 256, 0, s>>>(N, S.dinv, rhs, e);
+        count_launches(1);
+        return cudaGetLastError();
+    }
+    const Level &C = S.lev[l + 1];
+    const Stencil27<T> st = level_stencil27<T>(L);
+    const int n = L.n, half = (n + 1) / 2;
+    for (int t = 0; t < 8; ++t) {
+        if (t == 0)
+            k_gs3d<T><<<blocks_for((long long)n * n * n, 256), 256, 0, s>>>(n, 0, 0, 0, 1, st, rhs, e);
+        else
+            k_gs3d<T><<<blocks_for((long long)half * half * half, 256), 256, 0, s>>>(n, kGs3Seq[t][0], kGs3Seq[t][1],
+                                                                                  kGs3Seq[t][2], 0, st, rhs, e);
+        count_launches(1);
+    }
+    k_level_residual3d<T><<<blocks_for((long long)n * n * n, 256), 256, 0, s>>>(n, st, rhs, e, levT[l]);
+    count_launches(1);
+    k_level_restrict3d<T><<<blocks_for((long long)C.n * C.n * C.n, 256), 256, 0, s>>>(n, C.n, levT[l], levR[l + 1]);
+    count_launches(1);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    if ((err = vcycle3d<T>(S, l + 1, levR[l + 1], levE[l + 1], levE, levR, levT, s)) != cudaSuccess) return err;
+    k_level_prolong3d<T><<<blocks_for((long long)n * n * n, 256), 256, 0, s>>>(n, C.n, levE[l + 1], e);
+    count_launches(1);
+    for (int t = 7; t >= 0; --t) {
+        k_gs3d<T><<<blocks_for((long long)half * half * half, 256), 256, 0, s>>>(n, kGs3Seq[t][0], kGs3Seq[t][1],
+                                                                              kGs3Seq[t][2], 0, st, rhs, e);
+        count_launches(1);
+    }
+    return cudaGetLastError();
+}
+
+template <int P, typename T, typename TO>
+cudaError_t residual3d_p(const Solver &S, const T *Kb, const T *Mb, const T *u, const T *b, TO *d, double *part,
+                         cudaStream_t st)
+{
+    const size_t smem = sizeof(T) * res3d_smem_elems<P>();
+    static bool attr_set = false;   // per instantiation; idempotent
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_residual3d<P, T, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    dim3 grd((S.n + kR3X - 1) / kR3X, (S.n + kR3Y - 1) / kR3Y, (S.n + kR3Z - 1) / kR3Z);
+    k_residual3d<P, T, TO><<<grd, 256, smem, st>>>(S.n, Kb, Mb, u, b, d, part);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <typename T, typename TO>
+cudaError_t residual3d_any(const Solver &S, const T *Kb, const T *Mb, const T *u, const T *b, TO *d, double *part,
+                           cudaStream_t st)
+{
+    switch (S.p) {
+    case 2: return residual3d_p<2, T, TO>(S, Kb, Mb, u, b, d, part, st);
+    case 3: return residual3d_p<3, T, TO>(S, Kb, Mb, u, b, d, part, st);
+    case 4: return residual3d_p<4, T, TO>(S, Kb, Mb, u, b, d, part, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int P, typename T>
+cudaError_t schwarz3d_p(const Solver &S, const T *Kb, const T *Mb, const T *binv, T *u, const T *b, bool reverse,
+                        cudaStream_t st)
+{
+    const int q = S.q, ncol = q * q * q, nbc = S.ht.nbc;
+    const int interior = (S.ht.L * nbc + S.ht.L) * nbc + S.ht.L;
+    for (int t = 0; t < ncol; ++t) {
+        const int c = reverse ? ncol - 1 - t : t;
+        const int ox = ((c % q) * S.g) % q, oy = (((c / q) % q) * S.g) % q, oz = ((c / (q * q)) * S.g) % q;
+        const int nbx = (S.n - ox + q - 1) / q, nby = (S.n - oy + q - 1) / q, nbz = (S.n - oz + q - 1) / q;
+        if (nbx <= 0 || nby <= 0 || nbz <= 0) continue;
+        k_schwarz_lattice3d<P, T><<<nbx * nby * nbz, 128, 0, st>>>(S.n, nbc, q, ox, oy, oz, nbx, nby, Kb, Mb, binv,
+                                                                    S.binv, interior, S.bcls, u, b);
+        count_launches(1);
+        cudaError_t err = cudaGetLastError();
+        if (err != cudaSuccess) return err;
+    }
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t schwarz3d_any(const Solver &S, const T *Kb, const T *Mb, const T *binv, T *u, const T *b, bool reverse,
+                          cudaStream_t st)
+{
+    if (S.s != 3) return cudaErrorInvalidValue;
+    switch (S.p) {
+    case 2: return schwarz3d_p<2, T>(S, Kb, Mb, binv, u, b, reverse, st);
+    case 3: return schwarz3d_p<3, T>(S, Kb, Mb, binv, u, b, reverse, st);
+    case 4: return schwarz3d_p<4, T>(S, Kb, Mb, binv, u, b, reverse, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// d (n^3) -> dc (nc^3) by the restriction band along x, y, z; tA, tB hold the passes
+template <typename T>
+cudaError_t restrict3d(const Solver &S, const T *Rb, const T *d, T *tA, T *tB, T *dc, cudaStream_t st)
+{
+    const int n = S.n, nc = S.nc, w = S.ht.wr;
+    long long c1 = (long long)nc * n * n, c2 = (long long)nc * nc * n, c3 = (long long)nc * nc * nc;
+    k_band_axis<T, T><<<blocks_for(c1, 256), 256, 0, st>>>(0, n, n, n, nc, n, w, Rb, S.Rlo, d, tA, nullptr, 0);
+    k_band_axis<T, T><<<blocks_for(c2, 256), 256, 0, st>>>(1, nc, n, n, nc, n, w, Rb, S.Rlo, tA, tB, nullptr, 0);
+    k_band_axis<T, T><<<blocks_for(c3, 256), 256, 0, st>>>(2, nc, nc, n, nc, n, w, Rb, S.Rlo, tB, dc, nullptr, 0);
+    count_launches(3);
+    return cudaGetLastError();
+}
+
+// u (+= delta) += R^T ec along x, y, z (column band of R)
+template <typename T, typename TU>
+cudaError_t prolong3d(const Solver &S, const T *Cb, const T *ec, T *tA, T *tB, const T *delta, TU *u,
+                      cudaStream_t st)
+{
+    const int n = S.n, nc = S.nc, w = S.ht.wc;
+    long long c1 = (long long)n * nc * nc, c2 = (long long)n * n * nc, c3 = (long long)n * n * n;
+    k_band_axis<T, T><<<blocks_for(c1, 256), 256, 0, st>>>(0, nc, nc, nc, n, nc, w, Cb, S.Clo, ec, tB, nullptr, 0);
+    k_band_axis<T, T><<<blocks_for(c2, 256), 256, 0, st>>>(1, n, nc, nc, n, nc, w, Cb, S.Clo, tB, tA, nullptr, 0);
+    k_band_axis<T, TU><<<blocks_for(c3, 256), 256, 0, st>>>(2, n, n, nc, n, nc, w, Cb, S.Clo, tA, u, delta, 1);
+    count_launches(3);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// ---- entry points used by the dimension-generic launchers ------------------------------
+
+int residual3d_partials(const Solver &S)
+{
+    return ((S.n + kR3X - 1) / kR3X) * ((S.n + kR3Y - 1) / kR3Y) * ((S.n + kR3Z - 1) / kR3Z);
+}
+
+cudaError_t launch3d_residual(const Solver &S, const double *u, const double *b, double *d, double *part,
+                              cudaStream_t st)
+{
+    return residual3d_any<double, double>(S, S.Kb, S.Mb, u, b, d, part, st);
+}
+
+cudaError_t launch3d_schwarz(const Solver &S, double *u, const double *b, bool reverse, cudaStream_t st)
+{
+    return schwarz3d_any<double>(S, S.Kb, S.Mb, S.binv, u, b, reverse, st);
+}
+
+cudaError_t launch3d_restrict(const Solver &S, const double *d, double *dc, cudaStream_t st)
+{
+    return restrict3d<double>(S, S.Rb, d, S.t, S.t2, dc, st);
+}
+
+cudaError_t launch3d_prolong_add(const Solver &S, const double *ec, double *u, cudaStream_t st)
+{
+    return prolong3d<double, double>(S, S.Cb, ec, S.t, S.t2, nullptr, u, st);
+}
+
+cudaError_t launch3d_coarse_solve(const Solver &S, const double *dc, double *ec, cudaStream_t st)
+{
+    std::vector<double *> E(S.lev.size()), Rr(S.lev.size()), Tt(S.lev.size());
+    for (size_t l = 0; l < S.lev.size(); ++l) { E[l] = S.lev[l].e; Rr[l] = S.lev[l].rhs; Tt[l] = S.lev[l].r; }
+    return vcycle3d<double>(S, 0, dc, ec, E.data(), Rr.data(), Tt.data(), st);
+}
+
+cudaError_t launch3d_mass(const Solver &S, const double *f, double *b, cudaStream_t st)
+{
+    // b = (M (x) M (x) M) f, the band of M as a row band with lo(i) = i - p
+    const int n = S.n, W = 2 * S.p + 1;
+    long long c = (long long)n * n * n;
+    k_band_axis<double, double><<<blocks_for(c, 256), 256, 0, st>>>(0, n, n, n, n, n, W, S.Mb, S.Mlo, f, S.d, nullptr, 0);
+    k_band_axis<double, double><<<blocks_for(c, 256), 256, 0, st>>>(1, n, n, n, n, n, W, S.Mb, S.Mlo, S.d, S.bwork, nullptr, 0);
+    k_band_axis<double, double><<<blocks_for(c, 256), 256, 0, st>>>(2, n, n, n, n, n, W, S.Mb, S.Mlo, S.bwork, b, nullptr, 0);
+    count_launches(3);
+    return cudaGetLastError();
+}
+
+cudaError_t launch3d_outer_residual(const Solver &S, const double *u, const double *b, float *r32, double *part,
+                                    cudaStream_t st)
+{
+    return residual3d_any<double, float>(S, S.Kb, S.Mb, u, b, r32, part, st);
+}
+
+cudaError_t launch3d_inner_fine(const Solver &S, const float *r32, cudaStream_t st)
+{
+    const MixedState &X = S.mx;
+    cudaError_t e = cudaMemsetAsync(X.delta, 0, sizeof(float) * S.N, st);
+    if (e == cudaSuccess) e = schwarz3d_any<float>(S, X.Kb, X.Mb, X.binv, X.delta, r32, false, st);
+    if (e == cudaSuccess) e = residual3d_any<float, float>(S, X.Kb, X.Mb, X.delta, r32, X.d, nullptr, st);
+    if (e == cudaSuccess) e = restrict3d<float>(S, X.Rb, X.d, X.t, X.t2, X.dc, st);
+    return e;
+}
+
+cudaError_t launch3d_inner_coarse(const Solver &S, cudaStream_t st)
+{
+    const MixedState &X = S.mx;
+    return vcycle3d<float>(S, 0, X.dc, X.ec, X.lev_e.data(), X.lev_rhs.data(), X.lev_r.data(), st);
+}
+
+cudaError_t launch3d_inner_update(const Solver &S, double *u, cudaStream_t st)
+{
+    const MixedState &X = S.mx;
+    return prolong3d<float, double>(S, X.Cb, X.ec, X.t, X.t2, X.delta, u, st);
+}
+
+}  // namespace iga2l

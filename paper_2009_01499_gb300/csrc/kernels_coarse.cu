@@ -369,6 +369,7 @@ cudaError_t vcycle(const Solver &S, int l, const T *rhs, T *e, T *const *levE, T
 
 cudaError_t launch_coarse_solve(const Solver &S, const double *dc, double *ec, cudaStream_t st)
 {
+    if (S.dim == 3) return launch3d_coarse_solve(S, dc, ec, st);
     std::vector<double *> E(S.lev.size()), Rr(S.lev.size());
     for (size_t l = 0; l < S.lev.size(); ++l) { E[l] = S.lev[l].e; Rr[l] = S.lev[l].rhs; }
     return vcycle<double>(S, 0, dc, ec, E.data(), Rr.data(), st);
@@ -376,6 +377,7 @@ cudaError_t launch_coarse_solve(const Solver &S, const double *dc, double *ec, c
 
 cudaError_t launch_inner_coarse(const Solver &S, cudaStream_t st)
 {
+    if (S.dim == 3) return launch3d_inner_coarse(S, st);
     const MixedState &X = S.mx;
     return vcycle<float>(S, 0, X.dc, X.ec, X.lev_e.data(), X.lev_rhs.data(), st);
 }

@@ -543,12 +543,14 @@ cudaError_t upload_interior_stencil(int p, const double *st64, int count)
 
 int residual_partials(const Solver &S)
 {
+    if (S.dim == 3) return residual3d_partials(S);
     return ((S.n + kResTX - 1) / kResTX) * ((S.n + kResTY - 1) / kResTY);
 }
 
 cudaError_t launch_residual(const Solver &S, const double *u, const double *b, double *d,
                             double *part, cudaStream_t st)
 {
+    if (S.dim == 3) return launch3d_residual(S, u, b, d, part, st);
     return residual_any<double, double>(S, S.stencil, u, b, d, part, st);
 }
 
@@ -567,16 +569,19 @@ cudaError_t launch_norm_finish(const Solver &S, const double *part, double *out,
 cudaError_t launch_schwarz(const Solver &S, double *u, const double *b, bool reverse,
                            cudaStream_t st)
 {
+    if (S.dim == 3) return launch3d_schwarz(S, u, b, reverse, st);
     return schwarz_any<double>(S, S.stencil, S.binv, u, b, reverse, st);
 }
 
 cudaError_t launch_restrict(const Solver &S, const double *d, double *dc, cudaStream_t st)
 {
+    if (S.dim == 3) return launch3d_restrict(S, d, dc, st);
     return restrict_any<double>(S, S.Rb, d, S.t, dc, st);
 }
 
 cudaError_t launch_prolong_add(const Solver &S, const double *ec, double *u, cudaStream_t st)
 {
+    if (S.dim == 3) return launch3d_prolong_add(S, ec, u, st);
     return prolong_any<double, double>(S, S.Cb, ec, S.t2, nullptr, u, st);
 }
 
@@ -585,11 +590,13 @@ cudaError_t launch_prolong_add(const Solver &S, const double *ec, double *u, cud
 cudaError_t launch_outer_residual(const Solver &S, const double *u, const double *b, float *r32,
                                   double *part, cudaStream_t st)
 {
+    if (S.dim == 3) return launch3d_outer_residual(S, u, b, r32, part, st);
     return residual_any<double, float>(S, S.stencil, u, b, r32, part, st);
 }
 
 cudaError_t launch_inner_fine(const Solver &S, const float *r32, bool reverse, cudaStream_t st)
 {
+    if (S.dim == 3) return launch3d_inner_fine(S, r32, st);
     const MixedState &X = S.mx;
     cudaError_t e = cudaMemsetAsync(X.delta, 0, sizeof(float) * S.N, st);
     if (e == cudaSuccess) e = schwarz_any<float>(S, X.stencil, X.binv, X.delta, r32, reverse, st);
@@ -600,12 +607,14 @@ cudaError_t launch_inner_fine(const Solver &S, const float *r32, bool reverse, c
 
 cudaError_t launch_inner_update(const Solver &S, double *u, cudaStream_t st)
 {
+    if (S.dim == 3) return launch3d_inner_update(S, u, st);
     const MixedState &X = S.mx;
     return prolong_any<float, double>(S, X.Cb, X.ec, X.t2, X.delta, u, st);
 }
 
 cudaError_t launch_mass2(const Solver &S, const double *f, double *b, cudaStream_t st)
 {
+    if (S.dim == 3) return launch3d_mass(S, f, b, st);
     dim3 grd((S.n + 127) / 128, S.n);
     switch (S.p) {
     case 2: k_mass2d<2><<<grd, 128, 0, st>>>(S.n, S.Mb, f, b); break;
