@@ -147,6 +147,26 @@ int iga2l_adjoint_solve(iga2l_handle h, const double *g, double tol, int max_cyc
  * B-spline coefficients (b_p = (f, phi_i), Section 2). */
 int iga2l_rhs_from_coeffs(iga2l_handle h, const double *f, double *b, void *stream);
 
+/* ncycles cycles of Algorithm 1 in place, without residual checks (the forward
+ * pass of an unrolled solve). */
+int iga2l_cycles(iga2l_handle h, double *u, const double *b, int ncycles, void *stream);
+
+/* Reverse pass of ncycles unrolled cycles u_k = u_{k-1} + C (b - A u_{k-1}): given
+ * ubar = dL/du_K, writes bbar = dL/db = sum_k C^T (I - A C^T)^{K-k} ubar.  The cycle
+ * is affine in u, so no forward states are needed; C^T is the transposed cycle
+ * (iga2l_cycle_adjoint from zero).  FP64.  bbar: n^d device doubles (overwritten). */
+int iga2l_unrolled_backward(iga2l_handle h, const double *ubar, int ncycles, double *bbar, void *stream);
+
+/* Differentiable 2D source (not in the paper; a parametrised right-hand side for
+ * gradient studies): f(x,y) = sum_k a_k exp(-((x-cx_k)^2 + (y-cy_k)^2) / (2 w^2)),
+ * theta = device array of nbumps triples (a_k, cx_k, cy_k), 1 <= nbumps <= 64.
+ * iga2l_bump_load writes b = (f, phi_ij) (p+3 Gauss points per element and axis).
+ * iga2l_bump_grad writes grad = dL/dtheta (nbumps triples, device) given
+ * bbar = dL/db.  Both are separable per bump and reduce in a fixed order. */
+int iga2l_bump_load(iga2l_handle h, int nbumps, const double *theta, double width, double *b, void *stream);
+int iga2l_bump_grad(iga2l_handle h, int nbumps, const double *theta, double width, const double *bbar,
+                    double *grad, void *stream);
+
 /* Host copies of the handle's 1D band tables, rows of width 2p+1 (entry a of
  * row i is the coefficient of DOF i + a - p), for tests: K then M, n*(2p+1) each. */
 int iga2l_get_bands(iga2l_handle h, double *K, double *M);

@@ -501,6 +501,24 @@ int iga2l_assemble(int p, int m, int dim, const iga2l_options *opt_in, iga2l_han
         release(S);
         return cuda_fail(ce, "workspace allocation");
     }
+    // differentiable source (2D): quadrature tables and per-bump buffers; backward workspace
+    if (dim == 2) {
+        std::vector<double> qx, qw, qB;
+        S->nq = p + 3;
+        quadrature_tables(p, m, S->nq, qx, qw, qB);
+        if ((ce = upload(S, &S->qx, qx)) != cudaSuccess || (ce = upload(S, &S->qw, qw)) != cudaSuccess ||
+            (ce = upload(S, &S->qB, qB)) != cudaSuccess ||
+            (ce = alloc(S, &S->gbuf, (size_t)kMaxBumps * 6 * n)) != cudaSuccess) {
+            release(S);
+            return cuda_fail(ce, "source tables");
+        }
+        S->gcap = kMaxBumps;
+    }
+    if ((ce = alloc(S, &S->adj1, S->N)) != cudaSuccess || (ce = alloc(S, &S->adj2, S->N)) != cudaSuccess ||
+        (ce = alloc(S, &S->adj3, S->N)) != cudaSuccess) {
+        release(S);
+        return cuda_fail(ce, "backward workspace");
+    }
     {
         std::vector<int> mlo(n);
         for (int i = 0; i < n; ++i) mlo[i] = i - p;
@@ -668,6 +686,60 @@ int iga2l_rhs_from_coeffs(iga2l_handle h, const double *f, double *b, void *stre
     if (rc != IGA2L_OK) return rc;
     if (!f || !b || f == b) return fail(IGA2L_ERR_INVALID_ARG, "null or aliased vector");
     return finish(launch_mass2(*h, f, b, as_stream(stream)), "rhs_from_coeffs");
+}
+
+int iga2l_cycles(iga2l_handle h, double *u, const double *b, int ncycles, void *stream)
+{
+    int rc = check_handle(h);
+    if (rc != IGA2L_OK) return rc;
+    if (!u || !b || ncycles < 0) return fail(IGA2L_ERR_INVALID_ARG, "bad arguments");
+    for (int k = 0; k < ncycles; ++k)
+        if ((rc = run_cycle(h, u, b, as_stream(stream), false)) != IGA2L_OK) return rc;
+    return IGA2L_OK;
+}
+
+int iga2l_unrolled_backward(iga2l_handle h, const double *ubar, int ncycles, double *bbar, void *stream)
+{
+    int rc = check_handle(h);
+    if (rc != IGA2L_OK) return rc;
+    if (!ubar || !bbar || ncycles < 0) return fail(IGA2L_ERR_INVALID_ARG, "bad arguments");
+    if (bbar == h->adj1 || bbar == h->adj2 || bbar == h->adj3) return fail(IGA2L_ERR_INVALID_ARG, "aliased output");
+    cudaStream_t st = as_stream(stream);
+    const size_t bytes = sizeof(double) * h->N;
+    double *ub = h->adj1, *v = h->adj2, *nx = h->adj3;
+    cudaError_t e = cudaMemcpyAsync(ub, ubar, bytes, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bbar, 0, bytes, st);
+    if (e != cudaSuccess) return cuda_fail(e, "unrolled backward");
+    // u_k = u_{k-1} + C (b - A u_{k-1}):  bbar += C^T ubar,  ubar <- (I - A C^T) ubar
+    for (int k = 0; k < ncycles; ++k) {
+        if ((e = cudaMemsetAsync(v, 0, bytes, st)) != cudaSuccess) return cuda_fail(e, "unrolled backward");
+        if ((rc = run_cycle(h, v, ub, st, true)) != IGA2L_OK) return rc;   // v = C^T ubar
+        if ((e = launch_axpy(h->N, 1.0, v, bbar, st)) != cudaSuccess) return cuda_fail(e, "unrolled backward");
+        if ((e = launch_residual(*h, v, ub, nx, nullptr, st)) != cudaSuccess) return cuda_fail(e, "unrolled backward");
+        double *t = ub; ub = nx; nx = t;
+    }
+    return IGA2L_OK;
+}
+
+int iga2l_bump_load(iga2l_handle h, int nbumps, const double *theta, double width, double *b, void *stream)
+{
+    int rc = check_handle(h);
+    if (rc != IGA2L_OK) return rc;
+    if (h->dim != 2) return fail(IGA2L_ERR_UNSUPPORTED, "the bump source is 2D");
+    if (nbumps < 1 || nbumps > h->gcap || !theta || !b || !(width > 0.0))
+        return fail(IGA2L_ERR_INVALID_ARG, "bad bump arguments (1 <= nbumps <= 64, width > 0)");
+    return finish(launch_bump_load(*h, nbumps, theta, width, b, as_stream(stream)), "bump load");
+}
+
+int iga2l_bump_grad(iga2l_handle h, int nbumps, const double *theta, double width, const double *bbar,
+                    double *grad, void *stream)
+{
+    int rc = check_handle(h);
+    if (rc != IGA2L_OK) return rc;
+    if (h->dim != 2) return fail(IGA2L_ERR_UNSUPPORTED, "the bump source is 2D");
+    if (nbumps < 1 || nbumps > h->gcap || !theta || !bbar || !grad || !(width > 0.0))
+        return fail(IGA2L_ERR_INVALID_ARG, "bad bump arguments (1 <= nbumps <= 64, width > 0)");
+    return finish(launch_bump_grad(*h, nbumps, theta, width, bbar, grad, as_stream(stream)), "bump gradient");
 }
 
 int iga2l_get_bands(iga2l_handle h, double *K, double *M)

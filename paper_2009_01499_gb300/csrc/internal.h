@@ -80,6 +80,12 @@ struct Solver {
     int npart = 0;
     double *bwork = nullptr;     // b built from coefficients in solve paths
     MixedState mx;
+    // differentiable source (2D): 1D quadrature tables, nq = p+3 points per element
+    int nq = 0;
+    double *qx = nullptr, *qw = nullptr, *qB = nullptr;
+    double *adj1 = nullptr, *adj2 = nullptr, *adj3 = nullptr;   // backward workspace (N each)
+    double *gbuf = nullptr;      // per-bump 1D loads and their centre derivatives
+    int gcap = 0;                // bumps gbuf can hold
     std::vector<void *> allocs;
 };
 
@@ -95,6 +101,8 @@ void set_last_error(const std::string &msg);
 int build_host_tables(int p, int m, int s, HostTables &ht, std::string &err);
 void bspline_band_1d(int p, int m, std::vector<double> &K, std::vector<double> &M);
 bool cholesky_inverse(int N, std::vector<double> &A);   // in place, SPD
+void quadrature_tables(int p, int m, int nq, std::vector<double> &x, std::vector<double> &w,
+                       std::vector<double> &B);
 int default_block_side(int p);
 void default_colouring(int p, int s, int &q, int &g);
 
@@ -117,6 +125,13 @@ cudaError_t launch_inner_fine(const Solver &S, const float *r32, bool reverse, c
 cudaError_t launch_inner_coarse(const Solver &S, cudaStream_t st);
 cudaError_t launch_inner_update(const Solver &S, double *u, cudaStream_t st);
 int residual_partials(const Solver &S);
+// differentiable source (kernels_grad.cu)
+constexpr int kMaxBumps = 64;
+cudaError_t launch_bump_load(const Solver &S, int nb, const double *theta, double w, double *b, cudaStream_t st);
+cudaError_t launch_bump_grad(const Solver &S, int nb, const double *theta, double w, const double *bbar,
+                             double *grad, cudaStream_t st);
+cudaError_t launch_axpy(long long n, double alpha, const double *x, double *y, cudaStream_t st);
+
 // 3D (kernels_3d.cu)
 int residual3d_partials(const Solver &S);
 cudaError_t launch3d_residual(const Solver &S, const double *u, const double *b, double *d, double *part,

@@ -183,6 +183,29 @@ bool cholesky_inverse(int N, std::vector<double> &A)
     return true;
 }
 
+// Gauss points, weights and the p+1 nonzero basis values of every element, nq points
+// per element: x[e*nq+q], w[e*nq+q], B[(e*nq+q)*(p+1)+a] = N_{e+a}(x) (full index).
+void quadrature_tables(int p, int m, int nq, std::vector<double> &x, std::vector<double> &w,
+                       std::vector<double> &B)
+{
+    const std::vector<double> U = open_knots(p, m);
+    std::vector<double> gx, gw;
+    gauss01(nq, gx, gw);
+    const double h = 1.0 / m;
+    x.assign((size_t)m * nq, 0.0);
+    w.assign((size_t)m * nq, 0.0);
+    B.assign((size_t)m * nq * (p + 1), 0.0);
+    double N[kMaxP + 2];
+    for (int e = 0; e < m; ++e)
+        for (int q = 0; q < nq; ++q) {
+            const size_t k = (size_t)e * nq + q;
+            x[k] = (e + gx[q]) * h;
+            w[k] = gw[q] * h;
+            span_basis(p, U, p + e, x[k], N);
+            for (int a = 0; a <= p; ++a) B[k * (p + 1) + a] = N[a];
+        }
+}
+
 int build_host_tables(int p, int m, int s, HostTables &ht, std::string &err)
 {
     ht.p = p;

@@ -29,6 +29,7 @@ EXPORTS = (
     "iga2l_solve", "iga2l_adjoint_solve", "iga2l_rhs_from_coeffs", "iga2l_get_bands",
     "iga2l_host_bands", "iga2l_host_restriction", "iga2l_destroy", "iga2l_strerror",
     "iga2l_last_error", "iga2l_kernel_launches", "iga2l_residual_norm2_noalloc",
+    "iga2l_cycles", "iga2l_unrolled_backward", "iga2l_bump_load", "iga2l_bump_grad",
 )
 
 
@@ -90,6 +91,10 @@ def load(build_if_missing: bool = True):
             "iga2l_strerror": (ctypes.c_char_p, [ctypes.c_int]),
             "iga2l_last_error": (ctypes.c_char_p, []),
             "iga2l_kernel_launches": (ctypes.c_longlong, []),
+            "iga2l_cycles": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp]),
+            "iga2l_unrolled_backward": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, _vp]),
+            "iga2l_bump_load": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_double, _vp, _vp]),
+            "iga2l_bump_grad": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_double, _vp, _vp, _vp]),
             "iga2l_residual_norm2_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _vp, _vp, _vp,
                                                             _vp, _vp, _vp, _vp]),
         }
@@ -248,6 +253,24 @@ class Solver:
                                                   ctypes.byref(cyc), ctypes.byref(rel), _stream(stream)),
                     allow_not_converged=True)
         return cyc.value, rel.value, rc == OK
+
+    def cycles(self, u, b, ncycles, stream=None):
+        _check(self._lib.iga2l_cycles(self._h, _ptr(u, numel=self.N), _ptr(b, numel=self.N), int(ncycles),
+                                      _stream(stream)))
+
+    def unrolled_backward(self, ubar, ncycles, bbar, stream=None):
+        _check(self._lib.iga2l_unrolled_backward(self._h, _ptr(ubar, numel=self.N), int(ncycles),
+                                                 _ptr(bbar, numel=self.N), _stream(stream)))
+
+    def bump_load(self, theta, width, b, stream=None):
+        nb = theta.numel() // 3
+        _check(self._lib.iga2l_bump_load(self._h, nb, _ptr(theta, numel=3 * nb), float(width),
+                                         _ptr(b, numel=self.N), _stream(stream)))
+
+    def bump_grad(self, theta, width, bbar, grad, stream=None):
+        nb = theta.numel() // 3
+        _check(self._lib.iga2l_bump_grad(self._h, nb, _ptr(theta, numel=3 * nb), float(width),
+                                         _ptr(bbar, numel=self.N), _ptr(grad, numel=3 * nb), _stream(stream)))
 
     def bands(self):
         w = 2 * self.p + 1

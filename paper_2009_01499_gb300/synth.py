@@ -59,3 +59,11 @@ def initial_guess(n_total: int, seed: int) -> np.ndarray:
 def coefficients(n_total: int, seed: int) -> np.ndarray:
     """Seeded uniform[-1,1] B-spline coefficients of f."""
     return uniform_pm1(seed ^ 0x5DEECE66D, n_total)
+
+
+def bumps(nb: int, seed: int) -> np.ndarray:
+    """nb Gaussian source bumps as rows (a_k, cx_k, cy_k): amplitudes N(0,1), centres
+    uniform in [0.1, 0.9]^2 (the width 0.05 keeps each bump inside the domain)."""
+    a = normal(seed, nb)
+    c = 0.1 + 0.8 * uniform01(seed ^ 0x9E37, 2 * nb)
+    return np.stack([a, c[0::2], c[1::2]], axis=1).astype(np.float64)
