@@ -85,6 +85,27 @@ void iga2l_default_options(iga2l_options *opt);
  * *out receives the handle (NULL on error).  opt may be NULL (defaults). */
 int iga2l_assemble(int p, int m, int dim, const iga2l_options *opt, iga2l_handle *out);
 
+/* Batch of nbatch independent 2D problems with the same p, m and options (the
+ * tables are shared; every problem has its own workspace).  Vectors passed to a
+ * batch handle hold all problems back to back: nbatch * n^2 doubles, problem k at
+ * offset k * n^2.  The per-step entry points (apply_A, residual without a norm,
+ * schwarz_sweep(_reverse), restrict, prolong_add, coarse_solve, cycle,
+ * cycle_adjoint, cycles, rhs_from_coeffs) act on every problem; iga2l_solve,
+ * iga2l_adjoint_solve, iga2l_unrolled_backward, the bump source and a residual
+ * with a norm are single-problem entry points and return IGA2L_ERR_INVALID_ARG. */
+int iga2l_assemble_batch(int p, int m, int nbatch, const iga2l_options *opt, iga2l_handle *out);
+
+/* Solves every problem of a batch to its own tolerance (Section 5 stopping rule):
+ * after each cycle a device kernel counts the cycle for each unfinished problem and
+ * retires the problems whose relative residual is <= tol; retired problems are
+ * skipped by every later kernel, so each problem's iterates and cycle count equal
+ * those of a single solve.  The host polls the number of unfinished problems every
+ * 4 cycles.  cycles (int) and relres (double) are host arrays of nbatch entries.
+ * Returns IGA2L_OK when all converged, IGA2L_NOT_CONVERGED at the cycle cap,
+ * IGA2L_ERR_NONFINITE if a norm is not finite. */
+int iga2l_solve_batch(iga2l_handle h, const double *b, double tol, int max_cycles, double *u, int *cycles,
+                      double *relres, void *stream);
+
 /* Sizes: total fine DOFs, DOFs per axis, total and per-axis second-level DOFs.
  * Any output pointer may be NULL. */
 int iga2l_num_dofs(iga2l_handle h, long long *n_total, int *n_axis,

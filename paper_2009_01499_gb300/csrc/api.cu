@@ -166,7 +166,7 @@ int enqueue_cycle(iga2l_handle h, double *u, const double *b, cudaStream_t st, b
         if (e == cudaSuccess) e = launch_inner_update(*h, u, st);
         if (e == cudaSuccess) e = launch_outer_residual(*h, u, b, h->mx.r, norm ? h->part : nullptr, st);
         if (e == cudaSuccess && norm) e = launch_norm_finish(*h, h->part, h->dev_norm, st);
-        if (e == cudaSuccess && norm)
+        if (e == cudaSuccess && norm && !h->active)
             e = cudaMemcpyAsync(h->host_norm, h->dev_norm, sizeof(double), cudaMemcpyDeviceToHost, st);
         return finish(e, "mixed-precision cycle");
     }
@@ -182,7 +182,7 @@ int enqueue_cycle(iga2l_handle h, double *u, const double *b, cudaStream_t st, b
     if (norm) {
         cudaError_t e = launch_residual(*h, u, b, nullptr, h->part, st);
         if (e == cudaSuccess) e = launch_norm_finish(*h, h->part, h->dev_norm, st);
-        if (e == cudaSuccess)
+        if (e == cudaSuccess && !h->active)
             e = cudaMemcpyAsync(h->host_norm, h->dev_norm, sizeof(double), cudaMemcpyDeviceToHost, st);
         if (e != cudaSuccess) return cuda_fail(e, "residual norm");
     }
@@ -314,7 +314,9 @@ void iga2l_default_options(iga2l_options *opt)
     opt->graphs = 1;
 }
 
-int iga2l_assemble(int p, int m, int dim, const iga2l_options *opt_in, iga2l_handle *out)
+}  // extern "C"
+
+static int assemble_impl(int p, int m, int dim, int nbatch, bool batch, const iga2l_options *opt_in, iga2l_handle *out)
 {
     if (!out) return fail(IGA2L_ERR_INVALID_ARG, "null output handle");
     *out = nullptr;
@@ -354,6 +356,7 @@ int iga2l_assemble(int p, int m, int dim, const iga2l_options *opt_in, iga2l_han
     S->dim = dim; S->p = p; S->m = m; S->s = s; S->r = (s - 1) / 2;
     S->n = m + p - 2;
     S->N = (long long)S->n * S->n * (dim == 3 ? S->n : 1);
+    S->nbatch = nbatch;
     S->opt = opt;
     S->q = q; S->g = g % q; S->tile = opt.tile;
     cudaError_t ce = cudaGetDevice(&S->device);
@@ -493,11 +496,12 @@ int iga2l_assemble(int p, int m, int dim, const iga2l_options *opt_in, iga2l_han
         return cuda_fail(ce, "table upload");
     }
     S->npart = residual_partials(*S);
-    if ((ce = alloc(S, &S->d, S->N)) != cudaSuccess || (ce = alloc(S, &S->bwork, S->N)) != cudaSuccess ||
-        (ce = alloc(S, &S->t, dim == 3 ? (size_t)n * n * S->nc : (size_t)n * S->nc)) != cudaSuccess ||
-        (ce = alloc(S, &S->t2, dim == 3 ? (size_t)n * S->nc * S->nc : (size_t)n * S->nc)) != cudaSuccess ||
-        (ce = alloc(S, &S->dc, S->Nc)) != cudaSuccess || (ce = alloc(S, &S->ec, S->Nc)) != cudaSuccess ||
-        (ce = alloc(S, &S->part, S->npart)) != cudaSuccess || (ce = alloc(S, &S->dev_norm, 1)) != cudaSuccess) {
+    const size_t B = (size_t)nbatch;   // every per-problem buffer holds nbatch problems
+    if ((ce = alloc(S, &S->d, B * S->N)) != cudaSuccess || (ce = alloc(S, &S->bwork, B * S->N)) != cudaSuccess ||
+        (ce = alloc(S, &S->t, B * (dim == 3 ? (size_t)n * n * S->nc : (size_t)n * S->nc))) != cudaSuccess ||
+        (ce = alloc(S, &S->t2, B * (dim == 3 ? (size_t)n * S->nc * S->nc : (size_t)n * S->nc))) != cudaSuccess ||
+        (ce = alloc(S, &S->dc, B * S->Nc)) != cudaSuccess || (ce = alloc(S, &S->ec, B * S->Nc)) != cudaSuccess ||
+        (ce = alloc(S, &S->part, B * S->npart)) != cudaSuccess || (ce = alloc(S, &S->dev_norm, B)) != cudaSuccess) {
         release(S);
         return cuda_fail(ce, "workspace allocation");
     }
@@ -525,7 +529,7 @@ int iga2l_assemble(int p, int m, int dim, const iga2l_options *opt_in, iga2l_han
         if ((ce = upload(S, &S->Mlo, mlo)) != cudaSuccess) { release(S); return cuda_fail(ce, "mass band"); }
     }
     for (Level &L : S->lev)
-        if ((ce = alloc(S, &L.e, L.N)) != cudaSuccess || (ce = alloc(S, &L.rhs, L.N)) != cudaSuccess ||
+        if ((ce = alloc(S, &L.e, B * L.N)) != cudaSuccess || (ce = alloc(S, &L.rhs, B * L.N)) != cudaSuccess ||
             (dim == 3 && (ce = alloc(S, &L.r, L.N)) != cudaSuccess)) {
             release(S);
             return cuda_fail(ce, "level allocation");
@@ -549,13 +553,13 @@ int iga2l_assemble(int p, int m, int dim, const iga2l_options *opt_in, iga2l_han
             (ce = upload(S, &X.binv, to_f(binv))) != cudaSuccess ||
             (ce = upload(S, &X.Rb, to_f(ht.Rb))) != cudaSuccess ||
             (ce = upload(S, &X.Cb, to_f(ht.Cb))) != cudaSuccess ||
-            (ce = allocf(&X.r, S->N)) != cudaSuccess || (ce = allocf(&X.delta, S->N)) != cudaSuccess ||
+            (ce = allocf(&X.r, B * S->N)) != cudaSuccess || (ce = allocf(&X.delta, B * S->N)) != cudaSuccess ||
             (ce = upload(S, &X.Kb, to_f(ht.Kb))) != cudaSuccess || (ce = upload(S, &X.Mb, to_f(ht.Mb))) != cudaSuccess ||
-            (ce = allocf(&X.d, S->N)) != cudaSuccess ||
-            (ce = allocf(&X.t, dim == 3 ? (size_t)n * n * S->nc : (size_t)n * S->nc)) != cudaSuccess ||
-            (ce = allocf(&X.t2, dim == 3 ? (size_t)n * S->nc * S->nc : (size_t)n * S->nc)) != cudaSuccess ||
-            (ce = allocf(&X.dc, S->Nc)) != cudaSuccess ||
-            (ce = allocf(&X.ec, S->Nc)) != cudaSuccess) {
+            (ce = allocf(&X.d, B * S->N)) != cudaSuccess ||
+            (ce = allocf(&X.t, B * (dim == 3 ? (size_t)n * n * S->nc : (size_t)n * S->nc))) != cudaSuccess ||
+            (ce = allocf(&X.t2, B * (dim == 3 ? (size_t)n * S->nc * S->nc : (size_t)n * S->nc))) != cudaSuccess ||
+            (ce = allocf(&X.dc, B * S->Nc)) != cudaSuccess ||
+            (ce = allocf(&X.ec, B * S->Nc)) != cudaSuccess) {
             release(S);
             return cuda_fail(ce, "mixed-precision allocation");
         }
@@ -563,16 +567,90 @@ int iga2l_assemble(int p, int m, int dim, const iga2l_options *opt_in, iga2l_han
         X.lev_rhs.assign(S->lev.size(), nullptr);
         X.lev_r.assign(S->lev.size(), nullptr);
         for (size_t l = 0; l < S->lev.size(); ++l)
-            if ((l > 0 && (ce = allocf(&X.lev_e[l], S->lev[l].N)) != cudaSuccess) ||
-                (l > 0 && (ce = allocf(&X.lev_rhs[l], S->lev[l].N)) != cudaSuccess) ||
+            if ((l > 0 && (ce = allocf(&X.lev_e[l], B * S->lev[l].N)) != cudaSuccess) ||
+                (l > 0 && (ce = allocf(&X.lev_rhs[l], B * S->lev[l].N)) != cudaSuccess) ||
                 (dim == 3 && (ce = allocf(&X.lev_r[l], S->lev[l].N)) != cudaSuccess)) {
                 release(S);
                 return cuda_fail(ce, "mixed-precision level allocation");
             }
         X.enabled = true;
     }
+    if (batch) {
+        void *pa = nullptr, *pc = nullptr, *pn = nullptr;
+        if ((ce = cudaMalloc(&pa, sizeof(int) * B)) != cudaSuccess ||
+            (S->allocs.push_back(pa), (ce = cudaMalloc(&pc, sizeof(int) * (B + 1))) != cudaSuccess) ||
+            (S->allocs.push_back(pc), (ce = cudaMalloc(&pn, sizeof(double) * 2 * B)) != cudaSuccess)) {
+            release(S);
+            return cuda_fail(ce, "batch state");
+        }
+        S->allocs.push_back(pn);
+        S->active = static_cast<int *>(pa);
+        S->bcycles = static_cast<int *>(pc);
+        S->bcount = S->bcycles + B;
+        S->bnorm0 = static_cast<double *>(pn);
+        S->brel = S->bnorm0 + B;
+    }
     *out = S;
     g_last_error.clear();
+    return IGA2L_OK;
+}
+
+extern "C" {
+
+int iga2l_assemble(int p, int m, int dim, const iga2l_options *opt, iga2l_handle *out)
+{
+    return assemble_impl(p, m, dim, 1, false, opt, out);
+}
+
+int iga2l_assemble_batch(int p, int m, int nbatch, const iga2l_options *opt, iga2l_handle *out)
+{
+    if (!out) return fail(IGA2L_ERR_INVALID_ARG, "null output handle");
+    *out = nullptr;
+    if (nbatch < 1 || nbatch > 65535) return fail(IGA2L_ERR_INVALID_ARG, "nbatch must be 1..65535");
+    return assemble_impl(p, m, 2, nbatch, true, opt, out);
+}
+
+int iga2l_solve_batch(iga2l_handle h, const double *b, double tol, int max_cycles, double *u, int *cycles,
+                      double *relres, void *stream)
+{
+    int rc = check_handle(h);
+    if (rc != IGA2L_OK) return rc;
+    if (!b || !u || !cycles || !relres) return fail(IGA2L_ERR_INVALID_ARG, "null argument");
+    if (!(tol >= 0.0)) return fail(IGA2L_ERR_INVALID_ARG, "tol must be >= 0");
+    if (!h->active) return fail(IGA2L_ERR_INVALID_ARG, "handle is not a batch (iga2l_assemble_batch)");
+    if (max_cycles <= 0) max_cycles = h->opt.max_cycles;
+    cudaStream_t st = as_stream(stream);
+    const int nb = h->nbatch;
+    // initial residuals of every problem (all active while they are computed)
+    std::vector<int> ones(nb, 1);
+    cudaError_t e = cudaMemcpyAsync(h->active, ones.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        if (h->mx.enabled) e = launch_outer_residual(*h, u, b, h->mx.r, h->part, st);
+        else e = launch_residual(*h, u, b, nullptr, h->part, st);
+    }
+    if (e == cudaSuccess) e = launch_norm_finish(*h, h->part, h->dev_norm, st);
+    if (e == cudaSuccess) e = launch_batch_init(*h, h->dev_norm, h->bnorm0, h->bcycles, h->brel, st);
+    if (e != cudaSuccess) return cuda_fail(e, "batch start");
+    // cycles; converged problems are masked on the device, the host polls every 4 cycles
+    int left = nb;
+    for (int k = 0; k < max_cycles && left > 0; ++k) {
+        if ((rc = run_cycle_graph(h, u, b, st, false, true)) != IGA2L_OK) return rc;
+        e = launch_batch_check(*h, tol, h->dev_norm, h->bnorm0, h->bcycles, h->brel, h->bcount, st);
+        if (e != cudaSuccess) return cuda_fail(e, "batch check");
+        if ((k % 4) == 3 || k == max_cycles - 1) {
+            e = cudaMemcpyAsync(&left, h->bcount, sizeof(int), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) return cuda_fail(e, "batch poll");
+        }
+    }
+    e = cudaMemcpyAsync(cycles, h->bcycles, sizeof(int) * nb, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(relres, h->brel, sizeof(double) * nb, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&left, h->bcount, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "batch results");
+    for (int k = 0; k < nb; ++k)
+        if (!std::isfinite(relres[k])) return fail(IGA2L_ERR_NONFINITE, "a residual norm is not finite");
+    if (left > 0) { g_last_error = "cycle cap reached"; return IGA2L_NOT_CONVERGED; }
     return IGA2L_OK;
 }
 
@@ -601,6 +679,7 @@ int iga2l_residual(iga2l_handle h, const double *u, const double *b, double *d, 
     if (!u || !b) return fail(IGA2L_ERR_INVALID_ARG, "null vector");
     cudaStream_t st = as_stream(stream);
     if (!norm) return finish(launch_residual(*h, u, b, d, nullptr, st), "residual");
+    if (h->active) return fail(IGA2L_ERR_INVALID_ARG, "residual norm of a batch: use iga2l_solve_batch");
     double sq = 0.0;
     rc = residual_norm2(h, u, b, d, st, &sq);
     if (rc != IGA2L_OK) return rc;
@@ -669,6 +748,7 @@ int iga2l_solve(iga2l_handle h, const double *b, double tol, int max_cycles, dou
 {
     int rc = check_handle(h);
     if (rc != IGA2L_OK) return rc;
+    if (h->active) return fail(IGA2L_ERR_INVALID_ARG, "single-problem entry point on a batch handle");
     return solve_impl(h, b, tol, max_cycles, u, cycles, relres, hist, stream, false);
 }
 
@@ -677,6 +757,7 @@ int iga2l_adjoint_solve(iga2l_handle h, const double *g, double tol, int max_cyc
 {
     int rc = check_handle(h);
     if (rc != IGA2L_OK) return rc;
+    if (h->active) return fail(IGA2L_ERR_INVALID_ARG, "single-problem entry point on a batch handle");
     return solve_impl(h, g, tol, max_cycles, lambda, cycles, relres, nullptr, stream, true);
 }
 
@@ -702,6 +783,7 @@ int iga2l_unrolled_backward(iga2l_handle h, const double *ubar, int ncycles, dou
 {
     int rc = check_handle(h);
     if (rc != IGA2L_OK) return rc;
+    if (h->active) return fail(IGA2L_ERR_INVALID_ARG, "single-problem entry point on a batch handle");
     if (!ubar || !bbar || ncycles < 0) return fail(IGA2L_ERR_INVALID_ARG, "bad arguments");
     if (bbar == h->adj1 || bbar == h->adj2 || bbar == h->adj3) return fail(IGA2L_ERR_INVALID_ARG, "aliased output");
     cudaStream_t st = as_stream(stream);
@@ -725,6 +807,7 @@ int iga2l_bump_load(iga2l_handle h, int nbumps, const double *theta, double widt
 {
     int rc = check_handle(h);
     if (rc != IGA2L_OK) return rc;
+    if (h->active) return fail(IGA2L_ERR_INVALID_ARG, "single-problem entry point on a batch handle");
     if (h->dim != 2) return fail(IGA2L_ERR_UNSUPPORTED, "the bump source is 2D");
     if (nbumps < 1 || nbumps > h->gcap || !theta || !b || !(width > 0.0))
         return fail(IGA2L_ERR_INVALID_ARG, "bad bump arguments (1 <= nbumps <= 64, width > 0)");
@@ -736,6 +819,7 @@ int iga2l_bump_grad(iga2l_handle h, int nbumps, const double *theta, double widt
 {
     int rc = check_handle(h);
     if (rc != IGA2L_OK) return rc;
+    if (h->active) return fail(IGA2L_ERR_INVALID_ARG, "single-problem entry point on a batch handle");
     if (h->dim != 2) return fail(IGA2L_ERR_UNSUPPORTED, "the bump source is 2D");
     if (nbumps < 1 || nbumps > h->gcap || !theta || !bbar || !grad || !(width > 0.0))
         return fail(IGA2L_ERR_INVALID_ARG, "bad bump arguments (1 <= nbumps <= 64, width > 0)");

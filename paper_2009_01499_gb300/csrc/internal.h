@@ -14,6 +14,14 @@ constexpr int kMaxP = 5;       // degrees with compiled kernels: 2..5
 constexpr int kMaxLevels = 24;
 constexpr int kTile = 32;       // side of the TILE schedule's tiles (block centres)
 
+// Batch addressing passed to 2D kernels: problem z of a batch owns vec (fine vector),
+// aux (scratch) and crs (second-level vector) entries starting at z * stride; problems
+// with active[z] == 0 are skipped (null: all active).  A single problem has nbatch = 1.
+struct BatchRef {
+    const int *active;
+    long long vec, aux, crs;
+};
+
 // Host-side tables built once per handle (setup.cpp); uploaded by api.cu.
 struct HostTables {
     int p = 0, m = 0, n = 0, s = 0, r = 0;
@@ -56,6 +64,10 @@ struct MixedState {
 struct Solver {
     int dim = 2, p = 2, m = 0, n = 0, s = 3, r = 1;
     long long N = 0;
+    int nbatch = 1;              // problems sharing (p, m, options), stored [problem][...]
+    int *active = nullptr;       // per-problem flag (device); null for a single problem
+    double *bnorm0 = nullptr, *brel = nullptr;   // batch: initial norms^2, relative residuals
+    int *bcycles = nullptr, *bcount = nullptr;   // batch: cycles per problem, active count
     iga2l_options opt{};
     int device = 0;
     int q = 5, g = 1, tile = 0;
@@ -125,6 +137,10 @@ cudaError_t launch_inner_fine(const Solver &S, const float *r32, bool reverse, c
 cudaError_t launch_inner_coarse(const Solver &S, cudaStream_t st);
 cudaError_t launch_inner_update(const Solver &S, double *u, cudaStream_t st);
 int residual_partials(const Solver &S);
+cudaError_t launch_batch_init(const Solver &S, const double *norm2, double *norm0, int *cycles, double *relres,
+                              cudaStream_t st);
+cudaError_t launch_batch_check(const Solver &S, double tol, const double *norm2, const double *norm0, int *cycles,
+                               double *relres, int *count, cudaStream_t st);
 // differentiable source (kernels_grad.cu)
 constexpr int kMaxBumps = 64;
 cudaError_t launch_bump_load(const Solver &S, int nb, const double *theta, double w, double *b, cudaStream_t st);

@@ -40,11 +40,13 @@ Stencil9<T> level_stencil(const Level &L)
 // of a sub-lattice are coupled by the 9-point stencil.
 template <typename T>
 __global__ void k_gs_sublattice(int n, int px, int py, Stencil9<T> st, const T *__restrict__ rhs,
-                                T *__restrict__ e)
+                                T *__restrict__ e, BatchRef bt)
 {
     const int a = blockIdx.x * blockDim.x + threadIdx.x, bidx = blockIdx.y * blockDim.y + threadIdx.y;
     const int x = 2 * a + px, y = 2 * bidx + py;
-    if (x >= n || y >= n) return;
+    if (x >= n || y >= n || (bt.active && !bt.active[blockIdx.z])) return;
+    rhs += blockIdx.z * bt.vec;
+    e += blockIdx.z * bt.vec;
     T acc = T(0);
 #pragma unroll
     for (int dy = 0; dy < 3; ++dy) {
@@ -63,10 +65,12 @@ __global__ void k_gs_sublattice(int n, int px, int py, Stencil9<T> st, const T *
 // neighbours are all zero), every other point is zeroed.  Same values as zeroing e and
 // relaxing sub-lattice (0,0).
 template <typename T>
-__global__ void k_gs_first(int n, Stencil9<T> st, const T *__restrict__ rhs, T *__restrict__ e)
+__global__ void k_gs_first(int n, Stencil9<T> st, const T *__restrict__ rhs, T *__restrict__ e, BatchRef bt)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= n || y >= n) return;
+    if (x >= n || y >= n || (bt.active && !bt.active[blockIdx.z])) return;
+    rhs += blockIdx.z * bt.vec;
+    e += blockIdx.z * bt.vec;
     const size_t i = (size_t)y * n + x;
     e[i] = ((x | y) & 1) ? T(0) : (rhs[i] - T(0)) / st.c[1][1];
 }
@@ -75,10 +79,13 @@ __global__ void k_gs_first(int n, Stencil9<T> st, const T *__restrict__ rhs, T *
 // residual at the 3x3 fine points under coarse hat (I, J), restricted in place.
 template <typename T>
 __global__ void k_level_residual_restrict(int nf, int nc, Stencil9<T> st, const T *__restrict__ rhs,
-                                          const T *__restrict__ e, T *__restrict__ rc)
+                                          const T *__restrict__ e, T *__restrict__ rc, BatchRef bt)
 {
     const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y;
-    if (I >= nc || J >= nc) return;
+    if (I >= nc || J >= nc || (bt.active && !bt.active[blockIdx.z])) return;
+    rhs += blockIdx.z * bt.vec;
+    e += blockIdx.z * bt.vec;
+    rc += blockIdx.z * bt.crs;
     const T w[3] = {T(0.5), T(1), T(0.5)};
     T acc = T(0);
 #pragma unroll
@@ -109,10 +116,12 @@ __global__ void k_level_residual_restrict(int nf, int nc, Stencil9<T> st, const 
 
 // e[y][x] += sum over the coarse points whose hats cover fine node (x, y)
 template <typename T>
-__global__ void k_level_prolong_add(int nf, int nc, const T *__restrict__ ec, T *__restrict__ e)
+__global__ void k_level_prolong_add(int nf, int nc, const T *__restrict__ ec, T *__restrict__ e, BatchRef bt)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= nf || y >= nf) return;
+    if (x >= nf || y >= nf || (bt.active && !bt.active[blockIdx.z])) return;
+    ec += blockIdx.z * bt.crs;
+    e += blockIdx.z * bt.vec;
     // fine index x is coarse I = (x-1)/2 when odd (weight 1); between I = x/2-1 and x/2 when even
     int Ix[2], Iy[2];
     T wx[2], wy[2];
@@ -137,10 +146,12 @@ __global__ void k_level_prolong_add(int nf, int nc, const T *__restrict__ ec, T 
 // x = Ainv rhs in FP64, one warp per row (dense inverse of the directly solved level)
 template <typename T>
 __global__ void k_dense_matvec(int N, const double *__restrict__ Ainv, const T *__restrict__ rhs,
-                               T *__restrict__ x)
+                               T *__restrict__ x, BatchRef bt)
 {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (warp >= N) return;
+    if (warp >= N || (bt.active && !bt.active[blockIdx.y])) return;
+    rhs += blockIdx.y * bt.vec;
+    x += blockIdx.y * bt.vec;
     const double *row = Ainv + (size_t)warp * N;
     double s = 0.0;
     for (int j = lane; j < N; j += 32) s = fma(row[j], (double)rhs[j], s);
@@ -158,6 +169,8 @@ constexpr int kTailMaxLevels = 8;
 
 template <typename T>
 struct TailArgs {
+    const int *active;                // per-problem flags (one CTA per problem) or null
+    long long vec0;                   // batch stride of rhs0 / e0
     int nl;                           // levels in the tail (last one solved directly)
     int n[kTailMaxLevels];
     Stencil9<T> st[kTailMaxLevels];
@@ -199,6 +212,9 @@ template <typename T>
 __global__ void __launch_bounds__(1024) k_vcycle_tail(TailArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char tail_smem[];
+    if (a.active && !a.active[blockIdx.x]) return;
+    a.rhs0 += blockIdx.x * a.vec0;
+    a.e0 += blockIdx.x * a.vec0;
     T *E[kTailMaxLevels], *Rh[kTailMaxLevels];
     {
         T *p = reinterpret_cast<T *>(tail_smem);
@@ -296,23 +312,28 @@ dim3 grid2(int nx, int ny, dim3 blk)
     return dim3((nx + blk.x - 1) / blk.x, (ny + blk.y - 1) / blk.y);
 }
 
+dim3 grid3(int nx, int ny, int nz, dim3 blk)
+{
+    return dim3((nx + blk.x - 1) / blk.x, (ny + blk.y - 1) / blk.y, nz);
+}
+
 // red-black order: red sub-lattices (0,0), (1,1) then black (1,0), (0,1)
 constexpr int kGsSeq[4][2] = {{0, 0}, {1, 1}, {1, 0}, {0, 1}};
 
 template <typename T>
 cudaError_t gs_pass(const Level &L, const Stencil9<T> &st, const T *rhs, T *e, bool forward,
-                    bool from_zero, cudaStream_t s)
+                    bool from_zero, int nb, const BatchRef &bt, cudaStream_t s)
 {
     dim3 blk(32, 4);
     const int half = (L.n + 1) / 2;
     for (int t = 0; t < 4; ++t) {
         const int c = forward ? t : 3 - t;
         if (from_zero && t == 0) {   // forward pass from e = 0: the first colour is (0,0)
-            k_gs_first<T><<<grid2(L.n, L.n, blk), blk, 0, s>>>(L.n, st, rhs, e);
+            k_gs_first<T><<<grid3(L.n, L.n, nb, blk), blk, 0, s>>>(L.n, st, rhs, e, bt);
             count_launches(1);
             continue;
         }
-        k_gs_sublattice<T><<<grid2(half, half, blk), blk, 0, s>>>(L.n, kGsSeq[c][0], kGsSeq[c][1], st, rhs, e);
+        k_gs_sublattice<T><<<grid3(half, half, nb, blk), blk, 0, s>>>(L.n, kGsSeq[c][0], kGsSeq[c][1], st, rhs, e, bt);
         count_launches(1);
     }
     return cudaGetLastError();
@@ -324,16 +345,20 @@ cudaError_t vcycle(const Solver &S, int l, const T *rhs, T *e, T *const *levE, T
 {
     const Level &L = S.lev[l];
     const int last = (int)S.lev.size() - 1;
+    const int nb = S.nbatch;
     if (l == last) {
         const int N = S.ndirect;
-        k_dense_matvec<T><<<(N * 32 + 255) / 256, 256, 0, s>>>(N, S.dinv, rhs, e);
+        k_dense_matvec<T><<<dim3((N * 32 + 255) / 256, nb), 256, 0, s>>>(N, S.dinv, rhs, e,
+                                                                         BatchRef{S.active, L.N, 0, 0});
         count_launches(1);
         return cudaGetLastError();
     }
-    // small levels: the rest of the cycle in one thread block, in shared memory
+    // small levels: the rest of the cycle in one thread block per problem, in shared memory
     const int tail_n = sizeof(T) == sizeof(float) ? 63 : 31;
     if (L.n <= tail_n && last - l + 1 <= kTailMaxLevels) {
         TailArgs<T> a{};
+        a.active = S.active;
+        a.vec0 = L.N;
         a.nl = last - l + 1;
         size_t smem = 0;
         for (int k = 0; k < a.nl; ++k) {
@@ -345,24 +370,25 @@ cudaError_t vcycle(const Solver &S, int l, const T *rhs, T *e, T *const *levE, T
             a.rhs0 = rhs;
             a.e0 = e;
             a.dinv = S.dinv;
-            k_vcycle_tail<T><<<1, 1024, smem, s>>>(a);
+            k_vcycle_tail<T><<<nb, 1024, smem, s>>>(a);
             count_launches(1);
             return cudaGetLastError();
         }
     }
     const Level &C = S.lev[l + 1];
     const Stencil9<T> st = level_stencil<T>(L);
+    const BatchRef bt{S.active, L.N, 0, C.N};
     dim3 blk(32, 4);
     cudaError_t err;
-    if ((err = gs_pass<T>(L, st, rhs, e, true, true, s)) != cudaSuccess) return err;
-    k_level_residual_restrict<T><<<grid2(C.n, C.n, blk), blk, 0, s>>>(L.n, C.n, st, rhs, e, levR[l + 1]);
+    if ((err = gs_pass<T>(L, st, rhs, e, true, true, nb, bt, s)) != cudaSuccess) return err;
+    k_level_residual_restrict<T><<<grid3(C.n, C.n, nb, blk), blk, 0, s>>>(L.n, C.n, st, rhs, e, levR[l + 1], bt);
     count_launches(1);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     if ((err = vcycle<T>(S, l + 1, levR[l + 1], levE[l + 1], levE, levR, s)) != cudaSuccess) return err;
-    k_level_prolong_add<T><<<grid2(L.n, L.n, blk), blk, 0, s>>>(L.n, C.n, levE[l + 1], e);
+    k_level_prolong_add<T><<<grid3(L.n, L.n, nb, blk), blk, 0, s>>>(L.n, C.n, levE[l + 1], e, bt);
     count_launches(1);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
-    return gs_pass<T>(L, st, rhs, e, false, false, s);
+    return gs_pass<T>(L, st, rhs, e, false, false, nb, bt, s);
 }
 
 }  // namespace

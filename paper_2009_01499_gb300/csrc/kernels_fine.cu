@@ -33,12 +33,18 @@ template <int P, typename T, typename TO>
 __global__ void __launch_bounds__(kResTX *kResTY)
 k_residual2d(int n, int npc, const T *__restrict__ stencil, const int *__restrict__ pcls,
              const T *__restrict__ u, const T *__restrict__ b, TO *__restrict__ d,
-             double *__restrict__ part)
+             double *__restrict__ part, BatchRef bt)
 {
     constexpr int W = 2 * P + 1;
     constexpr int SX = kResTX + 2 * P, SY = kResTY + 2 * P;
     __shared__ T su[SY][SX];
     __shared__ double red[kResTX * kResTY / 32];
+    const int z = blockIdx.z;
+    if (bt.active && !bt.active[z]) return;
+    u += z * bt.vec;
+    if (b) b += z * bt.vec;
+    if (d) d += z * bt.vec;
+    if (part) part += z * bt.aux;
     const int x0 = blockIdx.x * kResTX, y0 = blockIdx.y * kResTY;
     const int tid = threadIdx.x + kResTX * threadIdx.y;
     for (int t = tid; t < SX * SY; t += kResTX * kResTY) {
@@ -77,6 +83,8 @@ k_residual2d(int n, int npc, const T *__restrict__ stencil, const int *__restric
 __global__ void k_sum_partials(const double *__restrict__ part, int np, double *__restrict__ out)
 {
     __shared__ double sh[1024];
+    part += (size_t)blockIdx.x * np;   // one problem per CTA
+    out += blockIdx.x;
     double s = 0.0;
     for (int i = threadIdx.x; i < np; i += blockDim.x) s += part[i];
     sh[threadIdx.x] = s;
@@ -99,11 +107,14 @@ __global__ void __launch_bounds__(256)
 k_schwarz_lattice2d(int n, int npc, int nbc, int q, int ox, int oy, int nbx, int nblocks,
                     const T *__restrict__ stencil, const int *__restrict__ pcls,
                     const T *__restrict__ binv, const double *__restrict__ binv64, int interior,
-                    const int *__restrict__ bcls, T *__restrict__ u, const T *__restrict__ b)
+                    const int *__restrict__ bcls, T *__restrict__ u, const T *__restrict__ b, BatchRef bt)
 {
     constexpr int W = 2 * P + 1, SS = S * S, R = (S - 1) / 2;
     constexpr int BPC = 256 / SS;   // Schwarz blocks per CTA
     __shared__ T rs[BPC * SS];
+    if (bt.active && !bt.active[blockIdx.y]) return;
+    u += blockIdx.y * bt.vec;
+    b += blockIdx.y * bt.vec;
     const int lb = threadIdx.x / SS, e = threadIdx.x % SS;
     const int blk = blockIdx.x * BPC + lb;
     const bool active = lb < BPC && blk < nblocks;
@@ -183,8 +194,11 @@ __global__ void __launch_bounds__(512, sizeof(T) == sizeof(float) ? 2 : 1)
 k_schwarz_tile2d(int n, int npc, int nbc, int q, int g, int rev, int px, int py, int ntpx,
                  const T *__restrict__ stencil, const T *__restrict__ binv,
                  const double *__restrict__ binv64, int interior, T *__restrict__ u,
-                 const T *__restrict__ b)
+                 const T *__restrict__ b, BatchRef bt)
 {
+    if (bt.active && !bt.active[blockIdx.y]) return;
+    u += blockIdx.y * bt.vec;
+    b += blockIdx.y * bt.vec;
     constexpr int W = 2 * P + 1, SS = S * S, R = (S - 1) / 2, H = R + P, L = P - 1 + R;
     constexpr int SW = TT + 2 * H, BW = TT + 2 * R;
     constexpr int QMIN = S + P, NB1 = (TT + QMIN - 1) / QMIN, NBLK = NB1 * NB1;
@@ -311,10 +325,12 @@ k_schwarz_tile2d(int n, int npc, int nbc, int q, int g, int rev, int px, int py,
 template <typename T>
 __global__ void k_restrict_x(int n, int nc, int wr, const T *__restrict__ Rb,
                              const int *__restrict__ Rlo, const T *__restrict__ d,
-                             T *__restrict__ t)
+                             T *__restrict__ t, BatchRef bt)
 {
     const int I = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
-    if (I >= nc) return;
+    if (I >= nc || (bt.active && !bt.active[blockIdx.z])) return;
+    d += blockIdx.z * bt.vec;
+    t += blockIdx.z * bt.aux;
     const int lo = Rlo[I];
     const T *row = d + (size_t)j * n;
     T acc = T(0);
@@ -329,10 +345,12 @@ __global__ void k_restrict_x(int n, int nc, int wr, const T *__restrict__ Rb,
 template <typename T>
 __global__ void k_restrict_y(int n, int nc, int wr, const T *__restrict__ Rb,
                              const int *__restrict__ Rlo, const T *__restrict__ t,
-                             T *__restrict__ dc)
+                             T *__restrict__ dc, BatchRef bt)
 {
     const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y;
-    if (I >= nc) return;
+    if (I >= nc || (bt.active && !bt.active[blockIdx.z])) return;
+    t += blockIdx.z * bt.aux;
+    dc += blockIdx.z * bt.crs;
     const int lo = Rlo[J];
     T acc = T(0);
     for (int w = 0; w < wr; ++w) {
@@ -346,10 +364,12 @@ __global__ void k_restrict_y(int n, int nc, int wr, const T *__restrict__ Rb,
 template <typename T>
 __global__ void k_prolong_x(int n, int nc, int wc, const T *__restrict__ Cb,
                             const int *__restrict__ Clo, const T *__restrict__ ec,
-                            T *__restrict__ t2)
+                            T *__restrict__ t2, BatchRef bt)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y;
-    if (i >= n) return;
+    if (i >= n || (bt.active && !bt.active[blockIdx.z])) return;
+    ec += blockIdx.z * bt.crs;
+    t2 += blockIdx.z * bt.aux;
     const int lo = Clo[i];
     T acc = T(0);
     for (int w = 0; w < wc; ++w) {
@@ -364,10 +384,13 @@ __global__ void k_prolong_x(int n, int nc, int wc, const T *__restrict__ Cb,
 template <typename T, typename TU>
 __global__ void k_prolong_y(int n, int nc, int wc, const T *__restrict__ Cb,
                             const int *__restrict__ Clo, const T *__restrict__ t2,
-                            const T *__restrict__ delta, TU *__restrict__ u)
+                            const T *__restrict__ delta, TU *__restrict__ u, BatchRef bt)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
-    if (i >= n) return;
+    if (i >= n || (bt.active && !bt.active[blockIdx.z])) return;
+    t2 += blockIdx.z * bt.aux;
+    if (delta) delta += blockIdx.z * bt.vec;
+    u += blockIdx.z * bt.vec;
     const int lo = Clo[j];
     T acc = T(0);
     for (int w = 0; w < wc; ++w) {
@@ -382,11 +405,13 @@ __global__ void k_prolong_y(int n, int nc, int wc, const T *__restrict__ Cb,
 // b[j][i] = sum_b M[j][b] sum_a M[i][a] f[j+b-p][i+a-p]
 template <int P>
 __global__ void k_mass2d(int n, const double *__restrict__ Mb, const double *__restrict__ f,
-                         double *__restrict__ b)
+                         double *__restrict__ b, long long vec)
 {
     constexpr int W = 2 * P + 1;
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
     if (i >= n) return;
+    f += blockIdx.z * vec;
+    b += blockIdx.z * vec;
     double acc = 0.0;
     for (int bb = 0; bb < W; ++bb) {
         const int jj = j + bb - P;
@@ -405,8 +430,9 @@ template <int P, typename T, typename TO>
 cudaError_t residual_p(const Solver &S, const T *stencil, const T *u, const T *b, TO *d, double *part,
                        cudaStream_t st)
 {
-    dim3 blk(kResTX, kResTY), grd((S.n + kResTX - 1) / kResTX, (S.n + kResTY - 1) / kResTY);
-    k_residual2d<P, T, TO><<<grd, blk, 0, st>>>(S.n, S.ht.npc, stencil, S.pcls, u, b, d, part);
+    dim3 blk(kResTX, kResTY), grd((S.n + kResTX - 1) / kResTX, (S.n + kResTY - 1) / kResTY, S.nbatch);
+    k_residual2d<P, T, TO><<<grd, blk, 0, st>>>(S.n, S.ht.npc, stencil, S.pcls, u, b, d, part,
+                                                 BatchRef{S.active, S.N, residual_partials(S), 0});
     count_launches(1);
     return cudaGetLastError();
 }
@@ -439,9 +465,9 @@ cudaError_t schwarz_lattice_p(const Solver &S, const T *stencil, const T *binv, 
         const int nblocks = nbx * nby;
         if (nblocks <= 0) continue;
         const int grid = (nblocks + BPC - 1) / BPC;
-        k_schwarz_lattice2d<P, SB, T><<<grid, 256, 0, st>>>(S.n, S.ht.npc, S.ht.nbc, q, ox, oy, nbx,
+        k_schwarz_lattice2d<P, SB, T><<<dim3(grid, S.nbatch), 256, 0, st>>>(S.n, S.ht.npc, S.ht.nbc, q, ox, oy, nbx,
                                                              nblocks, stencil, S.pcls, binv, S.binv,
-                                                             interior, S.bcls, u, b);
+                                                             interior, S.bcls, u, b, BatchRef{S.active, S.N, 0, 0});
         count_launches(1);
         cudaError_t err = cudaGetLastError();
         if (err != cudaSuccess) return err;
@@ -461,9 +487,10 @@ cudaError_t schwarz_tile_p(const Solver &S, const T *stencil, const T *binv, T *
         const int px = ph & 1, py = ph >> 1;
         const int ntpx = (nt - px + 1) / 2, ntpy = (nt - py + 1) / 2;
         if (ntpx <= 0 || ntpy <= 0) continue;
-        k_schwarz_tile2d<P, SB, TT, T><<<ntpx * ntpy, 512, 0, st>>>(S.n, S.ht.npc, S.ht.nbc, S.q, S.g,
+        k_schwarz_tile2d<P, SB, TT, T><<<dim3(ntpx * ntpy, S.nbatch), 512, 0, st>>>(S.n, S.ht.npc, S.ht.nbc, S.q, S.g,
                                                                      reverse ? 1 : 0, px, py, ntpx, stencil,
-                                                                     binv, S.binv, interior, u, b);
+                                                                     binv, S.binv, interior, u, b,
+                                                                     BatchRef{S.active, S.N, 0, 0});
         count_launches(1);
         cudaError_t err = cudaGetLastError();
         if (err != cudaSuccess) return err;
@@ -500,9 +527,10 @@ template <typename T>
 cudaError_t restrict_any(const Solver &S, const T *Rb, const T *d, T *t, T *dc, cudaStream_t st)
 {
     const int nc = S.nc, n = S.n;
-    k_restrict_x<T><<<dim3((nc + 127) / 128, n), 128, 0, st>>>(n, nc, S.ht.wr, Rb, S.Rlo, d, t);
+    const BatchRef bt{S.active, S.N, (long long)n * nc, S.Nc};
+    k_restrict_x<T><<<dim3((nc + 127) / 128, n, S.nbatch), 128, 0, st>>>(n, nc, S.ht.wr, Rb, S.Rlo, d, t, bt);
     count_launches(1);
-    k_restrict_y<T><<<dim3((nc + 127) / 128, nc), 128, 0, st>>>(n, nc, S.ht.wr, Rb, S.Rlo, t, dc);
+    k_restrict_y<T><<<dim3((nc + 127) / 128, nc, S.nbatch), 128, 0, st>>>(n, nc, S.ht.wr, Rb, S.Rlo, t, dc, bt);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -512,9 +540,10 @@ cudaError_t prolong_any(const Solver &S, const T *Cb, const T *ec, T *t2, const 
                         cudaStream_t st)
 {
     const int nc = S.nc, n = S.n;
-    k_prolong_x<T><<<dim3((n + 127) / 128, nc), 128, 0, st>>>(n, nc, S.ht.wc, Cb, S.Clo, ec, t2);
+    const BatchRef bt{S.active, S.N, (long long)n * nc, S.Nc};
+    k_prolong_x<T><<<dim3((n + 127) / 128, nc, S.nbatch), 128, 0, st>>>(n, nc, S.ht.wc, Cb, S.Clo, ec, t2, bt);
     count_launches(1);
-    k_prolong_y<T, TU><<<dim3((n + 127) / 128, n), 128, 0, st>>>(n, nc, S.ht.wc, Cb, S.Clo, t2, delta, u);
+    k_prolong_y<T, TU><<<dim3((n + 127) / 128, n, S.nbatch), 128, 0, st>>>(n, nc, S.ht.wc, Cb, S.Clo, t2, delta, u, bt);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -561,7 +590,7 @@ cudaError_t launch_apply_A(const Solver &S, const double *u, double *y, cudaStre
 
 cudaError_t launch_norm_finish(const Solver &S, const double *part, double *out, cudaStream_t st)
 {
-    k_sum_partials<<<1, 1024, 0, st>>>(part, residual_partials(S), out);
+    k_sum_partials<<<S.nbatch, 1024, 0, st>>>(part, residual_partials(S), out);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -585,6 +614,57 @@ cudaError_t launch_prolong_add(const Solver &S, const double *ec, double *u, cud
     return prolong_any<double, double>(S, S.Cb, ec, S.t2, nullptr, u, st);
 }
 
+// ---- batch control -----------------------------------------------------------------
+
+// start of a batched solve: problems with a zero initial residual are done at once
+__global__ void k_batch_init(int nb, const double *__restrict__ norm2, double *__restrict__ norm0,
+                             int *__restrict__ active, int *__restrict__ cycles, double *__restrict__ relres)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nb) return;
+    norm0[k] = norm2[k];
+    active[k] = norm2[k] > 0.0 ? 1 : 0;
+    cycles[k] = 0;
+    relres[k] = 0.0;
+}
+
+// after a cycle: count it for every active problem and retire those at the tolerance;
+// count[0] = number of problems still active (nonfinite norms retire with relres = nan)
+__global__ void k_batch_check(int nb, double tol, const double *__restrict__ norm2, const double *__restrict__ norm0,
+                              int *__restrict__ active, int *__restrict__ cycles, double *__restrict__ relres,
+                              int *__restrict__ count)
+{
+    __shared__ int act;
+    if (threadIdx.x == 0) act = 0;
+    __syncthreads();
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+        if (!active[k]) continue;
+        cycles[k] += 1;
+        const double rel = sqrt(norm2[k] / norm0[k]);
+        relres[k] = rel;
+        if (rel <= tol || !(rel == rel)) active[k] = 0;
+        else atomicAdd(&act, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) count[0] = act;
+}
+
+cudaError_t launch_batch_init(const Solver &S, const double *norm2, double *norm0, int *cycles, double *relres,
+                              cudaStream_t st)
+{
+    k_batch_init<<<(S.nbatch + 127) / 128, 128, 0, st>>>(S.nbatch, norm2, norm0, S.active, cycles, relres);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_check(const Solver &S, double tol, const double *norm2, const double *norm0, int *cycles,
+                               double *relres, int *count, cudaStream_t st)
+{
+    k_batch_check<<<1, 256, 0, st>>>(S.nbatch, tol, norm2, norm0, S.active, cycles, relres, count);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 // ---- mixed precision -------------------------------------------------------------
 
 cudaError_t launch_outer_residual(const Solver &S, const double *u, const double *b, float *r32,
@@ -598,7 +678,7 @@ cudaError_t launch_inner_fine(const Solver &S, const float *r32, bool reverse, c
 {
     if (S.dim == 3) return launch3d_inner_fine(S, r32, st);
     const MixedState &X = S.mx;
-    cudaError_t e = cudaMemsetAsync(X.delta, 0, sizeof(float) * S.N, st);
+    cudaError_t e = cudaMemsetAsync(X.delta, 0, sizeof(float) * S.N * S.nbatch, st);
     if (e == cudaSuccess) e = schwarz_any<float>(S, X.stencil, X.binv, X.delta, r32, reverse, st);
     if (e == cudaSuccess) e = residual_any<float, float>(S, X.stencil, X.delta, r32, X.d, nullptr, st);
     if (e == cudaSuccess) e = restrict_any<float>(S, X.Rb, X.d, X.t, X.dc, st);
@@ -615,12 +695,12 @@ cudaError_t launch_inner_update(const Solver &S, double *u, cudaStream_t st)
 cudaError_t launch_mass2(const Solver &S, const double *f, double *b, cudaStream_t st)
 {
     if (S.dim == 3) return launch3d_mass(S, f, b, st);
-    dim3 grd((S.n + 127) / 128, S.n);
+    dim3 grd((S.n + 127) / 128, S.n, S.nbatch);
     switch (S.p) {
-    case 2: k_mass2d<2><<<grd, 128, 0, st>>>(S.n, S.Mb, f, b); break;
-    case 3: k_mass2d<3><<<grd, 128, 0, st>>>(S.n, S.Mb, f, b); break;
-    case 4: k_mass2d<4><<<grd, 128, 0, st>>>(S.n, S.Mb, f, b); break;
-    case 5: k_mass2d<5><<<grd, 128, 0, st>>>(S.n, S.Mb, f, b); break;
+    case 2: k_mass2d<2><<<grd, 128, 0, st>>>(S.n, S.Mb, f, b, S.N); break;
+    case 3: k_mass2d<3><<<grd, 128, 0, st>>>(S.n, S.Mb, f, b, S.N); break;
+    case 4: k_mass2d<4><<<grd, 128, 0, st>>>(S.n, S.Mb, f, b, S.N); break;
+    case 5: k_mass2d<5><<<grd, 128, 0, st>>>(S.n, S.Mb, f, b, S.N); break;
     default: return cudaErrorInvalidValue;
     }
     count_launches(1);

@@ -30,6 +30,7 @@ EXPORTS = (
     "iga2l_host_bands", "iga2l_host_restriction", "iga2l_destroy", "iga2l_strerror",
     "iga2l_last_error", "iga2l_kernel_launches", "iga2l_residual_norm2_noalloc",
     "iga2l_cycles", "iga2l_unrolled_backward", "iga2l_bump_load", "iga2l_bump_grad",
+    "iga2l_assemble_batch", "iga2l_solve_batch",
 )
 
 
@@ -92,6 +93,9 @@ def load(build_if_missing: bool = True):
             "iga2l_last_error": (ctypes.c_char_p, []),
             "iga2l_kernel_launches": (ctypes.c_longlong, []),
             "iga2l_cycles": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp]),
+            "iga2l_assemble_batch": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                    ctypes.POINTER(Options), ctypes.POINTER(_vp)]),
+            "iga2l_solve_batch": (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.c_int, _vp, _ip, _dp, _vp]),
             "iga2l_unrolled_backward": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, _vp]),
             "iga2l_bump_load": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_double, _vp, _vp]),
             "iga2l_bump_grad": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_double, _vp, _vp, _vp]),
@@ -173,19 +177,24 @@ def residual_norm2_noalloc(p, n, Kb, Mb, u, b, d, norm2, stream=None):
 
 
 class Solver:
-    """Handle of one assembled problem (degree p, m elements per axis, dimension dim)."""
+    """Handle of one assembled problem (degree p, m elements per axis, dimension dim),
+    or with nbatch > 1 of a batch of 2D problems sharing (p, m, options)."""
 
-    def __init__(self, p: int, m: int, dim: int = 2, **options):
+    def __init__(self, p: int, m: int, dim: int = 2, nbatch: int = 1, batch: bool = False, **options):
         self._lib = load()
         self.options = default_options(**options)
         h = _vp()
-        _check(self._lib.iga2l_assemble(p, m, dim, ctypes.byref(self.options), ctypes.byref(h)))
+        if nbatch > 1 or batch:
+            _check(self._lib.iga2l_assemble_batch(p, m, nbatch, ctypes.byref(self.options), ctypes.byref(h)))
+        else:
+            _check(self._lib.iga2l_assemble(p, m, dim, ctypes.byref(self.options), ctypes.byref(h)))
         self._h = h
-        self.p, self.m, self.dim = p, m, dim
+        self.p, self.m, self.dim, self.nbatch = p, m, dim, nbatch
         nt, na, nct, nca = ctypes.c_longlong(), ctypes.c_int(), ctypes.c_longlong(), ctypes.c_int()
         _check(self._lib.iga2l_num_dofs(h, ctypes.byref(nt), ctypes.byref(na), ctypes.byref(nct),
                                         ctypes.byref(nca)))
         self.N, self.n, self.Nc, self.nc = nt.value, na.value, nct.value, nca.value
+        self.NB, self.NcB = self.N * nbatch, self.Nc * nbatch   # vector lengths seen by the ABI
 
     def close(self):
         if getattr(self, "_h", None):
@@ -200,38 +209,38 @@ class Solver:
 
     # --- single steps -------------------------------------------------------
     def apply_A(self, u, y, stream=None):
-        _check(self._lib.iga2l_apply_A(self._h, _ptr(u, numel=self.N), _ptr(y, numel=self.N),
+        _check(self._lib.iga2l_apply_A(self._h, _ptr(u, numel=self.NB), _ptr(y, numel=self.NB),
                                        _stream(stream)))
 
     def residual(self, u, b, d=None, want_norm=False, stream=None):
         nrm = ctypes.c_double(0.0)
-        _check(self._lib.iga2l_residual(self._h, _ptr(u, numel=self.N), _ptr(b, numel=self.N),
-                                        _ptr(d, numel=self.N) if d is not None else None,
+        _check(self._lib.iga2l_residual(self._h, _ptr(u, numel=self.NB), _ptr(b, numel=self.NB),
+                                        _ptr(d, numel=self.NB) if d is not None else None,
                                         ctypes.byref(nrm) if want_norm else None, _stream(stream)))
         return nrm.value if want_norm else None
 
     def schwarz_sweep(self, u, b, reverse=False, stream=None):
         fn = self._lib.iga2l_schwarz_sweep_reverse if reverse else self._lib.iga2l_schwarz_sweep
-        _check(fn(self._h, _ptr(u, numel=self.N), _ptr(b, numel=self.N), _stream(stream)))
+        _check(fn(self._h, _ptr(u, numel=self.NB), _ptr(b, numel=self.NB), _stream(stream)))
 
     def restrict(self, d, dc, stream=None):
-        _check(self._lib.iga2l_restrict(self._h, _ptr(d, numel=self.N), _ptr(dc, numel=self.Nc),
+        _check(self._lib.iga2l_restrict(self._h, _ptr(d, numel=self.NB), _ptr(dc, numel=self.NcB),
                                         _stream(stream)))
 
     def prolong_add(self, ec, u, stream=None):
-        _check(self._lib.iga2l_prolong_add(self._h, _ptr(ec, numel=self.Nc), _ptr(u, numel=self.N),
+        _check(self._lib.iga2l_prolong_add(self._h, _ptr(ec, numel=self.NcB), _ptr(u, numel=self.NB),
                                            _stream(stream)))
 
     def coarse_solve(self, dc, ec, stream=None):
-        _check(self._lib.iga2l_coarse_solve(self._h, _ptr(dc, numel=self.Nc), _ptr(ec, numel=self.Nc),
+        _check(self._lib.iga2l_coarse_solve(self._h, _ptr(dc, numel=self.NcB), _ptr(ec, numel=self.NcB),
                                             _stream(stream)))
 
     def cycle(self, u, b, adjoint=False, stream=None):
         fn = self._lib.iga2l_cycle_adjoint if adjoint else self._lib.iga2l_cycle
-        _check(fn(self._h, _ptr(u, numel=self.N), _ptr(b, numel=self.N), _stream(stream)))
+        _check(fn(self._h, _ptr(u, numel=self.NB), _ptr(b, numel=self.NB), _stream(stream)))
 
     def rhs_from_coeffs(self, f, b, stream=None):
-        _check(self._lib.iga2l_rhs_from_coeffs(self._h, _ptr(f, numel=self.N), _ptr(b, numel=self.N),
+        _check(self._lib.iga2l_rhs_from_coeffs(self._h, _ptr(f, numel=self.NB), _ptr(b, numel=self.NB),
                                                _stream(stream)))
 
     # --- solves -------------------------------------------------------------
@@ -254,8 +263,18 @@ class Solver:
                     allow_not_converged=True)
         return cyc.value, rel.value, rc == OK
 
+    def solve_batch(self, b, u, tol=1e-8, max_cycles=0, stream=None):
+        """All problems of a batch handle to tol; returns (cycles[], relres[], converged)."""
+        nb = self.nbatch
+        cyc = (ctypes.c_int * nb)()
+        rel = np.zeros(nb)
+        rc = _check(self._lib.iga2l_solve_batch(self._h, _ptr(b, numel=nb * self.N), float(tol), int(max_cycles),
+                                                _ptr(u, numel=nb * self.N), cyc, rel.ctypes.data_as(_dp),
+                                                _stream(stream)), allow_not_converged=True)
+        return np.array(cyc[:], dtype=np.int64), rel, rc == OK
+
     def cycles(self, u, b, ncycles, stream=None):
-        _check(self._lib.iga2l_cycles(self._h, _ptr(u, numel=self.N), _ptr(b, numel=self.N), int(ncycles),
+        _check(self._lib.iga2l_cycles(self._h, _ptr(u, numel=self.NB), _ptr(b, numel=self.NB), int(ncycles),
                                       _stream(stream)))
 
     def unrolled_backward(self, ubar, ncycles, bbar, stream=None):

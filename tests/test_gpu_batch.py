@@ -1,0 +1,66 @@
+"""GPU tests of batched solves: a batch handle gives each problem exactly the iterates,
+cycle count and residual of a single solve (converged problems are masked on the
+device), in FP64 and in the mixed form; the multi-group solver of uneven (p, m)
+problems matches single solves per problem."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2009_01499_gb300 import iga2l, synth  # noqa: E402
+from paper_2009_01499_gb300.batch import BatchedSolver  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+COLOURING = {2: (5, 2), 3: (7, 2), 4: (7, 2)}
+
+
+@pytest.mark.parametrize("precision,sched", [(0, 1), (1, 2)])
+def test_batch_equals_single_solves(precision, sched):
+    p, m, nb = 3, 64, 6
+    q, g = COLOURING[p]
+    B = iga2l.Solver(p, m, nbatch=nb, period=q, stride=g, precision=precision, schedule=sched)
+    S = iga2l.Solver(p, m, period=q, stride=g, precision=precision, schedule=sched)
+    f = torch.tensor(np.concatenate([synth.coefficients(S.N, 100 + k) for k in range(nb)]), device="cuda")
+    # problem 2 gets a zero right-hand side and guess: done before any cycle
+    f[2 * S.N:3 * S.N] = 0.0
+    b = torch.empty_like(f)
+    B.rhs_from_coeffs(f, b)
+    u0 = torch.tensor(np.concatenate([synth.initial_guess(S.N, 200 + k) for k in range(nb)]), device="cuda")
+    u0[2 * S.N:3 * S.N] = 0.0
+    ub = u0.clone()
+    cyc, rel, ok = B.solve_batch(b, ub, tol=1e-8)
+    assert ok and cyc[2] == 0
+    for k in range(nb):
+        sl = slice(k * S.N, (k + 1) * S.N)
+        us = u0[sl].clone()
+        bs = b[sl].clone()
+        c1, r1, _, ok1 = S.solve(bs, us, tol=1e-8)
+        assert ok1 and c1 == cyc[k], (k, c1, cyc[k])
+        assert torch.equal(us, ub[sl]), k
+        if c1:
+            assert abs(r1 - rel[k]) <= 1e-12 * r1
+
+
+def test_uneven_groups_match_single_solves():
+    problems = [(2, 64), (3, 32), (2, 64), (4, 48), (3, 32), (2, 128), (4, 48), (3, 64)]
+    BS = BatchedSolver(problems, precision=iga2l.MIXED_FP32, autotune=True)
+    f = [torch.tensor(synth.coefficients((m + p - 2) ** 2, 300 + i), device="cuda") for i, (p, m) in enumerate(problems)]
+    u0 = [torch.tensor(synth.initial_guess((m + p - 2) ** 2, 400 + i), device="cuda") for i, (p, m) in enumerate(problems)]
+    b = BS.rhs_from_coeffs(BS.pack(f))
+    u = BS.pack(u0)
+    cycles, relres, ok = BS.solve(b, u, tol=1e-8)
+    torch.cuda.synchronize()
+    assert ok
+    ub = BS.unpack(u)
+    bb = BS.unpack(b)
+    for g in BS.groups:
+        p, m = g["p"], g["m"]
+        q, gg = COLOURING[p]
+        S = iga2l.Solver(p, m, period=q, stride=gg, precision=iga2l.MIXED_FP32, schedule=g["schedule"])
+        for i in g["members"]:
+            us = u0[i].clone()
+            c1, r1, _, ok1 = S.solve(bb[i].clone(), us, tol=1e-8)
+            assert ok1 and c1 == cycles[i] and torch.equal(us, ub[i]), (i, c1, cycles[i])
+        S.close()
+    BS.close()
