@@ -238,6 +238,84 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+
+def _time_solve(S, b, u0, u, tol, stream, flush):
+    flush.fill_(1.0)
+    u.copy_(u0)
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    c, rel, _, ok = S.solve(b, u, tol=tol)
+    e1.record(stream)
+    e1.synchronize()
+    if not ok:
+        raise RuntimeError("solve did not converge")
+    return e0.elapsed_time(e1), c
+
+
+def bench_3d(args, dev):
+    """3D Poisson, p = 3 on 128^3 elements (2.15M DOFs), FP64 and mixed, to 1e-8."""
+    import torch
+    from paper_2009_01499_gb300 import iga2l, synth
+    p, m = 3, 128
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    out = {"workload": "3D Poisson on the unit cube, p=3 on 128^3 elements (2,146,689 DOFs), seeded "
+                       "uniform[-1,1] coefficients of f, LATTICE (7,2) colouring, 3x3x3 blocks, to 1e-8"}
+    for name, prec in (("fp64", iga2l.FP64), ("mixed", iga2l.MIXED_FP32)):
+        S = iga2l.Solver(p, m, dim=3, period=7, stride=2, precision=prec)
+        f = torch.tensor(synth.coefficients(S.N, synth.BASE_SEED + 3), device=dev)
+        b = torch.empty_like(f)
+        S.rhs_from_coeffs(f, b)
+        u0 = torch.tensor(synth.initial_guess(S.N, synth.BASE_SEED + 4), device=dev)
+        u = torch.empty_like(u0)
+        _time_solve(S, b, u0, u, TOL, stream, flush)
+        runs = [_time_solve(S, b, u0, u, TOL, stream, flush) for _ in range(2)]
+        ms = min(r[0] for r in runs)
+        out[name] = {"value": S.N / (ms * 1e-3), "unit": "DOF/s", "ms": ms, "cycles": runs[-1][1]}
+        S.close()
+    out["speedup_mixed_vs_fp64"] = out["fp64"]["ms"] / out["mixed"]["ms"]
+    return out
+
+
+def bench_batched(args, dev):
+    """256 independent 2D problems, m from {64,128,256,512} and p from {2,3,4} by seed, mixed
+    precision, autotuned schedules, concurrent groups, to 1e-8."""
+    import numpy as np
+    import torch
+    from paper_2009_01499_gb300 import iga2l, synth
+    from paper_2009_01499_gb300.batch import BatchedSolver
+    nprob = 256
+    z = synth.splitmix64(synth.BASE_SEED + 4, 2 * nprob)
+    ms_choice = np.array([64, 128, 256, 512])[(z[0::2] % np.uint64(4)).astype(int)]
+    ps = np.array([2, 3, 4])[(z[1::2] % np.uint64(3)).astype(int)]
+    problems = [(int(p), int(m)) for p, m in zip(ps, ms_choice)]
+    BS = BatchedSolver(problems, precision=iga2l.MIXED_FP32, autotune=True)
+    f = [torch.tensor(synth.coefficients((m + p - 2) ** 2, 1000 + i), device=dev) for i, (p, m) in enumerate(problems)]
+    u0 = [torch.tensor(synth.initial_guess((m + p - 2) ** 2, 2000 + i), device=dev) for i, (p, m) in enumerate(problems)]
+    b = BS.rhs_from_coeffs(BS.pack(f))
+    u0p = BS.pack(u0)
+    ndofs = sum(BS.dofs)
+    times = []
+    for it in range(3):
+        u = [t.clone() for t in u0p]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        cycles, relres, ok = BS.solve(b, u, tol=TOL)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+        if not ok:
+            raise RuntimeError("batched solve did not converge")
+    sec = min(times[1:])
+    out = {"workload": "256 independent 2D Poisson problems, m uniform in {64,128,256,512}, p uniform in "
+                       "{2,3,4} (seeded), uniform[-1,1] coefficients of f, mixed precision, to 1e-8",
+           "value": ndofs / sec, "unit": "DOF/s", "dofs": ndofs, "seconds": sec, "groups": len(BS.groups),
+           "cycles_max": int(max(cycles)), "schedules": {f"p{g['p']}m{g['m']}": ("TILE" if g["schedule"] == 2 else "LATTICE")
+                                                       for g in BS.groups},
+           "timing": "host wall clock around the whole batch (groups on concurrent streams)"}
+    BS.close()
+    return out
+
 # ---------------------------------------------------------------------------- gpu arm
 def run_gpu(args):
     import torch
@@ -367,6 +445,13 @@ def run_gpu(args):
         for S in msolv.values():
             S.close()
 
+    # secondary configurations: 3D (p = 3, 128^3, FP64 and mixed) and the batch of 256
+    # uneven 2D problems (mixed, autotuned schedules, concurrent groups)
+    extra = {}
+    if not args.no_extra:
+        extra["3d"] = bench_3d(args, dev)
+        extra["batched"] = bench_batched(args, dev)
+
     # roofline of the dominant kernel, the Schwarz colour-phase kernel (FP64 pipe bound)
     sweep_flops, sweep_ms, per_p = 0.0, 0.0, {}
     for p in DEGREES:
@@ -419,6 +504,7 @@ def run_gpu(args):
         "roofline": roofline,
         "clocks": clk,
         "mixed": mixed,
+        "other_configs": extra,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         import oracle
@@ -466,6 +552,7 @@ def main():
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision leg")
+    ap.add_argument("--no-extra", action="store_true", help="skip the 3D and batched configurations")
     ap.add_argument("--profile-step", action="store_true",
                     help="profiling aid: warm-up solves then one solve per degree, no timing")
     ap.add_argument("--profile-m", type=int, default=M_ELEM)
