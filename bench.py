@@ -407,7 +407,7 @@ def run_gpu(args):
             e2e_ms.append(tot)
     e2e_step = allmax(statistics.mean(e2e_ms), ws, dev)
 
-    # mixed precision (FP32 inner cycle, TILE(32) schedule) inside FP64 refinement, same
+    # mixed precision (FP32 inner cycle, TILE schedule) inside FP64 refinement, same
     # workload and stopping rule
     mixed = None
     if not args.no_mixed:
@@ -439,7 +439,8 @@ def run_gpu(args):
         mms = allmax(statistics.mean([mstep() for _ in range(args.steps)]), ws, dev)
         mixed = {"value": ws * ndofs / (mms * 1e-3), "unit": "DOF/s", "ms_per_step": mms,
                  "speedup_vs_fp64": ms_step / mms, "dtype": "f32 inner cycle, f64 residual/update",
-                 "schedule": "TILE(32)", "cycles": {str(p): mcyc[p] for p in DEGREES},
+                 "schedule": {str(p): f"TILE({msolv[p].tile})" for p in DEGREES},
+                 "cycles": {str(p): mcyc[p] for p in DEGREES},
                  "accuracy": "same 1e-8 FP64 residual rule; refined to 1e-12 the solution is within "
                              "1e-8 of the FP64 oracle's (tests/test_gpu_mixed.py)"}
         for S in msolv.values():

@@ -61,7 +61,7 @@ typedef struct iga2l_solver *iga2l_handle;
 typedef struct {
     int precision;   /* IGA2L_FP64 or IGA2L_MIXED_FP32 */
     int schedule;    /* IGA2L_SCHED_LATTICE or IGA2L_SCHED_TILE */
-    int tile;        /* TILE side T >= period (0 = library default, 32; only 32 is compiled) */
+    int tile;        /* TILE side T >= period (0 = the side compiled for p: 20 for p = 2, 5; 21 for p = 3, 4) */
     int period;      /* colour period q >= s + p (0 = library default for p) */
     int stride;      /* colour stride g, gcd(g, q) = 1 (0 = library default) */
     int coarse;      /* IGA2L_COARSE_VCYCLE (Section 3.2) or IGA2L_COARSE_EXACT */
@@ -110,6 +110,11 @@ int iga2l_solve_batch(iga2l_handle h, const double *b, double tol, int max_cycle
  * Any output pointer may be NULL. */
 int iga2l_num_dofs(iga2l_handle h, long long *n_total, int *n_axis,
                    long long *nc_total, int *nc_axis);
+
+/* The Schwarz schedule the handle runs (Section 3.1.1 colouring, this library's
+ * reading): schedule (IGA2L_SCHED_*), colour period q, stride g, TILE side T (0 for
+ * LATTICE) and block side s, with every default resolved.  Outputs may be NULL. */
+int iga2l_schedule_info(iga2l_handle h, int *schedule, int *period, int *stride, int *tile, int *block_side);
 
 /* y = A_p u, A_p = K(x)M + M(x)K (Section 2, tensor-product stiffness). */
 int iga2l_apply_A(iga2l_handle h, const double *u, double *y, void *stream);

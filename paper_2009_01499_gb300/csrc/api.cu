@@ -335,8 +335,8 @@ static int assemble_impl(int p, int m, int dim, int nbatch, bool batch, const ig
     if (dim == 3 && opt.schedule != IGA2L_SCHED_LATTICE)
         return fail(IGA2L_ERR_UNSUPPORTED, "3D uses the LATTICE schedule");
     if (opt.schedule == IGA2L_SCHED_TILE) {
-        if (opt.tile == 0) opt.tile = kTile;
-        if (opt.tile != kTile) return fail(IGA2L_ERR_UNSUPPORTED, "only TILE side 32 is compiled");
+        if (opt.tile == 0) opt.tile = tile_side(p);
+        if (opt.tile != tile_side(p)) return fail(IGA2L_ERR_UNSUPPORTED, "TILE side not compiled for this degree");
     }
     if (opt.coarse != IGA2L_COARSE_VCYCLE && opt.coarse != IGA2L_COARSE_EXACT)
         return fail(IGA2L_ERR_INVALID_ARG, "unknown coarse solver");
@@ -475,7 +475,12 @@ static int assemble_impl(int p, int m, int dim, int nbatch, bool batch, const ig
         // the handle's own interior class uses the same values
         double *dst = &stencil[(size_t)((2 * p - 1) * ht.npc + (2 * p - 1)) * W * W];
         for (int i = 0; i < W * W; ++i) dst[i] = sti[i];
-        if ((ce = upload_interior_stencil(p, sti.data(), W * W)) != cudaSuccess) {
+        std::vector<double> k1(W), m1(W);
+        for (int a = 0; a < W; ++a) {
+            k1[a] = ref.Kb[(size_t)xr * W + a] / mref;   // h K_row, h = 1 / mref
+            m1[a] = ref.Mb[(size_t)xr * W + a] * mref;   // M_row / h
+        }
+        if ((ce = upload_interior_stencil(p, sti.data(), W * W, k1.data(), m1.data())) != cudaSuccess) {
             release(S);
             return cuda_fail(ce, "constant stencil upload");
         }
@@ -661,6 +666,17 @@ int iga2l_num_dofs(iga2l_handle h, long long *n_total, int *n_axis, long long *n
     if (n_axis) *n_axis = h->n;
     if (nc_total) *nc_total = h->Nc;
     if (nc_axis) *nc_axis = h->nc;
+    return IGA2L_OK;
+}
+
+int iga2l_schedule_info(iga2l_handle h, int *schedule, int *period, int *stride, int *tile, int *block_side)
+{
+    if (!h) return fail(IGA2L_ERR_INVALID_ARG, "null handle");
+    if (schedule) *schedule = h->opt.schedule;
+    if (period) *period = h->q;
+    if (stride) *stride = h->g;
+    if (tile) *tile = h->opt.schedule == IGA2L_SCHED_TILE ? h->tile : 0;
+    if (block_side) *block_side = h->s;
     return IGA2L_OK;
 }
 

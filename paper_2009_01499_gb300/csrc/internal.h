@@ -12,7 +12,9 @@ namespace iga2l {
 
 constexpr int kMaxP = 5;       // degrees with compiled kernels: 2..5
 constexpr int kMaxLevels = 24;
-constexpr int kTile = 32;       // side of the TILE schedule's tiles (block centres)
+// Side of the TILE schedule's tiles (block centres) compiled for degree p: a multiple
+// of the default colour period, at least 2R + P + 1 so tiles of one phase never interact.
+constexpr int tile_side(int p) { return p == 2 ? 20 : (p == 5 ? 20 : 21); }
 
 // Batch addressing passed to 2D kernels: problem z of a batch owns vec (fine vector),
 // aux (scratch) and crs (second-level vector) entries starting at z * stride; problems
@@ -162,8 +164,8 @@ cudaError_t launch3d_outer_residual(const Solver &S, const double *u, const doub
 cudaError_t launch3d_inner_fine(const Solver &S, const float *r32, cudaStream_t st);
 cudaError_t launch3d_inner_coarse(const Solver &S, cudaStream_t st);
 cudaError_t launch3d_inner_update(const Solver &S, double *u, cudaStream_t st);
-// Interior 2D residual stencil of degree p (h-independent) into constant memory; written
-// once per device and degree.
-cudaError_t upload_interior_stencil(int p, const double *st64, int count);
+// Interior 2D residual stencil of degree p and the interior 1D rows k = h K_row,
+// m = M_row / h (all h-independent) into constant memory; written once per device and degree.
+cudaError_t upload_interior_stencil(int p, const double *st64, int count, const double *k1, const double *m1);
 
 }  // namespace iga2l

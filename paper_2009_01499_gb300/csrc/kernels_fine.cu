@@ -177,145 +177,287 @@ __device__ __forceinline__ double cst<double>(int p, int i) { return c_stencil64
 template <>
 __device__ __forceinline__ float cst<float>(int p, int i) { return c_stencil32[p][i]; }
 
+// Interior rows of the 1D stiffness and mass matrices, scaled to be independent of h
+// (k = h K_row, m = M_row / h): the interior 2D coefficient K_y[b] M_x[a] + M_y[b] K_x[a]
+// equals k[b] m[a] + m[b] k[a].  Written with the 2D stencil, once per device and degree.
+__constant__ double c_k1d[kMaxP + 1][2 * kMaxP + 1], c_m1d[kMaxP + 1][2 * kMaxP + 1];
+__constant__ float c_k1f[kMaxP + 1][2 * kMaxP + 1], c_m1f[kMaxP + 1][2 * kMaxP + 1];
+
+template <typename T>
+__device__ __forceinline__ T ck1(int p, int a);
+template <typename T>
+__device__ __forceinline__ T cm1(int p, int a);
+template <>
+__device__ __forceinline__ double ck1<double>(int p, int a) { return c_k1d[p][a]; }
+template <>
+__device__ __forceinline__ float ck1<float>(int p, int a) { return c_k1f[p][a]; }
+template <>
+__device__ __forceinline__ double cm1<double>(int p, int a) { return c_m1d[p][a]; }
+template <>
+__device__ __forceinline__ float cm1<float>(int p, int a) { return c_m1f[p][a]; }
+
+// Geometry of one CTA of the TILE(TT) schedule.
+template <int P, int S, int TT>
+struct TileGeom {
+    static constexpr int W = 2 * P + 1, SS = S * S, R = (S - 1) / 2, H = R + P;
+    static constexpr int SW = TT + 2 * H;                  // staged u: tile + halo R + P
+    static constexpr int BW = TT + 2 * R;                  // staged b / rows a tile's blocks cover
+    static constexpr int NB1 = (TT + S + P - 1) / (S + P);  // blocks per axis of one colour (q >= S+P)
+    static constexpr int NBLK = NB1 * NB1;
+    static constexpr int BPW = 32 / SS;                    // blocks per warp (SS lanes each)
+    static constexpr int NWARP = (NBLK + BPW - 1) / BPW, NT = 32 * NWARP;
+    static constexpr int WIN = S + 2 * P;                  // window columns (and rows) of a block
+    // y sums of a block: 2 S rows (K_y, M_y) of YS entries; YS and the block stride YB
+    // keep the x pass's reads of the lanes of one warp in distinct banks
+    static constexpr int YS = S == 5 ? 19 : 11, YB = S == 5 ? 2 * S * YS : 67;
+    static constexpr int RSS = (SS + 3) / 4 * 4;           // residual stride (16-byte loads)
+    // resident CTAs per SM the register allocation must allow (FP32: a 1024^2 tile phase
+    // in one wave; FP64 keeps its registers)
+    template <typename T>
+    static constexpr int minb() { return sizeof(T) == sizeof(double) ? 1 : (NT >= 128 ? 5 : 4); }
+};
+
+// Stages a (tile-local, zero outside the grid) window into shared memory with all loads
+// of a thread issued before its stores.
+template <int NT, int ROWLEN, int NELEM, typename T>
+__device__ __forceinline__ void stage_window(T *dst, const T *__restrict__ src, int n, int gx0, int gy0, int tid)
+{
+    constexpr int K = (NELEM + NT - 1) / NT;
+    T v[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int i = tid + k * NT;
+        const int gx = gx0 + i % ROWLEN, gy = gy0 + i / ROWLEN;
+        v[k] = (i < NELEM && gx >= 0 && gx < n && gy >= 0 && gy < n) ? src[(size_t)gy * n + gx] : T(0);
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int i = tid + k * NT;
+        if (i < NELEM) dst[i] = v[k];
+    }
+}
+
+// out[0 .. N) = p[0 .. N) with 16-byte shared-memory loads (p 16-byte aligned, N % (16/sizeof(T)) == 0)
+template <int N>
+__device__ __forceinline__ void load16(const float *p, float *out)
+{
+#pragma unroll
+    for (int k = 0; k < N / 4; ++k) {
+        const float4 v = reinterpret_cast<const float4 *>(p)[k];
+        out[4 * k] = v.x; out[4 * k + 1] = v.y; out[4 * k + 2] = v.z; out[4 * k + 3] = v.w;
+    }
+}
+template <int N>
+__device__ __forceinline__ void load16(const double *p, double *out)
+{
+#pragma unroll
+    for (int k = 0; k < N / 2; ++k) {
+        const double2 v = reinterpret_cast<const double2 *>(p)[k];
+        out[2 * k] = v.x; out[2 * k + 1] = v.y;
+    }
+}
+
+// y pass of one block: for window column col (tile-local x = cxl - R - P + col) the
+// column slice rows cyl .. cyl + WIN - 1 of the staged u, then for every block row r
+//   Y1[r][col] = sum_b K_y[b] u(col, row r + b - P),  Y2[r][col] = the same with M_y.
+// FAST: interior rows (constant 1D rows); else the rows' own 1D rows (ky, my tables).
+template <int P, int S, int TT, bool FAST, typename T>
+__device__ __forceinline__ void tile_ypass(const T *su, int cxl, int cyl, int lane_e, T *yb,
+                                           const T *k1y, const T *m1y)
+{
+    using G = TileGeom<P, S, TT>;
+    constexpr int W = G::W, WIN = G::WIN, SW = G::SW;
+    for (int col = lane_e; col < WIN; col += G::SS) {
+        if (FAST) {
+            T v[WIN];
+#pragma unroll
+            for (int k = 0; k < WIN; ++k) v[k] = su[(cyl + k) * SW + cxl + col];
+#pragma unroll
+            for (int r = 0; r < S; ++r) {
+                T y1 = T(0), y2 = T(0);
+#pragma unroll
+                for (int bb = 0; bb < W; ++bb) {
+                    y1 = fma(ck1<T>(P, bb), v[r + bb], y1);
+                    y2 = fma(cm1<T>(P, bb), v[r + bb], y2);
+                }
+                yb[r * G::YS + col] = y1;
+                yb[(S + r) * G::YS + col] = y2;
+            }
+        } else {
+            // boundary tiles: per-row coefficients, u read from shared memory directly
+#pragma unroll 1
+            for (int r = 0; r < S; ++r) {
+                const T *kr = k1y + (cyl + r) * W, *mr = m1y + (cyl + r) * W;
+                const T *uc = su + (cyl + r) * SW + cxl + col;
+                T y1 = T(0), y2 = T(0);
+#pragma unroll
+                for (int bb = 0; bb < W; ++bb) {
+                    const T v = uc[bb * SW];
+                    y1 = fma(kr[bb], v, y1);
+                    y2 = fma(mr[bb], v, y2);
+                }
+                yb[r * G::YS + col] = y1;
+                yb[(S + r) * G::YS + col] = y2;
+            }
+        }
+    }
+}
+
+// x pass of one output (ey, ex) of a block: sum_a M_x[a] Y1[ey][ex + a] + K_x[a] Y2[ey][ex + a]
+template <int P, int S, int TT, bool FAST, typename T>
+__device__ __forceinline__ T tile_xpass(const T *yb, int ey, int ex, int xrow, const T *k1x, const T *m1x)
+{
+    using G = TileGeom<P, S, TT>;
+    constexpr int W = G::W;
+    const T *y1 = yb + ey * G::YS + ex, *y2 = y1 + S * G::YS;
+    T s0 = T(0), s1 = T(0);
+#pragma unroll
+    for (int a = 0; a < W; ++a) {
+        s0 = fma(FAST ? cm1<T>(P, a) : m1x[xrow * W + a], y1[a], s0);
+        s1 = fma(FAST ? ck1<T>(P, a) : k1x[xrow * W + a], y2[a], s1);
+    }
+    return s0 + s1;
+}
+
 // One tile phase of the TILE(TT) schedule: tiles (tx, ty) with tx = px, px+2, ... and
 // ty = py, py+2, ...; each CTA runs all q^2 lattice colours of its tile in order
-// (anchored at the tile origin), with u (tile + halo R+P) and b (tile + halo R) staged
-// in shared memory, then writes back the DOFs its blocks can change (tile + halo R).
-// Tiles of one phase are at least TT >= q apart: none reads what another writes.
+// (anchored at the tile origin) with u (tile + halo R+P) and b (tile + halo R) staged in
+// shared memory, then writes back the DOFs its blocks can change (tile + halo R).  Tiles
+// of one phase are 2 TT apart with TT >= 2R + P: none reads what another writes.
 //
-// Thread roles are fixed for all colours: a colour has at most NB1 x NB1 blocks in a
-// tile (NB1 = ceil(TT / (S+P)), since q >= S+P), and thread (block slot, entry)
-// computes that entry's residual (one accumulator per stencil row) and then applies
-// the matching row of the block inverse.  Tiles whose blocks and stencil rows are all interior (almost
-// all) take a path without bounds or class checks, with the interior stencil as
-// compile-time-indexed constant operands and the interior inverse in shared memory.
+// Thread (block slot, entry e) owns one DOF of one Schwarz block of the current colour;
+// a block's S^2 lanes sit in one warp.  The residual uses the y-then-x sum factorisation
+//   (A u)(x, y) = sum_b K_y[b] sum_a M_x[a] u(x+a-P, y+b-P) + M_y[b] sum_a K_x[a] u(...),
+// shared by the block's lanes: a y pass over the window columns (each lane slides down
+// one column), a warp barrier, then each lane's x pass.  Interior tiles (almost all)
+// take the interior 1D rows from constant memory; boundary tiles the 1D rows of their
+// own rows and columns.  After a second warp barrier each lane applies row e of its
+// block's inverse (the interior row kept in registers, boundary classes in FP64) and
+// adds the result to u in shared memory.  One CTA barrier per colour.
 template <int P, int S, int TT, typename T>
-__global__ void __launch_bounds__(512, sizeof(T) == sizeof(float) ? 2 : 1)
-k_schwarz_tile2d(int n, int npc, int nbc, int q, int g, int rev, int px, int py, int ntpx,
-                 const T *__restrict__ stencil, const T *__restrict__ binv,
-                 const double *__restrict__ binv64, int interior, T *__restrict__ u,
-                 const T *__restrict__ b, BatchRef bt)
+__global__ void __launch_bounds__(TileGeom<P, S, TT>::NT, TileGeom<P, S, TT>::template minb<T>())
+k_schwarz_tile2d(int n, int nbc, int q, int g, int rev, int px, int py, int ntpx,
+                 const T *__restrict__ kband, const T *__restrict__ mband,
+                 const T *__restrict__ binv, const double *__restrict__ binv64, int interior,
+                 T *__restrict__ u, const T *__restrict__ b, BatchRef bt)
 {
+    using G = TileGeom<P, S, TT>;
+    constexpr int W = G::W, SS = G::SS, R = G::R, H = G::H, L = P - 1 + R;
+    constexpr int SW = G::SW, BW = G::BW, NB1 = G::NB1, NT = G::NT;
+    constexpr int PCI = 2 * P - 1;   // first interior row class
+    __shared__ T su[SW * SW];
+    __shared__ T sb[BW * BW];
+    __shared__ __align__(16) T rs[G::NBLK * G::RSS];
+    __shared__ T yb[G::NBLK * G::YB];
+    __shared__ T k1y[BW * W], m1y[BW * W], k1x[BW * W], m1x[BW * W];   // boundary tiles
     if (bt.active && !bt.active[blockIdx.y]) return;
     u += blockIdx.y * bt.vec;
     b += blockIdx.y * bt.vec;
-    constexpr int W = 2 * P + 1, SS = S * S, R = (S - 1) / 2, H = R + P, L = P - 1 + R;
-    constexpr int SW = TT + 2 * H, BW = TT + 2 * R;
-    constexpr int QMIN = S + P, NB1 = (TT + QMIN - 1) / QMIN, NBLK = NB1 * NB1;
-    constexpr int PCI = 2 * P - 1;   // interior point class
-    static_assert(NBLK * SS <= 512, "one solve-phase thread per block entry");
-    __shared__ T su[SW * SW];
-    __shared__ T sb[BW * BW];
-    __shared__ T rs[NBLK * SS];
-    __shared__ T sbi[SS * SS];       // interior block inverse
-    const int tid = threadIdx.x, nth = blockDim.x;
-    const int tx = px + 2 * (blockIdx.x % ntpx), ty = py + 2 * (blockIdx.x / ntpx);
-    const int x0 = tx * TT, y0 = ty * TT;
-    for (int i = tid; i < SW * SW; i += nth) {
-        const int gx = x0 - H + i % SW, gy = y0 - H + i / SW;
-        su[i] = (gx >= 0 && gx < n && gy >= 0 && gy < n) ? u[(size_t)gy * n + gx] : T(0);
-    }
-    for (int i = tid; i < BW * BW; i += nth) {
-        const int gx = x0 - R + i % BW, gy = y0 - R + i / BW;
-        sb[i] = (gx >= 0 && gx < n && gy >= 0 && gy < n) ? b[(size_t)gy * n + gx] : T(0);
-    }
-    for (int i = tid; i < SS * SS; i += nth) sbi[i] = binv[(size_t)interior * SS * SS + i];
-    __syncthreads();
+    const int tid = threadIdx.x;
+    const int x0 = (px + 2 * (blockIdx.x % ntpx)) * TT, y0 = (py + 2 * (blockIdx.x / ntpx)) * TT;
     const int tw = min(TT, n - x0), th = min(TT, n - y0);   // centres of this tile
-    // every residual row and every block of the tile interior?
     const bool fast = x0 - R >= PCI && x0 + TT - 1 + R <= n - 2 * P && y0 - R >= PCI &&
                       y0 + TT - 1 + R <= n - 2 * P;
-    // fixed roles: (block slot, entry)
-    const int blk2 = tid / SS, e2 = tid % SS, bx2 = blk2 % NB1, by2 = blk2 / NB1;
-    const int ex2 = e2 % S, ey2 = e2 / S;
-    const bool role2 = tid < NBLK * SS;
-    const int ncol = q * q;
-    for (int t = 0; t < ncol; ++t) {
-        const int c = rev ? ncol - 1 - t : t;
-        const int cq = c / q;
-        const int ox = ((c - cq * q) * g) % q, oy = (cq * g) % q;
-        // residual phase: one block entry per thread, one accumulator per stencil row
-        if (role2) {
-            const int cxl = ox + q * bx2, cyl = oy + q * by2;
-            if (cxl < tw && cyl < th) {
-                const int lx = cxl - R + ex2, ly = cyl - R + ey2;
-                T rv = T(0);
-                if (fast) {
-                    const T *w0 = su + (ly + R) * SW + (lx + R);
-                    T racc[W];
-#pragma unroll
-                    for (int bb = 0; bb < W; ++bb) {
-                        racc[bb] = T(0);
-#pragma unroll
-                        for (int aa = 0; aa < W; ++aa)
-                            racc[bb] = fma(cst<T>(P, bb * W + aa), w0[bb * SW + aa], racc[bb]);
-                    }
-                    T acc = racc[0];
-#pragma unroll
-                    for (int bb = 1; bb < W; ++bb) acc += racc[bb];
-                    rv = sb[(ly + R) * BW + (lx + R)] - acc;
-                } else {
-                    const int gx = x0 + lx, gy = y0 + ly;
-                    if (gx >= 0 && gx < n && gy >= 0 && gy < n) {
-                        const int pcx = gx < PCI ? gx : (gx > n - 2 * P ? gx - n + 4 * P - 1 : PCI);
-                        const int pcy = gy < PCI ? gy : (gy > n - 2 * P ? gy - n + 4 * P - 1 : PCI);
-                        const T *st = stencil + (size_t)(pcy * npc + pcx) * (W * W);
-                        const T *w0 = su + (ly + R) * SW + (lx + R);
-                        T racc[W];
-#pragma unroll
-                        for (int bb = 0; bb < W; ++bb) {
-                            racc[bb] = T(0);
-#pragma unroll
-                            for (int aa = 0; aa < W; ++aa)
-                                racc[bb] = fma(__ldg(&st[bb * W + aa]), w0[bb * SW + aa], racc[bb]);
-                        }
-                        T acc = racc[0];
-#pragma unroll
-                        for (int bb = 1; bb < W; ++bb) acc += racc[bb];
-                        rv = sb[(ly + R) * BW + (lx + R)] - acc;
-                    }
-                }
-                rs[tid] = rv;
-            }
+    const int lane = tid & 31, bw = lane / SS, e = lane - bw * SS;
+    const int ey = e / S, ex = e - ey * S;
+    const int slot = (tid >> 5) * G::BPW + bw;
+    const bool role = bw < G::BPW && slot < G::NBLK;
+    stage_window<NT, SW, SW * SW>(su, u, n, x0 - H, y0 - H, tid);
+    stage_window<NT, BW, BW * BW>(sb, b, n, x0 - R, y0 - R, tid);
+    if (!fast) {
+        for (int i = tid; i < BW * W; i += NT) {
+            const int row = i / W, a = i - row * W;
+            const int gx = x0 - R + row, gy = y0 - R + row;
+            const bool inx = gx >= 0 && gx < n, iny = gy >= 0 && gy < n;
+            k1x[i] = inx ? kband[(size_t)gx * W + a] : T(0);
+            m1x[i] = inx ? mband[(size_t)gx * W + a] : T(0);
+            k1y[i] = iny ? kband[(size_t)gy * W + a] : T(0);
+            m1y[i] = iny ? mband[(size_t)gy * W + a] : T(0);
         }
-        __syncthreads();
-        // solve phase: one row of the block inverse per thread
-        if (role2) {
-            const int cxl = ox + q * bx2, cyl = oy + q * by2;
-            const int lx = cxl - R + ex2, ly = cyl - R + ey2;
-            const int gx = x0 + lx, gy = y0 + ly;
-            if (cxl < tw && cyl < th && gx >= 0 && gx < n && gy >= 0 && gy < n) {
-                const T *rb = rs + blk2 * SS;
-                T *dst = su + (ly + H) * SW + (lx + H);
-                int cls = interior;
-                if (!fast) {
-                    const int ccx = x0 + cxl, ccy = y0 + cyl;
-                    const int bx = ccx < L ? ccx : (ccx > n - 1 - L ? 2 * L - (n - 1 - ccx) : L);
-                    const int by = ccy < L ? ccy : (ccy > n - 1 - L ? 2 * L - (n - 1 - ccy) : L);
-                    cls = by * nbc + bx;
-                }
-                if (cls == interior) {
-                    const T *Bi = sbi + e2 * SS;
-                    T ev = T(0);
-#pragma unroll
-                    for (int f = 0; f < SS; ++f) ev = fma(Bi[f], rb[f], ev);
-                    *dst += ev;
-                } else if (sizeof(T) == sizeof(double)) {
-                    const T *Bi = binv + ((size_t)cls * SS + e2) * SS;
-                    T ev = T(0);
-                    for (int f = 0; f < SS; ++f) ev = fma(__ldg(&Bi[f]), rb[f], ev);
-                    *dst += ev;
-                } else {
-                    const double *Bi = binv64 + ((size_t)cls * SS + e2) * SS;
-                    double ev = 0.0;
-                    for (int f = 0; f < SS; ++f) ev = fma(__ldg(&Bi[f]), (double)rb[f], ev);
-                    *dst += (T)ev;
-                }
-            }
-        }
-        __syncthreads();
     }
-    for (int i = tid; i < BW * BW; i += nth) {
+    // row e of the interior block inverse, in registers for the whole tile
+    T brow[SS];
+#pragma unroll
+    for (int f = 0; f < SS; ++f) brow[f] = role ? __ldg(&binv[((size_t)interior * SS + e) * SS + f]) : T(0);
+    __syncthreads();
+    const int bi = slot % NB1, bj = slot / NB1;
+    T *ybs = yb + slot * G::YB;
+    T *rsb = rs + slot * G::RSS;
+    const int ncol = q * q;
+    // colour c visits offsets ((c mod q) g mod q, (c div q) g mod q), advanced incrementally
+    int cxr = rev ? q - 1 : 0;
+    int ox = rev ? q - g : 0, oy = ox;
+    for (int t = 0; t < ncol; ++t) {
+        const int cxl = ox + q * bi, cyl = oy + q * bj;   // tile-local centre
+        const bool act = role && cxl < tw && cyl < th;
+        const int lx = cxl - R + ex, ly = cyl - R + ey;   // tile-local DOF of this lane
+        if (act) {
+            if (fast) tile_ypass<P, S, TT, true>(su, cxl, cyl, e, ybs, k1y, m1y);
+            else tile_ypass<P, S, TT, false>(su, cxl, cyl, e, ybs, k1y, m1y);
+        }
+        __syncwarp();
+        const int gx = x0 + lx, gy = y0 + ly;
+        const bool in = fast || (gx >= 0 && gx < n && gy >= 0 && gy < n);
+        if (act) {
+            const T acc = fast ? tile_xpass<P, S, TT, true>(ybs, ey, ex, lx + R, k1x, m1x)
+                               : tile_xpass<P, S, TT, false>(ybs, ey, ex, lx + R, k1x, m1x);
+            rsb[e] = in ? sb[(ly + R) * BW + (lx + R)] - acc : T(0);
+        }
+        __syncwarp();
+        if (act) {
+            int cls = interior;
+            if (!fast) {
+                const int ccx = x0 + cxl, ccy = y0 + cyl;
+                const int bx = ccx < L ? ccx : (ccx > n - 1 - L ? 2 * L - (n - 1 - ccx) : L);
+                const int by = ccy < L ? ccy : (ccy > n - 1 - L ? 2 * L - (n - 1 - ccy) : L);
+                cls = by * nbc + bx;
+            }
+            constexpr int VN = 16 / sizeof(T);
+            T ev = T(0);
+            if (cls == interior) {
+#pragma unroll
+                for (int k = 0; k < G::RSS / VN; ++k) {
+                    T rv[VN];
+                    load16<VN>(rsb + k * VN, rv);
+#pragma unroll
+                    for (int j = 0; j < VN; ++j)
+                        if (k * VN + j < SS) ev = fma(brow[k * VN + j], rv[j], ev);
+                }
+            } else if (sizeof(T) == sizeof(double)) {
+                const T *Bi = binv + ((size_t)cls * SS + e) * SS;
+#pragma unroll
+                for (int k = 0; k < G::RSS / VN; ++k) {
+                    T rv[VN];
+                    load16<VN>(rsb + k * VN, rv);
+#pragma unroll
+                    for (int j = 0; j < VN; ++j)
+                        if (k * VN + j < SS) ev = fma(__ldg(&Bi[k * VN + j]), rv[j], ev);
+                }
+            } else {
+                const double *Bi = binv64 + ((size_t)cls * SS + e) * SS;
+                double ed = 0.0;
+#pragma unroll
+                for (int k = 0; k < G::RSS / VN; ++k) {
+                    T rv[VN];
+                    load16<VN>(rsb + k * VN, rv);
+#pragma unroll
+                    for (int j = 0; j < VN; ++j)
+                        if (k * VN + j < SS) ed = fma(__ldg(&Bi[k * VN + j]), (double)rv[j], ed);
+                }
+                ev = (T)ed;
+            }
+            if (in) su[(ly + H) * SW + (lx + H)] += ev;
+        }
+        __syncthreads();
+        if (!rev) {
+            if (++cxr == q) { cxr = 0; ox = 0; oy += g; if (oy >= q) oy -= q; }
+            else { ox += g; if (ox >= q) ox -= q; }
+        } else {
+            if (--cxr < 0) { cxr = q - 1; ox = q - g; oy -= g; if (oy < 0) oy += q; }
+            else { ox -= g; if (ox < 0) ox += q; }
+        }
+    }
+    for (int i = tid; i < BW * BW; i += NT) {
         const int gx = x0 - R + i % BW, gy = y0 - R + i / BW;
         if (gx >= 0 && gx < n && gy >= 0 && gy < n) u[(size_t)gy * n + gx] = su[(i / BW + P) * SW + (i % BW + P)];
     }
@@ -476,10 +618,11 @@ cudaError_t schwarz_lattice_p(const Solver &S, const T *stencil, const T *binv, 
 }
 
 template <int P, int SB, typename T>
-cudaError_t schwarz_tile_p(const Solver &S, const T *stencil, const T *binv, T *u, const T *b, bool reverse,
-                           cudaStream_t st)
+cudaError_t schwarz_tile_p(const Solver &S, const T *kband, const T *mband, const T *binv, T *u, const T *b,
+                           bool reverse, cudaStream_t st)
 {
-    constexpr int TT = kTile;
+    constexpr int TT = tile_side(P);
+    using G = TileGeom<P, SB, TT>;
     const int interior = S.ht.L * S.ht.nbc + S.ht.L;
     const int nt = (S.n + TT - 1) / TT;
     for (int t = 0; t < 4; ++t) {
@@ -487,10 +630,9 @@ cudaError_t schwarz_tile_p(const Solver &S, const T *stencil, const T *binv, T *
         const int px = ph & 1, py = ph >> 1;
         const int ntpx = (nt - px + 1) / 2, ntpy = (nt - py + 1) / 2;
         if (ntpx <= 0 || ntpy <= 0) continue;
-        k_schwarz_tile2d<P, SB, TT, T><<<dim3(ntpx * ntpy, S.nbatch), 512, 0, st>>>(S.n, S.ht.npc, S.ht.nbc, S.q, S.g,
-                                                                     reverse ? 1 : 0, px, py, ntpx, stencil,
-                                                                     binv, S.binv, interior, u, b,
-                                                                     BatchRef{S.active, S.N, 0, 0});
+        k_schwarz_tile2d<P, SB, TT, T><<<dim3(ntpx * ntpy, S.nbatch), G::NT, 0, st>>>(
+            S.n, S.ht.nbc, S.q, S.g, reverse ? 1 : 0, px, py, ntpx, kband, mband, binv, S.binv, interior, u, b,
+            BatchRef{S.active, S.N, 0, 0});
         count_launches(1);
         cudaError_t err = cudaGetLastError();
         if (err != cudaSuccess) return err;
@@ -499,26 +641,27 @@ cudaError_t schwarz_tile_p(const Solver &S, const T *stencil, const T *binv, T *
 }
 
 template <int P, int SB, typename T>
-cudaError_t schwarz_p(const Solver &S, const T *stencil, const T *binv, T *u, const T *b, bool reverse,
-                      cudaStream_t st)
+cudaError_t schwarz_p(const Solver &S, const T *stencil, const T *kband, const T *mband, const T *binv, T *u,
+                      const T *b, bool reverse, cudaStream_t st)
 {
-    if (S.opt.schedule == IGA2L_SCHED_TILE) return schwarz_tile_p<P, SB, T>(S, stencil, binv, u, b, reverse, st);
+    if (S.opt.schedule == IGA2L_SCHED_TILE)
+        return schwarz_tile_p<P, SB, T>(S, kband, mband, binv, u, b, reverse, st);
     return schwarz_lattice_p<P, SB, T>(S, stencil, binv, u, b, reverse, st);
 }
 
 template <typename T>
-cudaError_t schwarz_any(const Solver &S, const T *stencil, const T *binv, T *u, const T *b, bool reverse,
-                        cudaStream_t st)
+cudaError_t schwarz_any(const Solver &S, const T *stencil, const T *kband, const T *mband, const T *binv, T *u,
+                        const T *b, bool reverse, cudaStream_t st)
 {
     if (S.s == 3) {
         switch (S.p) {
-        case 2: return schwarz_p<2, 3, T>(S, stencil, binv, u, b, reverse, st);
-        case 3: return schwarz_p<3, 3, T>(S, stencil, binv, u, b, reverse, st);
-        case 4: return schwarz_p<4, 3, T>(S, stencil, binv, u, b, reverse, st);
+        case 2: return schwarz_p<2, 3, T>(S, stencil, kband, mband, binv, u, b, reverse, st);
+        case 3: return schwarz_p<3, 3, T>(S, stencil, kband, mband, binv, u, b, reverse, st);
+        case 4: return schwarz_p<4, 3, T>(S, stencil, kband, mband, binv, u, b, reverse, st);
         default: break;
         }
     } else if (S.s == 5 && S.p == 5) {
-        return schwarz_p<5, 5, T>(S, stencil, binv, u, b, reverse, st);
+        return schwarz_p<5, 5, T>(S, stencil, kband, mband, binv, u, b, reverse, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -550,7 +693,7 @@ cudaError_t prolong_any(const Solver &S, const T *Cb, const T *ec, T *t2, const 
 
 }  // namespace
 
-cudaError_t upload_interior_stencil(int p, const double *st64, int count)
+cudaError_t upload_interior_stencil(int p, const double *st64, int count, const double *k1, const double *m1)
 {
     static std::mutex mu;
     static bool done[64][kMaxP + 1] = {};
@@ -560,12 +703,18 @@ cudaError_t upload_interior_stencil(int p, const double *st64, int count)
     std::lock_guard<std::mutex> lock(mu);
     if (dev < 0 || dev >= 64 || p < 0 || p > kMaxP) return cudaErrorInvalidValue;
     if (done[dev][p]) return cudaSuccess;
-    float st32[(2 * kMaxP + 1) * (2 * kMaxP + 1)];
+    constexpr int W1 = 2 * kMaxP + 1;
+    float st32[W1 * W1], k32[W1], m32[W1];
     for (int i = 0; i < count; ++i) st32[i] = (float)st64[i];
-    const size_t row = sizeof(double) * (2 * kMaxP + 1) * (2 * kMaxP + 1);
+    const int w = 2 * p + 1;
+    for (int i = 0; i < w; ++i) { k32[i] = (float)k1[i]; m32[i] = (float)m1[i]; }
+    const size_t row = sizeof(double) * W1 * W1;
     e = cudaMemcpyToSymbol(c_stencil64, st64, sizeof(double) * count, row * p);
-    if (e == cudaSuccess)
-        e = cudaMemcpyToSymbol(c_stencil32, st32, sizeof(float) * count, (row / 2) * p);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_stencil32, st32, sizeof(float) * count, (row / 2) * p);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_k1d, k1, sizeof(double) * w, sizeof(double) * W1 * p);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_m1d, m1, sizeof(double) * w, sizeof(double) * W1 * p);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_k1f, k32, sizeof(float) * w, sizeof(float) * W1 * p);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_m1f, m32, sizeof(float) * w, sizeof(float) * W1 * p);
     if (e == cudaSuccess) done[dev][p] = true;
     return e;
 }
@@ -599,7 +748,7 @@ cudaError_t launch_schwarz(const Solver &S, double *u, const double *b, bool rev
                            cudaStream_t st)
 {
     if (S.dim == 3) return launch3d_schwarz(S, u, b, reverse, st);
-    return schwarz_any<double>(S, S.stencil, S.binv, u, b, reverse, st);
+    return schwarz_any<double>(S, S.stencil, S.Kb, S.Mb, S.binv, u, b, reverse, st);
 }
 
 cudaError_t launch_restrict(const Solver &S, const double *d, double *dc, cudaStream_t st)
@@ -679,7 +828,7 @@ cudaError_t launch_inner_fine(const Solver &S, const float *r32, bool reverse, c
     if (S.dim == 3) return launch3d_inner_fine(S, r32, st);
     const MixedState &X = S.mx;
     cudaError_t e = cudaMemsetAsync(X.delta, 0, sizeof(float) * S.N * S.nbatch, st);
-    if (e == cudaSuccess) e = schwarz_any<float>(S, X.stencil, X.binv, X.delta, r32, reverse, st);
+    if (e == cudaSuccess) e = schwarz_any<float>(S, X.stencil, X.Kb, X.Mb, X.binv, X.delta, r32, reverse, st);
     if (e == cudaSuccess) e = residual_any<float, float>(S, X.stencil, X.delta, r32, X.d, nullptr, st);
     if (e == cudaSuccess) e = restrict_any<float>(S, X.Rb, X.d, X.t, X.dc, st);
     return e;

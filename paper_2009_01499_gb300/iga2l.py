@@ -30,7 +30,7 @@ EXPORTS = (
     "iga2l_host_bands", "iga2l_host_restriction", "iga2l_destroy", "iga2l_strerror",
     "iga2l_last_error", "iga2l_kernel_launches", "iga2l_residual_norm2_noalloc",
     "iga2l_cycles", "iga2l_unrolled_backward", "iga2l_bump_load", "iga2l_bump_grad",
-    "iga2l_assemble_batch", "iga2l_solve_batch",
+    "iga2l_assemble_batch", "iga2l_solve_batch", "iga2l_schedule_info",
 )
 
 
@@ -71,6 +71,7 @@ def load(build_if_missing: bool = True):
             "iga2l_assemble": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                               ctypes.POINTER(Options), ctypes.POINTER(_vp)]),
             "iga2l_num_dofs": (ctypes.c_int, [_vp, _llp, _ip, _llp, _ip]),
+            "iga2l_schedule_info": (ctypes.c_int, [_vp, _ip, _ip, _ip, _ip, _ip]),
             "iga2l_apply_A": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
             "iga2l_residual": (ctypes.c_int, [_vp, _vp, _vp, _vp, _dp, _vp]),
             "iga2l_schwarz_sweep": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
@@ -195,6 +196,10 @@ class Solver:
                                         ctypes.byref(nca)))
         self.N, self.n, self.Nc, self.nc = nt.value, na.value, nct.value, nca.value
         self.NB, self.NcB = self.N * nbatch, self.Nc * nbatch   # vector lengths seen by the ABI
+        sc, q, g, t, s = (ctypes.c_int() for _ in range(5))
+        _check(self._lib.iga2l_schedule_info(h, ctypes.byref(sc), ctypes.byref(q), ctypes.byref(g), ctypes.byref(t),
+                                             ctypes.byref(s)))
+        self.schedule, self.period, self.stride, self.tile, self.block_side = sc.value, q.value, g.value, t.value, s.value
 
     def close(self):
         if getattr(self, "_h", None):

@@ -25,8 +25,9 @@ def _pair(oracle_mod, p, m, coarse="vcycle", sched="lattice"):
     sg = iga2l.SCHED_TILE if sched == "tile" else iga2l.SCHED_LATTICE
     so = oracle_mod.TILE if sched == "tile" else oracle_mod.LATTICE
     S = iga2l.Solver(p, m, period=q, stride=g, coarse=cg, schedule=sg)
-    O = oracle_mod.Problem(2, p, m, sched=so, tile=32, coarse=co, period=q, stride=g)
+    O = oracle_mod.Problem(2, p, m, sched=so, tile=S.tile or 32, coarse=co, period=q, stride=g)
     assert S.N == O.N and S.Nc == O.Nc
+    assert (S.period, S.stride) == (q, g)
     return S, O
 
 
@@ -75,7 +76,7 @@ def test_schwarz_sweep(oracle_mod, p, m, reverse, sched):
     ud = _dev(u)
     S.schwarz_sweep(ud, _dev(b), reverse=reverse)
     kind = oracle_mod.TILE if sched == "tile" else oracle_mod.LATTICE
-    _, order, _ = oracle_mod.schedule(2, S.n, O.s, p, kind, 32, *COLOURING[p])
+    _, order, _ = oracle_mod.schedule(2, S.n, O.s, p, kind, S.tile or 32, *COLOURING[p])
     if reverse:
         order = order[::-1].copy()
     K, M = oracle_mod.assemble_1d(p, m)
