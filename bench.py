@@ -262,7 +262,8 @@ def bench_3d(args, dev):
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     out = {"workload": "3D Poisson on the unit cube, p=3 on 128^3 elements (2,146,689 DOFs), seeded "
                        "uniform[-1,1] coefficients of f, LATTICE (7,2) colouring, 3x3x3 blocks, to 1e-8"}
-    for name, prec in (("fp64", iga2l.FP64), ("mixed", iga2l.MIXED_FP32)):
+    for name, prec in (("fp64", iga2l.FP64), ("mixed", iga2l.MIXED_FP32),
+                       ("mixed_fp32_boundary", iga2l.MIXED_FP32_ALL)):
         S = iga2l.Solver(p, m, dim=3, period=7, stride=2, precision=prec)
         f = torch.tensor(synth.coefficients(S.N, synth.BASE_SEED + 3), device=dev)
         b = torch.empty_like(f)
@@ -275,6 +276,7 @@ def bench_3d(args, dev):
         out[name] = {"value": S.N / (ms * 1e-3), "unit": "DOF/s", "ms": ms, "cycles": runs[-1][1]}
         S.close()
     out["speedup_mixed_vs_fp64"] = out["fp64"]["ms"] / out["mixed"]["ms"]
+    out["speedup_mixed_fp32_boundary_vs_fp64"] = out["fp64"]["ms"] / out["mixed_fp32_boundary"]["ms"]
     return out
 
 
@@ -408,43 +410,50 @@ def run_gpu(args):
     e2e_step = allmax(statistics.mean(e2e_ms), ws, dev)
 
     # mixed precision (FP32 inner cycle, TILE schedule) inside FP64 refinement, same
-    # workload and stopping rule
-    mixed = None
+    # workload and stopping rule: boundary-block inverses applied in FP64 ("mixed") or
+    # in FP32 as well ("mixed_fp32_boundary")
+    mixed, mixed_all = None, None
     if not args.no_mixed:
-        msolv = {}
-        for p in DEGREES:
-            q, g = COLOURING[p]
-            msolv[p] = iga2l.Solver(p, M_ELEM, period=q, stride=g, precision=iga2l.MIXED_FP32,
-                                    schedule=iga2l.SCHED_TILE)
-        mcyc = {}
-
-        def mstep():
-            tot = 0.0
+        def run_mixed(precision, boundary):
+            msolv = {}
             for p in DEGREES:
-                flush.fill_(1.0)
-                us[p].copy_(u0s[p])
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                c, rel, _, ok = msolv[p].solve(bs[p], us[p], tol=TOL)
-                e1.record(stream)
-                e1.synchronize()
-                if not ok:
-                    raise RuntimeError(f"mixed p={p} did not converge")
-                tot += e0.elapsed_time(e1)
-                mcyc[p] = c
-            return tot
+                q, g = COLOURING[p]
+                msolv[p] = iga2l.Solver(p, M_ELEM, period=q, stride=g, precision=precision,
+                                        schedule=iga2l.SCHED_TILE)
+            mcyc = {}
 
-        for _ in range(args.warmup):
-            mstep()
-        mms = allmax(statistics.mean([mstep() for _ in range(args.steps)]), ws, dev)
-        mixed = {"value": ws * ndofs / (mms * 1e-3), "unit": "DOF/s", "ms_per_step": mms,
-                 "speedup_vs_fp64": ms_step / mms, "dtype": "f32 inner cycle, f64 residual/update",
-                 "schedule": {str(p): f"TILE({msolv[p].tile})" for p in DEGREES},
-                 "cycles": {str(p): mcyc[p] for p in DEGREES},
-                 "accuracy": "same 1e-8 FP64 residual rule; refined to 1e-12 the solution is within "
-                             "1e-8 of the FP64 oracle's (tests/test_gpu_mixed.py)"}
-        for S in msolv.values():
-            S.close()
+            def mstep():
+                tot = 0.0
+                for p in DEGREES:
+                    flush.fill_(1.0)
+                    us[p].copy_(u0s[p])
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    c, rel, _, ok = msolv[p].solve(bs[p], us[p], tol=TOL)
+                    e1.record(stream)
+                    e1.synchronize()
+                    if not ok:
+                        raise RuntimeError(f"mixed p={p} did not converge")
+                    tot += e0.elapsed_time(e1)
+                    mcyc[p] = c
+                return tot
+
+            for _ in range(args.warmup):
+                mstep()
+            mms = allmax(statistics.mean([mstep() for _ in range(args.steps)]), ws, dev)
+            out = {"value": ws * ndofs / (mms * 1e-3), "unit": "DOF/s", "ms_per_step": mms,
+                   "speedup_vs_fp64": ms_step / mms,
+                   "dtype": f"f32 inner cycle ({boundary} boundary-block inverses), f64 residual/update/coarsest",
+                   "schedule": {str(p): f"TILE({msolv[p].tile})" for p in DEGREES},
+                   "cycles": {str(p): mcyc[p] for p in DEGREES},
+                   "accuracy": "same 1e-8 FP64 residual rule; refined to 1e-12 the solution is within "
+                               "1e-8 of the FP64 oracle's (tests/test_gpu_mixed.py)"}
+            for S in msolv.values():
+                S.close()
+            return out
+
+        mixed = run_mixed(iga2l.MIXED_FP32, "f64")
+        mixed_all = run_mixed(iga2l.MIXED_FP32_ALL, "f32")
 
     # secondary configurations: 3D (p = 3, 128^3, FP64 and mixed) and the batch of 256
     # uneven 2D problems (mixed, autotuned schedules, concurrent groups)
@@ -504,7 +513,7 @@ def run_gpu(args):
         "gpu_launches": int(launches),
         "roofline": roofline,
         "clocks": clk,
-        "mixed": mixed,
+        "mixed": mixed, "mixed_fp32_boundary": mixed_all,
         "other_configs": extra,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

@@ -49,6 +49,10 @@ extern "C" {
 /* FP64 outer residual, norm and update around an FP32 inner cycle (FP32 storage
  * and FMA; FP64 boundary-block inverses and coarsest solve): iterative refinement */
 #define IGA2L_MIXED_FP32 1
+/* The same with the boundary-block inverses also applied in FP32 (the Schwarz blocks
+ * of p <= 5 have condition numbers below 5e2, so this costs the inner cycle ~3e-5
+ * relative at most, which the FP64 refinement removes; coarsest solve still FP64) */
+#define IGA2L_MIXED_FP32_ALL 2
 /* schedule: colour classes of the multiplicative Schwarz step */
 #define IGA2L_SCHED_LATTICE 1
 #define IGA2L_SCHED_TILE 2
@@ -59,7 +63,7 @@ extern "C" {
 typedef struct iga2l_solver *iga2l_handle;
 
 typedef struct {
-    int precision;   /* IGA2L_FP64 or IGA2L_MIXED_FP32 */
+    int precision;   /* IGA2L_FP64, IGA2L_MIXED_FP32 or IGA2L_MIXED_FP32_ALL */
     int schedule;    /* IGA2L_SCHED_LATTICE or IGA2L_SCHED_TILE */
     int tile;        /* TILE side T >= period (0 = the side compiled for p: 20 for p = 2, 5; 21 for p = 3, 4) */
     int period;      /* colour period q >= s + p (0 = library default for p) */

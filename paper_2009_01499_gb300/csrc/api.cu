@@ -328,7 +328,7 @@ static int assemble_impl(int p, int m, int dim, int nbatch, bool batch, const ig
     if (dim == 3 && p > 4) return fail(IGA2L_ERR_UNSUPPORTED, "3D kernels are compiled for p = 2..4");
     if (m < 4 * p + 4 || (m % 2) != 0)
         return fail(IGA2L_ERR_INVALID_ARG, "m must be even and >= 4p+4 (aggressive 2h coarsening)");
-    if (opt.precision != IGA2L_FP64 && opt.precision != IGA2L_MIXED_FP32)
+    if (opt.precision != IGA2L_FP64 && opt.precision != IGA2L_MIXED_FP32 && opt.precision != IGA2L_MIXED_FP32_ALL)
         return fail(IGA2L_ERR_UNSUPPORTED, "precision not available");
     if (opt.schedule != IGA2L_SCHED_LATTICE && opt.schedule != IGA2L_SCHED_TILE)
         return fail(IGA2L_ERR_UNSUPPORTED, "schedule not available");
@@ -543,7 +543,7 @@ static int assemble_impl(int p, int m, int dim, int nbatch, bool batch, const ig
         release(S);
         return cuda_fail(ce, "pinned host scalar");
     }
-    if (opt.precision == IGA2L_MIXED_FP32) {
+    if (opt.precision == IGA2L_MIXED_FP32 || opt.precision == IGA2L_MIXED_FP32_ALL) {
         // FP32 copies of the tables for the inner cycle (the FP64 block inverses are kept
         // for boundary classes and the FP64 coarsest inverse for the direct solve)
         MixedState &X = S->mx;

@@ -101,6 +101,9 @@ struct Solver {
     double *gbuf = nullptr;      // per-bump 1D loads and their centre derivatives
     int gcap = 0;                // bumps gbuf can hold
     std::vector<void *> allocs;
+    // FP64 inverses of the boundary block classes for the FP32 Schwarz kernels, or null
+    // when those are applied in FP32 too (IGA2L_MIXED_FP32_ALL)
+    const double *boundary64() const { return opt.precision == IGA2L_MIXED_FP32 ? binv : nullptr; }
 };
 
 // Number of kernels this library has launched (process-wide), for benchmarks

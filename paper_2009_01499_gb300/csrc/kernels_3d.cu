@@ -205,7 +205,7 @@ k_schwarz_lattice3d(int n, int nbc, int q, int ox, int oy, int oz, int nbx, int 
         const int gx = cx - R + ex, gy = cy - R + ey, gz = cz - R + ez;
         if (gx >= 0 && gx < n && gy >= 0 && gy < n && gz >= 0 && gz < n) {
             const int cls = (bcls[cz] * nbc + bcls[cy]) * nbc + bcls[cx];
-            if (sizeof(T) == sizeof(double) || cls == interior) {
+            if (sizeof(T) == sizeof(double) || cls == interior || !binv64) {
                 const T *Bi = binv + ((size_t)cls * SS + tid) * SS;
                 T ev = T(0);
 #pragma unroll
@@ -481,7 +481,7 @@ cudaError_t schwarz3d_p(const Solver &S, const T *Kb, const T *Mb, const T *binv
         const int nbx = (S.n - ox + q - 1) / q, nby = (S.n - oy + q - 1) / q, nbz = (S.n - oz + q - 1) / q;
         if (nbx <= 0 || nby <= 0 || nbz <= 0) continue;
         k_schwarz_lattice3d<P, T><<<nbx * nby * nbz, 128, 0, st>>>(S.n, nbc, q, ox, oy, oz, nbx, nby, Kb, Mb, binv,
-                                                                    S.binv, interior, S.bcls, u, b);
+                                                                    S.boundary64(), interior, S.bcls, u, b);
         count_launches(1);
         cudaError_t err = cudaGetLastError();
         if (err != cudaSuccess) return err;

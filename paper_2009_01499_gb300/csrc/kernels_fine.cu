@@ -149,7 +149,7 @@ k_schwarz_lattice2d(int n, int npc, int nbc, int q, int ox, int oy, int nbx, int
     if (inside) {
         const int cls = bcls[cy] * nbc + bcls[cx];
         const T *rb = rs + lb * SS;
-        if (sizeof(T) == sizeof(double) || cls == interior) {
+        if (sizeof(T) == sizeof(double) || cls == interior || !binv64) {
             const T *Bi = binv + ((size_t)cls * SS + e) * SS;
             T ev = T(0);
 #pragma unroll
@@ -179,22 +179,40 @@ __device__ __forceinline__ float cst<float>(int p, int i) { return c_stencil32[p
 
 // Interior rows of the 1D stiffness and mass matrices, scaled to be independent of h
 // (k = h K_row, m = M_row / h): the interior 2D coefficient K_y[b] M_x[a] + M_y[b] K_x[a]
-// equals k[b] m[a] + m[b] k[a].  Written with the 2D stencil, once per device and degree.
-__constant__ double c_k1d[kMaxP + 1][2 * kMaxP + 1], c_m1d[kMaxP + 1][2 * kMaxP + 1];
-__constant__ float c_k1f[kMaxP + 1][2 * kMaxP + 1], c_m1f[kMaxP + 1][2 * kMaxP + 1];
+// equals k[b] m[a] + m[b] k[a].  Stored as pairs (k[a], m[a]) for the packed y pass and
+// (m[a], k[a]) for the packed x pass; written with the 2D stencil, once per device and degree.
+__constant__ double2 c_km1d[kMaxP + 1][2 * kMaxP + 1], c_mk1d[kMaxP + 1][2 * kMaxP + 1];
+__constant__ float2 c_km1f[kMaxP + 1][2 * kMaxP + 1], c_mk1f[kMaxP + 1][2 * kMaxP + 1];
+
+// two-lane values: float2 uses Blackwell's packed FP32 FMA (one instruction, each half
+// rounded as a scalar fmaf), double2 two scalar FMAs
+template <typename T>
+struct Vec2;
+template <>
+struct Vec2<float> { using type = float2; };
+template <>
+struct Vec2<double> { using type = double2; };
+
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ double2 fma2(double2 a, double2 b, double2 c)
+{
+    return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+template <typename T2>
+__device__ __forceinline__ T2 splat2(decltype(T2::x) v) { T2 r; r.x = v; r.y = v; return r; }
 
 template <typename T>
-__device__ __forceinline__ T ck1(int p, int a);
+__device__ __forceinline__ typename Vec2<T>::type ckm1(int p, int a);
 template <typename T>
-__device__ __forceinline__ T cm1(int p, int a);
+__device__ __forceinline__ typename Vec2<T>::type cmk1(int p, int a);
 template <>
-__device__ __forceinline__ double ck1<double>(int p, int a) { return c_k1d[p][a]; }
+__device__ __forceinline__ double2 ckm1<double>(int p, int a) { return c_km1d[p][a]; }
 template <>
-__device__ __forceinline__ float ck1<float>(int p, int a) { return c_k1f[p][a]; }
+__device__ __forceinline__ float2 ckm1<float>(int p, int a) { return c_km1f[p][a]; }
 template <>
-__device__ __forceinline__ double cm1<double>(int p, int a) { return c_m1d[p][a]; }
+__device__ __forceinline__ double2 cmk1<double>(int p, int a) { return c_mk1d[p][a]; }
 template <>
-__device__ __forceinline__ float cm1<float>(int p, int a) { return c_m1f[p][a]; }
+__device__ __forceinline__ float2 cmk1<float>(int p, int a) { return c_mk1f[p][a]; }
 
 // Geometry of one CTA of the TILE(TT) schedule.
 template <int P, int S, int TT>
@@ -207,10 +225,11 @@ struct TileGeom {
     static constexpr int BPW = 32 / SS;                    // blocks per warp (SS lanes each)
     static constexpr int NWARP = (NBLK + BPW - 1) / BPW, NT = 32 * NWARP;
     static constexpr int WIN = S + 2 * P;                  // window columns (and rows) of a block
-    // y sums of a block: 2 S rows (K_y, M_y) of YS entries; YS and the block stride YB
-    // keep the x pass's reads of the lanes of one warp in distinct banks
-    static constexpr int YS = S == 5 ? 19 : 11, YB = S == 5 ? 2 * S * YS : 67;
+    // y sums of a block: S rows of YS pairs (K_y u, M_y u); YS and the block stride YB keep
+    // the 8-byte reads of each half-warp in the x pass in distinct banks
+    static constexpr int YS = S == 5 ? 21 : 19, YB = S * YS;
     static constexpr int RSS = (SS + 3) / 4 * 4;           // residual stride (16-byte loads)
+    static constexpr int NB2 = (SS + 1) / 2;               // pairs of one inverse row
     // resident CTAs per SM the register allocation must allow (FP32: a 1024^2 tile phase
     // in one wave; FP64 keeps its registers)
     template <typename T>
@@ -237,86 +256,59 @@ __device__ __forceinline__ void stage_window(T *dst, const T *__restrict__ src, 
     }
 }
 
-// out[0 .. N) = p[0 .. N) with 16-byte shared-memory loads (p 16-byte aligned, N % (16/sizeof(T)) == 0)
-template <int N>
-__device__ __forceinline__ void load16(const float *p, float *out)
-{
-#pragma unroll
-    for (int k = 0; k < N / 4; ++k) {
-        const float4 v = reinterpret_cast<const float4 *>(p)[k];
-        out[4 * k] = v.x; out[4 * k + 1] = v.y; out[4 * k + 2] = v.z; out[4 * k + 3] = v.w;
-    }
-}
-template <int N>
-__device__ __forceinline__ void load16(const double *p, double *out)
-{
-#pragma unroll
-    for (int k = 0; k < N / 2; ++k) {
-        const double2 v = reinterpret_cast<const double2 *>(p)[k];
-        out[2 * k] = v.x; out[2 * k + 1] = v.y;
-    }
-}
-
 // y pass of one block: for window column col (tile-local x = cxl - R - P + col) the
 // column slice rows cyl .. cyl + WIN - 1 of the staged u, then for every block row r
-//   Y1[r][col] = sum_b K_y[b] u(col, row r + b - P),  Y2[r][col] = the same with M_y.
-// FAST: interior rows (constant 1D rows); else the rows' own 1D rows (ky, my tables).
+//   Y[r][col] = (sum_b K_y[b] u(col, row r + b - P), sum_b M_y[b] u(...)).
+// FAST: interior rows (constant 1D rows); else the rows' own 1D rows (km1y: (K, M) pairs).
 template <int P, int S, int TT, bool FAST, typename T>
-__device__ __forceinline__ void tile_ypass(const T *su, int cxl, int cyl, int lane_e, T *yb,
-                                           const T *k1y, const T *m1y)
+__device__ __forceinline__ void tile_ypass(const T *su, int cxl, int cyl, int lane_e, typename Vec2<T>::type *yb,
+                                           const typename Vec2<T>::type *km1y)
 {
     using G = TileGeom<P, S, TT>;
+    using T2 = typename Vec2<T>::type;
     constexpr int W = G::W, WIN = G::WIN, SW = G::SW;
-    for (int col = lane_e; col < WIN; col += G::SS) {
-        if (FAST) {
+    for (int col = lane_e; FAST && col < WIN; col += G::SS) {
+        {
             T v[WIN];
 #pragma unroll
             for (int k = 0; k < WIN; ++k) v[k] = su[(cyl + k) * SW + cxl + col];
 #pragma unroll
             for (int r = 0; r < S; ++r) {
-                T y1 = T(0), y2 = T(0);
+                T2 y = splat2<T2>(T(0));
 #pragma unroll
-                for (int bb = 0; bb < W; ++bb) {
-                    y1 = fma(ck1<T>(P, bb), v[r + bb], y1);
-                    y2 = fma(cm1<T>(P, bb), v[r + bb], y2);
-                }
-                yb[r * G::YS + col] = y1;
-                yb[(S + r) * G::YS + col] = y2;
+                for (int bb = 0; bb < W; ++bb) y = fma2(ckm1<T>(P, bb), splat2<T2>(v[r + bb]), y);
+                yb[r * G::YS + col] = y;
             }
-        } else {
-            // boundary tiles: per-row coefficients, u read from shared memory directly
-#pragma unroll 1
-            for (int r = 0; r < S; ++r) {
-                const T *kr = k1y + (cyl + r) * W, *mr = m1y + (cyl + r) * W;
-                const T *uc = su + (cyl + r) * SW + cxl + col;
-                T y1 = T(0), y2 = T(0);
+        }
+    }
+    if (!FAST) {
+        // blocks with boundary rows: per-row coefficients; the S x WIN points are spread
+        // over all the block's lanes, u read from shared memory directly
+        for (int pt = lane_e; pt < S * WIN; pt += G::SS) {
+            const int r = pt / WIN, col = pt - r * WIN;
+            const T2 *kr = km1y + (cyl + r) * W;
+            const T *uc = su + (cyl + r) * SW + cxl + col;
+            T2 y = splat2<T2>(T(0));
 #pragma unroll
-                for (int bb = 0; bb < W; ++bb) {
-                    const T v = uc[bb * SW];
-                    y1 = fma(kr[bb], v, y1);
-                    y2 = fma(mr[bb], v, y2);
-                }
-                yb[r * G::YS + col] = y1;
-                yb[(S + r) * G::YS + col] = y2;
-            }
+            for (int bb = 0; bb < W; ++bb) y = fma2(kr[bb], splat2<T2>(uc[bb * SW]), y);
+            yb[r * G::YS + col] = y;
         }
     }
 }
 
 // x pass of one output (ey, ex) of a block: sum_a M_x[a] Y1[ey][ex + a] + K_x[a] Y2[ey][ex + a]
 template <int P, int S, int TT, bool FAST, typename T>
-__device__ __forceinline__ T tile_xpass(const T *yb, int ey, int ex, int xrow, const T *k1x, const T *m1x)
+__device__ __forceinline__ T tile_xpass(const typename Vec2<T>::type *yb, int ey, int ex, int xrow,
+                                        const typename Vec2<T>::type *mk1x)
 {
     using G = TileGeom<P, S, TT>;
+    using T2 = typename Vec2<T>::type;
     constexpr int W = G::W;
-    const T *y1 = yb + ey * G::YS + ex, *y2 = y1 + S * G::YS;
-    T s0 = T(0), s1 = T(0);
+    const T2 *y = yb + ey * G::YS + ex;
+    T2 s = splat2<T2>(T(0));
 #pragma unroll
-    for (int a = 0; a < W; ++a) {
-        s0 = fma(FAST ? cm1<T>(P, a) : m1x[xrow * W + a], y1[a], s0);
-        s1 = fma(FAST ? ck1<T>(P, a) : k1x[xrow * W + a], y2[a], s1);
-    }
-    return s0 + s1;
+    for (int a = 0; a < W; ++a) s = fma2(FAST ? cmk1<T>(P, a) : mk1x[xrow * W + a], y[a], s);
+    return s.x + s.y;
 }
 
 // One tile phase of the TILE(TT) schedule: tiles (tx, ty) with tx = px, px+2, ... and
@@ -329,11 +321,12 @@ __device__ __forceinline__ T tile_xpass(const T *yb, int ey, int ex, int xrow, c
 // a block's S^2 lanes sit in one warp.  The residual uses the y-then-x sum factorisation
 //   (A u)(x, y) = sum_b K_y[b] sum_a M_x[a] u(x+a-P, y+b-P) + M_y[b] sum_a K_x[a] u(...),
 // shared by the block's lanes: a y pass over the window columns (each lane slides down
-// one column), a warp barrier, then each lane's x pass.  Interior tiles (almost all)
-// take the interior 1D rows from constant memory; boundary tiles the 1D rows of their
-// own rows and columns.  After a second warp barrier each lane applies row e of its
-// block's inverse (the interior row kept in registers, boundary classes in FP64) and
-// adds the result to u in shared memory.  One CTA barrier per colour.
+// one column), a warp barrier, then each lane's x pass; the K and M halves run as pairs
+// (packed FP32 FMA).  Interior tiles (almost all) take the interior 1D rows from constant
+// memory; boundary tiles the 1D rows of their own rows and columns.  After a second warp
+// barrier each lane applies row e of its block's inverse (the interior row kept in
+// registers, boundary classes in FP64) and adds the result to u in shared memory.  One
+// CTA barrier per colour.
 template <int P, int S, int TT, typename T>
 __global__ void __launch_bounds__(TileGeom<P, S, TT>::NT, TileGeom<P, S, TT>::template minb<T>())
 k_schwarz_tile2d(int n, int nbc, int q, int g, int rev, int px, int py, int ntpx,
@@ -342,14 +335,15 @@ k_schwarz_tile2d(int n, int nbc, int q, int g, int rev, int px, int py, int ntpx
                  T *__restrict__ u, const T *__restrict__ b, BatchRef bt)
 {
     using G = TileGeom<P, S, TT>;
+    using T2 = typename Vec2<T>::type;
     constexpr int W = G::W, SS = G::SS, R = G::R, H = G::H, L = P - 1 + R;
     constexpr int SW = G::SW, BW = G::BW, NB1 = G::NB1, NT = G::NT;
     constexpr int PCI = 2 * P - 1;   // first interior row class
     __shared__ T su[SW * SW];
     __shared__ T sb[BW * BW];
     __shared__ __align__(16) T rs[G::NBLK * G::RSS];
-    __shared__ T yb[G::NBLK * G::YB];
-    __shared__ T k1y[BW * W], m1y[BW * W], k1x[BW * W], m1x[BW * W];   // boundary tiles
+    __shared__ T2 yb[G::NBLK * G::YB];
+    __shared__ T2 km1y[BW * W], mk1x[BW * W];   // boundary tiles: (K, M) of rows, (M, K) of columns
     if (bt.active && !bt.active[blockIdx.y]) return;
     u += blockIdx.y * bt.vec;
     b += blockIdx.y * bt.vec;
@@ -364,24 +358,35 @@ k_schwarz_tile2d(int n, int nbc, int q, int g, int rev, int px, int py, int ntpx
     const bool role = bw < G::BPW && slot < G::NBLK;
     stage_window<NT, SW, SW * SW>(su, u, n, x0 - H, y0 - H, tid);
     stage_window<NT, BW, BW * BW>(sb, b, n, x0 - R, y0 - R, tid);
+    for (int i = tid; i < G::NBLK * G::RSS; i += NT) rs[i] = T(0);   // the padding stays zero
     if (!fast) {
+        // the rows scaled like the interior constants (h K, M / h), h = 1 / m, so that a
+        // block may mix interior and boundary factors
+        const T h = T(1) / T(n - P + 2), hinv = T(n - P + 2);
         for (int i = tid; i < BW * W; i += NT) {
             const int row = i / W, a = i - row * W;
             const int gx = x0 - R + row, gy = y0 - R + row;
             const bool inx = gx >= 0 && gx < n, iny = gy >= 0 && gy < n;
-            k1x[i] = inx ? kband[(size_t)gx * W + a] : T(0);
-            m1x[i] = inx ? mband[(size_t)gx * W + a] : T(0);
-            k1y[i] = iny ? kband[(size_t)gy * W + a] : T(0);
-            m1y[i] = iny ? mband[(size_t)gy * W + a] : T(0);
+            T2 km, mk;
+            km.x = iny ? kband[(size_t)gy * W + a] * h : T(0);
+            km.y = iny ? mband[(size_t)gy * W + a] * hinv : T(0);
+            mk.x = inx ? mband[(size_t)gx * W + a] * hinv : T(0);
+            mk.y = inx ? kband[(size_t)gx * W + a] * h : T(0);
+            km1y[i] = km;
+            mk1x[i] = mk;
         }
     }
-    // row e of the interior block inverse, in registers for the whole tile
-    T brow[SS];
+    // row e of the interior block inverse as pairs, in registers for the whole tile
+    T2 brow[G::NB2];
 #pragma unroll
-    for (int f = 0; f < SS; ++f) brow[f] = role ? __ldg(&binv[((size_t)interior * SS + e) * SS + f]) : T(0);
+    for (int k = 0; k < G::NB2; ++k) {
+        const size_t base = ((size_t)interior * SS + e) * SS;
+        brow[k].x = role ? __ldg(&binv[base + 2 * k]) : T(0);
+        brow[k].y = (role && 2 * k + 1 < SS) ? __ldg(&binv[base + 2 * k + 1]) : T(0);
+    }
     __syncthreads();
     const int bi = slot % NB1, bj = slot / NB1;
-    T *ybs = yb + slot * G::YB;
+    T2 *ybs = yb + slot * G::YB;
     T *rsb = rs + slot * G::RSS;
     const int ncol = q * q;
     // colour c visits offsets ((c mod q) g mod q, (c div q) g mod q), advanced incrementally
@@ -391,16 +396,19 @@ k_schwarz_tile2d(int n, int nbc, int q, int g, int rev, int px, int py, int ntpx
         const int cxl = ox + q * bi, cyl = oy + q * bj;   // tile-local centre
         const bool act = role && cxl < tw && cyl < th;
         const int lx = cxl - R + ex, ly = cyl - R + ey;   // tile-local DOF of this lane
+        // are the block's rows / columns all of the interior class?
+        const bool yint = fast || (y0 + cyl - R >= PCI && y0 + cyl + R <= n - 2 * P);
+        const bool xint = fast || (x0 + cxl - R >= PCI && x0 + cxl + R <= n - 2 * P);
         if (act) {
-            if (fast) tile_ypass<P, S, TT, true>(su, cxl, cyl, e, ybs, k1y, m1y);
-            else tile_ypass<P, S, TT, false>(su, cxl, cyl, e, ybs, k1y, m1y);
+            if (yint) tile_ypass<P, S, TT, true>(su, cxl, cyl, e, ybs, km1y);
+            else tile_ypass<P, S, TT, false>(su, cxl, cyl, e, ybs, km1y);
         }
         __syncwarp();
         const int gx = x0 + lx, gy = y0 + ly;
         const bool in = fast || (gx >= 0 && gx < n && gy >= 0 && gy < n);
         if (act) {
-            const T acc = fast ? tile_xpass<P, S, TT, true>(ybs, ey, ex, lx + R, k1x, m1x)
-                               : tile_xpass<P, S, TT, false>(ybs, ey, ex, lx + R, k1x, m1x);
+            const T acc = xint ? tile_xpass<P, S, TT, true, T>(ybs, ey, ex, lx + R, mk1x)
+                               : tile_xpass<P, S, TT, false, T>(ybs, ey, ex, lx + R, mk1x);
             rsb[e] = in ? sb[(ly + R) * BW + (lx + R)] - acc : T(0);
         }
         __syncwarp();
@@ -412,39 +420,26 @@ k_schwarz_tile2d(int n, int nbc, int q, int g, int rev, int px, int py, int ntpx
                 const int by = ccy < L ? ccy : (ccy > n - 1 - L ? 2 * L - (n - 1 - ccy) : L);
                 cls = by * nbc + bx;
             }
-            constexpr int VN = 16 / sizeof(T);
             T ev = T(0);
             if (cls == interior) {
+                T2 acc2 = splat2<T2>(T(0));
+                const T2 *r2 = reinterpret_cast<const T2 *>(rsb);   // 16-byte aligned, zero padded
 #pragma unroll
-                for (int k = 0; k < G::RSS / VN; ++k) {
-                    T rv[VN];
-                    load16<VN>(rsb + k * VN, rv);
-#pragma unroll
-                    for (int j = 0; j < VN; ++j)
-                        if (k * VN + j < SS) ev = fma(brow[k * VN + j], rv[j], ev);
-                }
-            } else if (sizeof(T) == sizeof(double)) {
+                for (int k = 0; k < G::NB2; ++k) acc2 = fma2(brow[k], r2[k], acc2);
+                ev = acc2.x + acc2.y;
+            } else if (sizeof(T) == sizeof(double) || !binv64) {
                 const T *Bi = binv + ((size_t)cls * SS + e) * SS;
 #pragma unroll
-                for (int k = 0; k < G::RSS / VN; ++k) {
-                    T rv[VN];
-                    load16<VN>(rsb + k * VN, rv);
-#pragma unroll
-                    for (int j = 0; j < VN; ++j)
-                        if (k * VN + j < SS) ev = fma(__ldg(&Bi[k * VN + j]), rv[j], ev);
-                }
+                for (int f = 0; f < SS; ++f) ev = fma(__ldg(&Bi[f]), rsb[f], ev);
             } else {
                 const double *Bi = binv64 + ((size_t)cls * SS + e) * SS;
-                double ed = 0.0;
+                double ed0 = 0.0, ed1 = 0.0;
 #pragma unroll
-                for (int k = 0; k < G::RSS / VN; ++k) {
-                    T rv[VN];
-                    load16<VN>(rsb + k * VN, rv);
-#pragma unroll
-                    for (int j = 0; j < VN; ++j)
-                        if (k * VN + j < SS) ed = fma(__ldg(&Bi[k * VN + j]), (double)rv[j], ed);
+                for (int f = 0; f < SS; ++f) {
+                    if (f & 1) ed1 = fma(__ldg(&Bi[f]), (double)rsb[f], ed1);
+                    else ed0 = fma(__ldg(&Bi[f]), (double)rsb[f], ed0);
                 }
-                ev = (T)ed;
+                ev = (T)(ed0 + ed1);
             }
             if (in) su[(ly + H) * SW + (lx + H)] += ev;
         }
@@ -608,7 +603,7 @@ cudaError_t schwarz_lattice_p(const Solver &S, const T *stencil, const T *binv, 
         if (nblocks <= 0) continue;
         const int grid = (nblocks + BPC - 1) / BPC;
         k_schwarz_lattice2d<P, SB, T><<<dim3(grid, S.nbatch), 256, 0, st>>>(S.n, S.ht.npc, S.ht.nbc, q, ox, oy, nbx,
-                                                             nblocks, stencil, S.pcls, binv, S.binv,
+                                                             nblocks, stencil, S.pcls, binv, S.boundary64(),
                                                              interior, S.bcls, u, b, BatchRef{S.active, S.N, 0, 0});
         count_launches(1);
         cudaError_t err = cudaGetLastError();
@@ -631,7 +626,7 @@ cudaError_t schwarz_tile_p(const Solver &S, const T *kband, const T *mband, cons
         const int ntpx = (nt - px + 1) / 2, ntpy = (nt - py + 1) / 2;
         if (ntpx <= 0 || ntpy <= 0) continue;
         k_schwarz_tile2d<P, SB, TT, T><<<dim3(ntpx * ntpy, S.nbatch), G::NT, 0, st>>>(
-            S.n, S.ht.nbc, S.q, S.g, reverse ? 1 : 0, px, py, ntpx, kband, mband, binv, S.binv, interior, u, b,
+            S.n, S.ht.nbc, S.q, S.g, reverse ? 1 : 0, px, py, ntpx, kband, mband, binv, S.boundary64(), interior, u, b,
             BatchRef{S.active, S.N, 0, 0});
         count_launches(1);
         cudaError_t err = cudaGetLastError();
@@ -704,17 +699,24 @@ cudaError_t upload_interior_stencil(int p, const double *st64, int count, const 
     if (dev < 0 || dev >= 64 || p < 0 || p > kMaxP) return cudaErrorInvalidValue;
     if (done[dev][p]) return cudaSuccess;
     constexpr int W1 = 2 * kMaxP + 1;
-    float st32[W1 * W1], k32[W1], m32[W1];
+    float st32[W1 * W1];
+    double2 km64[W1], mk64[W1];
+    float2 km32[W1], mk32[W1];
     for (int i = 0; i < count; ++i) st32[i] = (float)st64[i];
     const int w = 2 * p + 1;
-    for (int i = 0; i < w; ++i) { k32[i] = (float)k1[i]; m32[i] = (float)m1[i]; }
+    for (int i = 0; i < w; ++i) {
+        km64[i] = make_double2(k1[i], m1[i]);
+        mk64[i] = make_double2(m1[i], k1[i]);
+        km32[i] = make_float2((float)k1[i], (float)m1[i]);
+        mk32[i] = make_float2((float)m1[i], (float)k1[i]);
+    }
     const size_t row = sizeof(double) * W1 * W1;
     e = cudaMemcpyToSymbol(c_stencil64, st64, sizeof(double) * count, row * p);
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_stencil32, st32, sizeof(float) * count, (row / 2) * p);
-    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_k1d, k1, sizeof(double) * w, sizeof(double) * W1 * p);
-    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_m1d, m1, sizeof(double) * w, sizeof(double) * W1 * p);
-    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_k1f, k32, sizeof(float) * w, sizeof(float) * W1 * p);
-    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_m1f, m32, sizeof(float) * w, sizeof(float) * W1 * p);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_km1d, km64, sizeof(double2) * w, sizeof(double2) * W1 * p);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_mk1d, mk64, sizeof(double2) * w, sizeof(double2) * W1 * p);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_km1f, km32, sizeof(float2) * w, sizeof(float2) * W1 * p);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_mk1f, mk32, sizeof(float2) * w, sizeof(float2) * W1 * p);
     if (e == cudaSuccess) done[dev][p] = true;
     return e;
 }

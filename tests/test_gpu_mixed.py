@@ -26,12 +26,23 @@ def _host(t):
     return t.cpu().numpy()
 
 
-@pytest.mark.parametrize("p,m", [(2, 50), (3, 64), (4, 66), (5, 70)])
-def test_mixed_iterates_track_fp64_oracle(oracle_mod, p, m):
+MODES = [(iga2l.MIXED_FP32, "lattice"), (iga2l.MIXED_FP32_ALL, "lattice"), (iga2l.MIXED_FP32, "tile"),
+         (iga2l.MIXED_FP32_ALL, "tile")]
+
+
+def _pair(oracle_mod, p, m, precision, sched):
     q, g = COLOURING[p]
-    S = iga2l.Solver(p, m, period=q, stride=g, precision=iga2l.MIXED_FP32)
-    O = oracle_mod.Problem(2, p, m, sched=oracle_mod.LATTICE, coarse=oracle_mod.VCYCLE,
-                           period=q, stride=g)
+    sg = iga2l.SCHED_TILE if sched == "tile" else iga2l.SCHED_LATTICE
+    S = iga2l.Solver(p, m, period=q, stride=g, precision=precision, schedule=sg)
+    so = oracle_mod.TILE if sched == "tile" else oracle_mod.LATTICE
+    O = oracle_mod.Problem(2, p, m, sched=so, tile=S.tile or 32, coarse=oracle_mod.VCYCLE, period=q, stride=g)
+    return S, O
+
+
+@pytest.mark.parametrize("precision,sched", MODES)
+@pytest.mark.parametrize("p,m", [(2, 50), (3, 64), (4, 66), (5, 70)])
+def test_mixed_iterates_track_fp64_oracle(oracle_mod, p, m, precision, sched):
+    S, O = _pair(oracle_mod, p, m, precision, sched)
     f = synth.coefficients(S.N, 400 + p)
     u0 = synth.initial_guess(S.N, 401 + p)
     K, M = oracle_mod.assemble_1d(p, m)
@@ -49,8 +60,9 @@ def test_mixed_iterates_track_fp64_oracle(oracle_mod, p, m):
         assert e_before <= 1e-5 * ustar
 
 
+@pytest.mark.parametrize("precision,sched", MODES)
 @pytest.mark.parametrize("p", [2, 3, 4, 5])
-def test_mixed_refinement_reaches_fp64_solution(oracle_mod, p):
+def test_mixed_refinement_reaches_fp64_solution(oracle_mod, p, precision, sched):
     """At the 1e-8 stopping rule the mixed form takes the oracle's cycle count and is
     as accurate as the FP64 oracle (its error against a tightly converged solution
     matches the oracle's own); refined on to a 1e-12 residual it is within 1e-8 of
@@ -58,10 +70,7 @@ def test_mixed_refinement_reaches_fp64_solution(oracle_mod, p):
     the solution, a 1e-8 residual reduction leaves both forms ~1e-3 from the exact
     discrete solution, so the 1e-8 solution bar is applied after refinement.)"""
     m = 128
-    q, g = COLOURING[p]
-    S = iga2l.Solver(p, m, period=q, stride=g, precision=iga2l.MIXED_FP32)
-    O = oracle_mod.Problem(2, p, m, sched=oracle_mod.LATTICE, coarse=oracle_mod.VCYCLE,
-                           period=q, stride=g)
+    S, O = _pair(oracle_mod, p, m, precision, sched)
     f = synth.coefficients(S.N, 500 + p)
     u0 = synth.initial_guess(S.N, 501 + p)
     bd = torch.empty(S.N, dtype=torch.float64, device="cuda")
