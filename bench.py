@@ -537,9 +537,11 @@ def run_profile_step(args):
     from paper_2009_01499_gb300 import iga2l, synth
     dev = torch.device("cuda", 0)
     degrees = (args.profile_p,) if args.profile_p else DEGREES
+    prec = {"fp64": iga2l.FP64, "mixed": iga2l.MIXED_FP32, "mixed_all": iga2l.MIXED_FP32_ALL}[args.profile_precision]
+    sched = iga2l.SCHED_LATTICE if prec == iga2l.FP64 else iga2l.SCHED_TILE
     for p in degrees:
         q, g = COLOURING[p]
-        S = iga2l.Solver(p, args.profile_m, period=q, stride=g)
+        S = iga2l.Solver(p, args.profile_m, period=q, stride=g, precision=prec, schedule=sched)
         sf, su = seeds(p)
         f = torch.tensor(synth.coefficients(S.N, sf), device=dev)
         b = torch.empty_like(f)
@@ -567,6 +569,8 @@ def main():
                     help="profiling aid: warm-up solves then one solve per degree, no timing")
     ap.add_argument("--profile-m", type=int, default=M_ELEM)
     ap.add_argument("--profile-p", type=int, default=0)
+    ap.add_argument("--profile-precision", choices=["fp64", "mixed", "mixed_all"], default="fp64",
+                    help="form profiled by --profile-step (the benchmark's schedule for it)")
     args = ap.parse_args()
     if args.profile_step:
         run_profile_step(args)

@@ -535,7 +535,8 @@ static int assemble_impl(int p, int m, int dim, int nbatch, bool batch, const ig
     }
     for (Level &L : S->lev)
         if ((ce = alloc(S, &L.e, B * L.N)) != cudaSuccess || (ce = alloc(S, &L.rhs, B * L.N)) != cudaSuccess ||
-            (dim == 3 && (ce = alloc(S, &L.r, L.N)) != cudaSuccess)) {
+            (dim == 3 && (ce = alloc(S, &L.r, L.N)) != cudaSuccess) ||
+            (dim == 2 && (ce = alloc(S, &L.pre, B * L.N)) != cudaSuccess)) {
             release(S);
             return cuda_fail(ce, "level allocation");
         }
@@ -571,10 +572,12 @@ static int assemble_impl(int p, int m, int dim, int nbatch, bool batch, const ig
         X.lev_e.assign(S->lev.size(), nullptr);
         X.lev_rhs.assign(S->lev.size(), nullptr);
         X.lev_r.assign(S->lev.size(), nullptr);
+        X.lev_pre.assign(S->lev.size(), nullptr);
         for (size_t l = 0; l < S->lev.size(); ++l)
             if ((l > 0 && (ce = allocf(&X.lev_e[l], B * S->lev[l].N)) != cudaSuccess) ||
                 (l > 0 && (ce = allocf(&X.lev_rhs[l], B * S->lev[l].N)) != cudaSuccess) ||
-                (dim == 3 && (ce = allocf(&X.lev_r[l], S->lev[l].N)) != cudaSuccess)) {
+                (dim == 3 && (ce = allocf(&X.lev_r[l], S->lev[l].N)) != cudaSuccess) ||
+                (dim == 2 && (ce = allocf(&X.lev_pre[l], B * S->lev[l].N)) != cudaSuccess)) {
                 release(S);
                 return cuda_fail(ce, "mixed-precision level allocation");
             }

@@ -49,6 +49,7 @@ struct Level {                 // degree-1 level of the second-level hierarchy
     double k[3] = {0, 0, 0};   // 1D stiffness row  (-1, 2, -1)/H
     double mm[3] = {0, 0, 0};  // 1D mass row (1, 4, 1) H/6
     double *e = nullptr, *rhs = nullptr, *r = nullptr;   // device
+    double *pre = nullptr;     // pre-smoothed correction (2D V-cycle)
 };
 
 // FP32 state of the inner cycle of the mixed-precision form (device pointers).
@@ -61,6 +62,7 @@ struct MixedState {
     float *d = nullptr, *t = nullptr, *t2 = nullptr, *dc = nullptr, *ec = nullptr;
     std::vector<float *> lev_e, lev_rhs;   // level arrays (index 0 unused: dc / ec)
     std::vector<float *> lev_r;            // level residuals (3D)
+    std::vector<float *> lev_pre;          // pre-smoothed corrections (2D)
 };
 
 struct Solver {

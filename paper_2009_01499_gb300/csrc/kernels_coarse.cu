@@ -36,65 +36,80 @@ Stencil9<T> level_stencil(const Level &L)
     return s;
 }
 
-// Relax the sub-lattice {(2a+px, 2b+py)}: e += (rhs - A e) / A_diag.  No two points
-// of a sub-lattice are coupled by the 9-point stencil.
-template <typename T>
-__global__ void k_gs_sublattice(int n, int px, int py, Stencil9<T> st, const T *__restrict__ rhs,
-                                T *__restrict__ e, BatchRef bt)
+// ---- fused level kernels --------------------------------------------------------------
+// One relaxation of the V(1,1) smoother is four sub-lattice sweeps {(2a+px, 2b+py)}, each
+// e += (rhs - A e) / A_diag; no two points of a sub-lattice are coupled by the 9-point
+// stencil.  A CTA owns a TX x TY tile of the level and stages it with a halo of H >= 4:
+// after sweep k every staged point at distance >= k from the staged edge holds exactly the
+// value the four global sweeps give (its neighbours were exact after sweep k-1), so the
+// tile is exact after four sweeps and one launch replaces four.  Points outside the level
+// are zero and never updated.  Each point update uses the arithmetic, in the order, of a
+// plain per-sweep kernel.
+constexpr int kLvTX = 32, kLvTY = 16;
+
+template <typename T, int RX, int RY>
+__device__ __forceinline__ void level_sweeps(int n, int gx0, int gy0, const Stencil9<T> &st, T (*se)[RX],
+                                             const T (*sr)[RX], bool forward)
 {
-    const int a = blockIdx.x * blockDim.x + threadIdx.x, bidx = blockIdx.y * blockDim.y + threadIdx.y;
-    const int x = 2 * a + px, y = 2 * bidx + py;
-    if (x >= n || y >= n || (bt.active && !bt.active[blockIdx.z])) return;
-    rhs += blockIdx.z * bt.vec;
-    e += blockIdx.z * bt.vec;
-    T acc = T(0);
+    constexpr int HX = RX / 2, HY = RY / 2;   // sub-lattice points per row / column of the region
+    for (int t = 0; t < 4; ++t) {
+        const int c = forward ? t : 3 - t;
+        const int px = kGsSeqDev[c][0], py = kGsSeqDev[c][1];   // region origin is even
+        for (int i = threadIdx.x + blockDim.x * threadIdx.y; i < HX * HY; i += blockDim.x * blockDim.y) {
+            const int lx = 2 * (i % HX) + px, ly = 2 * (i / HX) + py;
+            const int d = min(min(lx, ly), min(RX - 1 - lx, RY - 1 - ly));
+            const int gx = gx0 + lx, gy = gy0 + ly;
+            if (d < t + 1 || gx < 0 || gx >= n || gy < 0 || gy >= n) continue;
+            T acc = T(0);
 #pragma unroll
-    for (int dy = 0; dy < 3; ++dy) {
-        const int yy = y + dy - 1;
-        if (yy < 0 || yy >= n) continue;
+            for (int dy = 0; dy < 3; ++dy) {
+                const int yy = gy + dy - 1;
+                if (yy < 0 || yy >= n) continue;
 #pragma unroll
-        for (int dx = 0; dx < 3; ++dx) {
-            const int xx = x + dx - 1;
-            if (xx >= 0 && xx < n) acc = fma(st.c[dy][dx], e[(size_t)yy * n + xx], acc);
+                for (int dx = 0; dx < 3; ++dx) {
+                    const int xx = gx + dx - 1;
+                    if (xx >= 0 && xx < n) acc = fma(st.c[dy][dx], se[ly + dy - 1][lx + dx - 1], acc);
+                }
+            }
+            se[ly][lx] += (sr[ly][lx] - acc) / st.c[1][1];
         }
+        __syncthreads();
     }
-    e[(size_t)y * n + x] += (rhs[(size_t)y * n + x] - acc) / st.c[1][1];
 }
 
-// First relaxation from e = 0: the first red sub-lattice (0,0) gets e = rhs / A_diag (its
-// neighbours are all zero), every other point is zeroed.  Same values as zeroing e and
-// relaxing sub-lattice (0,0).
+// Pre-smoothing from e = 0, then the level residual restricted to the next level:
+//   epre = S_fwd(0; rhs) on the tile,
+//   rc[J][I] = sum_{dy,dx} w_dy w_dx (rhs - A epre)[2J+dy][2I+dx], w = (1/2, 1, 1/2),
+// for the coarse points whose fine support lies in the tile plus one column / row (halo 6).
 template <typename T>
-__global__ void k_gs_first(int n, Stencil9<T> st, const T *__restrict__ rhs, T *__restrict__ e, BatchRef bt)
+__global__ void __launch_bounds__(kLvTX *kLvTY / 2)
+k_level_pre(int nf, int nc, Stencil9<T> st, const T *__restrict__ rhs, T *__restrict__ epre, T *__restrict__ rc,
+            BatchRef bt)
 {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= n || y >= n || (bt.active && !bt.active[blockIdx.z])) return;
+    constexpr int H = 6, RX = kLvTX + 2 * H, RY = kLvTY + 2 * H;
+    __shared__ T se[RY][RX], sr[RY][RX];
+    __shared__ T res[kLvTY + 1][kLvTX + 1];
+    if (bt.active && !bt.active[blockIdx.z]) return;
     rhs += blockIdx.z * bt.vec;
-    e += blockIdx.z * bt.vec;
-    const size_t i = (size_t)y * n + x;
-    e[i] = ((x | y) & 1) ? T(0) : (rhs[i] - T(0)) / st.c[1][1];
-}
-
-// rc[J][I] = sum_{dy,dx} w_dy w_dx (rhs - A e)[2J+dy][2I+dx], w = (1/2, 1, 1/2): the level
-// residual at the 3x3 fine points under coarse hat (I, J), restricted in place.
-template <typename T>
-__global__ void k_level_residual_restrict(int nf, int nc, Stencil9<T> st, const T *__restrict__ rhs,
-                                          const T *__restrict__ e, T *__restrict__ rc, BatchRef bt)
-{
-    const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y;
-    if (I >= nc || J >= nc || (bt.active && !bt.active[blockIdx.z])) return;
-    rhs += blockIdx.z * bt.vec;
-    e += blockIdx.z * bt.vec;
+    epre += blockIdx.z * bt.vec;
     rc += blockIdx.z * bt.crs;
-    const T w[3] = {T(0.5), T(1), T(0.5)};
-    T acc = T(0);
-#pragma unroll
-    for (int dy = 0; dy < 3; ++dy) {
-        const int y = 2 * J + dy;
-        T s = T(0);
-#pragma unroll
-        for (int dx = 0; dx < 3; ++dx) {
-            const int x = 2 * I + dx;
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y, nt = blockDim.x * blockDim.y;
+    const int x0 = blockIdx.x * kLvTX, y0 = blockIdx.y * kLvTY, gx0 = x0 - H, gy0 = y0 - H;
+    for (int i = tid; i < RX * RY; i += nt) {
+        const int lx = i % RX, ly = i / RX, gx = gx0 + lx, gy = gy0 + ly;
+        sr[ly][lx] = (gx >= 0 && gx < nf && gy >= 0 && gy < nf) ? rhs[(size_t)gy * nf + gx] : T(0);
+        se[ly][lx] = T(0);
+    }
+    __syncthreads();
+    level_sweeps<T, RX, RY>(nf, gx0, gy0, st, se, sr, true);
+    for (int i = tid; i < kLvTX * kLvTY; i += nt) {
+        const int x = x0 + i % kLvTX, y = y0 + i / kLvTX;
+        if (x < nf && y < nf) epre[(size_t)y * nf + x] = se[y - gy0][x - gx0];
+    }
+    for (int i = tid; i < (kLvTX + 1) * (kLvTY + 1); i += nt) {
+        const int rx = i % (kLvTX + 1), ry = i / (kLvTX + 1), x = x0 + rx, y = y0 + ry;
+        T r = T(0);
+        if (x < nf && y < nf) {
             T a = T(0);
 #pragma unroll
             for (int ey = 0; ey < 3; ++ey) {
@@ -103,44 +118,80 @@ __global__ void k_level_residual_restrict(int nf, int nc, Stencil9<T> st, const 
 #pragma unroll
                 for (int ex = 0; ex < 3; ++ex) {
                     const int xx = x + ex - 1;
-                    if (xx >= 0 && xx < nf) a = fma(st.c[ey][ex], e[(size_t)yy * nf + xx], a);
+                    if (xx >= 0 && xx < nf) a = fma(st.c[ey][ex], se[yy - gy0][xx - gx0], a);
                 }
             }
-            const T r = rhs[(size_t)y * nf + x] - a;
-            s = fma(w[dx], r, s);
+            r = sr[y - gy0][x - gx0] - a;
         }
-        acc = fma(w[dy], s, acc);
+        res[ry][rx] = r;
     }
-    rc[(size_t)J * nc + I] = acc;
+    __syncthreads();
+    const T w[3] = {T(0.5), T(1), T(0.5)};
+    for (int i = tid; i < (kLvTX / 2) * (kLvTY / 2); i += nt) {
+        const int I = x0 / 2 + i % (kLvTX / 2), J = y0 / 2 + i / (kLvTX / 2);
+        if (I >= nc || J >= nc) continue;
+        T acc = T(0);
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy) {
+            T sacc = T(0);
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx) sacc = fma(w[dx], res[2 * J + dy - y0][2 * I + dx - x0], sacc);
+            acc = fma(w[dy], sacc, acc);
+        }
+        rc[(size_t)J * nc + I] = acc;
+    }
 }
 
-// e[y][x] += sum over the coarse points whose hats cover fine node (x, y)
+// Coarse correction and post-smoothing: e_out = S_rev(epre + P ec; rhs) on the tile,
+// P the exact embedding of the coarse hats (weights 1/2, 1, 1/2) (halo 4).
 template <typename T>
-__global__ void k_level_prolong_add(int nf, int nc, const T *__restrict__ ec, T *__restrict__ e, BatchRef bt)
+__global__ void __launch_bounds__(kLvTX *kLvTY / 2)
+k_level_post(int nf, int nc, Stencil9<T> st, const T *__restrict__ rhs, const T *__restrict__ epre,
+             const T *__restrict__ ec, T *__restrict__ eout, BatchRef bt)
 {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= nf || y >= nf || (bt.active && !bt.active[blockIdx.z])) return;
+    constexpr int H = 4, RX = kLvTX + 2 * H, RY = kLvTY + 2 * H;
+    __shared__ T se[RY][RX], sr[RY][RX];
+    if (bt.active && !bt.active[blockIdx.z]) return;
+    rhs += blockIdx.z * bt.vec;
+    epre += blockIdx.z * bt.vec;
+    eout += blockIdx.z * bt.vec;
     ec += blockIdx.z * bt.crs;
-    e += blockIdx.z * bt.vec;
-    // fine index x is coarse I = (x-1)/2 when odd (weight 1); between I = x/2-1 and x/2 when even
-    int Ix[2], Iy[2];
-    T wx[2], wy[2];
-    int nx, ny;
-    if (x & 1) { Ix[0] = (x - 1) / 2; wx[0] = T(1); nx = 1; }
-    else { Ix[0] = x / 2 - 1; Ix[1] = x / 2; wx[0] = T(0.5); wx[1] = T(0.5); nx = 2; }
-    if (y & 1) { Iy[0] = (y - 1) / 2; wy[0] = T(1); ny = 1; }
-    else { Iy[0] = y / 2 - 1; Iy[1] = y / 2; wy[0] = T(0.5); wy[1] = T(0.5); ny = 2; }
-    T acc = T(0);
-    for (int b = 0; b < ny; ++b) {
-        if (Iy[b] < 0 || Iy[b] >= nc) continue;
-        T s = T(0);
-        for (int a = 0; a < nx; ++a) {
-            if (Ix[a] < 0 || Ix[a] >= nc) continue;
-            s = fma(wx[a], ec[(size_t)Iy[b] * nc + Ix[a]], s);
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y, nt = blockDim.x * blockDim.y;
+    const int x0 = blockIdx.x * kLvTX, y0 = blockIdx.y * kLvTY, gx0 = x0 - H, gy0 = y0 - H;
+    for (int i = tid; i < RX * RY; i += nt) {
+        const int lx = i % RX, ly = i / RX, x = gx0 + lx, y = gy0 + ly;
+        T ev = T(0), rv = T(0);
+        if (x >= 0 && x < nf && y >= 0 && y < nf) {
+            rv = rhs[(size_t)y * nf + x];
+            // fine x is coarse (x-1)/2 when odd (weight 1); between x/2-1 and x/2 when even
+            int Ix[2], Iy[2];
+            T wx[2], wy[2];
+            int nx, ny;
+            if (x & 1) { Ix[0] = (x - 1) / 2; wx[0] = T(1); nx = 1; }
+            else { Ix[0] = x / 2 - 1; Ix[1] = x / 2; wx[0] = T(0.5); wx[1] = T(0.5); nx = 2; }
+            if (y & 1) { Iy[0] = (y - 1) / 2; wy[0] = T(1); ny = 1; }
+            else { Iy[0] = y / 2 - 1; Iy[1] = y / 2; wy[0] = T(0.5); wy[1] = T(0.5); ny = 2; }
+            T acc = T(0);
+            for (int bq = 0; bq < ny; ++bq) {
+                if (Iy[bq] < 0 || Iy[bq] >= nc) continue;
+                T sacc = T(0);
+                for (int aq = 0; aq < nx; ++aq) {
+                    if (Ix[aq] < 0 || Ix[aq] >= nc) continue;
+                    sacc = fma(wx[aq], ec[(size_t)Iy[bq] * nc + Ix[aq]], sacc);
+                }
+                acc = fma(wy[bq], sacc, acc);
+            }
+            ev = epre[(size_t)y * nf + x] + acc;
         }
-        acc = fma(wy[b], s, acc);
+        se[ly][lx] = ev;
+        sr[ly][lx] = rv;
     }
-    e[(size_t)y * nf + x] += acc;
+    __syncthreads();
+    level_sweeps<T, RX, RY>(nf, gx0, gy0, st, se, sr, false);
+    for (int i = tid; i < kLvTX * kLvTY; i += nt) {
+        const int x = x0 + i % kLvTX, y = y0 + i / kLvTX;
+        if (x < nf && y < nf) eout[(size_t)y * nf + x] = se[y - gy0][x - gx0];
+    }
 }
 
 // x = Ainv rhs in FP64, one warp per row (dense inverse of the directly solved level)
@@ -307,41 +358,11 @@ __global__ void __launch_bounds__(1024) k_vcycle_tail(TailArgs<T> a)
     for (int i = threadIdx.x; i < a.n[0] * a.n[0]; i += blockDim.x) a.e0[i] = E[0][i];
 }
 
-dim3 grid2(int nx, int ny, dim3 blk)
-{
-    return dim3((nx + blk.x - 1) / blk.x, (ny + blk.y - 1) / blk.y);
-}
-
-dim3 grid3(int nx, int ny, int nz, dim3 blk)
-{
-    return dim3((nx + blk.x - 1) / blk.x, (ny + blk.y - 1) / blk.y, nz);
-}
-
-// red-black order: red sub-lattices (0,0), (1,1) then black (1,0), (0,1)
-constexpr int kGsSeq[4][2] = {{0, 0}, {1, 1}, {1, 0}, {0, 1}};
-
+// levE[l], levR[l]: the e and rhs arrays of level l >= 1 in the storage type T; levP[l]:
+// the pre-smoothed correction of level l
 template <typename T>
-cudaError_t gs_pass(const Level &L, const Stencil9<T> &st, const T *rhs, T *e, bool forward,
-                    bool from_zero, int nb, const BatchRef &bt, cudaStream_t s)
-{
-    dim3 blk(32, 4);
-    const int half = (L.n + 1) / 2;
-    for (int t = 0; t < 4; ++t) {
-        const int c = forward ? t : 3 - t;
-        if (from_zero && t == 0) {   // forward pass from e = 0: the first colour is (0,0)
-            k_gs_first<T><<<grid3(L.n, L.n, nb, blk), blk, 0, s>>>(L.n, st, rhs, e, bt);
-            count_launches(1);
-            continue;
-        }
-        k_gs_sublattice<T><<<grid3(half, half, nb, blk), blk, 0, s>>>(L.n, kGsSeq[c][0], kGsSeq[c][1], st, rhs, e, bt);
-        count_launches(1);
-    }
-    return cudaGetLastError();
-}
-
-// levE[l], levR[l]: the e and rhs arrays of level l >= 1 in the storage type T
-template <typename T>
-cudaError_t vcycle(const Solver &S, int l, const T *rhs, T *e, T *const *levE, T *const *levR, cudaStream_t s)
+cudaError_t vcycle(const Solver &S, int l, const T *rhs, T *e, T *const *levE, T *const *levR, T *const *levP,
+                   cudaStream_t s)
 {
     const Level &L = S.lev[l];
     const int last = (int)S.lev.size() - 1;
@@ -378,17 +399,15 @@ cudaError_t vcycle(const Solver &S, int l, const T *rhs, T *e, T *const *levE, T
     const Level &C = S.lev[l + 1];
     const Stencil9<T> st = level_stencil<T>(L);
     const BatchRef bt{S.active, L.N, 0, C.N};
-    dim3 blk(32, 4);
+    const dim3 blk(kLvTX, kLvTY / 2), grd((L.n + kLvTX - 1) / kLvTX, (L.n + kLvTY - 1) / kLvTY, nb);
     cudaError_t err;
-    if ((err = gs_pass<T>(L, st, rhs, e, true, true, nb, bt, s)) != cudaSuccess) return err;
-    k_level_residual_restrict<T><<<grid3(C.n, C.n, nb, blk), blk, 0, s>>>(L.n, C.n, st, rhs, e, levR[l + 1], bt);
+    k_level_pre<T><<<grd, blk, 0, s>>>(L.n, C.n, st, rhs, levP[l], levR[l + 1], bt);
     count_launches(1);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
-    if ((err = vcycle<T>(S, l + 1, levR[l + 1], levE[l + 1], levE, levR, s)) != cudaSuccess) return err;
-    k_level_prolong_add<T><<<grid3(L.n, L.n, nb, blk), blk, 0, s>>>(L.n, C.n, levE[l + 1], e, bt);
+    if ((err = vcycle<T>(S, l + 1, levR[l + 1], levE[l + 1], levE, levR, levP, s)) != cudaSuccess) return err;
+    k_level_post<T><<<grd, blk, 0, s>>>(L.n, C.n, st, rhs, levP[l], levE[l + 1], e, bt);
     count_launches(1);
-    if ((err = cudaGetLastError()) != cudaSuccess) return err;
-    return gs_pass<T>(L, st, rhs, e, false, false, nb, bt, s);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -396,16 +415,16 @@ cudaError_t vcycle(const Solver &S, int l, const T *rhs, T *e, T *const *levE, T
 cudaError_t launch_coarse_solve(const Solver &S, const double *dc, double *ec, cudaStream_t st)
 {
     if (S.dim == 3) return launch3d_coarse_solve(S, dc, ec, st);
-    std::vector<double *> E(S.lev.size()), Rr(S.lev.size());
-    for (size_t l = 0; l < S.lev.size(); ++l) { E[l] = S.lev[l].e; Rr[l] = S.lev[l].rhs; }
-    return vcycle<double>(S, 0, dc, ec, E.data(), Rr.data(), st);
+    std::vector<double *> E(S.lev.size()), Rr(S.lev.size()), Pp(S.lev.size());
+    for (size_t l = 0; l < S.lev.size(); ++l) { E[l] = S.lev[l].e; Rr[l] = S.lev[l].rhs; Pp[l] = S.lev[l].pre; }
+    return vcycle<double>(S, 0, dc, ec, E.data(), Rr.data(), Pp.data(), st);
 }
 
 cudaError_t launch_inner_coarse(const Solver &S, cudaStream_t st)
 {
     if (S.dim == 3) return launch3d_inner_coarse(S, st);
     const MixedState &X = S.mx;
-    return vcycle<float>(S, 0, X.dc, X.ec, X.lev_e.data(), X.lev_rhs.data(), st);
+    return vcycle<float>(S, 0, X.dc, X.ec, X.lev_e.data(), X.lev_rhs.data(), X.lev_pre.data(), st);
 }
 
 }  // namespace iga2l

@@ -27,58 +27,6 @@ namespace {
 
 constexpr int kResTX = 32, kResTY = 8;   // residual tile (outputs per CTA)
 
-// d = b - A u  (b != nullptr)  or  d = A u  (b == nullptr), arithmetic in T, output
-// stored as TO; part[cta] = sum of d^2 (in double) when part != nullptr.
-template <int P, typename T, typename TO>
-__global__ void __launch_bounds__(kResTX *kResTY)
-k_residual2d(int n, int npc, const T *__restrict__ stencil, const int *__restrict__ pcls,
-             const T *__restrict__ u, const T *__restrict__ b, TO *__restrict__ d,
-             double *__restrict__ part, BatchRef bt)
-{
-    constexpr int W = 2 * P + 1;
-    constexpr int SX = kResTX + 2 * P, SY = kResTY + 2 * P;
-    __shared__ T su[SY][SX];
-    __shared__ double red[kResTX * kResTY / 32];
-    const int z = blockIdx.z;
-    if (bt.active && !bt.active[z]) return;
-    u += z * bt.vec;
-    if (b) b += z * bt.vec;
-    if (d) d += z * bt.vec;
-    if (part) part += z * bt.aux;
-    const int x0 = blockIdx.x * kResTX, y0 = blockIdx.y * kResTY;
-    const int tid = threadIdx.x + kResTX * threadIdx.y;
-    for (int t = tid; t < SX * SY; t += kResTX * kResTY) {
-        const int ly = t / SX, lx = t % SX;
-        const int gx = x0 + lx - P, gy = y0 + ly - P;
-        su[ly][lx] = (gx >= 0 && gx < n && gy >= 0 && gy < n) ? u[(size_t)gy * n + gx] : T(0);
-    }
-    __syncthreads();
-    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
-    T dv = T(0);
-    if (x < n && y < n) {
-        const T *st = stencil + (size_t)(pcls[y] * npc + pcls[x]) * (W * W);
-        T acc = T(0);
-#pragma unroll
-        for (int bb = 0; bb < W; ++bb)
-#pragma unroll
-            for (int aa = 0; aa < W; ++aa)
-                acc = fma(__ldg(&st[bb * W + aa]), su[threadIdx.y + bb][threadIdx.x + aa], acc);
-        dv = b ? b[(size_t)y * n + x] - acc : acc;
-        if (d) d[(size_t)y * n + x] = (TO)dv;
-    }
-    if (part) {
-        double s = (double)dv * (double)dv;
-        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-        if ((tid & 31) == 0) red[tid >> 5] = s;
-        __syncthreads();
-        if (tid == 0) {
-            double tot = 0.0;
-            for (int w = 0; w < kResTX * kResTY / 32; ++w) tot += red[w];
-            part[blockIdx.x + gridDim.x * blockIdx.y] = tot;
-        }
-    }
-}
-
 // Fixed-order sum of the partials (deterministic norm).
 __global__ void k_sum_partials(const double *__restrict__ part, int np, double *__restrict__ out)
 {
@@ -213,6 +161,111 @@ template <>
 __device__ __forceinline__ double2 cmk1<double>(int p, int a) { return c_mk1d[p][a]; }
 template <>
 __device__ __forceinline__ float2 cmk1<float>(int p, int a) { return c_mk1f[p][a]; }
+
+// d = b - A u  (b != nullptr)  or  d = A u  (b == nullptr), arithmetic in T, output
+// stored as TO; part[cta] = sum of d^2 (in double) when part != nullptr.  A 32 x 8 tile
+// of outputs per CTA with u (tile + halo p) in shared memory and the y-then-x sum
+// factorisation A u = sum_b K_y[b] (sum_a M_x[a] u) + M_y[b] (sum_a K_x[a] u): first the
+// pairs (K_y u, M_y u) of every output row at every window column, then per output the
+// x sums (2(2p+1)(1 + 2p/32) + 2(2p+1) FMAs per output instead of (2p+1)^2).  Interior
+// tiles take the interior 1D rows from constant memory; boundary tiles the 1D rows of
+// their own rows and columns, scaled the same way (h K, M / h).
+template <int P, typename T, typename TO>
+__global__ void __launch_bounds__(kResTX *kResTY)
+k_residual2d(int n, const T *__restrict__ kband, const T *__restrict__ mband, const T *__restrict__ u,
+             const T *__restrict__ b, TO *__restrict__ d, double *__restrict__ part, BatchRef bt)
+{
+    using T2 = typename Vec2<T>::type;
+    constexpr int W = 2 * P + 1;
+    constexpr int SX = kResTX + 2 * P, SY = kResTY + 2 * P;
+    __shared__ T su[SY][SX];
+    __shared__ T2 yv[kResTY][SX];
+    __shared__ T2 kmy[kResTY][W], mkx[kResTX][W];   // boundary tiles
+    __shared__ double red[kResTX * kResTY / 32];
+    const int z = blockIdx.z;
+    if (bt.active && !bt.active[z]) return;
+    u += z * bt.vec;
+    if (b) b += z * bt.vec;
+    if (d) d += z * bt.vec;
+    if (part) part += z * bt.aux;
+    const int x0 = blockIdx.x * kResTX, y0 = blockIdx.y * kResTY;
+    const int tid = threadIdx.x + kResTX * threadIdx.y;
+    constexpr int NT = kResTX * kResTY;
+    constexpr int K = (SX * SY + NT - 1) / NT;
+    T v[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int t = tid + k * NT;
+        const int gx = x0 + t % SX - P, gy = y0 + t / SX - P;
+        v[k] = (t < SX * SY && gx >= 0 && gx < n && gy >= 0 && gy < n) ? u[(size_t)gy * n + gx] : T(0);
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int t = tid + k * NT;
+        if (t < SX * SY) su[t / SX][t % SX] = v[k];
+    }
+    const bool fast = x0 >= 2 * P - 1 && x0 + kResTX - 1 <= n - 2 * P && y0 >= 2 * P - 1 &&
+                      y0 + kResTY - 1 <= n - 2 * P;
+    if (!fast) {
+        const T h = T(1) / T(n - P + 2), hinv = T(n - P + 2);
+        for (int t = tid; t < (kResTX + kResTY) * W; t += NT) {
+            const int row = t / W, a = t - row * W;
+            if (row < kResTY) {
+                const int gy = y0 + row;
+                T2 km;
+                km.x = gy < n ? kband[(size_t)gy * W + a] * h : T(0);
+                km.y = gy < n ? mband[(size_t)gy * W + a] * hinv : T(0);
+                kmy[row][a] = km;
+            } else {
+                const int gx = x0 + row - kResTY;
+                T2 mk;
+                mk.x = gx < n ? mband[(size_t)gx * W + a] * hinv : T(0);
+                mk.y = gx < n ? kband[(size_t)gx * W + a] * h : T(0);
+                mkx[row - kResTY][a] = mk;
+            }
+        }
+    }
+    __syncthreads();
+    for (int pt = tid; pt < kResTY * SX; pt += NT) {
+        const int r = pt / SX, c = pt - r * SX;
+        T2 y = splat2<T2>(T(0));
+        if (fast) {
+#pragma unroll
+            for (int bb = 0; bb < W; ++bb) y = fma2(ckm1<T>(P, bb), splat2<T2>(su[r + bb][c]), y);
+        } else {
+#pragma unroll
+            for (int bb = 0; bb < W; ++bb) y = fma2(kmy[r][bb], splat2<T2>(su[r + bb][c]), y);
+        }
+        yv[r][c] = y;
+    }
+    __syncthreads();
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    T dv = T(0);
+    if (x < n && y < n) {
+        T2 s2 = splat2<T2>(T(0));
+        if (fast) {
+#pragma unroll
+            for (int a = 0; a < W; ++a) s2 = fma2(cmk1<T>(P, a), yv[threadIdx.y][threadIdx.x + a], s2);
+        } else {
+#pragma unroll
+            for (int a = 0; a < W; ++a) s2 = fma2(mkx[threadIdx.x][a], yv[threadIdx.y][threadIdx.x + a], s2);
+        }
+        const T acc = s2.x + s2.y;
+        dv = b ? b[(size_t)y * n + x] - acc : acc;
+        if (d) d[(size_t)y * n + x] = (TO)dv;
+    }
+    if (part) {
+        double s = (double)dv * (double)dv;
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+        if ((tid & 31) == 0) red[tid >> 5] = s;
+        __syncthreads();
+        if (tid == 0) {
+            double tot = 0.0;
+            for (int w = 0; w < kResTX * kResTY / 32; ++w) tot += red[w];
+            part[blockIdx.x + gridDim.x * blockIdx.y] = tot;
+        }
+    }
+}
 
 // Geometry of one CTA of the TILE(TT) schedule.
 template <int P, int S, int TT>
@@ -564,25 +617,25 @@ __global__ void k_mass2d(int n, const double *__restrict__ Mb, const double *__r
 }
 
 template <int P, typename T, typename TO>
-cudaError_t residual_p(const Solver &S, const T *stencil, const T *u, const T *b, TO *d, double *part,
+cudaError_t residual_p(const Solver &S, const T *kband, const T *mband, const T *u, const T *b, TO *d, double *part,
                        cudaStream_t st)
 {
     dim3 blk(kResTX, kResTY), grd((S.n + kResTX - 1) / kResTX, (S.n + kResTY - 1) / kResTY, S.nbatch);
-    k_residual2d<P, T, TO><<<grd, blk, 0, st>>>(S.n, S.ht.npc, stencil, S.pcls, u, b, d, part,
+    k_residual2d<P, T, TO><<<grd, blk, 0, st>>>(S.n, kband, mband, u, b, d, part,
                                                  BatchRef{S.active, S.N, residual_partials(S), 0});
     count_launches(1);
     return cudaGetLastError();
 }
 
 template <typename T, typename TO>
-cudaError_t residual_any(const Solver &S, const T *stencil, const T *u, const T *b, TO *d, double *part,
-                         cudaStream_t st)
+cudaError_t residual_any(const Solver &S, const T *kband, const T *mband, const T *u, const T *b, TO *d,
+                         double *part, cudaStream_t st)
 {
     switch (S.p) {
-    case 2: return residual_p<2, T, TO>(S, stencil, u, b, d, part, st);
-    case 3: return residual_p<3, T, TO>(S, stencil, u, b, d, part, st);
-    case 4: return residual_p<4, T, TO>(S, stencil, u, b, d, part, st);
-    case 5: return residual_p<5, T, TO>(S, stencil, u, b, d, part, st);
+    case 2: return residual_p<2, T, TO>(S, kband, mband, u, b, d, part, st);
+    case 3: return residual_p<3, T, TO>(S, kband, mband, u, b, d, part, st);
+    case 4: return residual_p<4, T, TO>(S, kband, mband, u, b, d, part, st);
+    case 5: return residual_p<5, T, TO>(S, kband, mband, u, b, d, part, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -731,7 +784,7 @@ cudaError_t launch_residual(const Solver &S, const double *u, const double *b, d
                             double *part, cudaStream_t st)
 {
     if (S.dim == 3) return launch3d_residual(S, u, b, d, part, st);
-    return residual_any<double, double>(S, S.stencil, u, b, d, part, st);
+    return residual_any<double, double>(S, S.Kb, S.Mb, u, b, d, part, st);
 }
 
 cudaError_t launch_apply_A(const Solver &S, const double *u, double *y, cudaStream_t st)
@@ -822,7 +875,7 @@ cudaError_t launch_outer_residual(const Solver &S, const double *u, const double
                                   double *part, cudaStream_t st)
 {
     if (S.dim == 3) return launch3d_outer_residual(S, u, b, r32, part, st);
-    return residual_any<double, float>(S, S.stencil, u, b, r32, part, st);
+    return residual_any<double, float>(S, S.Kb, S.Mb, u, b, r32, part, st);
 }
 
 cudaError_t launch_inner_fine(const Solver &S, const float *r32, bool reverse, cudaStream_t st)
@@ -831,7 +884,7 @@ cudaError_t launch_inner_fine(const Solver &S, const float *r32, bool reverse, c
     const MixedState &X = S.mx;
     cudaError_t e = cudaMemsetAsync(X.delta, 0, sizeof(float) * S.N * S.nbatch, st);
     if (e == cudaSuccess) e = schwarz_any<float>(S, X.stencil, X.Kb, X.Mb, X.binv, X.delta, r32, reverse, st);
-    if (e == cudaSuccess) e = residual_any<float, float>(S, X.stencil, X.delta, r32, X.d, nullptr, st);
+    if (e == cudaSuccess) e = residual_any<float, float>(S, X.Kb, X.Mb, X.delta, r32, X.d, nullptr, st);
     if (e == cudaSuccess) e = restrict_any<float>(S, X.Rb, X.d, X.t, X.dc, st);
     return e;
 }
