@@ -267,6 +267,129 @@ k_residual2d(int n, const T *__restrict__ kband, const T *__restrict__ mband, co
     }
 }
 
+// One colour of the LATTICE schedule with the residual sum-factorised and the work
+// packed across lanes (the FP32 sweeps, where the direct form is bound by its loads).  A CTA of 256 threads takes NB
+// consecutive blocks of the colour, centres (ox + q i, oy + q j):
+//   1. thread (block, window column c) loads the column slice of u (S + 2P values) and
+//      forms for each block row r the pair (sum_b K_y[b] u, sum_b M_y[b] u);
+//   2. thread per block DOF: the x sums sum_a M_x[a] Y1 + K_x[a] Y2, r = b - A u;
+//   3. thread per block DOF: row e of the block's inverse times r, added to u.
+// Interior rows/columns take the h-scaled interior 1D rows from constant memory, the
+// others their own 1D rows (scaled the same way); with T = float the boundary block
+// classes use the FP64 inverses binv64 when given.
+template <int P, int S, typename T>
+__global__ void __launch_bounds__(256)
+k_schwarz_lattice2d_sf(int n, int nbc, int q, int ox, int oy, int nbx, int nblocks,
+                       const T *__restrict__ kband, const T *__restrict__ mband,
+                       const T *__restrict__ binv, const double *__restrict__ binv64, int interior,
+                       const int *__restrict__ bcls, T *__restrict__ u, const T *__restrict__ b, BatchRef bt)
+{
+    using T2 = typename Vec2<T>::type;
+    constexpr int W = 2 * P + 1, SS = S * S, R = (S - 1) / 2, WIN = S + 2 * P, PCI = 2 * P - 1;
+    constexpr int NT = 256, NB = NT / WIN;
+    __shared__ T2 yb[NB][S][WIN];
+    __shared__ T rs[NB][SS];
+    __shared__ T sbi[SS * SS];
+    if (bt.active && !bt.active[blockIdx.y]) return;
+    u += blockIdx.y * bt.vec;
+    b += blockIdx.y * bt.vec;
+    const int tid = threadIdx.x;
+    const int blk0 = blockIdx.x * NB;
+    const T h = T(1) / T(n - P + 2), hinv = T(n - P + 2);
+    for (int i = tid; i < SS * SS; i += NT) sbi[i] = binv[(size_t)interior * SS * SS + i];
+    // 1. y pass
+    if (tid < NB * WIN) {
+        const int j = tid / WIN, c = tid - j * WIN, blk = blk0 + j;
+        if (blk < nblocks) {
+            const int cx = ox + q * (blk % nbx), cy = oy + q * (blk / nbx);
+            const int x = cx - R - P + c;
+            const bool xin = x >= 0 && x < n;
+            T v[WIN];
+#pragma unroll
+            for (int k = 0; k < WIN; ++k) {
+                const int y = cy - R - P + k;
+                v[k] = (xin && y >= 0 && y < n) ? u[(size_t)y * n + x] : T(0);
+            }
+            const bool yint = cy - R >= PCI && cy + R <= n - 2 * P;
+#pragma unroll
+            for (int r = 0; r < S; ++r) {
+                T2 acc = splat2<T2>(T(0));
+                if (yint) {
+#pragma unroll
+                    for (int bb = 0; bb < W; ++bb) acc = fma2(ckm1<T>(P, bb), splat2<T2>(v[r + bb]), acc);
+                } else {
+                    const int gy = cy - R + r;
+                    if (gy >= 0 && gy < n) {
+#pragma unroll
+                        for (int bb = 0; bb < W; ++bb) {
+                            T2 km;
+                            km.x = kband[(size_t)gy * W + bb] * h;
+                            km.y = mband[(size_t)gy * W + bb] * hinv;
+                            acc = fma2(km, splat2<T2>(v[r + bb]), acc);
+                        }
+                    }
+                }
+                yb[j][r][c] = acc;
+            }
+        }
+    }
+    __syncthreads();
+    // 2. x pass and block residuals
+    for (int o = tid; o < NB * SS; o += NT) {
+        const int j = o / SS, e = o - j * SS, blk = blk0 + j;
+        if (blk >= nblocks) continue;
+        const int cx = ox + q * (blk % nbx), cy = oy + q * (blk / nbx);
+        const int ey = e / S, ex = e - ey * S;
+        const int x = cx - R + ex, y = cy - R + ey;
+        T r = T(0);
+        if (x >= 0 && x < n && y >= 0 && y < n) {
+            const bool xint = cx - R >= PCI && cx + R <= n - 2 * P;
+            T2 acc = splat2<T2>(T(0));
+            if (xint) {
+#pragma unroll
+                for (int a = 0; a < W; ++a) acc = fma2(cmk1<T>(P, a), yb[j][ey][ex + a], acc);
+            } else {
+#pragma unroll
+                for (int a = 0; a < W; ++a) {
+                    T2 mk;
+                    mk.x = mband[(size_t)x * W + a] * hinv;
+                    mk.y = kband[(size_t)x * W + a] * h;
+                    acc = fma2(mk, yb[j][ey][ex + a], acc);
+                }
+            }
+            r = b[(size_t)y * n + x] - (acc.x + acc.y);
+        }
+        rs[j][e] = r;
+    }
+    __syncthreads();
+    // 3. block solves
+    for (int o = tid; o < NB * SS; o += NT) {
+        const int j = o / SS, e = o - j * SS, blk = blk0 + j;
+        if (blk >= nblocks) continue;
+        const int cx = ox + q * (blk % nbx), cy = oy + q * (blk / nbx);
+        const int x = cx - R + e % S, y = cy - R + e / S;
+        if (x < 0 || x >= n || y < 0 || y >= n) continue;
+        const int cls = bcls[cy] * nbc + bcls[cx];
+        T ev = T(0);
+        if (cls == interior) {
+            const T *Bi = sbi + e * SS;
+#pragma unroll
+            for (int f = 0; f < SS; ++f) ev = fma(Bi[f], rs[j][f], ev);
+        } else if (sizeof(T) == sizeof(double) || !binv64) {
+            const T *Bi = binv + ((size_t)cls * SS + e) * SS;
+#pragma unroll
+            for (int f = 0; f < SS; ++f) ev = fma(__ldg(&Bi[f]), rs[j][f], ev);
+        } else {
+            const double *Bi = binv64 + ((size_t)cls * SS + e) * SS;
+            double ed[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+            for (int f = 0; f < SS; ++f) ed[f & 3] = fma(__ldg(&Bi[f]), (double)rs[j][f], ed[f & 3]);
+            ev = (T)((ed[0] + ed[1]) + (ed[2] + ed[3]));
+        }
+        u[(size_t)y * n + x] += ev;
+    }
+}
+
 // Geometry of one CTA of the TILE(TT) schedule.
 template <int P, int S, int TT>
 struct TileGeom {
@@ -485,14 +608,18 @@ k_schwarz_tile2d(int n, int nbc, int q, int g, int rev, int px, int py, int ntpx
 #pragma unroll
                 for (int f = 0; f < SS; ++f) ev = fma(__ldg(&Bi[f]), rsb[f], ev);
             } else {
+                // FP64 row of a boundary-class inverse: loads first, four short chains
                 const double *Bi = binv64 + ((size_t)cls * SS + e) * SS;
-                double ed0 = 0.0, ed1 = 0.0;
+                double bv[SS], ed[4] = {0.0, 0.0, 0.0, 0.0};
+                T rv[2 * G::NB2];
 #pragma unroll
-                for (int f = 0; f < SS; ++f) {
-                    if (f & 1) ed1 = fma(__ldg(&Bi[f]), (double)rsb[f], ed1);
-                    else ed0 = fma(__ldg(&Bi[f]), (double)rsb[f], ed0);
-                }
-                ev = (T)(ed0 + ed1);
+                for (int f = 0; f < SS; ++f) bv[f] = __ldg(&Bi[f]);
+                const T2 *r2 = reinterpret_cast<const T2 *>(rsb);
+#pragma unroll
+                for (int k = 0; k < G::NB2; ++k) { const T2 v = r2[k]; rv[2 * k] = v.x; rv[2 * k + 1] = v.y; }
+#pragma unroll
+                for (int f = 0; f < SS; ++f) ed[f & 3] = fma(bv[f], (double)rv[f], ed[f & 3]);
+                ev = (T)((ed[0] + ed[1]) + (ed[2] + ed[3]));
             }
             if (in) su[(ly + H) * SW + (lx + H)] += ev;
         }
@@ -641,10 +768,15 @@ cudaError_t residual_any(const Solver &S, const T *kband, const T *mband, const 
 }
 
 template <int P, int SB, typename T>
-cudaError_t schwarz_lattice_p(const Solver &S, const T *stencil, const T *binv, T *u, const T *b, bool reverse,
-                              cudaStream_t st)
+cudaError_t schwarz_lattice_p(const Solver &S, const T *stencil, const T *kband, const T *mband, const T *binv, T *u,
+                              const T *b, bool reverse, cudaStream_t st)
 {
-    constexpr int BPC = 256 / (SB * SB);
+    // FP32: the packed sum-factorised kernel (the direct form is bound by its L1 loads);
+    // FP64: the direct form, which keeps the FP64 pipe busier (measured at 1024^2: p = 5
+    // sweep 7.2 ms direct against 9.2 ms factorised, whose CTAs wait on three dependent
+    // global-memory phases)
+    constexpr bool SF = sizeof(T) == sizeof(float);
+    constexpr int BPC = 256 / (SB * SB), NBSF = 256 / (SB + 2 * P);
     const int q = S.q, ncol = q * q;
     const int interior = S.ht.L * S.ht.nbc + S.ht.L;
     for (int t = 0; t < ncol; ++t) {
@@ -654,10 +786,15 @@ cudaError_t schwarz_lattice_p(const Solver &S, const T *stencil, const T *binv, 
         const int nbx = (S.n - ox + q - 1) / q, nby = (S.n - oy + q - 1) / q;
         const int nblocks = nbx * nby;
         if (nblocks <= 0) continue;
-        const int grid = (nblocks + BPC - 1) / BPC;
-        k_schwarz_lattice2d<P, SB, T><<<dim3(grid, S.nbatch), 256, 0, st>>>(S.n, S.ht.npc, S.ht.nbc, q, ox, oy, nbx,
-                                                             nblocks, stencil, S.pcls, binv, S.boundary64(),
-                                                             interior, S.bcls, u, b, BatchRef{S.active, S.N, 0, 0});
+        if constexpr (SF) {
+            k_schwarz_lattice2d_sf<P, SB, T><<<dim3((nblocks + NBSF - 1) / NBSF, S.nbatch), 256, 0, st>>>(
+                S.n, S.ht.nbc, q, ox, oy, nbx, nblocks, kband, mband, binv, S.boundary64(), interior, S.bcls, u, b,
+                BatchRef{S.active, S.N, 0, 0});
+        } else {
+            k_schwarz_lattice2d<P, SB, T><<<dim3((nblocks + BPC - 1) / BPC, S.nbatch), 256, 0, st>>>(
+                S.n, S.ht.npc, S.ht.nbc, q, ox, oy, nbx, nblocks, stencil, S.pcls, binv, S.boundary64(), interior,
+                S.bcls, u, b, BatchRef{S.active, S.N, 0, 0});
+        }
         count_launches(1);
         cudaError_t err = cudaGetLastError();
         if (err != cudaSuccess) return err;
@@ -694,7 +831,7 @@ cudaError_t schwarz_p(const Solver &S, const T *stencil, const T *kband, const T
 {
     if (S.opt.schedule == IGA2L_SCHED_TILE)
         return schwarz_tile_p<P, SB, T>(S, kband, mband, binv, u, b, reverse, st);
-    return schwarz_lattice_p<P, SB, T>(S, stencil, binv, u, b, reverse, st);
+    return schwarz_lattice_p<P, SB, T>(S, stencil, kband, mband, binv, u, b, reverse, st);
 }
 
 template <typename T>
