@@ -65,7 +65,8 @@ typedef struct iga2l_solver *iga2l_handle;
 typedef struct {
     int precision;   /* IGA2L_FP64, IGA2L_MIXED_FP32 or IGA2L_MIXED_FP32_ALL */
     int schedule;    /* IGA2L_SCHED_LATTICE or IGA2L_SCHED_TILE */
-    int tile;        /* TILE side T >= period (0 = the side compiled for p: 20 for p = 2, 5; 21 for p = 3, 4) */
+    int tile;        /* TILE side T >= period (0 = the side compiled for p: 20 for p = 2, 5; 21 for
+                        p = 3, 4; 22 for p = 6; the TILE schedule is compiled for p <= 6) */
     int period;      /* colour period q >= s + p (0 = library default for p) */
     int stride;      /* colour stride g, gcd(g, q) = 1 (0 = library default) */
     int coarse;      /* IGA2L_COARSE_VCYCLE (Section 3.2) or IGA2L_COARSE_EXACT */
@@ -78,7 +79,7 @@ typedef struct {
  * graphs on. */
 void iga2l_default_options(iga2l_options *opt);
 
-/* Builds the solver for degree p (2..5 in 2D, 2..4 in 3D), m elements per axis,
+/* Builds the solver for degree p (2..8 in 2D, 2..4 in 3D), m elements per axis,
  * dimension dim (2 or 3; 3D uses the LATTICE schedule).
  * Host work: 1D B-spline Galerkin tables (Section 2.1), the Schwarz block
  * inverses of every block class (Section 3.1.1), the lumped L2-projection

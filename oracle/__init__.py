@@ -182,7 +182,7 @@ def apply_A(dim: int, K: np.ndarray, M: np.ndarray, u: np.ndarray, w: int) -> np
 
 # Colour period q and stride g per degree used by the tests and the benchmark
 # (this project's choice; see or_schedule in iga_oracle.h).
-DEFAULT_COLOURING = {2: (5, 2), 3: (7, 2), 4: (7, 2), 5: (10, 3)}
+DEFAULT_COLOURING = {2: (5, 2), 3: (7, 2), 4: (7, 2), 5: (10, 3), 6: (11, 4), 7: (14, 5), 8: (17, 4)}
 
 
 def default_colouring(p: int, s: int):

@@ -22,7 +22,7 @@ import torch
 
 from . import iga2l, synth
 
-COLOURING = {2: (5, 2), 3: (7, 2), 4: (7, 2), 5: (10, 3)}
+COLOURING = {2: (5, 2), 3: (7, 2), 4: (7, 2), 5: (10, 3), 6: (11, 4), 7: (14, 5), 8: (17, 4)}
 CANDIDATES = (iga2l.SCHED_LATTICE, iga2l.SCHED_TILE)
 _cache: dict = {}
 _cache_lock = threading.Lock()
@@ -49,6 +49,8 @@ def autotune_schedule(p: int, m: int, precision: int, cache_path: str | None = N
     q, g = COLOURING[p]
     best, best_ms = None, float("inf")
     for sched in CANDIDATES:
+        if sched == iga2l.SCHED_TILE and p > 6:   # TILE is compiled for blocks up to 5x5
+            continue
         S = iga2l.Solver(p, m, period=q, stride=g, precision=precision, schedule=sched)
         f = torch.tensor(synth.coefficients(S.N, 77), device="cuda")
         b = torch.empty_like(f)

@@ -324,7 +324,7 @@ static int assemble_impl(int p, int m, int dim, int nbatch, bool batch, const ig
     if (opt_in) opt = *opt_in; else iga2l_default_options(&opt);
     if (opt.max_cycles <= 0) opt.max_cycles = 100;
     if (dim != 2 && dim != 3) return fail(IGA2L_ERR_INVALID_ARG, "dim must be 2 or 3");
-    if (p < 2 || p > kMaxP) return fail(IGA2L_ERR_INVALID_ARG, "p must be in 2..5");
+    if (p < 2 || p > kMaxP) return fail(IGA2L_ERR_INVALID_ARG, "p must be in 2..8");
     if (dim == 3 && p > 4) return fail(IGA2L_ERR_UNSUPPORTED, "3D kernels are compiled for p = 2..4");
     if (m < 4 * p + 4 || (m % 2) != 0)
         return fail(IGA2L_ERR_INVALID_ARG, "m must be even and >= 4p+4 (aggressive 2h coarsening)");
@@ -336,12 +336,13 @@ static int assemble_impl(int p, int m, int dim, int nbatch, bool batch, const ig
         return fail(IGA2L_ERR_UNSUPPORTED, "3D uses the LATTICE schedule");
     if (opt.schedule == IGA2L_SCHED_TILE) {
         if (opt.tile == 0) opt.tile = tile_side(p);
+        if (tile_side(p) == 0) return fail(IGA2L_ERR_UNSUPPORTED, "the TILE schedule is compiled for p <= 6");
         if (opt.tile != tile_side(p)) return fail(IGA2L_ERR_UNSUPPORTED, "TILE side not compiled for this degree");
     }
     if (opt.coarse != IGA2L_COARSE_VCYCLE && opt.coarse != IGA2L_COARSE_EXACT)
         return fail(IGA2L_ERR_INVALID_ARG, "unknown coarse solver");
     const int s = opt.block_side > 0 ? opt.block_side : default_block_side(p);
-    if (!((s == 3 && p <= 4) || (s == 5 && p == 5)))
+    if (!((s == 3 && p <= 4) || (s == 5 && (p == 5 || p == 6)) || (s == 7 && (p == 7 || p == 8))))
         return fail(IGA2L_ERR_UNSUPPORTED, "block side not compiled for this degree");
     int q = opt.period, g = opt.stride;
     if (q <= 0) default_colouring(p, s, q, g);

@@ -10,11 +10,12 @@
 
 namespace iga2l {
 
-constexpr int kMaxP = 5;       // degrees with compiled kernels: 2..5
+constexpr int kMaxP = 8;       // degrees with compiled kernels: 2..8 (2D), 2..4 (3D)
 constexpr int kMaxLevels = 24;
 // Side of the TILE schedule's tiles (block centres) compiled for degree p: a multiple
 // of the default colour period, at least 2R + P + 1 so tiles of one phase never interact.
-constexpr int tile_side(int p) { return p == 2 ? 20 : (p == 5 ? 20 : 21); }
+// The TILE kernel keeps a block in one warp, so it exists for blocks up to 5x5 (p <= 6).
+constexpr int tile_side(int p) { return p == 2 || p == 5 ? 20 : (p == 6 ? 22 : (p <= 4 ? 21 : 0)); }
 
 // Batch addressing passed to 2D kernels: problem z of a batch owns vec (fine vector),
 // aux (scratch) and crs (second-level vector) entries starting at z * stride; problems

@@ -763,6 +763,9 @@ cudaError_t residual_any(const Solver &S, const T *kband, const T *mband, const 
     case 3: return residual_p<3, T, TO>(S, kband, mband, u, b, d, part, st);
     case 4: return residual_p<4, T, TO>(S, kband, mband, u, b, d, part, st);
     case 5: return residual_p<5, T, TO>(S, kband, mband, u, b, d, part, st);
+    case 6: return residual_p<6, T, TO>(S, kband, mband, u, b, d, part, st);
+    case 7: return residual_p<7, T, TO>(S, kband, mband, u, b, d, part, st);
+    case 8: return residual_p<8, T, TO>(S, kband, mband, u, b, d, part, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -829,8 +832,10 @@ template <int P, int SB, typename T>
 cudaError_t schwarz_p(const Solver &S, const T *stencil, const T *kband, const T *mband, const T *binv, T *u,
                       const T *b, bool reverse, cudaStream_t st)
 {
-    if (S.opt.schedule == IGA2L_SCHED_TILE)
-        return schwarz_tile_p<P, SB, T>(S, kband, mband, binv, u, b, reverse, st);
+    if constexpr (SB * SB <= 32) {   // the TILE kernel keeps a block in one warp
+        if (S.opt.schedule == IGA2L_SCHED_TILE)
+            return schwarz_tile_p<P, SB, T>(S, kband, mband, binv, u, b, reverse, st);
+    }
     return schwarz_lattice_p<P, SB, T>(S, stencil, kband, mband, binv, u, b, reverse, st);
 }
 
@@ -845,8 +850,12 @@ cudaError_t schwarz_any(const Solver &S, const T *stencil, const T *kband, const
         case 4: return schwarz_p<4, 3, T>(S, stencil, kband, mband, binv, u, b, reverse, st);
         default: break;
         }
-    } else if (S.s == 5 && S.p == 5) {
-        return schwarz_p<5, 5, T>(S, stencil, kband, mband, binv, u, b, reverse, st);
+    } else if (S.s == 5) {
+        if (S.p == 5) return schwarz_p<5, 5, T>(S, stencil, kband, mband, binv, u, b, reverse, st);
+        if (S.p == 6) return schwarz_p<6, 5, T>(S, stencil, kband, mband, binv, u, b, reverse, st);
+    } else if (S.s == 7) {
+        if (S.p == 7) return schwarz_p<7, 7, T>(S, stencil, kband, mband, binv, u, b, reverse, st);
+        if (S.p == 8) return schwarz_p<8, 7, T>(S, stencil, kband, mband, binv, u, b, reverse, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -1042,6 +1051,9 @@ cudaError_t launch_mass2(const Solver &S, const double *f, double *b, cudaStream
     case 3: k_mass2d<3><<<grd, 128, 0, st>>>(S.n, S.Mb, f, b, S.N); break;
     case 4: k_mass2d<4><<<grd, 128, 0, st>>>(S.n, S.Mb, f, b, S.N); break;
     case 5: k_mass2d<5><<<grd, 128, 0, st>>>(S.n, S.Mb, f, b, S.N); break;
+    case 6: k_mass2d<6><<<grd, 128, 0, st>>>(S.n, S.Mb, f, b, S.N); break;
+    case 7: k_mass2d<7><<<grd, 128, 0, st>>>(S.n, S.Mb, f, b, S.N); break;
+    case 8: k_mass2d<8><<<grd, 128, 0, st>>>(S.n, S.Mb, f, b, S.N); break;
     default: return cudaErrorInvalidValue;
     }
     count_launches(1);

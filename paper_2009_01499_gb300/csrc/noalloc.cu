@@ -141,7 +141,7 @@ extern "C" int iga2l_residual_norm2_noalloc(int p, int n, const double *Kb, cons
                                             double *norm2, void *stream)
 {
     using namespace iga2l;
-    if (p < 2 || p > kMaxP || n < 1 || !Kb || !Mb || !u || !b || !norm2) {
+    if (p < 2 || p > 5 || n < 1 || !Kb || !Mb || !u || !b || !norm2) {
         set_last_error("residual_norm2_noalloc: p must be 2..5, n >= 1 and Kb, Mb, u, b, norm2 non-null");
         return IGA2L_ERR_INVALID_ARG;
     }

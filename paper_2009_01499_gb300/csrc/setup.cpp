@@ -114,6 +114,9 @@ void default_colouring(int p, int s, int &q, int &g)
     case 3: q = 7; g = 2; break;
     case 4: q = 7; g = 2; break;
     case 5: q = 10; g = 3; break;
+    case 6: q = 11; g = 4; break;
+    case 7: q = 14; g = 5; break;
+    case 8: q = 17; g = 4; break;
     default: q = s + p; g = 1; break;
     }
 }
