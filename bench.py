@@ -280,6 +280,36 @@ def bench_3d(args, dev):
     return out
 
 
+def bench_high_degree(args, dev):
+    """2D, p = 6, 7, 8 on 1024^2 elements (5x5 and 7x7 Schwarz blocks, Sections 4.3, 5.1):
+    FP64 (LATTICE) and mixed (TILE for p = 6, LATTICE for 7x7 blocks), to 1e-8."""
+    import torch
+    from paper_2009_01499_gb300 import iga2l, synth
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    out = {"workload": "2D Poisson, B-splines p=6,7,8 on 1024x1024 elements, seeded uniform[-1,1] coefficients "
+                       "of f, 5x5 (p=6) / 7x7 (p=7,8) blocks, colourings (11,4), (14,5), (17,4), to 1e-8"}
+    for p in (6, 7, 8):
+        row = {}
+        for name, prec, sched in (("fp64", iga2l.FP64, iga2l.SCHED_LATTICE),
+                                  ("mixed", iga2l.MIXED_FP32, iga2l.SCHED_TILE if p <= 6 else iga2l.SCHED_LATTICE)):
+            S = iga2l.Solver(p, M_ELEM, precision=prec, schedule=sched)
+            f = torch.tensor(synth.coefficients(S.N, synth.BASE_SEED + 10 + p), device=dev)
+            b = torch.empty_like(f)
+            S.rhs_from_coeffs(f, b)
+            u0 = torch.tensor(synth.initial_guess(S.N, synth.BASE_SEED + 20 + p), device=dev)
+            u = torch.empty_like(u0)
+            _time_solve(S, b, u0, u, TOL, stream, flush)
+            runs = [_time_solve(S, b, u0, u, TOL, stream, flush) for _ in range(2)]
+            ms = min(r[0] for r in runs)
+            row[name] = {"value": S.N / (ms * 1e-3), "unit": "DOF/s", "ms": ms, "cycles": runs[-1][1],
+                         "schedule": "TILE" if sched == iga2l.SCHED_TILE else "LATTICE"}
+            S.close()
+        row["speedup_mixed_vs_fp64"] = row["fp64"]["ms"] / row["mixed"]["ms"]
+        out[str(p)] = row
+    return out
+
+
 def bench_batched(args, dev):
     """256 independent 2D problems, m from {64,128,256,512} and p from {2,3,4} by seed, mixed
     precision, autotuned schedules, concurrent groups, to 1e-8."""
@@ -455,12 +485,13 @@ def run_gpu(args):
         mixed = run_mixed(iga2l.MIXED_FP32, "f64")
         mixed_all = run_mixed(iga2l.MIXED_FP32_ALL, "f32")
 
-    # secondary configurations: 3D (p = 3, 128^3, FP64 and mixed) and the batch of 256
-    # uneven 2D problems (mixed, autotuned schedules, concurrent groups)
+    # secondary configurations: 3D (p = 3, 128^3, FP64 and mixed), the batch of 256 uneven
+    # 2D problems (mixed, autotuned schedules, concurrent groups), and p = 6..8 at 1024^2
     extra = {}
     if not args.no_extra:
         extra["3d"] = bench_3d(args, dev)
         extra["batched"] = bench_batched(args, dev)
+        extra["high_degree"] = bench_high_degree(args, dev)
 
     # roofline of the dominant kernel, the Schwarz colour-phase kernel (FP64 pipe bound)
     sweep_flops, sweep_ms, per_p = 0.0, 0.0, {}
