@@ -375,7 +375,7 @@ cudaError_t vcycle(const Solver &S, int l, const T *rhs, T *e, T *const *levE, T
         return cudaGetLastError();
     }
     // small levels: the rest of the cycle in one thread block per problem, in shared memory
-    const int tail_n = sizeof(T) == sizeof(float) ? 63 : 31;
+    const int tail_n = 31;   // larger levels: the fused multi-CTA level kernels are faster
     if (L.n <= tail_n && last - l + 1 <= kTailMaxLevels) {
         TailArgs<T> a{};
         a.active = S.active;

@@ -25,6 +25,28 @@ namespace iga2l {
 
 namespace {
 
+// Programmatic dependent launch: the colour kernels of a sweep are launched with the
+// programmatic-serialisation attribute, so a colour's grid is set up while the previous
+// colour drains; every such kernel waits here, before its first global access, until the
+// previous grid has completed and its writes are visible.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename Kernel, typename... Args>
+cudaError_t launch_pdl(Kernel kernel, dim3 grid, dim3 block, cudaStream_t st, Args... args)
+{
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 constexpr int kResTX = 32, kResTY = 8;   // residual tile (outputs per CTA)
 
 // Fixed-order sum of the partials (deterministic norm).
@@ -60,6 +82,7 @@ k_schwarz_lattice2d(int n, int npc, int nbc, int q, int ox, int oy, int nbx, int
     constexpr int W = 2 * P + 1, SS = S * S, R = (S - 1) / 2;
     constexpr int BPC = 256 / SS;   // Schwarz blocks per CTA
     __shared__ T rs[BPC * SS];
+    grid_dependency_wait();
     if (bt.active && !bt.active[blockIdx.y]) return;
     u += blockIdx.y * bt.vec;
     b += blockIdx.y * bt.vec;
@@ -290,6 +313,7 @@ k_schwarz_lattice2d_sf(int n, int nbc, int q, int ox, int oy, int nbx, int nbloc
     __shared__ T2 yb[NB][S][WIN];
     __shared__ T rs[NB][SS];
     __shared__ T sbi[SS * SS];
+    grid_dependency_wait();
     if (bt.active && !bt.active[blockIdx.y]) return;
     u += blockIdx.y * bt.vec;
     b += blockIdx.y * bt.vec;
@@ -789,17 +813,17 @@ cudaError_t schwarz_lattice_p(const Solver &S, const T *stencil, const T *kband,
         const int nbx = (S.n - ox + q - 1) / q, nby = (S.n - oy + q - 1) / q;
         const int nblocks = nbx * nby;
         if (nblocks <= 0) continue;
+        cudaError_t err;
         if constexpr (SF) {
-            k_schwarz_lattice2d_sf<P, SB, T><<<dim3((nblocks + NBSF - 1) / NBSF, S.nbatch), 256, 0, st>>>(
-                S.n, S.ht.nbc, q, ox, oy, nbx, nblocks, kband, mband, binv, S.boundary64(), interior, S.bcls, u, b,
-                BatchRef{S.active, S.N, 0, 0});
+            err = launch_pdl(k_schwarz_lattice2d_sf<P, SB, T>, dim3((nblocks + NBSF - 1) / NBSF, S.nbatch), dim3(256),
+                             st, S.n, S.ht.nbc, q, ox, oy, nbx, nblocks, kband, mband, binv, S.boundary64(), interior,
+                             (const int *)S.bcls, u, b, BatchRef{S.active, S.N, 0, 0});
         } else {
-            k_schwarz_lattice2d<P, SB, T><<<dim3((nblocks + BPC - 1) / BPC, S.nbatch), 256, 0, st>>>(
-                S.n, S.ht.npc, S.ht.nbc, q, ox, oy, nbx, nblocks, stencil, S.pcls, binv, S.boundary64(), interior,
-                S.bcls, u, b, BatchRef{S.active, S.N, 0, 0});
+            err = launch_pdl(k_schwarz_lattice2d<P, SB, T>, dim3((nblocks + BPC - 1) / BPC, S.nbatch), dim3(256), st,
+                             S.n, S.ht.npc, S.ht.nbc, q, ox, oy, nbx, nblocks, stencil, (const int *)S.pcls, binv,
+                             S.boundary64(), interior, (const int *)S.bcls, u, b, BatchRef{S.active, S.N, 0, 0});
         }
         count_launches(1);
-        cudaError_t err = cudaGetLastError();
         if (err != cudaSuccess) return err;
     }
     return cudaSuccess;
