@@ -332,9 +332,10 @@ static int assemble_impl(int p, int m, int dim, int nbatch, bool batch, const ig
         return fail(IGA2L_ERR_UNSUPPORTED, "precision not available");
     if (opt.schedule != IGA2L_SCHED_LATTICE && opt.schedule != IGA2L_SCHED_TILE)
         return fail(IGA2L_ERR_UNSUPPORTED, "schedule not available");
-    if (dim == 3 && opt.schedule != IGA2L_SCHED_LATTICE)
-        return fail(IGA2L_ERR_UNSUPPORTED, "3D uses the LATTICE schedule");
-    if (opt.schedule == IGA2L_SCHED_TILE) {
+    if (dim == 3 && opt.schedule == IGA2L_SCHED_TILE) {
+        if (opt.tile == 0) opt.tile = tile_side3d(p);
+        if (opt.tile != tile_side3d(p)) return fail(IGA2L_ERR_UNSUPPORTED, "3D TILE side not compiled for this degree");
+    } else if (opt.schedule == IGA2L_SCHED_TILE) {
         if (opt.tile == 0) opt.tile = tile_side(p);
         if (tile_side(p) == 0) return fail(IGA2L_ERR_UNSUPPORTED, "the TILE schedule is compiled for p <= 6");
         if (opt.tile != tile_side(p)) return fail(IGA2L_ERR_UNSUPPORTED, "TILE side not compiled for this degree");

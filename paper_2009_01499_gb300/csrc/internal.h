@@ -16,6 +16,9 @@ constexpr int kMaxLevels = 24;
 // of the default colour period, at least 2R + P + 1 so tiles of one phase never interact.
 // The TILE kernel keeps a block in one warp, so it exists for blocks up to 5x5 (p <= 6).
 constexpr int tile_side(int p) { return p == 2 || p == 5 ? 20 : (p == 6 ? 22 : (p <= 4 ? 21 : 0)); }
+// 3D TILE side (3x3x3 blocks, p = 2..4): the default colour period, so a colour has one
+// block per tile; at least 2R + P, so tiles of one phase never interact.
+constexpr int tile_side3d(int p) { return p == 2 ? 5 : 7; }
 
 // Batch addressing passed to 2D kernels: problem z of a batch owns vec (fine vector),
 // aux (scratch) and crs (second-level vector) entries starting at z * stride; problems

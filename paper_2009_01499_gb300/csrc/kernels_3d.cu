@@ -222,6 +222,318 @@ k_schwarz_lattice3d(int n, int nbc, int q, int ox, int oy, int oz, int nbx, int 
     }
 }
 
+// One LATTICE colour in 3D with NB Schwarz blocks per CTA (256 threads) and every pass
+// spread over all threads of the CTA: the patches (S + 2P)^3 of the NB blocks are staged
+// together, then the x pass (pairs K_x u, M_x u), the y pass (S1 = M_y tK + K_y tM,
+// MM = M_y tM), the z pass with the block residual, and the block solves, each a loop over
+// all (block, point) items of the CTA.  Same arithmetic as k_schwarz_lattice3d per item;
+// the x and z passes run as pairs (packed FP32 FMA for T = float).
+template <typename T>
+struct Vec2_3d;
+template <>
+struct Vec2_3d<float> { using type = float2; };
+template <>
+struct Vec2_3d<double> { using type = double2; };
+
+__device__ __forceinline__ float2 fma2_3d(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ double2 fma2_3d(double2 a, double2 b, double2 c)
+{
+    return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+
+template <int P, typename T>
+struct Lattice3dGeom {
+    static constexpr int S = 3, R = 1, W = 2 * P + 1, SS = S * S * S, PW = S + 2 * P;
+    static constexpr int NB = sizeof(T) == sizeof(float) ? 4 : 2;   // blocks per CTA (shared memory)
+};
+
+template <int P, typename T>
+__global__ void __launch_bounds__(256)
+k_schwarz_lattice3d_mb(int n, int nbc, int q, int ox, int oy, int oz, int nbx, int nby, int nblocks,
+                       const T *__restrict__ Kb, const T *__restrict__ Mb, const T *__restrict__ binv,
+                       const double *__restrict__ binv64, int interior, const int *__restrict__ bcls,
+                       T *__restrict__ u, const T *__restrict__ b)
+{
+    using G = Lattice3dGeom<P, T>;
+    using T2 = typename Vec2_3d<T>::type;
+    constexpr int S = G::S, R = G::R, W = G::W, SS = G::SS, PW = G::PW, NB = G::NB;
+    constexpr int NT = 256;
+    __shared__ T pu[NB][PW * PW * PW];
+    __shared__ T2 tKM[NB][PW * PW * S];     // (K_x u, M_x u)
+    __shared__ T2 sMM[NB][PW * S * S];      // (S1, MM)
+    __shared__ T rs[NB][SS];
+    __shared__ int cen[NB][3];
+    const int tid = threadIdx.x;
+    const int blk0 = blockIdx.x * NB;
+    if (tid < NB) {
+        const int blk = blk0 + tid;
+        const int bi = blk < nblocks ? blk : 0;
+        cen[tid][0] = ox + q * (bi % nbx);
+        cen[tid][1] = oy + q * ((bi / nbx) % nby);
+        cen[tid][2] = oz + q * (bi / (nbx * nby));
+    }
+    __syncthreads();
+    for (int i = tid; i < NB * PW * PW * PW; i += NT) {
+        const int j = i / (PW * PW * PW), k = i - j * (PW * PW * PW);
+        const int gx = cen[j][0] - R - P + k % PW, gy = cen[j][1] - R - P + (k / PW) % PW,
+                  gz = cen[j][2] - R - P + k / (PW * PW);
+        pu[j][k] = (blk0 + j < nblocks && gx >= 0 && gx < n && gy >= 0 && gy < n && gz >= 0 && gz < n)
+                       ? u[((size_t)gz * n + gy) * n + gx] : T(0);
+    }
+    __syncthreads();
+    for (int i = tid; i < NB * PW * PW * S; i += NT) {   // x pass
+        const int j = i / (PW * PW * S), k = i - j * (PW * PW * S);
+        const int ex = k % S, r = k / S;
+        const int gx = cen[j][0] - R + ex;
+        T2 acc;
+        acc.x = T(0);
+        acc.y = T(0);
+        if (gx >= 0 && gx < n) {
+            const T *kr = Kb + (size_t)gx * W, *mr = Mb + (size_t)gx * W;
+            const T *ur = pu[j] + r * PW + ex;
+#pragma unroll
+            for (int a = 0; a < W; ++a) {
+                T2 c, v;
+                c.x = kr[a]; c.y = mr[a];
+                v.x = ur[a]; v.y = ur[a];
+                acc = fma2_3d(c, v, acc);
+            }
+        }
+        tKM[j][k] = acc;
+    }
+    __syncthreads();
+    for (int i = tid; i < NB * PW * S * S; i += NT) {    // y pass
+        const int j = i / (PW * S * S), k = i - j * (PW * S * S);
+        const int ex = k % S, ey = (k / S) % S, z = k / (S * S);
+        const int gy = cen[j][1] - R + ey;
+        T s1 = T(0), mm = T(0);
+        if (gy >= 0 && gy < n) {
+            const T *kr = Kb + (size_t)gy * W, *mr = Mb + (size_t)gy * W;
+#pragma unroll
+            for (int bb = 0; bb < W; ++bb) {
+                const T2 t = tKM[j][(z * PW + ey + bb) * S + ex];
+                s1 = fma(mr[bb], t.x, s1);
+                s1 = fma(kr[bb], t.y, s1);
+                mm = fma(mr[bb], t.y, mm);
+            }
+        }
+        T2 o;
+        o.x = s1;
+        o.y = mm;
+        sMM[j][k] = o;
+    }
+    __syncthreads();
+    for (int i = tid; i < NB * SS; i += NT) {            // z pass and block residual
+        const int j = i / SS, e = i - j * SS;
+        const int ex = e % S, ey = (e / S) % S, ez = e / (S * S);
+        const int gx = cen[j][0] - R + ex, gy = cen[j][1] - R + ey, gz = cen[j][2] - R + ez;
+        T rv = T(0);
+        if (blk0 + j < nblocks && gx >= 0 && gx < n && gy >= 0 && gy < n && gz >= 0 && gz < n) {
+            const T *kr = Kb + (size_t)gz * W, *mr = Mb + (size_t)gz * W;
+            T2 acc;
+            acc.x = T(0);
+            acc.y = T(0);
+#pragma unroll
+            for (int c = 0; c < W; ++c) {
+                T2 cf;
+                cf.x = mr[c]; cf.y = kr[c];
+                acc = fma2_3d(cf, sMM[j][((ez + c) * S + ey) * S + ex], acc);
+            }
+            rv = b[((size_t)gz * n + gy) * n + gx] - (acc.x + acc.y);
+        }
+        rs[j][e] = rv;
+    }
+    __syncthreads();
+    for (int i = tid; i < NB * SS; i += NT) {            // block solve and update
+        const int j = i / SS, e = i - j * SS;
+        const int ex = e % S, ey = (e / S) % S, ez = e / (S * S);
+        const int cx = cen[j][0], cy = cen[j][1], cz = cen[j][2];
+        const int gx = cx - R + ex, gy = cy - R + ey, gz = cz - R + ez;
+        if (blk0 + j >= nblocks || gx < 0 || gx >= n || gy < 0 || gy >= n || gz < 0 || gz >= n) continue;
+        const int cls = (bcls[cz] * nbc + bcls[cy]) * nbc + bcls[cx];
+        if (sizeof(T) == sizeof(double) || cls == interior || !binv64) {
+            const T *Bi = binv + ((size_t)cls * SS + e) * SS;
+            T ev = T(0);
+#pragma unroll
+            for (int f = 0; f < SS; ++f) ev = fma(__ldg(&Bi[f]), rs[j][f], ev);
+            u[((size_t)gz * n + gy) * n + gx] += ev;
+        } else {
+            const double *Bi = binv64 + ((size_t)cls * SS + e) * SS;
+            double ev = 0.0;
+#pragma unroll
+            for (int f = 0; f < SS; ++f) ev = fma(__ldg(&Bi[f]), (double)rs[j][f], ev);
+            u[((size_t)gz * n + gy) * n + gx] += (T)ev;
+        }
+    }
+}
+
+// One tile phase of the TILE(TT) schedule in 3D: tiles (tx, ty, tz) of the phase's
+// parities, each CTA running all q^3 lattice colours of its tile (anchored at the tile
+// origin) with u (tile + halo R + P) and b (tile + halo R) in shared memory.  TT is the
+// default colour period, so a colour has one block per tile (in general: every block of
+// the colour in the tile, one after another).  Per block: the x pass (pairs K_x u, M_x u
+// over the (z, y) patch rows), the y pass (S1 = M_y tK + K_y tM, MM = M_y tM), the z pass
+// with the block residual, and the block solve, separated by CTA barriers; the 1D rows of
+// the tile's output coordinates are staged per axis.  Tiles of one phase are 2 TT apart
+// with TT >= 2R + P: none reads what another writes.
+template <int P, int TT, typename T>
+struct Tile3dGeom {
+    static constexpr int S = 3, R = 1, W = 2 * P + 1, SS = S * S * S, H = R + P, PW = S + 2 * P;
+    static constexpr int SW = TT + 2 * H, BW = TT + 2 * R;
+    static constexpr size_t align16(size_t x) { return (x + 15) / 16 * 16; }
+    // dynamic shared memory layout (bytes)
+    static constexpr size_t o_su = 0;
+    static constexpr size_t o_sb = align16(o_su + sizeof(T) * SW * SW * SW);
+    static constexpr size_t o_tkm = align16(o_sb + sizeof(T) * BW * BW * BW);
+    static constexpr size_t o_smm = align16(o_tkm + 2 * sizeof(T) * PW * PW * S);
+    static constexpr size_t o_rs = align16(o_smm + 2 * sizeof(T) * PW * S * S);
+    static constexpr size_t o_tab = align16(o_rs + sizeof(T) * SS);
+    static constexpr size_t o_bi = align16(o_tab + 2 * sizeof(T) * 3 * BW * W);
+    static constexpr size_t bytes = align16(o_bi + sizeof(T) * SS * SS);
+};
+
+template <int P, int TT, typename T>
+__global__ void __launch_bounds__(128)
+k_schwarz_tile3d(int n, int nbc, int q, int g, int rev, int px, int py, int pz, int ntpx, int ntpy,
+                 const T *__restrict__ Kb, const T *__restrict__ Mb, const T *__restrict__ binv,
+                 const double *__restrict__ binv64, int interior, const int *__restrict__ bcls,
+                 T *__restrict__ u, const T *__restrict__ b)
+{
+    using G = Tile3dGeom<P, TT, T>;
+    using T2 = typename Vec2_3d<T>::type;
+    constexpr int S = G::S, R = G::R, W = G::W, SS = G::SS, H = G::H, PW = G::PW, SW = G::SW, BW = G::BW;
+    constexpr int NT = 128;
+    extern __shared__ __align__(16) unsigned char smem_t3[];
+    T *su = reinterpret_cast<T *>(smem_t3 + G::o_su);
+    T *sb = reinterpret_cast<T *>(smem_t3 + G::o_sb);
+    T2 *tKM = reinterpret_cast<T2 *>(smem_t3 + G::o_tkm);
+    T2 *sMM = reinterpret_cast<T2 *>(smem_t3 + G::o_smm);
+    T *rs = reinterpret_cast<T *>(smem_t3 + G::o_rs);
+    T *ktab = reinterpret_cast<T *>(smem_t3 + G::o_tab);     // [axis][BW][W]
+    T *mtab = ktab + 3 * BW * W;
+    T *sbi = reinterpret_cast<T *>(smem_t3 + G::o_bi);
+    const int tid = threadIdx.x;
+    const int bx = blockIdx.x;
+    const int x0 = (px + 2 * (bx % ntpx)) * TT, y0 = (py + 2 * ((bx / ntpx) % ntpy)) * TT,
+              z0 = (pz + 2 * (bx / (ntpx * ntpy))) * TT;
+    const int org[3] = {x0, y0, z0};
+    const int tw = min(TT, n - x0), th = min(TT, n - y0), td = min(TT, n - z0);
+    for (int i = tid; i < SW * SW * SW; i += NT) {
+        const int gx = x0 - H + i % SW, gy = y0 - H + (i / SW) % SW, gz = z0 - H + i / (SW * SW);
+        su[i] = (gx >= 0 && gx < n && gy >= 0 && gy < n && gz >= 0 && gz < n) ? u[((size_t)gz * n + gy) * n + gx]
+                                                                               : T(0);
+    }
+    for (int i = tid; i < BW * BW * BW; i += NT) {
+        const int gx = x0 - R + i % BW, gy = y0 - R + (i / BW) % BW, gz = z0 - R + i / (BW * BW);
+        sb[i] = (gx >= 0 && gx < n && gy >= 0 && gy < n && gz >= 0 && gz < n) ? b[((size_t)gz * n + gy) * n + gx]
+                                                                               : T(0);
+    }
+    for (int i = tid; i < 3 * BW * W; i += NT) {
+        const int ax = i / (BW * W), r = (i / W) % BW, a = i % W;
+        const int gc = org[ax] - R + r;
+        ktab[i] = (gc >= 0 && gc < n) ? Kb[(size_t)gc * W + a] : T(0);
+        mtab[i] = (gc >= 0 && gc < n) ? Mb[(size_t)gc * W + a] : T(0);
+    }
+    for (int i = tid; i < SS * SS; i += NT) sbi[i] = binv[(size_t)interior * SS * SS + i];
+    __syncthreads();
+    const int ncol = q * q * q;
+    for (int t = 0; t < ncol; ++t) {
+        const int c = rev ? ncol - 1 - t : t;
+        const int ox = ((c % q) * g) % q, oy = (((c / q) % q) * g) % q, oz = ((c / (q * q)) * g) % q;
+        for (int cz = oz; cz < td; cz += q)
+            for (int cy = oy; cy < th; cy += q)
+                for (int cx = ox; cx < tw; cx += q) {
+                    // x pass over the (z, y) patch rows: su rows start at tile-local cx - R - P
+                    for (int i = tid; i < PW * PW * S; i += NT) {
+                        const int ex = i % S, rr = i / S, yy = rr % PW, zz = rr / PW;
+                        const T *ur = su + ((cz + zz) * SW + (cy + yy)) * SW + cx + ex;
+                        const T *kr = ktab + (0 * BW + cx + ex) * W, *mr = mtab + (0 * BW + cx + ex) * W;
+                        T2 acc;
+                        acc.x = T(0);
+                        acc.y = T(0);
+#pragma unroll
+                        for (int a = 0; a < W; ++a) {
+                            T2 cf, v;
+                            cf.x = kr[a]; cf.y = mr[a];
+                            v.x = ur[a]; v.y = ur[a];
+                            acc = fma2_3d(cf, v, acc);
+                        }
+                        tKM[i] = acc;
+                    }
+                    __syncthreads();
+                    for (int i = tid; i < PW * S * S; i += NT) {   // y pass
+                        const int ex = i % S, ey = (i / S) % S, z = i / (S * S);
+                        const T *kr = ktab + (1 * BW + cy + ey) * W, *mr = mtab + (1 * BW + cy + ey) * W;
+                        T s1 = T(0), mm = T(0);
+#pragma unroll
+                        for (int bb = 0; bb < W; ++bb) {
+                            const T2 tv = tKM[(z * PW + ey + bb) * S + ex];
+                            s1 = fma(mr[bb], tv.x, s1);
+                            s1 = fma(kr[bb], tv.y, s1);
+                            mm = fma(mr[bb], tv.y, mm);
+                        }
+                        T2 o;
+                        o.x = s1;
+                        o.y = mm;
+                        sMM[i] = o;
+                    }
+                    __syncthreads();
+                    if (tid < SS) {                                  // z pass and block residual
+                        const int ex = tid % S, ey = (tid / S) % S, ez = tid / (S * S);
+                        const int gx = x0 + cx - R + ex, gy = y0 + cy - R + ey, gz = z0 + cz - R + ez;
+                        T rv = T(0);
+                        if (gx >= 0 && gx < n && gy >= 0 && gy < n && gz >= 0 && gz < n) {
+                            const T *kr = ktab + (2 * BW + cz + ez) * W, *mr = mtab + (2 * BW + cz + ez) * W;
+                            T2 acc;
+                            acc.x = T(0);
+                            acc.y = T(0);
+#pragma unroll
+                            for (int cc = 0; cc < W; ++cc) {
+                                T2 cf;
+                                cf.x = mr[cc]; cf.y = kr[cc];
+                                acc = fma2_3d(cf, sMM[((ez + cc) * S + ey) * S + ex], acc);
+                            }
+                            rv = sb[((cz + ez) * BW + cy + ey) * BW + cx + ex] - (acc.x + acc.y);
+                        }
+                        rs[tid] = rv;
+                    }
+                    __syncthreads();
+                    if (tid < SS) {                                  // block solve and update
+                        const int ex = tid % S, ey = (tid / S) % S, ez = tid / (S * S);
+                        const int gcx = x0 + cx, gcy = y0 + cy, gcz = z0 + cz;
+                        const int gx = gcx - R + ex, gy = gcy - R + ey, gz = gcz - R + ez;
+                        if (gx >= 0 && gx < n && gy >= 0 && gy < n && gz >= 0 && gz < n) {
+                            const int cls = (bcls[gcz] * nbc + bcls[gcy]) * nbc + bcls[gcx];
+                            T ev = T(0);
+                            if (cls == interior) {
+                                const T *Bi = sbi + tid * SS;
+#pragma unroll
+                                for (int f = 0; f < SS; ++f) ev = fma(Bi[f], rs[f], ev);
+                            } else if (sizeof(T) == sizeof(double) || !binv64) {
+                                const T *Bi = binv + ((size_t)cls * SS + tid) * SS;
+#pragma unroll
+                                for (int f = 0; f < SS; ++f) ev = fma(__ldg(&Bi[f]), rs[f], ev);
+                            } else {
+                                const double *Bi = binv64 + ((size_t)cls * SS + tid) * SS;
+                                double ed = 0.0;
+#pragma unroll
+                                for (int f = 0; f < SS; ++f) ed = fma(__ldg(&Bi[f]), (double)rs[f], ed);
+                                ev = (T)ed;
+                            }
+                            su[((cz + P + ez) * SW + cy + P + ey) * SW + cx + P + ex] += ev;
+                        }
+                    }
+                    __syncthreads();
+                }
+    }
+    for (int i = tid; i < BW * BW * BW; i += NT) {
+        const int lx = i % BW, ly = (i / BW) % BW, lz = i / (BW * BW);
+        const int gx = x0 - R + lx, gy = y0 - R + ly, gz = z0 - R + lz;
+        if (gx >= 0 && gx < n && gy >= 0 && gy < n && gz >= 0 && gz < n)
+            u[((size_t)gz * n + gy) * n + gx] = su[((lz + P) * SW + ly + P) * SW + lx + P];
+    }
+}
+
 // out[z][y][x'] = sum_w B[x'][w] in[z][y][lo[x'] + w] along axis `ax` (0 = x, 1 = y, 2 = z):
 // in has dims (nx, ny, nz), out the same with the axis length replaced by nout.  With
 // accumulate = 1 the result is added to out (TU) after adding delta (if not null).
@@ -470,9 +782,41 @@ cudaError_t residual3d_any(const Solver &S, const T *Kb, const T *Mb, const T *u
 }
 
 template <int P, typename T>
+cudaError_t schwarz_tile3d_p(const Solver &S, const T *Kb, const T *Mb, const T *binv, T *u, const T *b,
+                             bool reverse, cudaStream_t st)
+{
+    constexpr int TT = tile_side3d(P);
+    using G = Tile3dGeom<P, TT, T>;
+    const int nbc = S.ht.nbc;
+    const int interior = (S.ht.L * nbc + S.ht.L) * nbc + S.ht.L;
+    static bool attr_set[64] = {};   // per device: the dynamic shared memory limit of this instantiation
+    if (S.device >= 0 && S.device < 64 && !attr_set[S.device]) {
+        cudaError_t e = cudaFuncSetAttribute(k_schwarz_tile3d<P, TT, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)G::bytes);
+        if (e != cudaSuccess) return e;
+        attr_set[S.device] = true;
+    }
+    const int nt = (S.n + TT - 1) / TT;
+    for (int t = 0; t < 8; ++t) {
+        const int ph = reverse ? 7 - t : t;
+        const int px = ph & 1, py = (ph >> 1) & 1, pz = ph >> 2;
+        const int ntpx = (nt - px + 1) / 2, ntpy = (nt - py + 1) / 2, ntpz = (nt - pz + 1) / 2;
+        if (ntpx <= 0 || ntpy <= 0 || ntpz <= 0) continue;
+        k_schwarz_tile3d<P, TT, T><<<ntpx * ntpy * ntpz, 128, G::bytes, st>>>(
+            S.n, nbc, S.q, S.g, reverse ? 1 : 0, px, py, pz, ntpx, ntpy, Kb, Mb, binv, S.boundary64(), interior,
+            S.bcls, u, b);
+        count_launches(1);
+        cudaError_t err = cudaGetLastError();
+        if (err != cudaSuccess) return err;
+    }
+    return cudaSuccess;
+}
+
+template <int P, typename T>
 cudaError_t schwarz3d_p(const Solver &S, const T *Kb, const T *Mb, const T *binv, T *u, const T *b, bool reverse,
                         cudaStream_t st)
 {
+    if (S.opt.schedule == IGA2L_SCHED_TILE) return schwarz_tile3d_p<P, T>(S, Kb, Mb, binv, u, b, reverse, st);
     const int q = S.q, ncol = q * q * q, nbc = S.ht.nbc;
     const int interior = (S.ht.L * nbc + S.ht.L) * nbc + S.ht.L;
     for (int t = 0; t < ncol; ++t) {
@@ -480,8 +824,17 @@ cudaError_t schwarz3d_p(const Solver &S, const T *Kb, const T *Mb, const T *binv
         const int ox = ((c % q) * S.g) % q, oy = (((c / q) % q) * S.g) % q, oz = ((c / (q * q)) * S.g) % q;
         const int nbx = (S.n - ox + q - 1) / q, nby = (S.n - oy + q - 1) / q, nbz = (S.n - oz + q - 1) / q;
         if (nbx <= 0 || nby <= 0 || nbz <= 0) continue;
-        k_schwarz_lattice3d<P, T><<<nbx * nby * nbz, 128, 0, st>>>(S.n, nbc, q, ox, oy, oz, nbx, nby, Kb, Mb, binv,
-                                                                    S.boundary64(), interior, S.bcls, u, b);
+        // FP64: several blocks per CTA (175 against 180 ms for the 128^3 p=3 solve); FP32: one
+        // block per CTA (the multi-block form was slower, 65.5 against 57.5 ms)
+        const int nblocks = nbx * nby * nbz;
+        if constexpr (sizeof(T) == sizeof(double)) {
+            constexpr int NB = Lattice3dGeom<P, T>::NB;
+            k_schwarz_lattice3d_mb<P, T><<<(nblocks + NB - 1) / NB, 256, 0, st>>>(
+                S.n, nbc, q, ox, oy, oz, nbx, nby, nblocks, Kb, Mb, binv, S.boundary64(), interior, S.bcls, u, b);
+        } else {
+            k_schwarz_lattice3d<P, T><<<nblocks, 128, 0, st>>>(S.n, nbc, q, ox, oy, oz, nbx, nby, Kb, Mb, binv,
+                                                                S.boundary64(), interior, S.bcls, u, b);
+        }
         count_launches(1);
         cudaError_t err = cudaGetLastError();
         if (err != cudaSuccess) return err;

@@ -109,3 +109,61 @@ def test_mixed_3d_matches_fp64_gpu():
     B.solve(b, ub, tol=1e-12, max_cycles=60)
     err = float(torch.linalg.norm(ua - ub) / torch.linalg.norm(ua))
     assert err <= 1e-8, err
+
+
+def _tile_pair(oracle_mod, p, m, precision=0):
+    q, g = COLOURING[p]
+    S = iga2l.Solver(p, m, dim=3, period=q, stride=g, precision=precision, schedule=iga2l.SCHED_TILE)
+    O = oracle_mod.Problem(3, p, m, sched=oracle_mod.TILE, tile=S.tile, period=q, stride=g,
+                           coarse=oracle_mod.VCYCLE)
+    assert S.tile == q   # the 3D TILE side is the colour period
+    return S, O
+
+
+@pytest.mark.parametrize("p,m", [(2, 12), (3, 16), (3, 20), (4, 20)])
+@pytest.mark.parametrize("reverse", [False, True])
+def test_schwarz_tile_3d(oracle_mod, p, m, reverse):
+    """3D TILE sweep (tile side = colour period, 8 tile phases, ragged last tiles) against
+    the oracle's TILE order, forward and reverse."""
+    S, O = _tile_pair(oracle_mod, p, m)
+    b, u = synth.coefficients(S.N, 50 + p), synth.initial_guess(S.N, 51 + p)
+    ud = _dev(u)
+    S.schwarz_sweep(ud, _dev(b), reverse=reverse)
+    q, g = COLOURING[p]
+    _, order, _ = oracle_mod.schedule(3, S.n, O.s, p, oracle_mod.TILE, S.tile, q, g)
+    if reverse:
+        order = order[::-1].copy()
+    K, M = oracle_mod.assemble_1d(p, m)
+    _close(_host(ud), oracle_mod.schwarz_sweep(3, K, M, p, O.s, order, b, u))
+
+
+def test_cycles_per_iterate_tile_3d(oracle_mod):
+    S, O = _tile_pair(oracle_mod, 3, 32)
+    b, u0 = synth.coefficients(S.N, 61), synth.initial_guess(S.N, 62)
+    ud, bd, uo = _dev(u0), _dev(b), u0.copy()
+    for k in range(3):
+        S.cycle(ud, bd)
+        uo = O.cycle(uo, b)
+        rel = np.linalg.norm(_host(ud) - uo) / np.linalg.norm(uo)
+        assert rel <= TOL, (k, rel)
+
+
+@pytest.mark.parametrize("precision", [iga2l.MIXED_FP32, iga2l.MIXED_FP32_ALL])
+def test_mixed_tile_3d_matches_oracle(oracle_mod, precision):
+    """3D mixed TILE form: the oracle's TILE cycle count within one at 1e-8; refined to a
+    1e-12 residual, within 1e-8 of the oracle's solution refined the same way."""
+    p, m = 3, 32
+    S, O = _tile_pair(oracle_mod, p, m, precision)
+    f, u0 = synth.coefficients(S.N, 71), synth.initial_guess(S.N, 72)
+    bd = torch.empty(S.N, dtype=torch.float64, device="cuda")
+    S.rhs_from_coeffs(_dev(f), bd)
+    b = _host(bd)
+    ud = _dev(u0)
+    c, _, _, ok = S.solve(bd, ud, tol=1e-8, max_cycles=40)
+    uo, co, _, _, oko = O.solve(b, u0, tol=1e-8, maxc=40)
+    assert ok and oko and abs(c - co) <= 1, (c, co)
+    ud = _dev(u0)
+    S.solve(bd, ud, tol=1e-12, max_cycles=60)
+    uo, _, _, _, oko = O.solve(b, u0, tol=1e-12, maxc=60)
+    err = np.linalg.norm(_host(ud) - uo) / np.linalg.norm(uo)
+    assert err <= 1e-8, err

@@ -54,6 +54,7 @@ SCHED_CASES = [
     (2, 5, 45, 2, 20, 10, 3),
     (3, 2, 8, 1, 0, 5, 2),
     (3, 3, 9, 2, 7, 7, 2),
+    (3, 2, 12, 2, 5, 5, 2),   # 3D tile side = period, two tiles of one phase per axis
 ]
 
 
