@@ -359,9 +359,14 @@ def run_gpu(args):
 
     iga2l.load()
     solvers, bs, u0s, us, fhost, u0host, uhost = {}, {}, {}, {}, {}, {}, {}
+    setup_ms = {}
     for p in DEGREES:
         q, g = COLOURING[p]
-        S = iga2l.Solver(p, M_ELEM, period=q, stride=g)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S = iga2l.Solver(p, M_ELEM, period=q, stride=g)   # assemble: host tables + one upload
+        torch.cuda.synchronize()
+        setup_ms[str(p)] = round((time.perf_counter() - t0) * 1e3, 2)
         sf, su = seeds(p)
         f = torch.tensor(synth.coefficients(S.N, sf), device=dev)
         b = torch.empty_like(f)
@@ -537,6 +542,7 @@ def run_gpu(args):
         "config": {"workload": WORKLOAD, "m": M_ELEM, "degrees": list(DEGREES), "tol": TOL,
                    "dofs_per_step": ndofs, "cycles": {str(p): cycles[p] for p in DEGREES},
                    "l2": "flushed (256 MiB write) before every solve", "schedule": "LATTICE",
+                   "setup_ms": setup_ms,
                    "colouring": {str(p): list(COLOURING[p]) for p in DEGREES},
                    "parallelism": f"replicas x{ws}"},
         "e2e": {"value": ws * ndofs / (e2e_step * 1e-3), "unit": "DOF/s", "h2d_bytes_per_step": h2d,
@@ -567,12 +573,14 @@ def run_profile_step(args):
     import torch
     from paper_2009_01499_gb300 import iga2l, synth
     dev = torch.device("cuda", 0)
-    degrees = (args.profile_p,) if args.profile_p else DEGREES
+    dim = args.profile_dim
+    degrees = (args.profile_p,) if args.profile_p else ((3,) if dim == 3 else DEGREES)
+    m = args.profile_m or (128 if dim == 3 else M_ELEM)
     prec = {"fp64": iga2l.FP64, "mixed": iga2l.MIXED_FP32, "mixed_all": iga2l.MIXED_FP32_ALL}[args.profile_precision]
-    sched = iga2l.SCHED_LATTICE if prec == iga2l.FP64 else iga2l.SCHED_TILE
+    sched = iga2l.SCHED_LATTICE if (prec == iga2l.FP64 or dim == 3) else iga2l.SCHED_TILE
     for p in degrees:
         q, g = COLOURING[p]
-        S = iga2l.Solver(p, args.profile_m, period=q, stride=g, precision=prec, schedule=sched)
+        S = iga2l.Solver(p, m, dim=dim, period=q, stride=g, precision=prec, schedule=sched)
         sf, su = seeds(p)
         f = torch.tensor(synth.coefficients(S.N, sf), device=dev)
         b = torch.empty_like(f)
@@ -583,7 +591,7 @@ def run_profile_step(args):
             u.copy_(u0)
             cyc, rel, _, ok = S.solve(b, u, tol=TOL)
         torch.cuda.synchronize()
-        print(f"p={p} m={args.profile_m}: {cyc} cycles, rel {rel:.3e}, converged {ok}", flush=True)
+        print(f"p={p} m={m} dim={dim}: {cyc} cycles, rel {rel:.3e}, converged {ok}", flush=True)
         S.close()
 
 
@@ -598,7 +606,8 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the 3D and batched configurations")
     ap.add_argument("--profile-step", action="store_true",
                     help="profiling aid: warm-up solves then one solve per degree, no timing")
-    ap.add_argument("--profile-m", type=int, default=M_ELEM)
+    ap.add_argument("--profile-m", type=int, default=0, help="elements per axis (default 1024 in 2D, 128 in 3D)")
+    ap.add_argument("--profile-dim", type=int, choices=[2, 3], default=2)
     ap.add_argument("--profile-p", type=int, default=0)
     ap.add_argument("--profile-precision", choices=["fp64", "mixed", "mixed_all"], default="fp64",
                     help="form profiled by --profile-step (the benchmark's schedule for it)")
