@@ -319,7 +319,6 @@ k_schwarz_lattice2d_sf(int n, int nbc, int q, int ox, int oy, int nbx, int nbloc
     b += blockIdx.y * bt.vec;
     const int tid = threadIdx.x;
     const int blk0 = blockIdx.x * NB;
-    const T h = T(1) / T(n - P + 2), hinv = T(n - P + 2);
     for (int i = tid; i < SS * SS; i += NT) sbi[i] = binv[(size_t)interior * SS * SS + i];
     // 1. y pass
     if (tid < NB * WIN) {
@@ -343,6 +342,7 @@ k_schwarz_lattice2d_sf(int n, int nbc, int q, int ox, int oy, int nbx, int nbloc
                     for (int bb = 0; bb < W; ++bb) acc = fma2(ckm1<T>(P, bb), splat2<T2>(v[r + bb]), acc);
                 } else {
                     const int gy = cy - R + r;
+                    const T h = T(1) / T(n - P + 2), hinv = T(n - P + 2);   // boundary rows only
                     if (gy >= 0 && gy < n) {
 #pragma unroll
                         for (int bb = 0; bb < W; ++bb) {
@@ -373,6 +373,7 @@ k_schwarz_lattice2d_sf(int n, int nbc, int q, int ox, int oy, int nbx, int nbloc
 #pragma unroll
                 for (int a = 0; a < W; ++a) acc = fma2(cmk1<T>(P, a), yb[j][ey][ex + a], acc);
             } else {
+                const T h = T(1) / T(n - P + 2), hinv = T(n - P + 2);   // boundary columns only
 #pragma unroll
                 for (int a = 0; a < W; ++a) {
                     T2 mk;
@@ -799,9 +800,9 @@ cudaError_t schwarz_lattice_p(const Solver &S, const T *stencil, const T *kband,
                               const T *b, bool reverse, cudaStream_t st)
 {
     // FP32: the packed sum-factorised kernel (the direct form is bound by its L1 loads);
-    // FP64: the direct form, which keeps the FP64 pipe busier (measured at 1024^2: p = 5
-    // sweep 7.2 ms direct against 9.2 ms factorised, whose CTAs wait on three dependent
-    // global-memory phases)
+    // FP64: the direct form.  At p = 5 the factorised form needs 18% fewer FP64 FMAs but
+    // measured slower (1024^2: ~86-90 us per colour against ~78 us): its three phases per
+    // CTA, separated by barriers, keep the FP64 pipe only 60-68% busy against 90%+.
     constexpr bool SF = sizeof(T) == sizeof(float);
     constexpr int BPC = 256 / (SB * SB), NBSF = 256 / (SB + 2 * P);
     const int q = S.q, ncol = q * q;
