@@ -134,8 +134,7 @@ int finish(cudaError_t e, const char *where)
 int residual_norm2(iga2l_handle h, const double *u, const double *b, double *d, cudaStream_t st,
                    double *out)
 {
-    cudaError_t e = launch_residual(*h, u, b, d, h->part, st);
-    if (e == cudaSuccess) e = launch_norm_finish(*h, h->part, h->dev_norm, st);
+    cudaError_t e = launch_residual_norm(*h, u, b, d, h->dev_norm, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h->host_norm, h->dev_norm, sizeof(double), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -164,8 +163,9 @@ int enqueue_cycle(iga2l_handle h, double *u, const double *b, cudaStream_t st, b
         cudaError_t e = launch_inner_fine(*h, h->mx.r, false, st);
         if (e == cudaSuccess) e = launch_inner_coarse(*h, st);
         if (e == cudaSuccess) e = launch_inner_update(*h, u, st);
-        if (e == cudaSuccess) e = launch_outer_residual(*h, u, b, h->mx.r, norm ? h->part : nullptr, st);
-        if (e == cudaSuccess && norm) e = launch_norm_finish(*h, h->part, h->dev_norm, st);
+        if (e == cudaSuccess)
+            e = norm ? launch_outer_residual_norm(*h, u, b, h->mx.r, h->dev_norm, st)
+                     : launch_outer_residual(*h, u, b, h->mx.r, nullptr, st);
         if (e == cudaSuccess && norm && !h->active)
             e = cudaMemcpyAsync(h->host_norm, h->dev_norm, sizeof(double), cudaMemcpyDeviceToHost, st);
         return finish(e, "mixed-precision cycle");
@@ -180,8 +180,7 @@ int enqueue_cycle(iga2l_handle h, double *u, const double *b, cudaStream_t st, b
         if (e != cudaSuccess) return cuda_fail(e, "reverse schwarz sweep");
     }
     if (norm) {
-        cudaError_t e = launch_residual(*h, u, b, nullptr, h->part, st);
-        if (e == cudaSuccess) e = launch_norm_finish(*h, h->part, h->dev_norm, st);
+        cudaError_t e = launch_residual_norm(*h, u, b, nullptr, h->dev_norm, st);
         if (e == cudaSuccess && !h->active)
             e = cudaMemcpyAsync(h->host_norm, h->dev_norm, sizeof(double), cudaMemcpyDeviceToHost, st);
         if (e != cudaSuccess) return cuda_fail(e, "residual norm");
@@ -260,8 +259,7 @@ int solve_impl(iga2l_handle h, const double *b, double tol, int max_cycles, doub
     double r0sq = 0.0;
     int rc;
     if (h->mx.enabled && !adjoint) {   // r_0 in FP64, kept in FP32 for the first inner cycle
-        cudaError_t e = launch_outer_residual(*h, u, b, h->mx.r, h->part, st);
-        if (e == cudaSuccess) e = launch_norm_finish(*h, h->part, h->dev_norm, st);
+        cudaError_t e = launch_outer_residual_norm(*h, u, b, h->mx.r, h->dev_norm, st);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(h->host_norm, h->dev_norm, sizeof(double), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -512,6 +510,15 @@ static int assemble_impl(int p, int m, int dim, int nbatch, bool batch, const ig
         release(S);
         return cuda_fail(ce, "workspace allocation");
     }
+    {   // completion counters of the fused residual norm, zero between launches
+        void *pc = nullptr;
+        if ((ce = cudaMalloc(&pc, sizeof(unsigned int) * B)) != cudaSuccess ||
+            (S->allocs.push_back(pc), ce = cudaMemset(pc, 0, sizeof(unsigned int) * B)) != cudaSuccess) {
+            release(S);
+            return cuda_fail(ce, "workspace allocation");
+        }
+        S->rcount = static_cast<unsigned int *>(pc);
+    }
     // differentiable source (2D): quadrature tables and per-bump buffers; backward workspace
     if (dim == 2) {
         std::vector<double> qx, qw, qB;
@@ -635,10 +642,9 @@ int iga2l_solve_batch(iga2l_handle h, const double *b, double tol, int max_cycle
     std::vector<int> ones(nb, 1);
     cudaError_t e = cudaMemcpyAsync(h->active, ones.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) {
-        if (h->mx.enabled) e = launch_outer_residual(*h, u, b, h->mx.r, h->part, st);
-        else e = launch_residual(*h, u, b, nullptr, h->part, st);
+        if (h->mx.enabled) e = launch_outer_residual_norm(*h, u, b, h->mx.r, h->dev_norm, st);
+        else e = launch_residual_norm(*h, u, b, nullptr, h->dev_norm, st);
     }
-    if (e == cudaSuccess) e = launch_norm_finish(*h, h->part, h->dev_norm, st);
     if (e == cudaSuccess) e = launch_batch_init(*h, h->dev_norm, h->bnorm0, h->bcycles, h->brel, st);
     if (e != cudaSuccess) return cuda_fail(e, "batch start");
     // cycles; converged problems are masked on the device, the host polls every 4 cycles

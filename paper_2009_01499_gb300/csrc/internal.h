@@ -97,6 +97,7 @@ struct Solver {
     // workspace
     double *d = nullptr, *t = nullptr, *dc = nullptr, *ec = nullptr, *t2 = nullptr;
     double *part = nullptr;      // per-CTA partial sums of squares
+    unsigned int *rcount = nullptr;   // per problem: residual CTAs done (fused norm), re-armed to 0
     int npart = 0;
     double *bwork = nullptr;     // b built from coefficients in solve paths
     MixedState mx;
@@ -134,6 +135,11 @@ cudaError_t launch_residual(const Solver &S, const double *u, const double *b, d
                             double *part, cudaStream_t st);
 cudaError_t launch_apply_A(const Solver &S, const double *u, double *y, cudaStream_t st);
 cudaError_t launch_norm_finish(const Solver &S, const double *part, double *out, cudaStream_t st);
+// residual with its squared norm finished in the same launch (2D) into norm2[problem]
+cudaError_t launch_residual_norm(const Solver &S, const double *u, const double *b, double *d, double *norm2,
+                                 cudaStream_t st);
+cudaError_t launch_outer_residual_norm(const Solver &S, const double *u, const double *b, float *r32,
+                                       double *norm2, cudaStream_t st);
 cudaError_t launch_schwarz(const Solver &S, double *u, const double *b, bool reverse,
                            cudaStream_t st);
 cudaError_t launch_restrict(const Solver &S, const double *d, double *dc, cudaStream_t st);

@@ -196,7 +196,8 @@ __device__ __forceinline__ float2 cmk1<float>(int p, int a) { return c_mk1f[p][a
 template <int P, typename T, typename TO>
 __global__ void __launch_bounds__(kResTX *kResTY)
 k_residual2d(int n, const T *__restrict__ kband, const T *__restrict__ mband, const T *__restrict__ u,
-             const T *__restrict__ b, TO *__restrict__ d, double *__restrict__ part, BatchRef bt)
+             const T *__restrict__ b, TO *__restrict__ d, double *__restrict__ part, unsigned int *__restrict__ done,
+             double *__restrict__ norm2, BatchRef bt)
 {
     using T2 = typename Vec2<T>::type;
     constexpr int W = 2 * P + 1;
@@ -282,10 +283,36 @@ k_residual2d(int n, const T *__restrict__ kband, const T *__restrict__ mband, co
         for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
         if ((tid & 31) == 0) red[tid >> 5] = s;
         __syncthreads();
+        __shared__ bool last;
         if (tid == 0) {
             double tot = 0.0;
             for (int w = 0; w < kResTX * kResTY / 32; ++w) tot += red[w];
             part[blockIdx.x + gridDim.x * blockIdx.y] = tot;
+            last = false;
+            if (norm2) {   // the last CTA of this problem to finish sums the partials
+                __threadfence();
+                last = atomicAdd(&done[z], 1u) == gridDim.x * gridDim.y - 1;
+            }
+        }
+        __syncthreads();
+        if (last) {
+            // fixed-order sum of the partials (deterministic), then re-arm the counter
+            __threadfence();
+            const int np = gridDim.x * gridDim.y;
+            constexpr int NT = kResTX * kResTY;
+            __shared__ double sh[NT];
+            double acc = 0.0;
+            for (int i = tid; i < np; i += NT) acc += __ldcg(&part[i]);
+            sh[tid] = acc;
+            __syncthreads();
+            for (int w = NT / 2; w > 0; w >>= 1) {
+                if (tid < w) sh[tid] += sh[tid + w];
+                __syncthreads();
+            }
+            if (tid == 0) {
+                norm2[z] = sh[0];
+                done[z] = 0u;
+            }
         }
     }
 }
@@ -768,12 +795,14 @@ __global__ void k_mass2d(int n, const double *__restrict__ Mb, const double *__r
     b[(size_t)j * n + i] = acc;
 }
 
+// norm2 != nullptr (with part): the squared norm of every problem is finished inside the
+// launch into norm2[problem] (the last CTA of a problem sums its partials)
 template <int P, typename T, typename TO>
 cudaError_t residual_p(const Solver &S, const T *kband, const T *mband, const T *u, const T *b, TO *d, double *part,
-                       cudaStream_t st)
+                       double *norm2, cudaStream_t st)
 {
     dim3 blk(kResTX, kResTY), grd((S.n + kResTX - 1) / kResTX, (S.n + kResTY - 1) / kResTY, S.nbatch);
-    k_residual2d<P, T, TO><<<grd, blk, 0, st>>>(S.n, kband, mband, u, b, d, part,
+    k_residual2d<P, T, TO><<<grd, blk, 0, st>>>(S.n, kband, mband, u, b, d, part, S.rcount, norm2,
                                                  BatchRef{S.active, S.N, residual_partials(S), 0});
     count_launches(1);
     return cudaGetLastError();
@@ -781,16 +810,16 @@ cudaError_t residual_p(const Solver &S, const T *kband, const T *mband, const T 
 
 template <typename T, typename TO>
 cudaError_t residual_any(const Solver &S, const T *kband, const T *mband, const T *u, const T *b, TO *d,
-                         double *part, cudaStream_t st)
+                         double *part, cudaStream_t st, double *norm2 = nullptr)
 {
     switch (S.p) {
-    case 2: return residual_p<2, T, TO>(S, kband, mband, u, b, d, part, st);
-    case 3: return residual_p<3, T, TO>(S, kband, mband, u, b, d, part, st);
-    case 4: return residual_p<4, T, TO>(S, kband, mband, u, b, d, part, st);
-    case 5: return residual_p<5, T, TO>(S, kband, mband, u, b, d, part, st);
-    case 6: return residual_p<6, T, TO>(S, kband, mband, u, b, d, part, st);
-    case 7: return residual_p<7, T, TO>(S, kband, mband, u, b, d, part, st);
-    case 8: return residual_p<8, T, TO>(S, kband, mband, u, b, d, part, st);
+    case 2: return residual_p<2, T, TO>(S, kband, mband, u, b, d, part, norm2, st);
+    case 3: return residual_p<3, T, TO>(S, kband, mband, u, b, d, part, norm2, st);
+    case 4: return residual_p<4, T, TO>(S, kband, mband, u, b, d, part, norm2, st);
+    case 5: return residual_p<5, T, TO>(S, kband, mband, u, b, d, part, norm2, st);
+    case 6: return residual_p<6, T, TO>(S, kband, mband, u, b, d, part, norm2, st);
+    case 7: return residual_p<7, T, TO>(S, kband, mband, u, b, d, part, norm2, st);
+    case 8: return residual_p<8, T, TO>(S, kband, mband, u, b, d, part, norm2, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -958,6 +987,16 @@ cudaError_t launch_residual(const Solver &S, const double *u, const double *b, d
     return residual_any<double, double>(S, S.Kb, S.Mb, u, b, d, part, st);
 }
 
+cudaError_t launch_residual_norm(const Solver &S, const double *u, const double *b, double *d, double *norm2,
+                                 cudaStream_t st)
+{
+    if (S.dim == 3) {
+        cudaError_t e = launch3d_residual(S, u, b, d, S.part, st);
+        return e == cudaSuccess ? launch_norm_finish(S, S.part, norm2, st) : e;
+    }
+    return residual_any<double, double>(S, S.Kb, S.Mb, u, b, d, S.part, st, norm2);
+}
+
 cudaError_t launch_apply_A(const Solver &S, const double *u, double *y, cudaStream_t st)
 {
     return launch_residual(S, u, nullptr, y, nullptr, st);
@@ -1047,6 +1086,16 @@ cudaError_t launch_outer_residual(const Solver &S, const double *u, const double
 {
     if (S.dim == 3) return launch3d_outer_residual(S, u, b, r32, part, st);
     return residual_any<double, float>(S, S.Kb, S.Mb, u, b, r32, part, st);
+}
+
+cudaError_t launch_outer_residual_norm(const Solver &S, const double *u, const double *b, float *r32,
+                                       double *norm2, cudaStream_t st)
+{
+    if (S.dim == 3) {
+        cudaError_t e = launch3d_outer_residual(S, u, b, r32, S.part, st);
+        return e == cudaSuccess ? launch_norm_finish(S, S.part, norm2, st) : e;
+    }
+    return residual_any<double, float>(S, S.Kb, S.Mb, u, b, r32, S.part, st, norm2);
 }
 
 cudaError_t launch_inner_fine(const Solver &S, const float *r32, bool reverse, cudaStream_t st)
