@@ -64,3 +64,46 @@ def test_uneven_groups_match_single_solves():
             assert ok1 and c1 == cycles[i] and torch.equal(us, ub[i]), (i, c1, cycles[i])
         S.close()
     BS.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_concurrent_handles_match_sequential(precision):
+    """Independent handles solving at once on their own streams and host threads (as the
+    benchmark's concurrent step does) give exactly the sequential iterates."""
+    import threading
+    probs = [(2, 96), (3, 80), (4, 88), (5, 72)]
+    solvers, bs, u0s = [], [], []
+    for i, (p, m) in enumerate(probs):
+        S = iga2l.Solver(p, m, precision=precision,
+                         schedule=iga2l.SCHED_TILE if precision else iga2l.SCHED_LATTICE)
+        f = torch.tensor(synth.coefficients(S.N, 300 + i), device="cuda")
+        b = torch.empty_like(f)
+        S.rhs_from_coeffs(f, b)
+        solvers.append(S)
+        bs.append(b)
+        u0s.append(torch.tensor(synth.initial_guess(S.N, 400 + i), device="cuda"))
+    seq = []
+    for S, b, u0 in zip(solvers, bs, u0s):
+        u = u0.clone()
+        c, rel, _, ok = S.solve(b, u, tol=1e-8)
+        assert ok
+        seq.append((u, c, rel))
+    torch.cuda.synchronize()
+    streams = [torch.cuda.Stream() for _ in probs]
+    us = [u0.clone() for u0 in u0s]
+    torch.cuda.synchronize()
+    out = [None] * len(probs)
+
+    def run(k):
+        out[k] = solvers[k].solve(bs[k], us[k], tol=1e-8, stream=streams[k])
+
+    threads = [threading.Thread(target=run, args=(k,)) for k in range(len(probs))]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    torch.cuda.synchronize()
+    for k in range(len(probs)):
+        c, rel, _, ok = out[k]
+        assert ok and c == seq[k][1] and rel == seq[k][2], k
+        assert torch.equal(us[k], seq[k][0]), k
