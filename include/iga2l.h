@@ -53,6 +53,10 @@ extern "C" {
  * of p <= 5 have condition numbers below 5e2, so this costs the inner cycle ~3e-5
  * relative at most, which the FP64 refinement removes; coarsest solve still FP64) */
 #define IGA2L_MIXED_FP32_ALL 2
+/* IGA2L_MIXED_FP32 with the interior blocks of every LATTICE colour computed as one
+ * tensor-core GEMM (tcgen05, TF32 operands, FP32 accumulation): e_B = [A_B^-1 | -A_B^-1
+ * A_(B,patch)] [b_B ; u_patch]; 2D, LATTICE schedule, p <= 6 */
+#define IGA2L_MIXED_TF32 3
 /* schedule: colour classes of the multiplicative Schwarz step */
 #define IGA2L_SCHED_LATTICE 1
 #define IGA2L_SCHED_TILE 2
@@ -63,7 +67,7 @@ extern "C" {
 typedef struct iga2l_solver *iga2l_handle;
 
 typedef struct {
-    int precision;   /* IGA2L_FP64, IGA2L_MIXED_FP32 or IGA2L_MIXED_FP32_ALL */
+    int precision;   /* IGA2L_FP64, IGA2L_MIXED_FP32, IGA2L_MIXED_FP32_ALL or IGA2L_MIXED_TF32 */
     int schedule;    /* IGA2L_SCHED_LATTICE or IGA2L_SCHED_TILE */
     int tile;        /* TILE side T >= period (0 = the side compiled for p: 20 for p = 2, 5; 21 for
                         p = 3, 4; 22 for p = 6; the TILE schedule is compiled for p <= 6) */

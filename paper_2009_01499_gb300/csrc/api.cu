@@ -292,6 +292,15 @@ int solve_impl(iga2l_handle h, const double *b, double tol, int max_cycles, doub
     if (cycles) *cycles = k;
     if (relres) *relres = rel;
     if (status != IGA2L_OK) g_last_error = "cycle cap reached";
+    if (h->mx.tc_status) {   // a tensor-core wait that gave up left its blocks uncorrected
+        int bad = 0;
+        cudaError_t e = cudaMemcpy(&bad, h->mx.tc_status, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "tensor-core status");
+        if (bad) {
+            cudaMemset(h->mx.tc_status, 0, sizeof(int));
+            return fail(IGA2L_ERR_DEVICE_TIMEOUT, "a tensor-core MMA wait gave up");
+        }
+    }
     return status;
 }
 
@@ -326,8 +335,11 @@ static int assemble_impl(int p, int m, int dim, int nbatch, bool batch, const ig
     if (dim == 3 && p > 4) return fail(IGA2L_ERR_UNSUPPORTED, "3D kernels are compiled for p = 2..4");
     if (m < 4 * p + 4 || (m % 2) != 0)
         return fail(IGA2L_ERR_INVALID_ARG, "m must be even and >= 4p+4 (aggressive 2h coarsening)");
-    if (opt.precision != IGA2L_FP64 && opt.precision != IGA2L_MIXED_FP32 && opt.precision != IGA2L_MIXED_FP32_ALL)
+    if (opt.precision != IGA2L_FP64 && opt.precision != IGA2L_MIXED_FP32 && opt.precision != IGA2L_MIXED_FP32_ALL &&
+        opt.precision != IGA2L_MIXED_TF32)
         return fail(IGA2L_ERR_UNSUPPORTED, "precision not available");
+    if (opt.precision == IGA2L_MIXED_TF32 && (dim != 2 || opt.schedule != IGA2L_SCHED_LATTICE || p > kTcMaxP))
+        return fail(IGA2L_ERR_UNSUPPORTED, "the tensor-core form is compiled for 2D, LATTICE, p <= 6");
     if (opt.schedule != IGA2L_SCHED_LATTICE && opt.schedule != IGA2L_SCHED_TILE)
         return fail(IGA2L_ERR_UNSUPPORTED, "schedule not available");
     if (dim == 3 && opt.schedule == IGA2L_SCHED_TILE) {
@@ -553,7 +565,8 @@ static int assemble_impl(int p, int m, int dim, int nbatch, bool batch, const ig
         release(S);
         return cuda_fail(ce, "pinned host scalar");
     }
-    if (opt.precision == IGA2L_MIXED_FP32 || opt.precision == IGA2L_MIXED_FP32_ALL) {
+    if (opt.precision == IGA2L_MIXED_FP32 || opt.precision == IGA2L_MIXED_FP32_ALL ||
+        opt.precision == IGA2L_MIXED_TF32) {
         // FP32 copies of the tables for the inner cycle (the FP64 block inverses are kept
         // for boundary classes and the FP64 coarsest inverse for the direct solve)
         MixedState &X = S->mx;
@@ -590,6 +603,20 @@ static int assemble_impl(int p, int m, int dim, int nbatch, bool batch, const ig
                 release(S);
                 return cuda_fail(ce, "mixed-precision level allocation");
             }
+        if (opt.precision == IGA2L_MIXED_TF32) {
+            const int interior = ht.L * ht.nbc + ht.L;
+            std::vector<double> ainv(binv.begin() + (size_t)interior * SS * SS,
+                                     binv.begin() + (size_t)(interior + 1) * SS * SS);
+            std::vector<float> g;
+            build_gtc(*S, ainv, g, X.gtc_n, X.gtc_k);
+            void *pst = nullptr;
+            if ((ce = upload(S, &X.gtc, g)) != cudaSuccess || (ce = cudaMalloc(&pst, sizeof(int))) != cudaSuccess ||
+                (S->allocs.push_back(pst), ce = cudaMemset(pst, 0, sizeof(int))) != cudaSuccess) {
+                release(S);
+                return cuda_fail(ce, "tensor-core operator upload");
+            }
+            X.tc_status = static_cast<int *>(pst);
+        }
         X.enabled = true;
     }
     if (batch) {

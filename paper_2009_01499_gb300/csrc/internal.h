@@ -61,6 +61,11 @@ struct MixedState {
     bool enabled = false;
     float *stencil = nullptr, *binv = nullptr, *Rb = nullptr, *Cb = nullptr;
     float *Kb = nullptr, *Mb = nullptr;   // FP32 band rows (3D kernels)
+    // IGA2L_MIXED_TF32: the interior block operator G = [A_B^-1 | -A_B^-1 A_(B,patch)] (rounded
+    // to TF32) in the tensor-core operand layout, gtc_n x gtc_k (block DOFs x [b_B; u_patch])
+    float *gtc = nullptr;
+    int gtc_n = 0, gtc_k = 0;
+    int *tc_status = nullptr;   // device: bounded waits of the tensor-core kernel that gave up
     float *r = nullptr;       // outer residual b - A u, computed in FP64, stored in FP32
     float *delta = nullptr;   // correction of the Schwarz step
     float *d = nullptr, *t = nullptr, *t2 = nullptr, *dc = nullptr, *ec = nullptr;
@@ -110,7 +115,10 @@ struct Solver {
     std::vector<void *> allocs;
     // FP64 inverses of the boundary block classes for the FP32 Schwarz kernels, or null
     // when those are applied in FP32 too (IGA2L_MIXED_FP32_ALL)
-    const double *boundary64() const { return opt.precision == IGA2L_MIXED_FP32 ? binv : nullptr; }
+    const double *boundary64() const
+    {
+        return opt.precision == IGA2L_MIXED_FP32 || opt.precision == IGA2L_MIXED_TF32 ? binv : nullptr;
+    }
 };
 
 // Number of kernels this library has launched (process-wide), for benchmarks
@@ -179,6 +187,17 @@ cudaError_t launch3d_outer_residual(const Solver &S, const double *u, const doub
 cudaError_t launch3d_inner_fine(const Solver &S, const float *r32, cudaStream_t st);
 cudaError_t launch3d_inner_coarse(const Solver &S, cudaStream_t st);
 cudaError_t launch3d_inner_update(const Solver &S, double *u, cudaStream_t st);
+// tensor-core Schwarz (kernels_tc.cu): the colour's block-index range [i0, i0 + ni) along one
+// axis whose blocks (and their patches) see only interior rows, and one colour's interior
+// rectangle of blocks as a TF32 GEMM on tcgen05 (2D, p <= 6)
+void tc_interior_rect(const Solver &S, int o, int nb, int &i0, int &ni);
+cudaError_t launch_schwarz_tc(const Solver &S, int ox, int oy, int ix0, int iy0, int nix, int niy, const float *b,
+                              float *u, cudaStream_t st);
+// host: G of the interior block in the operand layout (kernels_tc.cu)
+void build_gtc(const Solver &S, const std::vector<double> &binv_interior, std::vector<float> &g, int &nrows,
+               int &kcols);
+constexpr int kTcMaxP = 6;
+
 // Interior 2D residual stencil of degree p and the interior 1D rows k = h K_row,
 // m = M_row / h (all h-independent) into constant memory; written once per device and degree.
 cudaError_t upload_interior_stencil(int p, const double *st64, int count, const double *k1, const double *m1);

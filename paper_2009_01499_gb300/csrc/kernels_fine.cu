@@ -327,9 +327,29 @@ k_residual2d(int n, const T *__restrict__ kband, const T *__restrict__ mband, co
 // Interior rows/columns take the h-scaled interior 1D rows from constant memory, the
 // others their own 1D rows (scaled the same way); with T = float the boundary block
 // classes use the FP64 inverses binv64 when given.
+// Block (i, j) of a colour's nbx-wide block grid from an index over the grid minus the
+// rectangle [ix0, ix0 + nix) x [iy0, iy0 + niy) (the blocks the tensor-core kernel takes);
+// with nix = niy = 0 this is the plain row-major order.
+__device__ __forceinline__ void frame_block(int f, int nbx, int ix0, int iy0, int nix, int niy, int &i, int &j)
+{
+    const int top = iy0 * nbx, cnt = nbx - nix;
+    if (f < top || niy == 0) { i = f % nbx; j = f / nbx; return; }
+    f -= top;
+    if (f < niy * cnt) {
+        const int row = f / cnt, c = f - row * cnt;
+        j = iy0 + row;
+        i = c < ix0 ? c : ix0 + nix + (c - ix0);
+        return;
+    }
+    f -= niy * cnt;
+    j = iy0 + niy + f / nbx;
+    i = f % nbx;
+}
+
 template <int P, int S, typename T>
 __global__ void __launch_bounds__(256)
-k_schwarz_lattice2d_sf(int n, int nbc, int q, int ox, int oy, int nbx, int nblocks,
+k_schwarz_lattice2d_sf(int n, int nbc, int q, int ox, int oy, int nbx, int ix0, int iy0, int nix, int niy,
+                       int nblocks,
                        const T *__restrict__ kband, const T *__restrict__ mband,
                        const T *__restrict__ binv, const double *__restrict__ binv64, int interior,
                        const int *__restrict__ bcls, T *__restrict__ u, const T *__restrict__ b, BatchRef bt)
@@ -351,7 +371,9 @@ k_schwarz_lattice2d_sf(int n, int nbc, int q, int ox, int oy, int nbx, int nbloc
     if (tid < NB * WIN) {
         const int j = tid / WIN, c = tid - j * WIN, blk = blk0 + j;
         if (blk < nblocks) {
-            const int cx = ox + q * (blk % nbx), cy = oy + q * (blk / nbx);
+            int bi_, bj_;
+            frame_block(blk, nbx, ix0, iy0, nix, niy, bi_, bj_);
+            const int cx = ox + q * bi_, cy = oy + q * bj_;
             const int x = cx - R - P + c;
             const bool xin = x >= 0 && x < n;
             T v[WIN];
@@ -389,7 +411,9 @@ k_schwarz_lattice2d_sf(int n, int nbc, int q, int ox, int oy, int nbx, int nbloc
     for (int o = tid; o < NB * SS; o += NT) {
         const int j = o / SS, e = o - j * SS, blk = blk0 + j;
         if (blk >= nblocks) continue;
-        const int cx = ox + q * (blk % nbx), cy = oy + q * (blk / nbx);
+        int bi_, bj_;
+        frame_block(blk, nbx, ix0, iy0, nix, niy, bi_, bj_);
+        const int cx = ox + q * bi_, cy = oy + q * bj_;
         const int ey = e / S, ex = e - ey * S;
         const int x = cx - R + ex, y = cy - R + ey;
         T r = T(0);
@@ -418,7 +442,9 @@ k_schwarz_lattice2d_sf(int n, int nbc, int q, int ox, int oy, int nbx, int nbloc
     for (int o = tid; o < NB * SS; o += NT) {
         const int j = o / SS, e = o - j * SS, blk = blk0 + j;
         if (blk >= nblocks) continue;
-        const int cx = ox + q * (blk % nbx), cy = oy + q * (blk / nbx);
+        int bi_, bj_;
+        frame_block(blk, nbx, ix0, iy0, nix, niy, bi_, bj_);
+        const int cx = ox + q * bi_, cy = oy + q * bj_;
         const int x = cx - R + e % S, y = cy - R + e / S;
         if (x < 0 || x >= n || y < 0 || y >= n) continue;
         const int cls = bcls[cy] * nbc + bcls[cx];
@@ -845,9 +871,25 @@ cudaError_t schwarz_lattice_p(const Solver &S, const T *stencil, const T *kband,
         if (nblocks <= 0) continue;
         cudaError_t err;
         if constexpr (SF) {
-            err = launch_pdl(k_schwarz_lattice2d_sf<P, SB, T>, dim3((nblocks + NBSF - 1) / NBSF, S.nbatch), dim3(256),
-                             st, S.n, S.ht.nbc, q, ox, oy, nbx, nblocks, kband, mband, binv, S.boundary64(), interior,
-                             (const int *)S.bcls, u, b, BatchRef{S.active, S.N, 0, 0});
+            // interior blocks of the colour as one tensor-core GEMM (IGA2L_MIXED_TF32), the
+            // frame of the other blocks here
+            int ix0 = 0, iy0 = 0, nix = 0, niy = 0;
+            if (S.mx.gtc) {
+                tc_interior_rect(S, ox, nbx, ix0, nix);
+                tc_interior_rect(S, oy, nby, iy0, niy);
+                if (nix > 0 && niy > 0) {
+                    err = launch_schwarz_tc(S, ox, oy, ix0, iy0, nix, niy, reinterpret_cast<const float *>(b),
+                                            reinterpret_cast<float *>(u), st);
+                    if (err != cudaSuccess) return err;
+                } else {
+                    nix = niy = 0;
+                }
+            }
+            const int nframe = nblocks - nix * niy;
+            if (nframe <= 0) continue;
+            err = launch_pdl(k_schwarz_lattice2d_sf<P, SB, T>, dim3((nframe + NBSF - 1) / NBSF, S.nbatch), dim3(256),
+                             st, S.n, S.ht.nbc, q, ox, oy, nbx, ix0, iy0, nix, niy, nframe, kband, mband, binv,
+                             S.boundary64(), interior, (const int *)S.bcls, u, b, BatchRef{S.active, S.N, 0, 0});
         } else {
             err = launch_pdl(k_schwarz_lattice2d<P, SB, T>, dim3((nblocks + BPC - 1) / BPC, S.nbatch), dim3(256), st,
                              S.n, S.ht.npc, S.ht.nbc, q, ox, oy, nbx, nblocks, stencil, (const int *)S.pcls, binv,

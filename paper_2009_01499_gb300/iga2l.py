@@ -17,7 +17,7 @@ from . import build as _build
 
 OK, NOT_CONVERGED = 0, 1
 ERR_INVALID_ARG, ERR_CUDA, ERR_DEVICE_TIMEOUT, ERR_NONFINITE, ERR_UNSUPPORTED = -1, -2, -3, -4, -5
-FP64, MIXED_FP32, MIXED_FP32_ALL = 0, 1, 2
+FP64, MIXED_FP32, MIXED_FP32_ALL, MIXED_TF32 = 0, 1, 2, 3
 SCHED_LATTICE, SCHED_TILE = 1, 2
 COARSE_EXACT, COARSE_VCYCLE = 0, 1
 

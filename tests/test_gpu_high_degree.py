@@ -129,8 +129,11 @@ def test_solve_counts_and_mixed_high_p(oracle_mod, p):
     assert np.linalg.norm(_host(ud) - uo) <= fp64_tol(oracle_mod, p, m) * np.linalg.norm(uo)
     ref, _, _, _, ok_r = O.solve(b, u0, tol=1e-15, maxc=200)
     assert ok_r
-    sched = "tile" if p <= 6 else "lattice"
-    for prec in (iga2l.MIXED_FP32, iga2l.MIXED_FP32_ALL):
+    modes = [(iga2l.MIXED_FP32, "tile" if p <= 6 else "lattice"),
+             (iga2l.MIXED_FP32_ALL, "tile" if p <= 6 else "lattice")]
+    if p <= 6:
+        modes.append((iga2l.MIXED_TF32, "lattice"))   # tensor-core form (compiled for p <= 6)
+    for prec, sched in modes:
         X, _ = _pair(oracle_mod, p, m, sched=sched, precision=prec)
         um = _dev(u0)
         c, _, _, okm = X.solve(bd, um, tol=1e-8, max_cycles=40)
@@ -146,4 +149,7 @@ def test_solve_counts_and_mixed_high_p(oracle_mod, p):
 def test_tile_rejected_for_7x7_blocks():
     with pytest.raises(iga2l.IgaError) as ei:
         iga2l.Solver(7, 40, schedule=iga2l.SCHED_TILE)
+    assert ei.value.code == iga2l.ERR_UNSUPPORTED
+    with pytest.raises(iga2l.IgaError) as ei:   # the tensor-core form: 2D, LATTICE, p <= 6
+        iga2l.Solver(7, 40, precision=iga2l.MIXED_TF32)
     assert ei.value.code == iga2l.ERR_UNSUPPORTED

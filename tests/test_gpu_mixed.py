@@ -27,7 +27,12 @@ def _host(t):
 
 
 MODES = [(iga2l.MIXED_FP32, "lattice"), (iga2l.MIXED_FP32_ALL, "lattice"), (iga2l.MIXED_FP32, "tile"),
-         (iga2l.MIXED_FP32_ALL, "tile")]
+         (iga2l.MIXED_FP32_ALL, "tile"), (iga2l.MIXED_TF32, "lattice")]
+# one inner cycle perturbs the correction by the inner arithmetic's rounding amplified by
+# the block operator: FP32 (u = 6e-8) well below 1e-5; the tensor-core form's TF32 operands
+# (u = 2^-11 = 4.9e-4) times the interior block condition (53 at p = 5) ~ 2.6e-2 at most
+# (measured 3.7e-3 at p = 5)
+INNER_TOL = {iga2l.MIXED_FP32: 1e-5, iga2l.MIXED_FP32_ALL: 1e-5, iga2l.MIXED_TF32: 2.6e-2}
 
 
 def _pair(oracle_mod, p, m, precision, sched):
@@ -54,10 +59,9 @@ def test_mixed_iterates_track_fp64_oracle(oracle_mod, p, m, precision, sched):
         e_before = np.linalg.norm(_host(ud) - uo)
         S.cycle(ud, bd)
         uo = O.cycle(uo, b)
-        # an FP32 inner cycle perturbs the correction by ~1e-7 of its size
         corr = np.linalg.norm(uo - _host(ud))
-        assert corr <= 1e-5 * ustar, (k, corr / ustar)
-        assert e_before <= 1e-5 * ustar
+        assert corr <= INNER_TOL[precision] * ustar, (k, corr / ustar)
+        assert e_before <= INNER_TOL[precision] * ustar
 
 
 @pytest.mark.parametrize("precision,sched", MODES)
@@ -87,7 +91,9 @@ def test_mixed_refinement_reaches_fp64_solution(oracle_mod, p, precision, sched)
     assert r <= 1.001e-8                       # the reported residual is a true FP64 residual
     err_mixed = np.linalg.norm(_host(ud) - ustar)
     err_fp64 = np.linalg.norm(uo - ustar)
-    assert err_mixed <= 1.01 * err_fp64 + 1e-14 * np.linalg.norm(ustar)
+    # within 1% of the FP64 oracle's error at the stopping rule (5% with TF32 operands)
+    factor = 1.05 if precision == iga2l.MIXED_TF32 else 1.01
+    assert err_mixed <= factor * err_fp64 + 1e-14 * np.linalg.norm(ustar)
     # refinement continued to a 1e-12 residual
     ud = _dev(u0)
     cyc, rel, hist, ok = S.solve(bd, ud, tol=1e-12, max_cycles=60)
