@@ -494,14 +494,13 @@ def run_gpu(args):
     # mixed precision (FP32 inner cycle, TILE schedule) inside FP64 refinement, same
     # workload and stopping rule: boundary-block inverses applied in FP64 ("mixed") or
     # in FP32 as well ("mixed_fp32_boundary")
-    mixed, mixed_all = None, None
+    mixed, mixed_all, mixed_tf32 = None, None, None
     if not args.no_mixed:
-        def run_mixed(precision, boundary):
+        def run_mixed(precision, boundary, schedule=iga2l.SCHED_TILE):
             msolv = {}
             for p in DEGREES:
                 q, g = COLOURING[p]
-                msolv[p] = iga2l.Solver(p, M_ELEM, period=q, stride=g, precision=precision,
-                                        schedule=iga2l.SCHED_TILE)
+                msolv[p] = iga2l.Solver(p, M_ELEM, period=q, stride=g, precision=precision, schedule=schedule)
             mcyc = {}
 
             def mstep():
@@ -530,7 +529,7 @@ def run_gpu(args):
             out = {"value": ws * ndofs / (mms * 1e-3), "unit": "DOF/s", "ms_per_step": mms,
                    "speedup_vs_fp64": ms_step / mms,
                    "dtype": f"f32 inner cycle ({boundary} boundary-block inverses), f64 residual/update/coarsest",
-                   "schedule": {str(p): f"TILE({msolv[p].tile})" for p in DEGREES},
+                   "schedule": {str(p): (f"TILE({msolv[p].tile})" if msolv[p].tile else "LATTICE") for p in DEGREES},
                    "cycles": {str(p): mcyc[p] for p in DEGREES},
                    "accuracy": "same 1e-8 FP64 residual rule; refined to 1e-12 the solution is within "
                                "1e-8 of the FP64 oracle's (tests/test_gpu_mixed.py)",
@@ -541,6 +540,10 @@ def run_gpu(args):
 
         mixed = run_mixed(iga2l.MIXED_FP32, "f64")
         mixed_all = run_mixed(iga2l.MIXED_FP32_ALL, "f32")
+        # the interior blocks of every LATTICE colour as a tcgen05 TF32 GEMM
+        mixed_tf32 = run_mixed(iga2l.MIXED_TF32, "f64", iga2l.SCHED_LATTICE)
+        mixed_tf32["dtype"] = ("tf32 tensor-core interior block solves (tcgen05, f32 accumulation), f32 boundary "
+                               "frame, f64 residual/update/coarsest")
 
     # secondary configurations: 3D (p = 3, 128^3, FP64 and mixed), the batch of 256 uneven
     # 2D problems (mixed, autotuned schedules, concurrent groups), and p = 6..8 at 1024^2
@@ -602,7 +605,7 @@ def run_gpu(args):
         "gpu_launches": int(launches),
         "roofline": roofline,
         "clocks": clk,
-        "concurrent": concurrent, "mixed": mixed, "mixed_fp32_boundary": mixed_all,
+        "concurrent": concurrent, "mixed": mixed, "mixed_fp32_boundary": mixed_all, "mixed_tf32_tensor_core": mixed_tf32,
         "other_configs": extra,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
