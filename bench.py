@@ -631,8 +631,9 @@ def run_profile_step(args):
     dim = args.profile_dim
     degrees = (args.profile_p,) if args.profile_p else ((3,) if dim == 3 else DEGREES)
     m = args.profile_m or (128 if dim == 3 else M_ELEM)
-    prec = {"fp64": iga2l.FP64, "mixed": iga2l.MIXED_FP32, "mixed_all": iga2l.MIXED_FP32_ALL}[args.profile_precision]
-    sched = iga2l.SCHED_LATTICE if (prec == iga2l.FP64 or dim == 3) else iga2l.SCHED_TILE
+    prec = {"fp64": iga2l.FP64, "mixed": iga2l.MIXED_FP32, "mixed_all": iga2l.MIXED_FP32_ALL,
+            "mixed_tf32": iga2l.MIXED_TF32}[args.profile_precision]
+    sched = iga2l.SCHED_LATTICE if (prec in (iga2l.FP64, iga2l.MIXED_TF32) or dim == 3) else iga2l.SCHED_TILE
     for p in degrees:
         q, g = COLOURING[p]
         S = iga2l.Solver(p, m, dim=dim, period=q, stride=g, precision=prec, schedule=sched)
@@ -664,7 +665,7 @@ def main():
     ap.add_argument("--profile-m", type=int, default=0, help="elements per axis (default 1024 in 2D, 128 in 3D)")
     ap.add_argument("--profile-dim", type=int, choices=[2, 3], default=2)
     ap.add_argument("--profile-p", type=int, default=0)
-    ap.add_argument("--profile-precision", choices=["fp64", "mixed", "mixed_all"], default="fp64",
+    ap.add_argument("--profile-precision", choices=["fp64", "mixed", "mixed_all", "mixed_tf32"], default="fp64",
                     help="form profiled by --profile-step (the benchmark's schedule for it)")
     args = ap.parse_args()
     if args.profile_step:
