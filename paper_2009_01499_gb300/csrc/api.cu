@@ -372,7 +372,9 @@ static int assemble_impl(int p, int m, int dim, int nbatch, bool batch, const ig
     S->opt = opt;
     S->q = q; S->g = g % q; S->tile = opt.tile;
     cudaError_t ce = cudaGetDevice(&S->device);
+    if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&S->nsm, cudaDevAttrMultiProcessorCount, S->device);
     if (ce != cudaSuccess) { release(S); return cuda_fail(ce, "cudaGetDevice"); }
+    if (S->nsm < 1) S->nsm = 1;
 
     std::string err;
     int rc = build_host_tables(p, m, s, S->ht, err);
@@ -603,6 +605,14 @@ static int assemble_impl(int p, int m, int dim, int nbatch, bool batch, const ig
                 release(S);
                 return cuda_fail(ce, "mixed-precision level allocation");
             }
+        if (opt.precision == IGA2L_MIXED_FP32 || opt.precision == IGA2L_MIXED_TF32) {
+            std::vector<float> lo(binv.size());
+            for (size_t i = 0; i < binv.size(); ++i) lo[i] = (float)(binv[i] - (double)(float)binv[i]);
+            if ((ce = upload(S, &X.binv_lo, lo)) != cudaSuccess) {
+                release(S);
+                return cuda_fail(ce, "block-inverse pair upload");
+            }
+        }
         if (opt.precision == IGA2L_MIXED_TF32) {
             const int interior = ht.L * ht.nbc + ht.L;
             std::vector<double> ainv(binv.begin() + (size_t)interior * SS * SS,

@@ -66,6 +66,9 @@ struct MixedState {
     float *gtc = nullptr;
     int gtc_n = 0, gtc_k = 0;
     int *tc_status = nullptr;   // device: bounded waits of the tensor-core kernel that gave up
+    // IGA2L_MIXED_FP32 / TF32: the FP64 block inverses as unevaluated pairs binv + binv_lo
+    // (binv_lo = fl32(B - binv)), for the compensated FP32 application in the TILE kernel
+    float *binv_lo = nullptr;
     float *r = nullptr;       // outer residual b - A u, computed in FP64, stored in FP32
     float *delta = nullptr;   // correction of the Schwarz step
     float *d = nullptr, *t = nullptr, *t2 = nullptr, *dc = nullptr, *ec = nullptr;
@@ -84,6 +87,7 @@ struct Solver {
     iga2l_options opt{};
     int device = 0;
     int q = 5, g = 1, tile = 0;
+    int nsm = 1;                 // SMs of the device (launch balancing)
     HostTables ht;
     // device tables
     double *Kb = nullptr, *Mb = nullptr;
@@ -119,12 +123,52 @@ struct Solver {
     {
         return opt.precision == IGA2L_MIXED_FP32 || opt.precision == IGA2L_MIXED_TF32 ? binv : nullptr;
     }
+    // the low halves of the FP32 pairs of those inverses, or null likewise
+    const float *boundary_lo() const
+    {
+        return opt.precision == IGA2L_MIXED_FP32 || opt.precision == IGA2L_MIXED_TF32 ? mx.binv_lo : nullptr;
+    }
 };
 
 // Number of kernels this library has launched (process-wide), for benchmarks
 // that report how many of the timed region's kernels are this library's.
 void count_launches(long long k);
 long long launches_so_far();
+
+#ifdef __CUDACC__
+// Programmatic dependent launch.  The kernels of a cycle are launched with the
+// programmatic-serialisation attribute; each reads only constant tables before
+// pdl_wait(), which returns once the previous grid has completed and its writes are
+// visible, so that part overlaps the previous kernel's completion.  Every thread calls
+// pdl_wait() before it exits, so a grid's completion implies its predecessors'.  No kernel
+// triggers its dependents early (griddepcontrol.launch_dependents): with early triggers
+// the p = 4 FP64 sweep measured 35% slower and four concurrent mixed solves 30% slower
+// (the next grid's waiting CTAs are placed on whichever SMs drain first, which likely
+// spreads a single-wave colour phase unevenly, and they hold slots other streams need).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename Kernel, typename... Args>
+cudaError_t launch_pdl_smem(Kernel kernel, dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args)
+{
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+template <typename Kernel, typename... Args>
+cudaError_t launch_pdl(Kernel kernel, dim3 grid, dim3 block, cudaStream_t st, Args... args)
+{
+    return launch_pdl_smem(kernel, grid, block, 0, st, args...);
+}
+#endif
 
 // Sets the text returned by iga2l_last_error on the calling thread (api.cu).
 void set_last_error(const std::string &msg);

@@ -668,22 +668,34 @@ __global__ void k_level_prolong3d(int nf, int nc, const T *__restrict__ ec, T *_
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (long long)nf * nf * nf) return;
     const int c3[3] = {(int)(i % nf), (int)((i / nf) % nf), (int)(i / ((long long)nf * nf))};
-    int I[3][2], cnt[3];
+    // per axis two coarse slots: odd x -> ((x-1)/2, weight 1), even x -> (x/2-1, x/2,
+    // weights 1/2); an unused or out-of-range slot has weight 0 and is skipped
+    int I[3][2];
     T w[3][2];
+#pragma unroll
     for (int k = 0; k < 3; ++k) {
         const int x = c3[k];
-        if (x & 1) { I[k][0] = (x - 1) / 2; w[k][0] = T(1); cnt[k] = 1; }
-        else { I[k][0] = x / 2 - 1; I[k][1] = x / 2; w[k][0] = T(0.5); w[k][1] = T(0.5); cnt[k] = 2; }
+        const bool odd = x & 1;
+        I[k][0] = odd ? (x - 1) / 2 : x / 2 - 1;
+        I[k][1] = x / 2;
+        w[k][0] = odd ? T(1) : T(0.5);
+        w[k][1] = odd ? T(0) : T(0.5);
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+            if (I[k][c] < 0 || I[k][c] >= nc) w[k][c] = T(0);
     }
     T acc = T(0);
-    for (int cz = 0; cz < cnt[2]; ++cz) {
-        if (I[2][cz] < 0 || I[2][cz] >= nc) continue;
+#pragma unroll
+    for (int cz = 0; cz < 2; ++cz) {
+        if (w[2][cz] == T(0)) continue;
         T sy = T(0);
-        for (int cy = 0; cy < cnt[1]; ++cy) {
-            if (I[1][cy] < 0 || I[1][cy] >= nc) continue;
+#pragma unroll
+        for (int cy = 0; cy < 2; ++cy) {
+            if (w[1][cy] == T(0)) continue;
             T sx = T(0);
-            for (int cx = 0; cx < cnt[0]; ++cx) {
-                if (I[0][cx] < 0 || I[0][cx] >= nc) continue;
+#pragma unroll
+            for (int cx = 0; cx < 2; ++cx) {
+                if (w[0][cx] == T(0)) continue;
                 sx = fma(w[0][cx], ec[((size_t)I[2][cz] * nc + I[1][cy]) * nc + I[0][cx]], sx);
             }
             sy = fma(w[1][cy], sx, sy);

@@ -22,6 +22,7 @@ namespace {
 template <typename T>
 struct Stencil9 {
     T c[3][3];   // c[dy][dx], dx, dy in {0,1,2} <-> offsets -1, 0, +1
+    T dinv;      // 1 / c[1][1] (rounded once): a Gauss-Seidel update multiplies by it
 };
 
 // red-black order of the sub-lattices: red (0,0), (1,1) then black (1,0), (0,1)
@@ -33,13 +34,15 @@ Stencil9<T> level_stencil(const Level &L)
     Stencil9<T> s;
     for (int dy = 0; dy < 3; ++dy)
         for (int dx = 0; dx < 3; ++dx) s.c[dy][dx] = (T)(L.k[dx] * L.mm[dy] + L.mm[dx] * L.k[dy]);
+    s.dinv = (T)(1.0 / (L.k[1] * L.mm[1] + L.mm[1] * L.k[1]));
     return s;
 }
 
 // ---- fused level kernels --------------------------------------------------------------
 // One relaxation of the V(1,1) smoother is four sub-lattice sweeps {(2a+px, 2b+py)}, each
-// e += (rhs - A e) / A_diag; no two points of a sub-lattice are coupled by the 9-point
-// stencil.  A CTA owns a TX x TY tile of the level and stages it with a halo of H >= 4:
+// e += (rhs - A e) / A_diag, the quotient taken as a product with the once-rounded
+// reciprocal of the diagonal (within about an ulp of the quotient); no two points of a
+// sub-lattice are coupled by the 9-point stencil.  A CTA owns a TX x TY tile of the level and stages it with a halo of H >= 4:
 // after sweep k every staged point at distance >= k from the staged edge holds exactly the
 // value the four global sweeps give (its neighbours were exact after sweep k-1), so the
 // tile is exact after four sweeps and one launch replaces four.  Points outside the level
@@ -71,7 +74,7 @@ __device__ __forceinline__ void level_sweeps(int n, int gx0, int gy0, const Sten
                     if (xx >= 0 && xx < n) acc = fma(st.c[dy][dx], se[ly + dy - 1][lx + dx - 1], acc);
                 }
             }
-            se[ly][lx] += (sr[ly][lx] - acc) / st.c[1][1];
+            se[ly][lx] += (sr[ly][lx] - acc) * st.dinv;
         }
         __syncthreads();
     }
@@ -89,6 +92,7 @@ k_level_pre(int nf, int nc, Stencil9<T> st, const T *__restrict__ rhs, T *__rest
     constexpr int H = 6, RX = kLvTX + 2 * H, RY = kLvTY + 2 * H;
     __shared__ T se[RY][RX], sr[RY][RX];
     __shared__ T res[kLvTY + 1][kLvTX + 1];
+    pdl_wait();
     if (bt.active && !bt.active[blockIdx.z]) return;
     rhs += blockIdx.z * bt.vec;
     epre += blockIdx.z * bt.vec;
@@ -151,6 +155,7 @@ k_level_post(int nf, int nc, Stencil9<T> st, const T *__restrict__ rhs, const T 
 {
     constexpr int H = 4, RX = kLvTX + 2 * H, RY = kLvTY + 2 * H;
     __shared__ T se[RY][RX], sr[RY][RX];
+    pdl_wait();
     if (bt.active && !bt.active[blockIdx.z]) return;
     rhs += blockIdx.z * bt.vec;
     epre += blockIdx.z * bt.vec;
@@ -199,6 +204,7 @@ template <typename T>
 __global__ void k_dense_matvec(int N, const double *__restrict__ Ainv, const T *__restrict__ rhs,
                                T *__restrict__ x, BatchRef bt)
 {
+    pdl_wait();
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (warp >= N || (bt.active && !bt.active[blockIdx.y])) return;
     rhs += blockIdx.y * bt.vec;
@@ -237,7 +243,7 @@ __device__ void tail_gs(int n, const Stencil9<T> &st, const T *rhs, T *e, int px
     if (first) {
         for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
             const int x = i % n, y = i / n;
-            e[i] = ((x | y) & 1) ? T(0) : (rhs[i] - T(0)) / st.c[1][1];
+            e[i] = ((x | y) & 1) ? T(0) : (rhs[i] - T(0)) * st.dinv;
         }
         return;
     }
@@ -255,32 +261,39 @@ __device__ void tail_gs(int n, const Stencil9<T> &st, const T *rhs, T *e, int px
                 if (xx >= 0 && xx < n) acc = fma(st.c[dy][dx], e[yy * n + xx], acc);
             }
         }
-        e[y * n + x] += (rhs[y * n + x] - acc) / st.c[1][1];
+        e[y * n + x] += (rhs[y * n + x] - acc) * st.dinv;
     }
 }
 
+// The arguments are read in place (__grid_constant__: per-level values indexed at run
+// time come from the constant bank, not from a per-thread local copy of the struct).
+// Level l's correction E and right-hand side Rh lie one after the other in shared
+// memory, after those of the levels above it.
 template <typename T>
-__global__ void __launch_bounds__(1024) k_vcycle_tail(TailArgs<T> a)
+__device__ __forceinline__ T *tail_level(T *base, const TailArgs<T> &a, int l)
+{
+    for (int k = 0; k < l; ++k) base += 2 * a.n[k] * a.n[k];
+    return base;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_vcycle_tail(const __grid_constant__ TailArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char tail_smem[];
+    T *const base = reinterpret_cast<T *>(tail_smem);
+    pdl_wait();
     if (a.active && !a.active[blockIdx.x]) return;
-    a.rhs0 += blockIdx.x * a.vec0;
-    a.e0 += blockIdx.x * a.vec0;
-    T *E[kTailMaxLevels], *Rh[kTailMaxLevels];
-    {
-        T *p = reinterpret_cast<T *>(tail_smem);
-        for (int l = 0; l < a.nl; ++l) {
-            E[l] = p; p += a.n[l] * a.n[l];
-            Rh[l] = p; p += a.n[l] * a.n[l];
-        }
-    }
-    for (int i = threadIdx.x; i < a.n[0] * a.n[0]; i += blockDim.x) Rh[0][i] = a.rhs0[i];
+    const T *rhs0 = a.rhs0 + blockIdx.x * a.vec0;
+    T *e0 = a.e0 + blockIdx.x * a.vec0;
+    for (int i = threadIdx.x; i < a.n[0] * a.n[0]; i += blockDim.x) base[a.n[0] * a.n[0] + i] = rhs0[i];
     __syncthreads();
     const int last = a.nl - 1;
     for (int l = 0; l < last; ++l) {
         const int n = a.n[l], nc = a.n[l + 1];
+        T *E = tail_level(base, a, l), *Rh = E + n * n, *Rc = Rh + n * n + nc * nc;
+        const Stencil9<T> st = a.st[l];
         for (int t = 0; t < 4; ++t) {
-            tail_gs<T>(n, a.st[l], Rh[l], E[l], kGsSeqDev[t][0], kGsSeqDev[t][1], t == 0);
+            tail_gs<T>(n, st, Rh, E, kGsSeqDev[t][0], kGsSeqDev[t][1], t == 0);
             __syncthreads();
         }
         const T w[3] = {T(0.5), T(1), T(0.5)};
@@ -302,32 +315,34 @@ __global__ void __launch_bounds__(1024) k_vcycle_tail(TailArgs<T> a)
 #pragma unroll
                         for (int ex = 0; ex < 3; ++ex) {
                             const int xx = x + ex - 1;
-                            if (xx >= 0 && xx < n) aa = fma(a.st[l].c[ey][ex], E[l][yy * n + xx], aa);
+                            if (xx >= 0 && xx < n) aa = fma(st.c[ey][ex], E[yy * n + xx], aa);
                         }
                     }
-                    const T r = Rh[l][y * n + x] - aa;
+                    const T r = Rh[y * n + x] - aa;
                     sacc = fma(w[dx], r, sacc);
                 }
                 acc = fma(w[dy], sacc, acc);
             }
-            Rh[l + 1][J * nc + I] = acc;
+            Rc[J * nc + I] = acc;
         }
         __syncthreads();
     }
     {   // direct solve: warp-per-row dot products, the reduction order of k_dense_matvec
         const int N = a.n[last] * a.n[last];
+        T *El = tail_level(base, a, last), *Rl = El + N;
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
         for (int row = warp; row < N; row += nw) {
             const double *rp = a.dinv + (size_t)row * N;
             double sacc = 0.0;
-            for (int j = lane; j < N; j += 32) sacc = fma(rp[j], (double)Rh[last][j], sacc);
+            for (int j = lane; j < N; j += 32) sacc = fma(rp[j], (double)Rl[j], sacc);
             for (int off = 16; off > 0; off >>= 1) sacc += __shfl_down_sync(0xffffffffu, sacc, off);
-            if (lane == 0) E[last][row] = (T)sacc;
+            if (lane == 0) El[row] = (T)sacc;
         }
         __syncthreads();
     }
     for (int l = last - 1; l >= 0; --l) {
         const int nf = a.n[l], nc = a.n[l + 1];
+        T *E = tail_level(base, a, l), *Rh = E + nf * nf, *Ec = Rh + nf * nf;
         for (int i = threadIdx.x; i < nf * nf; i += blockDim.x) {
             const int x = i % nf, y = i / nf;
             int Ix[2], Iy[2];
@@ -343,19 +358,20 @@ __global__ void __launch_bounds__(1024) k_vcycle_tail(TailArgs<T> a)
                 T sacc = T(0);
                 for (int aq = 0; aq < nx; ++aq) {
                     if (Ix[aq] < 0 || Ix[aq] >= nc) continue;
-                    sacc = fma(wx[aq], E[l + 1][Iy[bq] * nc + Ix[aq]], sacc);
+                    sacc = fma(wx[aq], Ec[Iy[bq] * nc + Ix[aq]], sacc);
                 }
                 acc = fma(wy[bq], sacc, acc);
             }
-            E[l][i] += acc;
+            E[i] += acc;
         }
         __syncthreads();
+        const Stencil9<T> st = a.st[l];
         for (int t = 3; t >= 0; --t) {
-            tail_gs<T>(nf, a.st[l], Rh[l], E[l], kGsSeqDev[t][0], kGsSeqDev[t][1], false);
+            tail_gs<T>(nf, st, Rh, E, kGsSeqDev[t][0], kGsSeqDev[t][1], false);
             __syncthreads();
         }
     }
-    for (int i = threadIdx.x; i < a.n[0] * a.n[0]; i += blockDim.x) a.e0[i] = E[0][i];
+    for (int i = threadIdx.x; i < a.n[0] * a.n[0]; i += blockDim.x) e0[i] = base[i];
 }
 
 // levE[l], levR[l]: the e and rhs arrays of level l >= 1 in the storage type T; levP[l]:
@@ -369,10 +385,10 @@ cudaError_t vcycle(const Solver &S, int l, const T *rhs, T *e, T *const *levE, T
     const int nb = S.nbatch;
     if (l == last) {
         const int N = S.ndirect;
-        k_dense_matvec<T><<<dim3((N * 32 + 255) / 256, nb), 256, 0, s>>>(N, S.dinv, rhs, e,
-                                                                         BatchRef{S.active, L.N, 0, 0});
+        const cudaError_t err = launch_pdl(k_dense_matvec<T>, dim3((N * 32 + 255) / 256, nb), dim3(256), s, N,
+                                           (const double *)S.dinv, rhs, e, BatchRef{S.active, L.N, 0, 0});
         count_launches(1);
-        return cudaGetLastError();
+        return err;
     }
     // small levels: the rest of the cycle in one thread block per problem, in shared memory
     const int tail_n = 31;   // larger levels: the fused multi-CTA level kernels are faster
@@ -391,9 +407,9 @@ cudaError_t vcycle(const Solver &S, int l, const T *rhs, T *e, T *const *levE, T
             a.rhs0 = rhs;
             a.e0 = e;
             a.dinv = S.dinv;
-            k_vcycle_tail<T><<<nb, 1024, smem, s>>>(a);
+            const cudaError_t err = launch_pdl_smem(k_vcycle_tail<T>, dim3(nb), dim3(1024), smem, s, a);
             count_launches(1);
-            return cudaGetLastError();
+            return err;
         }
     }
     const Level &C = S.lev[l + 1];
@@ -401,13 +417,14 @@ cudaError_t vcycle(const Solver &S, int l, const T *rhs, T *e, T *const *levE, T
     const BatchRef bt{S.active, L.N, 0, C.N};
     const dim3 blk(kLvTX, kLvTY / 2), grd((L.n + kLvTX - 1) / kLvTX, (L.n + kLvTY - 1) / kLvTY, nb);
     cudaError_t err;
-    k_level_pre<T><<<grd, blk, 0, s>>>(L.n, C.n, st, rhs, levP[l], levR[l + 1], bt);
+    err = launch_pdl(k_level_pre<T>, grd, blk, s, L.n, C.n, st, rhs, levP[l], levR[l + 1], bt);
     count_launches(1);
-    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    if (err != cudaSuccess) return err;
     if ((err = vcycle<T>(S, l + 1, levR[l + 1], levE[l + 1], levE, levR, levP, s)) != cudaSuccess) return err;
-    k_level_post<T><<<grd, blk, 0, s>>>(L.n, C.n, st, rhs, levP[l], levE[l + 1], e, bt);
+    err = launch_pdl(k_level_post<T>, grd, blk, s, L.n, C.n, st, rhs, (const T *)levP[l], (const T *)levE[l + 1], e,
+                     bt);
     count_launches(1);
-    return cudaGetLastError();
+    return err;
 }
 
 }  // namespace

@@ -25,28 +25,6 @@ namespace iga2l {
 
 namespace {
 
-// Programmatic dependent launch: the colour kernels of a sweep are launched with the
-// programmatic-serialisation attribute, so a colour's grid is set up while the previous
-// colour drains; every such kernel waits here, before its first global access, until the
-// previous grid has completed and its writes are visible.
-__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-
-template <typename Kernel, typename... Args>
-cudaError_t launch_pdl(Kernel kernel, dim3 grid, dim3 block, cudaStream_t st, Args... args)
-{
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = st;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kernel, args...);
-}
-
 constexpr int kResTX = 32, kResTY = 8;   // residual tile (outputs per CTA)
 
 // Fixed-order sum of the partials (deterministic norm).
@@ -71,8 +49,10 @@ __global__ void k_sum_partials(const double *__restrict__ part, int np, double *
 // then row e of A_B^{-1} times the block residual, and adds it to u.  Blocks of
 // one colour neither share DOFs nor read each other's DOFs, so they run in parallel.
 // With T = float, blocks of the interior class use the FP32 inverse and the other
-// (boundary) classes the FP64 inverse binv64.
-template <int P, int S, typename T>
+// (boundary) classes the FP64 inverse binv64.  A CTA takes BPC <= 256 / S^2 blocks
+// (blockDim = BPC S^2 rounded up to a warp); the launch picks BPC among compiled
+// variants so that the colour's CTAs spread evenly over the SMs (lattice_bpc).
+template <int P, int S, int BPC, typename T>
 __global__ void __launch_bounds__(256)
 k_schwarz_lattice2d(int n, int npc, int nbc, int q, int ox, int oy, int nbx, int nblocks,
                     const T *__restrict__ stencil, const int *__restrict__ pcls,
@@ -80,9 +60,8 @@ k_schwarz_lattice2d(int n, int npc, int nbc, int q, int ox, int oy, int nbx, int
                     const int *__restrict__ bcls, T *__restrict__ u, const T *__restrict__ b, BatchRef bt)
 {
     constexpr int W = 2 * P + 1, SS = S * S, R = (S - 1) / 2;
-    constexpr int BPC = 256 / SS;   // Schwarz blocks per CTA
     __shared__ T rs[BPC * SS];
-    grid_dependency_wait();
+    pdl_wait();
     if (bt.active && !bt.active[blockIdx.y]) return;
     u += blockIdx.y * bt.vec;
     b += blockIdx.y * bt.vec;
@@ -207,30 +186,13 @@ k_residual2d(int n, const T *__restrict__ kband, const T *__restrict__ mband, co
     __shared__ T2 kmy[kResTY][W], mkx[kResTX][W];   // boundary tiles
     __shared__ double red[kResTX * kResTY / 32];
     const int z = blockIdx.z;
-    if (bt.active && !bt.active[z]) return;
-    u += z * bt.vec;
-    if (b) b += z * bt.vec;
-    if (d) d += z * bt.vec;
-    if (part) part += z * bt.aux;
     const int x0 = blockIdx.x * kResTX, y0 = blockIdx.y * kResTY;
     const int tid = threadIdx.x + kResTX * threadIdx.y;
     constexpr int NT = kResTX * kResTY;
     constexpr int K = (SX * SY + NT - 1) / NT;
-    T v[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const int t = tid + k * NT;
-        const int gx = x0 + t % SX - P, gy = y0 + t / SX - P;
-        v[k] = (t < SX * SY && gx >= 0 && gx < n && gy >= 0 && gy < n) ? u[(size_t)gy * n + gx] : T(0);
-    }
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const int t = tid + k * NT;
-        if (t < SX * SY) su[t / SX][t % SX] = v[k];
-    }
     const bool fast = x0 >= 2 * P - 1 && x0 + kResTX - 1 <= n - 2 * P && y0 >= 2 * P - 1 &&
                       y0 + kResTY - 1 <= n - 2 * P;
-    if (!fast) {
+    if (!fast) {   // constant tables: read before the wait
         const T h = T(1) / T(n - P + 2), hinv = T(n - P + 2);
         for (int t = tid; t < (kResTX + kResTY) * W; t += NT) {
             const int row = t / W, a = t - row * W;
@@ -248,6 +210,24 @@ k_residual2d(int n, const T *__restrict__ kband, const T *__restrict__ mband, co
                 mkx[row - kResTY][a] = mk;
             }
         }
+    }
+    pdl_wait();
+    if (bt.active && !bt.active[z]) return;
+    u += z * bt.vec;
+    if (b) b += z * bt.vec;
+    if (d) d += z * bt.vec;
+    if (part) part += z * bt.aux;
+    T v[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int t = tid + k * NT;
+        const int gx = x0 + t % SX - P, gy = y0 + t / SX - P;
+        v[k] = (t < SX * SY && gx >= 0 && gx < n && gy >= 0 && gy < n) ? u[(size_t)gy * n + gx] : T(0);
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int t = tid + k * NT;
+        if (t < SX * SY) su[t / SX][t % SX] = v[k];
     }
     __syncthreads();
     for (int pt = tid; pt < kResTY * SX; pt += NT) {
@@ -360,13 +340,13 @@ k_schwarz_lattice2d_sf(int n, int nbc, int q, int ox, int oy, int nbx, int ix0, 
     __shared__ T2 yb[NB][S][WIN];
     __shared__ T rs[NB][SS];
     __shared__ T sbi[SS * SS];
-    grid_dependency_wait();
+    const int tid = threadIdx.x;
+    for (int i = tid; i < SS * SS; i += NT) sbi[i] = binv[(size_t)interior * SS * SS + i];   // constant table
+    pdl_wait();
     if (bt.active && !bt.active[blockIdx.y]) return;
     u += blockIdx.y * bt.vec;
     b += blockIdx.y * bt.vec;
-    const int tid = threadIdx.x;
     const int blk0 = blockIdx.x * NB;
-    for (int i = tid; i < SS * SS; i += NT) sbi[i] = binv[(size_t)interior * SS * SS + i];
     // 1. y pass
     if (tid < NB * WIN) {
         const int j = tid / WIN, c = tid - j * WIN, blk = blk0 + j;
@@ -466,6 +446,37 @@ k_schwarz_lattice2d_sf(int n, int nbc, int q, int ox, int oy, int nbx, int ix0, 
         }
         u[(size_t)y * n + x] += ev;
     }
+}
+
+// Row e of an FP64 block inverse, held as the FP32 pair hi + lo, times the FP32 block
+// residual r, by Dot2 of Ogita, Rump and Oishi ("Accurate sum and dot product", SIAM J.
+// Sci. Comput. 26(6), 2005): every product split exactly into p + ep (TwoProduct by FMA),
+// every running sum into t + es (TwoSum), the error terms gathered in c; the result is as
+// accurate as the sum computed in about twice the FP32 precision and then rounded once.
+// Two interleaved chains (even and odd f) halve the dependent adds.  Explicit _rn
+// intrinsics keep the compiler from contracting the error-free transformations.
+template <int SS>
+__device__ __forceinline__ float dot2_row(const float *__restrict__ hi, const float *__restrict__ lo,
+                                          const float *rv)
+{
+    float s0 = 0.f, s1 = 0.f, c0 = 0.f, c1 = 0.f;
+#pragma unroll
+    for (int f = 0; f < SS; ++f) {
+        float &s = (f & 1) ? s1 : s0;
+        float &c = (f & 1) ? c1 : c0;
+        const float a = __ldg(&hi[f]), r = rv[f];
+        const float p = __fmul_rn(a, r);
+        const float ep = __fmaf_rn(a, r, -p);                  // a r = p + ep
+        const float t = __fadd_rn(s, p);
+        const float z = __fsub_rn(t, s);
+        const float es = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));   // s + p = t + es
+        s = t;
+        c = __fmaf_rn(__ldg(&lo[f]), r, __fadd_rn(c, __fadd_rn(ep, es)));
+    }
+    const float t = __fadd_rn(s0, s1);
+    const float z = __fsub_rn(t, s0);
+    const float e = __fadd_rn(__fsub_rn(s0, __fsub_rn(t, z)), __fsub_rn(s1, z));   // s0 + s1 = t + e
+    return __fadd_rn(t, __fadd_rn(e, __fadd_rn(c0, c1)));
 }
 
 // Geometry of one CTA of the TILE(TT) schedule.
@@ -579,13 +590,14 @@ __device__ __forceinline__ T tile_xpass(const typename Vec2<T>::type *yb, int ey
 // (packed FP32 FMA).  Interior tiles (almost all) take the interior 1D rows from constant
 // memory; boundary tiles the 1D rows of their own rows and columns.  After a second warp
 // barrier each lane applies row e of its block's inverse (the interior row kept in
-// registers, boundary classes in FP64) and adds the result to u in shared memory.  One
+// registers; boundary classes with their FP64 inverse, in compensated FP32 arithmetic)
+// and adds the result to u in shared memory.  One
 // CTA barrier per colour.
 template <int P, int S, int TT, typename T>
 __global__ void __launch_bounds__(TileGeom<P, S, TT>::NT, TileGeom<P, S, TT>::template minb<T>())
 k_schwarz_tile2d(int n, int nbc, int q, int g, int rev, int px, int py, int ntpx,
                  const T *__restrict__ kband, const T *__restrict__ mband,
-                 const T *__restrict__ binv, const double *__restrict__ binv64, int interior,
+                 const T *__restrict__ binv, const float *__restrict__ binv_lo, int interior,
                  T *__restrict__ u, const T *__restrict__ b, BatchRef bt)
 {
     using G = TileGeom<P, S, TT>;
@@ -598,9 +610,6 @@ k_schwarz_tile2d(int n, int nbc, int q, int g, int rev, int px, int py, int ntpx
     __shared__ __align__(16) T rs[G::NBLK * G::RSS];
     __shared__ T2 yb[G::NBLK * G::YB];
     __shared__ T2 km1y[BW * W], mk1x[BW * W];   // boundary tiles: (K, M) of rows, (M, K) of columns
-    if (bt.active && !bt.active[blockIdx.y]) return;
-    u += blockIdx.y * bt.vec;
-    b += blockIdx.y * bt.vec;
     const int tid = threadIdx.x;
     const int x0 = (px + 2 * (blockIdx.x % ntpx)) * TT, y0 = (py + 2 * (blockIdx.x / ntpx)) * TT;
     const int tw = min(TT, n - x0), th = min(TT, n - y0);   // centres of this tile
@@ -610,9 +619,8 @@ k_schwarz_tile2d(int n, int nbc, int q, int g, int rev, int px, int py, int ntpx
     const int ey = e / S, ex = e - ey * S;
     const int slot = (tid >> 5) * G::BPW + bw;
     const bool role = bw < G::BPW && slot < G::NBLK;
-    stage_window<NT, SW, SW * SW>(su, u, n, x0 - H, y0 - H, tid);
-    stage_window<NT, BW, BW * BW>(sb, b, n, x0 - R, y0 - R, tid);
     for (int i = tid; i < G::NBLK * G::RSS; i += NT) rs[i] = T(0);   // the padding stays zero
+    // constant tables (read before the wait)
     if (!fast) {
         // the rows scaled like the interior constants (h K, M / h), h = 1 / m, so that a
         // block may mix interior and boundary factors
@@ -638,6 +646,12 @@ k_schwarz_tile2d(int n, int nbc, int q, int g, int rev, int px, int py, int ntpx
         brow[k].x = role ? __ldg(&binv[base + 2 * k]) : T(0);
         brow[k].y = (role && 2 * k + 1 < SS) ? __ldg(&binv[base + 2 * k + 1]) : T(0);
     }
+    pdl_wait();
+    if (bt.active && !bt.active[blockIdx.y]) return;
+    u += blockIdx.y * bt.vec;
+    b += blockIdx.y * bt.vec;
+    stage_window<NT, SW, SW * SW>(su, u, n, x0 - H, y0 - H, tid);
+    stage_window<NT, BW, BW * BW>(sb, b, n, x0 - R, y0 - R, tid);
     __syncthreads();
     const int bi = slot % NB1, bj = slot / NB1;
     T2 *ybs = yb + slot * G::YB;
@@ -681,23 +695,20 @@ k_schwarz_tile2d(int n, int nbc, int q, int g, int rev, int px, int py, int ntpx
 #pragma unroll
                 for (int k = 0; k < G::NB2; ++k) acc2 = fma2(brow[k], r2[k], acc2);
                 ev = acc2.x + acc2.y;
-            } else if (sizeof(T) == sizeof(double) || !binv64) {
+            } else if (sizeof(T) == sizeof(double) || !binv_lo) {
                 const T *Bi = binv + ((size_t)cls * SS + e) * SS;
 #pragma unroll
                 for (int f = 0; f < SS; ++f) ev = fma(__ldg(&Bi[f]), rsb[f], ev);
-            } else {
-                // FP64 row of a boundary-class inverse: loads first, four short chains
-                const double *Bi = binv64 + ((size_t)cls * SS + e) * SS;
-                double bv[SS], ed[4] = {0.0, 0.0, 0.0, 0.0};
+            } else if constexpr (sizeof(T) == sizeof(float)) {
+                // FP64 row of a boundary-class inverse (as the pair binv + binv_lo), applied
+                // in compensated FP32 arithmetic: GB300's FP64 pipe is 1/58 of its FP32
+                // rate, and these rows set the boundary tiles' critical path
+                const size_t row = ((size_t)cls * SS + e) * SS;
                 T rv[2 * G::NB2];
-#pragma unroll
-                for (int f = 0; f < SS; ++f) bv[f] = __ldg(&Bi[f]);
                 const T2 *r2 = reinterpret_cast<const T2 *>(rsb);
 #pragma unroll
                 for (int k = 0; k < G::NB2; ++k) { const T2 v = r2[k]; rv[2 * k] = v.x; rv[2 * k + 1] = v.y; }
-#pragma unroll
-                for (int f = 0; f < SS; ++f) ed[f & 3] = fma(bv[f], (double)rv[f], ed[f & 3]);
-                ev = (T)((ed[0] + ed[1]) + (ed[2] + ed[3]));
+                ev = dot2_row<SS>(binv + row, binv_lo + row, rv);
             }
             if (in) su[(ly + H) * SW + (lx + H)] += ev;
         }
@@ -722,6 +733,7 @@ __global__ void k_restrict_x(int n, int nc, int wr, const T *__restrict__ Rb,
                              const int *__restrict__ Rlo, const T *__restrict__ d,
                              T *__restrict__ t, BatchRef bt)
 {
+    pdl_wait();
     const int I = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
     if (I >= nc || (bt.active && !bt.active[blockIdx.z])) return;
     d += blockIdx.z * bt.vec;
@@ -742,6 +754,7 @@ __global__ void k_restrict_y(int n, int nc, int wr, const T *__restrict__ Rb,
                              const int *__restrict__ Rlo, const T *__restrict__ t,
                              T *__restrict__ dc, BatchRef bt)
 {
+    pdl_wait();
     const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y;
     if (I >= nc || (bt.active && !bt.active[blockIdx.z])) return;
     t += blockIdx.z * bt.aux;
@@ -761,6 +774,7 @@ __global__ void k_prolong_x(int n, int nc, int wc, const T *__restrict__ Cb,
                             const int *__restrict__ Clo, const T *__restrict__ ec,
                             T *__restrict__ t2, BatchRef bt)
 {
+    pdl_wait();
     const int i = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y;
     if (i >= n || (bt.active && !bt.active[blockIdx.z])) return;
     ec += blockIdx.z * bt.crs;
@@ -781,6 +795,7 @@ __global__ void k_prolong_y(int n, int nc, int wc, const T *__restrict__ Cb,
                             const int *__restrict__ Clo, const T *__restrict__ t2,
                             const T *__restrict__ delta, TU *__restrict__ u, BatchRef bt)
 {
+    pdl_wait();
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
     if (i >= n || (bt.active && !bt.active[blockIdx.z])) return;
     t2 += blockIdx.z * bt.aux;
@@ -828,10 +843,10 @@ cudaError_t residual_p(const Solver &S, const T *kband, const T *mband, const T 
                        double *norm2, cudaStream_t st)
 {
     dim3 blk(kResTX, kResTY), grd((S.n + kResTX - 1) / kResTX, (S.n + kResTY - 1) / kResTY, S.nbatch);
-    k_residual2d<P, T, TO><<<grd, blk, 0, st>>>(S.n, kband, mband, u, b, d, part, S.rcount, norm2,
-                                                 BatchRef{S.active, S.N, residual_partials(S), 0});
+    const cudaError_t err = launch_pdl(k_residual2d<P, T, TO>, grd, blk, st, S.n, kband, mband, u, b, d, part,
+                                       S.rcount, norm2, BatchRef{S.active, S.N, residual_partials(S), 0});
     count_launches(1);
-    return cudaGetLastError();
+    return err;
 }
 
 template <typename T, typename TO>
@@ -848,6 +863,44 @@ cudaError_t residual_any(const Solver &S, const T *kband, const T *mband, const 
     case 8: return residual_p<8, T, TO>(S, kband, mband, u, b, d, part, norm2, st);
     default: return cudaErrorInvalidValue;
     }
+}
+
+// Blocks per CTA for a colour of nblocks Schwarz blocks of ss DOFs, among bmax, bmax / 2
+// and bmax / 4 (bmax = 256 / ss, the compiled variants): the busiest SM holds
+// ceil(CTAs / SMs) CTAs, each of ceil(c ss / 32) warps, and every warp costs the same
+// FP64 pipe time, so the choice with the fewest warps on the busiest SM wins (a smaller
+// CTA only when that is 2% fewer; for a many-wave grid the hardware balances the SMs
+// anyway).  A single-wave colour of 772 CTAs on 152 SMs (p = 3, 4 at 1024^2) otherwise
+// leaves some SMs with 6 CTAs and the mean at 5.1: 19% above the mean; 64-thread CTAs
+// bring that to 4%.
+inline int lattice_bpc(long long nblocks, int ss, int nsm)
+{
+    const int bmax = 256 / ss;
+    int best = bmax;
+    long long best_load = -1;
+    for (int c = bmax; c >= 1 && (c == bmax || c * 2 == bmax || c * 4 == bmax); c /= 2) {
+        const long long ncta = (nblocks + c - 1) / c;
+        const long long load = (ncta + nsm - 1) / nsm * ((c * ss + 31) / 32);
+        if (best_load < 0 || load * 50 < best_load * 49) { best = c; best_load = load; }
+    }
+    return best;
+}
+
+// launches the compiled variant with bpc blocks per CTA (BPC, BPC / 2 or BPC / 4, the ones
+// lattice_bpc offers)
+template <int P, int SB, int BPC, typename T>
+cudaError_t launch_lattice_direct(const Solver &S, int q, int ox, int oy, int nbx, int nblocks, const T *stencil,
+                                  const T *binv, int interior, T *u, const T *b, cudaStream_t st, int bpc)
+{
+    if constexpr (BPC % 2 == 0) {
+        if (bpc < BPC)
+            return launch_lattice_direct<P, SB, BPC / 2, T>(S, q, ox, oy, nbx, nblocks, stencil, binv, interior, u, b,
+                                                            st, bpc);
+    }
+    return launch_pdl(k_schwarz_lattice2d<P, SB, BPC, T>, dim3((nblocks + BPC - 1) / BPC, S.nbatch),
+                      dim3((BPC * SB * SB + 31) / 32 * 32), st, S.n, S.ht.npc, S.ht.nbc, q, ox, oy, nbx, nblocks,
+                      stencil, (const int *)S.pcls, binv, S.boundary64(), interior, (const int *)S.bcls, u, b,
+                      BatchRef{S.active, S.N, 0, 0});
 }
 
 template <int P, int SB, typename T>
@@ -891,9 +944,9 @@ cudaError_t schwarz_lattice_p(const Solver &S, const T *stencil, const T *kband,
                              st, S.n, S.ht.nbc, q, ox, oy, nbx, ix0, iy0, nix, niy, nframe, kband, mband, binv,
                              S.boundary64(), interior, (const int *)S.bcls, u, b, BatchRef{S.active, S.N, 0, 0});
         } else {
-            err = launch_pdl(k_schwarz_lattice2d<P, SB, T>, dim3((nblocks + BPC - 1) / BPC, S.nbatch), dim3(256), st,
-                             S.n, S.ht.npc, S.ht.nbc, q, ox, oy, nbx, nblocks, stencil, (const int *)S.pcls, binv,
-                             S.boundary64(), interior, (const int *)S.bcls, u, b, BatchRef{S.active, S.N, 0, 0});
+            const int bpc = lattice_bpc((long long)nblocks * S.nbatch, SB * SB, S.nsm);
+            err = launch_lattice_direct<P, SB, BPC, T>(S, q, ox, oy, nbx, nblocks, stencil, binv, interior, u, b, st,
+                                                       bpc);
         }
         count_launches(1);
         if (err != cudaSuccess) return err;
@@ -914,11 +967,10 @@ cudaError_t schwarz_tile_p(const Solver &S, const T *kband, const T *mband, cons
         const int px = ph & 1, py = ph >> 1;
         const int ntpx = (nt - px + 1) / 2, ntpy = (nt - py + 1) / 2;
         if (ntpx <= 0 || ntpy <= 0) continue;
-        k_schwarz_tile2d<P, SB, TT, T><<<dim3(ntpx * ntpy, S.nbatch), G::NT, 0, st>>>(
-            S.n, S.ht.nbc, S.q, S.g, reverse ? 1 : 0, px, py, ntpx, kband, mband, binv, S.boundary64(), interior, u, b,
-            BatchRef{S.active, S.N, 0, 0});
+        const cudaError_t err = launch_pdl(k_schwarz_tile2d<P, SB, TT, T>, dim3(ntpx * ntpy, S.nbatch), dim3(G::NT),
+                                           st, S.n, S.ht.nbc, S.q, S.g, reverse ? 1 : 0, px, py, ntpx, kband, mband,
+                                           binv, S.boundary_lo(), interior, u, b, BatchRef{S.active, S.N, 0, 0});
         count_launches(1);
-        cudaError_t err = cudaGetLastError();
         if (err != cudaSuccess) return err;
     }
     return cudaSuccess;
@@ -961,11 +1013,14 @@ cudaError_t restrict_any(const Solver &S, const T *Rb, const T *d, T *t, T *dc, 
 {
     const int nc = S.nc, n = S.n;
     const BatchRef bt{S.active, S.N, (long long)n * nc, S.Nc};
-    k_restrict_x<T><<<dim3((nc + 127) / 128, n, S.nbatch), 128, 0, st>>>(n, nc, S.ht.wr, Rb, S.Rlo, d, t, bt);
+    cudaError_t err = launch_pdl(k_restrict_x<T>, dim3((nc + 127) / 128, n, S.nbatch), dim3(128), st, n, nc,
+                                 S.ht.wr, Rb, (const int *)S.Rlo, d, t, bt);
     count_launches(1);
-    k_restrict_y<T><<<dim3((nc + 127) / 128, nc, S.nbatch), 128, 0, st>>>(n, nc, S.ht.wr, Rb, S.Rlo, t, dc, bt);
+    if (err != cudaSuccess) return err;
+    err = launch_pdl(k_restrict_y<T>, dim3((nc + 127) / 128, nc, S.nbatch), dim3(128), st, n, nc, S.ht.wr, Rb,
+                     (const int *)S.Rlo, (const T *)t, dc, bt);
     count_launches(1);
-    return cudaGetLastError();
+    return err;
 }
 
 template <typename T, typename TU>
@@ -974,11 +1029,14 @@ cudaError_t prolong_any(const Solver &S, const T *Cb, const T *ec, T *t2, const 
 {
     const int nc = S.nc, n = S.n;
     const BatchRef bt{S.active, S.N, (long long)n * nc, S.Nc};
-    k_prolong_x<T><<<dim3((n + 127) / 128, nc, S.nbatch), 128, 0, st>>>(n, nc, S.ht.wc, Cb, S.Clo, ec, t2, bt);
+    cudaError_t err = launch_pdl(k_prolong_x<T>, dim3((n + 127) / 128, nc, S.nbatch), dim3(128), st, n, nc,
+                                 S.ht.wc, Cb, (const int *)S.Clo, ec, t2, bt);
     count_launches(1);
-    k_prolong_y<T, TU><<<dim3((n + 127) / 128, n, S.nbatch), 128, 0, st>>>(n, nc, S.ht.wc, Cb, S.Clo, t2, delta, u, bt);
+    if (err != cudaSuccess) return err;
+    err = launch_pdl(k_prolong_y<T, TU>, dim3((n + 127) / 128, n, S.nbatch), dim3(128), st, n, nc, S.ht.wc, Cb,
+                     (const int *)S.Clo, (const T *)t2, delta, u, bt);
     count_launches(1);
-    return cudaGetLastError();
+    return err;
 }
 
 }  // namespace
