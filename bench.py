@@ -57,11 +57,18 @@ def seeds(p):
 
 
 def schwarz_flops_per_dof(p, s, dim=2):
-    """Algorithmic FP64 flops of one Schwarz block (one per DOF): the block residual
-    (s^d rows of (2p+1)^d multiply-adds and one subtraction), the block solve with the
-    precomputed inverse (s^{2d} multiply-adds) and the update (s^d adds)."""
+    """Algorithmic FP64 flops of one Schwarz block (one per DOF) as the FP64 colour kernel
+    computes it: the block residual, the block solve with the precomputed inverse
+    (s^{2d} multiply-adds) and the update (s^d adds).  3x3 and 5x5 blocks
+    (k_schwarz_lattice2d): the residual as s^d rows of (2p+1)^d multiply-adds and one
+    subtraction.  7x7 blocks in 2D (k_schwarz_lattice2d_pd, sum-factorised): s (s + 2p)
+    pairs of (2p+1) multiply-adds (y pass), s^2 pairs of (2p+1) multiply-adds, one add
+    and one subtraction (x pass)."""
     sd = s ** dim
-    return 2 * sd * (2 * p + 1) ** dim + sd + 2 * sd * sd + sd
+    w = 2 * p + 1
+    if dim == 2 and s >= 7:
+        return 4 * w * s * (s + 2 * p) + 4 * w * sd + 2 * sd + 2 * sd * sd + sd
+    return 2 * sd * w ** dim + sd + 2 * sd * sd + sd
 
 
 def block_side(p):

@@ -494,9 +494,9 @@ static int assemble_impl(int p, int m, int dim, int nbatch, bool batch, const ig
             k1[a] = ref.Kb[(size_t)xr * W + a] / mref;   // h K_row, h = 1 / mref
             m1[a] = ref.Mb[(size_t)xr * W + a] * mref;   // M_row / h
         }
-        if ((ce = upload_interior_stencil(p, sti.data(), W * W, k1.data(), m1.data())) != cudaSuccess) {
+        if ((ce = upload_interior_rows(p, k1.data(), m1.data())) != cudaSuccess) {
             release(S);
-            return cuda_fail(ce, "constant stencil upload");
+            return cuda_fail(ce, "constant 1D rows upload");
         }
     }
     // upload

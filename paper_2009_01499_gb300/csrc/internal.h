@@ -242,8 +242,8 @@ void build_gtc(const Solver &S, const std::vector<double> &binv_interior, std::v
                int &kcols);
 constexpr int kTcMaxP = 6;
 
-// Interior 2D residual stencil of degree p and the interior 1D rows k = h K_row,
-// m = M_row / h (all h-independent) into constant memory; written once per device and degree.
-cudaError_t upload_interior_stencil(int p, const double *st64, int count, const double *k1, const double *m1);
+// The interior 1D rows k = h K_row, m = M_row / h of degree p (h-independent) into
+// constant memory; written once per device and degree.
+cudaError_t upload_interior_rows(int p, const double *k1, const double *m1);
 
 }  // namespace iga2l

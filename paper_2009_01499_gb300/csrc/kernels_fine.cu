@@ -115,22 +115,10 @@ k_schwarz_lattice2d(int n, int npc, int nbc, int q, int ox, int oy, int nbx, int
     }
 }
 
-// Interior residual stencil of each degree (2D; independent of h), written once per
-// process per degree and read as compile-time-indexed constant operands.
-__constant__ double c_stencil64[kMaxP + 1][(2 * kMaxP + 1) * (2 * kMaxP + 1)];
-__constant__ float c_stencil32[kMaxP + 1][(2 * kMaxP + 1) * (2 * kMaxP + 1)];
-
-template <typename T>
-__device__ __forceinline__ T cst(int p, int i);
-template <>
-__device__ __forceinline__ double cst<double>(int p, int i) { return c_stencil64[p][i]; }
-template <>
-__device__ __forceinline__ float cst<float>(int p, int i) { return c_stencil32[p][i]; }
-
 // Interior rows of the 1D stiffness and mass matrices, scaled to be independent of h
 // (k = h K_row, m = M_row / h): the interior 2D coefficient K_y[b] M_x[a] + M_y[b] K_x[a]
 // equals k[b] m[a] + m[b] k[a].  Stored as pairs (k[a], m[a]) for the packed y pass and
-// (m[a], k[a]) for the packed x pass; written with the 2D stencil, once per device and degree.
+// (m[a], k[a]) for the packed x pass; written once per device and degree.
 __constant__ double2 c_km1d[kMaxP + 1][2 * kMaxP + 1], c_mk1d[kMaxP + 1][2 * kMaxP + 1];
 __constant__ float2 c_km1f[kMaxP + 1][2 * kMaxP + 1], c_mk1f[kMaxP + 1][2 * kMaxP + 1];
 
@@ -444,6 +432,114 @@ k_schwarz_lattice2d_sf(int n, int nbc, int q, int ox, int oy, int nbx, int ix0, 
             for (int f = 0; f < SS; ++f) ed[f & 3] = fma(__ldg(&Bi[f]), (double)rs[j][f], ed[f & 3]);
             ev = (T)((ed[0] + ed[1]) + (ed[2] + ed[3]));
         }
+        u[(size_t)y * n + x] += ev;
+    }
+}
+
+// One colour of the LATTICE schedule in FP64 for 7x7 (or 5x5) blocks, the residual
+// sum-factorised with S^2 threads per block in every step (BPC blocks per CTA):
+//   0. the block's (S + 2P)^2 window of u into shared memory;
+//   1. the S x (S + 2P) pairs (sum_b K_y[b] u, sum_b M_y[b] u) of the block's rows at its
+//      window columns, items e, e + S^2, ... of thread e;
+//   2. thread e: the x sums of its DOF, r_e = b - A u;
+//   3. thread e: row e of the block's inverse times r, added to u.
+// Per DOF and colour this is 2W(S + 2P)/S + 2W + S^2 FMAs against W^2 + S^2 for the direct
+// stencil (p = 5: 113 against 146; p = 7: 169 against 274), with every step spread evenly
+// over the block's threads.  Interior rows/columns use the h-scaled interior 1D rows from
+// constant memory, the others their own 1D rows.
+template <int P, int S, int BPC>
+__global__ void __launch_bounds__(256)
+k_schwarz_lattice2d_pd(int n, int nbc, int q, int ox, int oy, int nbx, int nblocks,
+                       const double *__restrict__ kband, const double *__restrict__ mband,
+                       const double *__restrict__ binv, const int *__restrict__ bcls, double *__restrict__ u,
+                       const double *__restrict__ b, BatchRef bt)
+{
+    constexpr int W = 2 * P + 1, SS = S * S, R = (S - 1) / 2, WIN = S + 2 * P, PCI = 2 * P - 1;
+    constexpr int NY = S * WIN;   // y items of a block
+    __shared__ double su[BPC][WIN][WIN];
+    __shared__ double2 yb[BPC][S][WIN];
+    __shared__ double rs[BPC][SS];
+    pdl_wait();
+    if (bt.active && !bt.active[blockIdx.y]) return;
+    u += blockIdx.y * bt.vec;
+    b += blockIdx.y * bt.vec;
+    const int lb = threadIdx.x / SS, e = threadIdx.x % SS;
+    const int blk = blockIdx.x * BPC + lb;
+    const bool active = lb < BPC && blk < nblocks;
+    const int cx = ox + q * (blk % nbx), cy = oy + q * (blk / nbx);
+    const double h = 1.0 / (double)(n - P + 2), hinv = (double)(n - P + 2);
+    // 0. window rows cy - R - P .., columns cx - R - P .. (zero outside the grid)
+    if (active) {
+        constexpr int K = (WIN * WIN + SS - 1) / SS;
+        double v[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int i = e + k * SS, wr = i / WIN, wc = i - wr * WIN;
+            const int gx = cx - R - P + wc, gy = cy - R - P + wr;
+            v[k] = (i < WIN * WIN && gx >= 0 && gx < n && gy >= 0 && gy < n) ? u[(size_t)gy * n + gx] : 0.0;
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int i = e + k * SS;
+            if (i < WIN * WIN) su[lb][i / WIN][i % WIN] = v[k];
+        }
+    }
+    __syncthreads();
+    // 1. y pass
+    if (active) {
+        const bool yint = cy - R >= PCI && cy + R <= n - 2 * P;
+        for (int i = e; i < NY; i += SS) {
+            const int r = i / WIN, c = i - r * WIN;
+            double2 acc = make_double2(0.0, 0.0);
+            if (yint) {
+#pragma unroll
+                for (int bb = 0; bb < W; ++bb) acc = fma2(ckm1<double>(P, bb), splat2<double2>(su[lb][r + bb][c]), acc);
+            } else {
+                const int gy = cy - R + r;
+                if (gy >= 0 && gy < n) {
+#pragma unroll
+                    for (int bb = 0; bb < W; ++bb) {
+                        const double2 km =
+                            make_double2(kband[(size_t)gy * W + bb] * h, mband[(size_t)gy * W + bb] * hinv);
+                        acc = fma2(km, splat2<double2>(su[lb][r + bb][c]), acc);
+                    }
+                }
+            }
+            yb[lb][r][c] = acc;
+        }
+    }
+    __syncthreads();
+    // 2. x pass and the block residual
+    const int ey = e / S, ex = e - ey * S;
+    const int x = cx - R + ex, y = cy - R + ey;
+    const bool inside = active && x >= 0 && x < n && y >= 0 && y < n;
+    if (active) {
+        double rv = 0.0;
+        if (inside) {
+            const bool xint = cx - R >= PCI && cx + R <= n - 2 * P;
+            double2 acc = make_double2(0.0, 0.0);
+            if (xint) {
+#pragma unroll
+                for (int a = 0; a < W; ++a) acc = fma2(cmk1<double>(P, a), yb[lb][ey][ex + a], acc);
+            } else {
+#pragma unroll
+                for (int a = 0; a < W; ++a) {
+                    const double2 mk = make_double2(mband[(size_t)x * W + a] * hinv, kband[(size_t)x * W + a] * h);
+                    acc = fma2(mk, yb[lb][ey][ex + a], acc);
+                }
+            }
+            rv = b[(size_t)y * n + x] - (acc.x + acc.y);
+        }
+        rs[lb][e] = rv;
+    }
+    __syncthreads();
+    // 3. block solve
+    if (inside) {
+        const int cls = bcls[cy] * nbc + bcls[cx];
+        const double *Bi = binv + ((size_t)cls * SS + e) * SS;
+        double ev = 0.0;
+#pragma unroll
+        for (int f = 0; f < SS; ++f) ev = fma(__ldg(&Bi[f]), rs[lb][f], ev);
         u[(size_t)y * n + x] += ev;
     }
 }
@@ -903,14 +999,31 @@ cudaError_t launch_lattice_direct(const Solver &S, int q, int ox, int oy, int nb
                       BatchRef{S.active, S.N, 0, 0});
 }
 
+// the FP64 sum-factorised colour kernel (5x5 and 7x7 blocks) with bpc blocks per CTA
+template <int P, int SB, int BPC>
+cudaError_t launch_lattice_pd(const Solver &S, int q, int ox, int oy, int nbx, int nblocks, const double *kband,
+                              const double *mband, const double *binv, double *u, const double *b, cudaStream_t st,
+                              int bpc)
+{
+    if constexpr (BPC % 2 == 0) {
+        if (bpc < BPC)
+            return launch_lattice_pd<P, SB, BPC / 2>(S, q, ox, oy, nbx, nblocks, kband, mband, binv, u, b, st, bpc);
+    }
+    return launch_pdl(k_schwarz_lattice2d_pd<P, SB, BPC>, dim3((nblocks + BPC - 1) / BPC, S.nbatch),
+                      dim3((BPC * SB * SB + 31) / 32 * 32), st, S.n, S.ht.nbc, q, ox, oy, nbx, nblocks, kband, mband,
+                      binv, (const int *)S.bcls, u, b, BatchRef{S.active, S.N, 0, 0});
+}
+
 template <int P, int SB, typename T>
 cudaError_t schwarz_lattice_p(const Solver &S, const T *stencil, const T *kband, const T *mband, const T *binv, T *u,
                               const T *b, bool reverse, cudaStream_t st)
 {
     // FP32: the packed sum-factorised kernel (the direct form is bound by its L1 loads);
-    // FP64: the direct form.  At p = 5 the factorised form needs 18% fewer FP64 FMAs but
-    // measured slower (1024^2: ~86-90 us per colour against ~78 us): its three phases per
-    // CTA, separated by barriers, keep the FP64 pipe only 60-68% busy against 90%+.
+    // FP64: the direct form for 3x3 and 5x5 blocks, the per-DOF factorised kernel for 7x7
+    // blocks.  Measured at 1024^2: p = 7, 8 sweeps 22% faster factorised (38% fewer FMAs);
+    // p = 5, 6 (23% and 20% fewer FMAs) equal or 4% slower, so they keep the direct form,
+    // whose FP64 pipe is 96% busy against 87% for the factorised one; with 3x3 blocks the
+    // factorised residual needs more FMAs than the stencil.
     constexpr bool SF = sizeof(T) == sizeof(float);
     constexpr int BPC = 256 / (SB * SB), NBSF = 256 / (SB + 2 * P);
     const int q = S.q, ncol = q * q;
@@ -945,8 +1058,11 @@ cudaError_t schwarz_lattice_p(const Solver &S, const T *stencil, const T *kband,
                              S.boundary64(), interior, (const int *)S.bcls, u, b, BatchRef{S.active, S.N, 0, 0});
         } else {
             const int bpc = lattice_bpc((long long)nblocks * S.nbatch, SB * SB, S.nsm);
-            err = launch_lattice_direct<P, SB, BPC, T>(S, q, ox, oy, nbx, nblocks, stencil, binv, interior, u, b, st,
-                                                       bpc);
+            if constexpr (SB >= 7)   // sum factorisation pays once the block is as wide as the stencil
+                err = launch_lattice_pd<P, SB, BPC>(S, q, ox, oy, nbx, nblocks, kband, mband, binv, u, b, st, bpc);
+            else
+                err = launch_lattice_direct<P, SB, BPC, T>(S, q, ox, oy, nbx, nblocks, stencil, binv, interior, u, b,
+                                                           st, bpc);
         }
         count_launches(1);
         if (err != cudaSuccess) return err;
@@ -1041,7 +1157,7 @@ cudaError_t prolong_any(const Solver &S, const T *Cb, const T *ec, T *t2, const 
 
 }  // namespace
 
-cudaError_t upload_interior_stencil(int p, const double *st64, int count, const double *k1, const double *m1)
+cudaError_t upload_interior_rows(int p, const double *k1, const double *m1)
 {
     static std::mutex mu;
     static bool done[64][kMaxP + 1] = {};
@@ -1052,10 +1168,8 @@ cudaError_t upload_interior_stencil(int p, const double *st64, int count, const 
     if (dev < 0 || dev >= 64 || p < 0 || p > kMaxP) return cudaErrorInvalidValue;
     if (done[dev][p]) return cudaSuccess;
     constexpr int W1 = 2 * kMaxP + 1;
-    float st32[W1 * W1];
     double2 km64[W1], mk64[W1];
     float2 km32[W1], mk32[W1];
-    for (int i = 0; i < count; ++i) st32[i] = (float)st64[i];
     const int w = 2 * p + 1;
     for (int i = 0; i < w; ++i) {
         km64[i] = make_double2(k1[i], m1[i]);
@@ -1063,10 +1177,7 @@ cudaError_t upload_interior_stencil(int p, const double *st64, int count, const 
         km32[i] = make_float2((float)k1[i], (float)m1[i]);
         mk32[i] = make_float2((float)m1[i], (float)k1[i]);
     }
-    const size_t row = sizeof(double) * W1 * W1;
-    e = cudaMemcpyToSymbol(c_stencil64, st64, sizeof(double) * count, row * p);
-    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_stencil32, st32, sizeof(float) * count, (row / 2) * p);
-    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_km1d, km64, sizeof(double2) * w, sizeof(double2) * W1 * p);
+    e = cudaMemcpyToSymbol(c_km1d, km64, sizeof(double2) * w, sizeof(double2) * W1 * p);
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_mk1d, mk64, sizeof(double2) * w, sizeof(double2) * W1 * p);
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_km1f, km32, sizeof(float2) * w, sizeof(float2) * W1 * p);
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_mk1f, mk32, sizeof(float2) * w, sizeof(float2) * W1 * p);
