@@ -168,7 +168,10 @@ int iga2l_cycle_adjoint(iga2l_handle h, double *u, const double *b, void *stream
  * Writes the cycle count, the final relative residual and, if hist is not
  * NULL, the relative residual after every cycle (host array of max_cycles).
  * Returns IGA2L_OK, IGA2L_NOT_CONVERGED or an error (IGA2L_ERR_NONFINITE if a
- * residual norm is not finite).  Synchronises the stream once per cycle. */
+ * residual norm is not finite).  With CUDA graphs on (the default) and max_cycles
+ * <= 1024 the cycles and their stopping test run on the device (one graph whose
+ * WHILE node repeats cycle + check), and the call synchronises the stream twice
+ * (initial residual, result); otherwise once per cycle.  Same results either way. */
 int iga2l_solve(iga2l_handle h, const double *b, double tol, int max_cycles, double *u,
                 int *cycles, double *relres, double *hist, void *stream);
 

@@ -41,6 +41,19 @@ struct iga2l_solver : public Solver {
     std::vector<CycleGraph> graphs;
     unsigned long long tick = 0;
     cudaStream_t cap_stream = nullptr;
+    // Device-driven solves: per (u, b, kind) one graph whose WHILE node repeats the cycle
+    // and its convergence check until the check stops it; 4 most recently used kept.
+    struct SolveGraph {
+        const double *u, *b;
+        int kind;
+        cudaGraphExec_t exec;
+        long long kernels_per_cycle;
+        unsigned long long last_use;
+    };
+    std::vector<SolveGraph> solve_graphs;
+    bool solve_graph_failed = false;   // the driver refused one: use the host-driven loop
+    SolveCtl *ctl = nullptr, *ctl_host = nullptr;   // device / pinned host copy
+    double *dev_hist = nullptr, *host_hist = nullptr;
 };
 
 namespace {
@@ -88,6 +101,10 @@ void release(iga2l_solver *S)
     if (cur != S->device) cudaSetDevice(S->device);
     for (auto &g : S->graphs) cudaGraphExecDestroy(g.exec);
     S->graphs.clear();
+    for (auto &g : S->solve_graphs) cudaGraphExecDestroy(g.exec);
+    S->solve_graphs.clear();
+    if (S->ctl_host) cudaFreeHost(S->ctl_host);
+    if (S->host_hist) cudaFreeHost(S->host_hist);
     if (S->cap_stream) cudaStreamDestroy(S->cap_stream);
     for (void *p : S->allocs) cudaFree(p);
     S->allocs.clear();
@@ -156,7 +173,8 @@ int coarse_correction(iga2l_handle h, double *u, const double *b, cudaStream_t s
 // Mixed precision (forward cycles only): the FP32 inner cycle on A delta = r from
 // delta = 0, then u += delta in FP64, then the FP64 residual r = b - A u (stored in
 // FP32 for the next inner cycle) -- r must already hold b - A u on entry.
-int enqueue_cycle(iga2l_handle h, double *u, const double *b, cudaStream_t st, bool adjoint, bool norm)
+int enqueue_cycle(iga2l_handle h, double *u, const double *b, cudaStream_t st, bool adjoint, bool norm,
+                  bool host_copy = true)
 {
     int rc;
     if (h->mx.enabled && !adjoint) {
@@ -166,7 +184,7 @@ int enqueue_cycle(iga2l_handle h, double *u, const double *b, cudaStream_t st, b
         if (e == cudaSuccess)
             e = norm ? launch_outer_residual_norm(*h, u, b, h->mx.r, h->dev_norm, st)
                      : launch_outer_residual(*h, u, b, h->mx.r, nullptr, st);
-        if (e == cudaSuccess && norm && !h->active)
+        if (e == cudaSuccess && norm && host_copy && !h->active)
             e = cudaMemcpyAsync(h->host_norm, h->dev_norm, sizeof(double), cudaMemcpyDeviceToHost, st);
         return finish(e, "mixed-precision cycle");
     }
@@ -181,7 +199,7 @@ int enqueue_cycle(iga2l_handle h, double *u, const double *b, cudaStream_t st, b
     }
     if (norm) {
         cudaError_t e = launch_residual_norm(*h, u, b, nullptr, h->dev_norm, st);
-        if (e == cudaSuccess && !h->active)
+        if (e == cudaSuccess && host_copy && !h->active)
             e = cudaMemcpyAsync(h->host_norm, h->dev_norm, sizeof(double), cudaMemcpyDeviceToHost, st);
         if (e != cudaSuccess) return cuda_fail(e, "residual norm");
     }
@@ -249,6 +267,73 @@ int run_cycle(iga2l_handle h, double *u, const double *b, cudaStream_t st, bool 
     return run_cycle_graph(h, u, b, st, adjoint, false);
 }
 
+// The graph of a device-driven solve for (u, b, kind): a WHILE node whose body is one
+// cycle, its residual norm and k_solve_check.  Returns null (and remembers it) when the
+// driver refuses to build it; the caller then drives the cycles from the host.
+iga2l_solver::SolveGraph *solve_graph(iga2l_handle h, double *u, const double *b, bool adjoint)
+{
+    const int kind = (adjoint ? 1 : 0) | (h->mx.enabled ? 4 : 0);
+    for (auto &c : h->solve_graphs)
+        if (c.u == u && c.b == b && c.kind == kind) return &c;
+    cudaError_t e = cudaSuccess;
+    if (!h->cap_stream && (e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return nullptr;
+    cudaGraph_t graph = nullptr, body = nullptr;
+    cudaGraphConditionalHandle cond;
+    cudaGraphNode_t node;
+    cudaGraphNodeParams np = {};
+    bool ok = cudaGraphCreate(&graph, 0) == cudaSuccess &&
+              cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+    if (ok) {
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = cond;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        ok = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np) == cudaSuccess;
+    }
+    if (ok) {
+        body = np.conditional.phGraph_out[0];
+        ok = cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+            g_capturing = true;
+            int rc = enqueue_cycle(h, u, b, h->cap_stream, adjoint, true, false);
+            if (rc == IGA2L_OK && launch_solve_check(h->dev_norm, h->ctl, h->dev_hist, cond, h->cap_stream) != cudaSuccess)
+                rc = IGA2L_ERR_CUDA;
+            g_capturing = false;
+            cudaGraph_t captured = nullptr;
+            ok = cudaStreamEndCapture(h->cap_stream, &captured) == cudaSuccess && rc == IGA2L_OK;
+        }
+    }
+    long long kernels = 0;
+    if (ok) {
+        size_t nn = 0;
+        cudaGraphGetNodes(body, nullptr, &nn);
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if (nn && cudaGraphGetNodes(body, nodes.data(), &nn) == cudaSuccess)
+            for (auto nd : nodes) {
+                cudaGraphNodeType t;
+                if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kernels;
+            }
+    }
+    cudaGraphExec_t exec = nullptr;
+    if (ok) ok = cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();   // a refused build leaves no sticky error
+    if (!ok) {
+        h->solve_graph_failed = true;
+        return nullptr;
+    }
+    if (h->solve_graphs.size() >= 4) {
+        auto lru = std::min_element(h->solve_graphs.begin(), h->solve_graphs.end(),
+                                    [](const auto &x, const auto &y) { return x.last_use < y.last_use; });
+        cudaGraphExecDestroy(lru->exec);
+        h->solve_graphs.erase(lru);
+    }
+    h->solve_graphs.push_back({u, b, kind, exec, kernels, 0});
+    return &h->solve_graphs.back();
+}
+
 int solve_impl(iga2l_handle h, const double *b, double tol, int max_cycles, double *u, int *cycles,
                double *relres, double *hist, void *stream, bool adjoint)
 {
@@ -273,7 +358,37 @@ int solve_impl(iga2l_handle h, const double *b, double tol, int max_cycles, doub
     int k = 0;
     double rel = 0.0;
     int status = r0 == 0.0 ? IGA2L_OK : IGA2L_NOT_CONVERGED;
-    while (status != IGA2L_OK && k < max_cycles) {
+    // Device-driven: one graph launch runs every cycle and its check on the GPU (no host
+    // round trip between cycles); one read-back at the end.
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    iga2l_solver::SolveGraph *sg = nullptr;
+    if (status != IGA2L_OK && h->opt.graphs && !h->solve_graph_failed && max_cycles <= kSolveHistCap &&
+        cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone)
+        sg = solve_graph(h, u, b, adjoint);
+    if (sg) {
+        *h->ctl_host = SolveCtl{r0, tol, 0.0, max_cycles, 0, -1};
+        cudaError_t e = cudaMemcpyAsync(h->ctl, h->ctl_host, sizeof(SolveCtl), cudaMemcpyHostToDevice, st);
+        sg->last_use = ++h->tick;
+        if (e == cudaSuccess) e = cudaGraphLaunch(sg->exec, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && hist)
+            e = cudaMemcpyAsync(h->host_hist, h->dev_hist, sizeof(double) * max_cycles, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "solve");
+        const SolveCtl c = *h->ctl_host;
+        k = c.k;
+        count_launches(sg->kernels_per_cycle * k);
+        if (hist)
+            for (int i = 0; i < k; ++i) hist[i] = h->host_hist[i];
+        if (c.status == 2) {
+            if (cycles) *cycles = k;
+            return fail(IGA2L_ERR_NONFINITE, "residual norm is not finite");
+        }
+        rel = c.rel;
+        status = c.status == 1 ? IGA2L_OK : IGA2L_NOT_CONVERGED;
+    }
+    while (!sg && status != IGA2L_OK && k < max_cycles) {
         // one cycle and its residual norm, read back once per cycle
         rc = run_cycle_graph(h, u, b, st, adjoint, true);
         if (rc != IGA2L_OK) return rc;
@@ -563,9 +678,20 @@ static int assemble_impl(int p, int m, int dim, int nbatch, bool batch, const ig
             release(S);
             return cuda_fail(ce, "level allocation");
         }
-    if ((ce = cudaMallocHost(&S->host_norm, sizeof(double))) != cudaSuccess) {
+    if ((ce = cudaMallocHost(&S->host_norm, sizeof(double))) != cudaSuccess ||
+        (ce = cudaMallocHost(&S->ctl_host, sizeof(SolveCtl))) != cudaSuccess ||
+        (ce = cudaMallocHost(&S->host_hist, sizeof(double) * kSolveHistCap)) != cudaSuccess) {
         release(S);
-        return cuda_fail(ce, "pinned host scalar");
+        return cuda_fail(ce, "pinned host buffers");
+    }
+    {
+        void *pc = nullptr;
+        if ((ce = cudaMalloc(&pc, sizeof(SolveCtl))) != cudaSuccess ||
+            (S->allocs.push_back(pc), (ce = alloc(S, &S->dev_hist, kSolveHistCap))) != cudaSuccess) {
+            release(S);
+            return cuda_fail(ce, "solve control block");
+        }
+        S->ctl = static_cast<SolveCtl *>(pc);
     }
     if (opt.precision == IGA2L_MIXED_FP32 || opt.precision == IGA2L_MIXED_FP32_ALL ||
         opt.precision == IGA2L_MIXED_TF32) {

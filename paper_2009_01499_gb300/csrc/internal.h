@@ -130,6 +130,18 @@ struct Solver {
     }
 };
 
+// Control block of a device-driven solve (one WHILE graph node runs the cycles): written
+// by the host before the launch, updated by the convergence check after every cycle.
+struct SolveCtl {
+    double r0;     // ||b - A u_0||
+    double tol;    // relative residual to reach
+    double rel;    // out: last relative residual
+    int maxc;      // cycle cap
+    int k;         // out: cycles done (0 on entry)
+    int status;    // out: 1 converged, 2 non-finite norm, 0 cycle cap reached
+};
+constexpr int kSolveHistCap = 1024;   // device-driven solves: at most this many cycles
+
 // Number of kernels this library has launched (process-wide), for benchmarks
 // that report how many of the timed region's kernels are this library's.
 void count_launches(long long k);
@@ -172,6 +184,12 @@ cudaError_t launch_pdl(Kernel kernel, dim3 grid, dim3 block, cudaStream_t st, Ar
 
 // Sets the text returned by iga2l_last_error on the calling thread (api.cu).
 void set_last_error(const std::string &msg);
+
+// After a cycle of a device-driven solve: count it, record rel = sqrt(norm2) / r0 in
+// hist, and set the WHILE node's condition to 0 once rel <= tol, the norm is not
+// finite or maxc cycles are done (kernels_fine.cu).
+cudaError_t launch_solve_check(const double *norm2, SolveCtl *ctl, double *hist, cudaGraphConditionalHandle cond,
+                               cudaStream_t st);
 
 // setup.cpp
 int build_host_tables(int p, int m, int s, HostTables &ht, std::string &err);

@@ -1290,6 +1290,38 @@ cudaError_t launch_batch_check(const Solver &S, double tol, const double *norm2,
     return cudaGetLastError();
 }
 
+// ---- device-driven solve ----------------------------------------------------------
+
+// One thread: the host loop's test after a cycle, on the device (same arithmetic:
+// rel = sqrt(norm2) / r0, IEEE square root and quotient), then the WHILE condition.
+__global__ void k_solve_check(const double *__restrict__ norm2, SolveCtl *__restrict__ c, double *__restrict__ hist,
+                              cudaGraphConditionalHandle cond)
+{
+    const double rsq = norm2[0];
+    const int k = c->k + 1;
+    c->k = k;
+    unsigned int more = 0;
+    if (!isfinite(rsq)) {
+        c->status = 2;
+    } else {
+        const double rel = sqrt(rsq) / c->r0;
+        c->rel = rel;
+        if (k <= kSolveHistCap) hist[k - 1] = rel;
+        if (rel <= c->tol) c->status = 1;
+        else if (k >= c->maxc) c->status = 0;
+        else more = 1;
+    }
+    cudaGraphSetConditional(cond, more);
+}
+
+cudaError_t launch_solve_check(const double *norm2, SolveCtl *ctl, double *hist, cudaGraphConditionalHandle cond,
+                               cudaStream_t st)
+{
+    k_solve_check<<<1, 1, 0, st>>>(norm2, ctl, hist, cond);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 // ---- mixed precision -------------------------------------------------------------
 
 cudaError_t launch_outer_residual(const Solver &S, const double *u, const double *b, float *r32,
