@@ -272,7 +272,8 @@ int run_cycle(iga2l_handle h, double *u, const double *b, cudaStream_t st, bool 
 // driver refuses to build it; the caller then drives the cycles from the host.
 iga2l_solver::SolveGraph *solve_graph(iga2l_handle h, double *u, const double *b, bool adjoint)
 {
-    const int kind = (adjoint ? 1 : 0) | (h->mx.enabled ? 4 : 0);
+    const bool batch = h->active != nullptr;   // batch handles: k_batch_check stops the loop
+    const int kind = (adjoint ? 1 : 0) | (h->mx.enabled ? 4 : 0) | (batch ? 8 : 0);
     for (auto &c : h->solve_graphs)
         if (c.u == u && c.b == b && c.kind == kind) return &c;
     cudaError_t e = cudaSuccess;
@@ -298,7 +299,10 @@ iga2l_solver::SolveGraph *solve_graph(iga2l_handle h, double *u, const double *b
         if (ok) {
             g_capturing = true;
             int rc = enqueue_cycle(h, u, b, h->cap_stream, adjoint, true, false);
-            if (rc == IGA2L_OK && launch_solve_check(h->dev_norm, h->ctl, h->dev_hist, cond, h->cap_stream) != cudaSuccess)
+            if (rc == IGA2L_OK &&
+                (batch ? launch_batch_check_loop(*h, h->dev_norm, h->bnorm0, h->bcycles, h->brel, h->bcount, h->ctl,
+                                                 cond, h->cap_stream)
+                       : launch_solve_check(h->dev_norm, h->ctl, h->dev_hist, cond, h->cap_stream)) != cudaSuccess)
                 rc = IGA2L_ERR_CUDA;
             g_capturing = false;
             cudaGraph_t captured = nullptr;
@@ -810,9 +814,27 @@ int iga2l_solve_batch(iga2l_handle h, const double *b, double tol, int max_cycle
     }
     if (e == cudaSuccess) e = launch_batch_init(*h, h->dev_norm, h->bnorm0, h->bcycles, h->brel, st);
     if (e != cudaSuccess) return cuda_fail(e, "batch start");
-    // cycles; converged problems are masked on the device, the host polls every 4 cycles
     int left = nb;
-    for (int k = 0; k < max_cycles && left > 0; ++k) {
+    // device-driven: one graph launch runs the cycles until no problem is active or
+    // max_cycles ran (k_batch_check sets the WHILE condition)
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    iga2l_solver::SolveGraph *sg = nullptr;
+    if (h->opt.graphs && !h->solve_graph_failed && cudaStreamIsCapturing(st, &cs) == cudaSuccess &&
+        cs == cudaStreamCaptureStatusNone)
+        sg = solve_graph(h, u, b, false);
+    if (sg) {
+        *h->ctl_host = SolveCtl{0.0, tol, 0.0, max_cycles, 0, -1};
+        e = cudaMemcpyAsync(h->ctl, h->ctl_host, sizeof(SolveCtl), cudaMemcpyHostToDevice, st);
+        sg->last_use = ++h->tick;
+        if (e == cudaSuccess) e = cudaGraphLaunch(sg->exec, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "batched solve");
+        count_launches(sg->kernels_per_cycle * h->ctl_host->k);
+    }
+    // host-driven: converged problems are masked on the device, the host polls every 4 cycles
+    for (int k = 0; !sg && k < max_cycles && left > 0; ++k) {
         if ((rc = run_cycle_graph(h, u, b, st, false, true)) != IGA2L_OK) return rc;
         e = launch_batch_check(*h, tol, h->dev_norm, h->bnorm0, h->bcycles, h->brel, h->bcount, st);
         if (e != cudaSuccess) return cuda_fail(e, "batch check");

@@ -228,6 +228,11 @@ cudaError_t launch_batch_init(const Solver &S, const double *norm2, double *norm
                               cudaStream_t st);
 cudaError_t launch_batch_check(const Solver &S, double tol, const double *norm2, const double *norm0, int *cycles,
                                double *relres, int *count, cudaStream_t st);
+// the same inside a device-driven batched solve: tol from ctl, ctl->k counted, and the
+// WHILE condition set to continue while a problem is active and fewer than maxc cycles ran
+cudaError_t launch_batch_check_loop(const Solver &S, const double *norm2, const double *norm0, int *cycles,
+                                    double *relres, int *count, SolveCtl *ctl, cudaGraphConditionalHandle cond,
+                                    cudaStream_t st);
 // differentiable source (kernels_grad.cu)
 constexpr int kMaxBumps = 64;
 cudaError_t launch_bump_load(const Solver &S, int nb, const double *theta, double w, double *b, cudaStream_t st);

@@ -1254,13 +1254,16 @@ __global__ void k_batch_init(int nb, const double *__restrict__ norm2, double *_
 }
 
 // after a cycle: count it for every active problem and retire those at the tolerance;
-// count[0] = number of problems still active (nonfinite norms retire with relres = nan)
+// count[0] = number of problems still active (nonfinite norms retire with relres = nan).
+// With ctl (a device-driven batched solve): tol comes from ctl, ctl->k counts the cycles
+// and the WHILE condition is set to continue while a problem is active and k < maxc.
 __global__ void k_batch_check(int nb, double tol, const double *__restrict__ norm2, const double *__restrict__ norm0,
                               int *__restrict__ active, int *__restrict__ cycles, double *__restrict__ relres,
-                              int *__restrict__ count)
+                              int *__restrict__ count, SolveCtl *ctl, cudaGraphConditionalHandle cond)
 {
     __shared__ int act;
     if (threadIdx.x == 0) act = 0;
+    if (ctl) tol = ctl->tol;
     __syncthreads();
     for (int k = threadIdx.x; k < nb; k += blockDim.x) {
         if (!active[k]) continue;
@@ -1271,7 +1274,14 @@ __global__ void k_batch_check(int nb, double tol, const double *__restrict__ nor
         else atomicAdd(&act, 1);
     }
     __syncthreads();
-    if (threadIdx.x == 0) count[0] = act;
+    if (threadIdx.x == 0) {
+        count[0] = act;
+        if (ctl) {
+            const int k = ctl->k + 1;
+            ctl->k = k;
+            cudaGraphSetConditional(cond, act > 0 && k < ctl->maxc ? 1u : 0u);
+        }
+    }
 }
 
 cudaError_t launch_batch_init(const Solver &S, const double *norm2, double *norm0, int *cycles, double *relres,
@@ -1285,7 +1295,17 @@ cudaError_t launch_batch_init(const Solver &S, const double *norm2, double *norm
 cudaError_t launch_batch_check(const Solver &S, double tol, const double *norm2, const double *norm0, int *cycles,
                                double *relres, int *count, cudaStream_t st)
 {
-    k_batch_check<<<1, 256, 0, st>>>(S.nbatch, tol, norm2, norm0, S.active, cycles, relres, count);
+    k_batch_check<<<1, 256, 0, st>>>(S.nbatch, tol, norm2, norm0, S.active, cycles, relres, count, nullptr,
+                                     cudaGraphConditionalHandle{});
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_check_loop(const Solver &S, const double *norm2, const double *norm0, int *cycles,
+                                    double *relres, int *count, SolveCtl *ctl, cudaGraphConditionalHandle cond,
+                                    cudaStream_t st)
+{
+    k_batch_check<<<1, 256, 0, st>>>(S.nbatch, 0.0, norm2, norm0, S.active, cycles, relres, count, ctl, cond);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -82,3 +82,26 @@ def test_device_loop_counts_its_kernels():
     cyc, _, _, ok = A.solve(b, u, tol=1e-8)
     per_cycle = (iga2l.kernel_launches() - n0 - 1) / cyc   # minus the initial residual
     assert ok and per_cycle == int(per_cycle) and per_cycle > 25
+
+
+@pytest.mark.parametrize("precision,sched", [(iga2l.FP64, iga2l.SCHED_LATTICE), (iga2l.MIXED_FP32, iga2l.SCHED_TILE)])
+def test_batched_device_loop_equals_host_loop(precision, sched):
+    """Batch handles: the WHILE loop stops once no problem is active (k_batch_check)."""
+    p, m, nb = 2, 48, 5
+    q, g = COLOURING[p]
+    A = iga2l.Solver(p, m, nbatch=nb, period=q, stride=g, precision=precision, schedule=sched, graphs=1)
+    B = iga2l.Solver(p, m, nbatch=nb, period=q, stride=g, precision=precision, schedule=sched, graphs=0)
+    N = (m + p - 2) ** 2
+    f = torch.tensor(np.concatenate([synth.coefficients(N, 400 + k) for k in range(nb)]), device="cuda")
+    b = torch.empty_like(f)
+    A.rhs_from_coeffs(f, b)
+    u0 = torch.tensor(np.concatenate([synth.initial_guess(N, 500 + k) for k in range(nb)]), device="cuda")
+    ua, ub = u0.clone(), u0.clone()
+    ca, ra, oka = A.solve_batch(b, ua, tol=1e-9)
+    cb, rb, okb = B.solve_batch(b, ub, tol=1e-9)
+    assert oka and okb and list(ca) == list(cb) and np.array_equal(ra, rb) and torch.equal(ua, ub)
+    # at a cycle cap every problem stops after exactly that many cycles
+    ua, ub = u0.clone(), u0.clone()
+    ca, ra, oka = A.solve_batch(b, ua, tol=1e-30, max_cycles=2)
+    cb, rb, okb = B.solve_batch(b, ub, tol=1e-30, max_cycles=2)
+    assert not oka and not okb and list(ca) == list(cb) == [2] * nb and torch.equal(ua, ub)
