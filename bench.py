@@ -631,7 +631,10 @@ def run_gpu(args):
 
 
 def run_profile_step(args):
-    """For ncu: --warmup solves per degree, then one solve per degree, nothing else."""
+    """For ncu: --warmup solves per degree, then one solve per degree, nothing else.  The
+    solvers use plain launches (graphs off): ncu does not list the kernels that run inside
+    a graph's conditional WHILE node (the device-driven solve), and per-kernel durations
+    and counters do not depend on how the kernels were launched."""
     import torch
     from paper_2009_01499_gb300 import iga2l, synth
     dev = torch.device("cuda", 0)
@@ -643,7 +646,7 @@ def run_profile_step(args):
     sched = iga2l.SCHED_LATTICE if (prec in (iga2l.FP64, iga2l.MIXED_TF32) or dim == 3) else iga2l.SCHED_TILE
     for p in degrees:
         q, g = COLOURING[p]
-        S = iga2l.Solver(p, m, dim=dim, period=q, stride=g, precision=prec, schedule=sched)
+        S = iga2l.Solver(p, m, dim=dim, period=q, stride=g, precision=prec, schedule=sched, graphs=0)
         sf, su = seeds(p)
         f = torch.tensor(synth.coefficients(S.N, sf), device=dev)
         b = torch.empty_like(f)
