@@ -645,8 +645,8 @@ def run_profile_step(args):
             "mixed_tf32": iga2l.MIXED_TF32}[args.profile_precision]
     sched = iga2l.SCHED_LATTICE if (prec in (iga2l.FP64, iga2l.MIXED_TF32) or dim == 3) else iga2l.SCHED_TILE
     for p in degrees:
-        q, g = COLOURING[p]
-        S = iga2l.Solver(p, m, dim=dim, period=q, stride=g, precision=prec, schedule=sched, graphs=0)
+        col = {"period": COLOURING[p][0], "stride": COLOURING[p][1]} if p in COLOURING else {}   # else the default
+        S = iga2l.Solver(p, m, dim=dim, precision=prec, schedule=sched, graphs=0, **col)
         sf, su = seeds(p)
         f = torch.tensor(synth.coefficients(S.N, sf), device=dev)
         b = torch.empty_like(f)

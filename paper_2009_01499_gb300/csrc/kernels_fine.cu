@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include <mutex>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -754,69 +755,78 @@ k_schwarz_tile2d(int n, int nbc, int q, int g, int rev, int px, int py, int ntpx
     T *rsb = rs + slot * G::RSS;
     const int ncol = q * q;
     // colour c visits offsets ((c mod q) g mod q, (c div q) g mod q), advanced incrementally
-    int cxr = rev ? q - 1 : 0;
-    int ox = rev ? q - g : 0, oy = ox;
-    for (int t = 0; t < ncol; ++t) {
-        const int cxl = ox + q * bi, cyl = oy + q * bj;   // tile-local centre
-        const bool act = role && cxl < tw && cyl < th;
-        const int lx = cxl - R + ex, ly = cyl - R + ey;   // tile-local DOF of this lane
-        // are the block's rows / columns all of the interior class?
-        const bool yint = fast || (y0 + cyl - R >= PCI && y0 + cyl + R <= n - 2 * P);
-        const bool xint = fast || (x0 + cxl - R >= PCI && x0 + cxl + R <= n - 2 * P);
-        if (act) {
-            if (yint) tile_ypass<P, S, TT, true>(su, cxl, cyl, e, ybs, km1y);
-            else tile_ypass<P, S, TT, false>(su, cxl, cyl, e, ybs, km1y);
-        }
-        __syncwarp();
-        const int gx = x0 + lx, gy = y0 + ly;
-        const bool in = fast || (gx >= 0 && gx < n && gy >= 0 && gy < n);
-        if (act) {
-            const T acc = xint ? tile_xpass<P, S, TT, true, T>(ybs, ey, ex, lx + R, mk1x)
-                               : tile_xpass<P, S, TT, false, T>(ybs, ey, ex, lx + R, mk1x);
-            rsb[e] = in ? sb[(ly + R) * BW + (lx + R)] - acc : T(0);
-        }
-        __syncwarp();
-        if (act) {
-            int cls = interior;
-            if (!fast) {
-                const int ccx = x0 + cxl, ccy = y0 + cyl;
-                const int bx = ccx < L ? ccx : (ccx > n - 1 - L ? 2 * L - (n - 1 - ccx) : L);
-                const int by = ccy < L ? ccy : (ccy > n - 1 - L ? 2 * L - (n - 1 - ccy) : L);
-                cls = by * nbc + bx;
+    // the colour loop, compiled twice: FAST (interior tiles: every block of the interior
+    // class and inside the grid) and the general form
+    auto colours = [&](auto fast_tag) {
+        constexpr bool FAST = decltype(fast_tag)::value;
+        int cxr = rev ? q - 1 : 0;
+        int ox = rev ? q - g : 0, oy = ox;
+        for (int t = 0; t < ncol; ++t) {
+            const int cxl = ox + q * bi, cyl = oy + q * bj;   // tile-local centre
+            // (q may exceed the minimum period the slots are laid out for, so some slots
+            // fall outside the tile in every colour, interior tiles included)
+            const bool act = role && cxl < tw && cyl < th;
+            const int lx = cxl - R + ex, ly = cyl - R + ey;   // tile-local DOF of this lane
+            // are the block's rows / columns all of the interior class?
+            const bool yint = FAST || (y0 + cyl - R >= PCI && y0 + cyl + R <= n - 2 * P);
+            const bool xint = FAST || (x0 + cxl - R >= PCI && x0 + cxl + R <= n - 2 * P);
+            if (act) {
+                if (yint) tile_ypass<P, S, TT, true>(su, cxl, cyl, e, ybs, km1y);
+                else tile_ypass<P, S, TT, false>(su, cxl, cyl, e, ybs, km1y);
             }
-            T ev = T(0);
-            if (cls == interior) {
-                T2 acc2 = splat2<T2>(T(0));
-                const T2 *r2 = reinterpret_cast<const T2 *>(rsb);   // 16-byte aligned, zero padded
-#pragma unroll
-                for (int k = 0; k < G::NB2; ++k) acc2 = fma2(brow[k], r2[k], acc2);
-                ev = acc2.x + acc2.y;
-            } else if (sizeof(T) == sizeof(double) || !binv_lo) {
-                const T *Bi = binv + ((size_t)cls * SS + e) * SS;
-#pragma unroll
-                for (int f = 0; f < SS; ++f) ev = fma(__ldg(&Bi[f]), rsb[f], ev);
-            } else if constexpr (sizeof(T) == sizeof(float)) {
-                // FP64 row of a boundary-class inverse (as the pair binv + binv_lo), applied
-                // in compensated FP32 arithmetic: GB300's FP64 pipe is 1/58 of its FP32
-                // rate, and these rows set the boundary tiles' critical path
-                const size_t row = ((size_t)cls * SS + e) * SS;
-                T rv[2 * G::NB2];
-                const T2 *r2 = reinterpret_cast<const T2 *>(rsb);
-#pragma unroll
-                for (int k = 0; k < G::NB2; ++k) { const T2 v = r2[k]; rv[2 * k] = v.x; rv[2 * k + 1] = v.y; }
-                ev = dot2_row<SS>(binv + row, binv_lo + row, rv);
+            __syncwarp();
+            const int gx = x0 + lx, gy = y0 + ly;
+            const bool in = FAST || (gx >= 0 && gx < n && gy >= 0 && gy < n);
+            if (act) {
+                const T acc = xint ? tile_xpass<P, S, TT, true, T>(ybs, ey, ex, lx + R, mk1x)
+                                   : tile_xpass<P, S, TT, false, T>(ybs, ey, ex, lx + R, mk1x);
+                rsb[e] = in ? sb[(ly + R) * BW + (lx + R)] - acc : T(0);
             }
-            if (in) su[(ly + H) * SW + (lx + H)] += ev;
+            __syncwarp();
+            if (act) {
+                int cls = interior;
+                if (!FAST) {
+                    const int ccx = x0 + cxl, ccy = y0 + cyl;
+                    const int bx = ccx < L ? ccx : (ccx > n - 1 - L ? 2 * L - (n - 1 - ccx) : L);
+                    const int by = ccy < L ? ccy : (ccy > n - 1 - L ? 2 * L - (n - 1 - ccy) : L);
+                    cls = by * nbc + bx;
+                }
+                T ev = T(0);
+                if (cls == interior) {
+                    T2 acc2 = splat2<T2>(T(0));
+                    const T2 *r2 = reinterpret_cast<const T2 *>(rsb);   // 16-byte aligned, zero padded
+    #pragma unroll
+                    for (int k = 0; k < G::NB2; ++k) acc2 = fma2(brow[k], r2[k], acc2);
+                    ev = acc2.x + acc2.y;
+                } else if (sizeof(T) == sizeof(double) || !binv_lo) {
+                    const T *Bi = binv + ((size_t)cls * SS + e) * SS;
+    #pragma unroll
+                    for (int f = 0; f < SS; ++f) ev = fma(__ldg(&Bi[f]), rsb[f], ev);
+                } else if constexpr (sizeof(T) == sizeof(float)) {
+                    // FP64 row of a boundary-class inverse (as the pair binv + binv_lo), applied
+                    // in compensated FP32 arithmetic: GB300's FP64 pipe is 1/58 of its FP32
+                    // rate, and these rows set the boundary tiles' critical path
+                    const size_t row = ((size_t)cls * SS + e) * SS;
+                    T rv[2 * G::NB2];
+                    const T2 *r2 = reinterpret_cast<const T2 *>(rsb);
+    #pragma unroll
+                    for (int k = 0; k < G::NB2; ++k) { const T2 v = r2[k]; rv[2 * k] = v.x; rv[2 * k + 1] = v.y; }
+                    ev = dot2_row<SS>(binv + row, binv_lo + row, rv);
+                }
+                if (in) su[(ly + H) * SW + (lx + H)] += ev;
+            }
+            __syncthreads();
+            if (!rev) {
+                if (++cxr == q) { cxr = 0; ox = 0; oy += g; if (oy >= q) oy -= q; }
+                else { ox += g; if (ox >= q) ox -= q; }
+            } else {
+                if (--cxr < 0) { cxr = q - 1; ox = q - g; oy -= g; if (oy < 0) oy += q; }
+                else { ox -= g; if (ox < 0) ox += q; }
+            }
         }
-        __syncthreads();
-        if (!rev) {
-            if (++cxr == q) { cxr = 0; ox = 0; oy += g; if (oy >= q) oy -= q; }
-            else { ox += g; if (ox >= q) ox -= q; }
-        } else {
-            if (--cxr < 0) { cxr = q - 1; ox = q - g; oy -= g; if (oy < 0) oy += q; }
-            else { ox -= g; if (ox < 0) ox += q; }
-        }
-    }
+    };
+    if (fast) colours(std::true_type{});
+    else colours(std::false_type{});
     for (int i = tid; i < BW * BW; i += NT) {
         const int gx = x0 - R + i % BW, gy = y0 - R + i / BW;
         if (gx >= 0 && gx < n && gy >= 0 && gy < n) u[(size_t)gy * n + gx] = su[(i / BW + P) * SW + (i % BW + P)];
