@@ -1,7 +1,7 @@
 """GPU tests of the mixed-precision form (FP64 outer residual and update around an
 FP32 inner cycle) against the FP64 oracle.
 
-Bar (the benchmark spec): after refinement to a 1e-8 relative residual, the solution is
+Bar: after refinement to a 1e-8 relative residual, the solution is
 within 1e-8 (relative, 2-norm) of the FP64 oracle's solution, with the same
 cycle count.  Single inner cycles agree with the FP64 cycle to FP32 accuracy.
 """

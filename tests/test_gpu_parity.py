@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path through the C ABI against the FP64 oracle.
 
-Bar (the benchmark spec): FP64 per-iterate agreement to 1e-12 relative (2-norm), and
+Bar: FP64 per-iterate agreement to 1e-12 relative (2-norm), and
 element-wise agreement to 1e-12 of the vector's max for single steps.  Sizes
 span several tiles with ragged tails; the full 1024^2 workload is checked on
 properties the oracle can evaluate at that size.
