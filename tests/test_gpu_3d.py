@@ -167,3 +167,29 @@ def test_mixed_tile_3d_matches_oracle(oracle_mod, precision):
     uo, _, _, _, oko = O.solve(b, u0, tol=1e-12, maxc=60)
     err = np.linalg.norm(_host(ud) - uo) / np.linalg.norm(uo)
     assert err <= 1e-8, err
+
+
+def test_full_size_3d_solves(oracle_mod):
+    """128^3 elements, p = 3 (the 3D workload at the size the benchmark times): FP64 and
+    mixed solves to 1e-8, each converged solution's residual re-evaluated by the oracle."""
+    p, m = 3, 128
+    q, g = COLOURING[p]
+    O = oracle_mod.Problem(3, p, m, sched=oracle_mod.LATTICE, period=q, stride=g, coarse=oracle_mod.VCYCLE)
+    cycles = {}
+    for prec in (iga2l.FP64, iga2l.MIXED_FP32):
+        S = iga2l.Solver(p, m, dim=3, period=q, stride=g, precision=prec)
+        assert S.N == O.N
+        f = _dev(synth.coefficients(S.N, 51))
+        b = torch.empty_like(f)
+        S.rhs_from_coeffs(f, b)
+        u0 = synth.initial_guess(S.N, 52)
+        ud = _dev(u0)
+        cyc, rel, _, ok = S.solve(b, ud, tol=1e-8, max_cycles=40)
+        assert ok and rel <= 1e-8 and 3 <= cyc <= 20
+        bh = _host(b)
+        r_end = np.linalg.norm(O.residual(_host(ud), bh))
+        r_0 = np.linalg.norm(O.residual(u0, bh))
+        assert r_end <= 1.0001e-8 * r_0, (prec, r_end / r_0)
+        cycles[prec] = cyc
+        S.close()
+    assert abs(cycles[iga2l.FP64] - cycles[iga2l.MIXED_FP32]) <= 1
