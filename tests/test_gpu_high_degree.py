@@ -153,3 +153,32 @@ def test_tile_rejected_for_7x7_blocks():
     with pytest.raises(iga2l.IgaError) as ei:   # the tensor-core form: 2D, LATTICE, p <= 6
         iga2l.Solver(7, 40, precision=iga2l.MIXED_TF32)
     assert ei.value.code == iga2l.ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("p", [6, 7, 8])
+def test_full_size_high_degree_solves(oracle_mod, p):
+    """1024x1024 elements (the size the benchmark times for p = 6..8): FP64 and mixed solves
+    to 1e-8 with the default colouring, each converged solution's residual re-evaluated by
+    the oracle; the mixed form's cycle count within one of the FP64 form's."""
+    m = 1024
+    O = None
+    cycles = {}
+    for prec in (iga2l.FP64, iga2l.MIXED_FP32):
+        S = iga2l.Solver(p, m, precision=prec)
+        if O is None:
+            O = oracle_mod.Problem(2, p, m, sched=oracle_mod.LATTICE, coarse=oracle_mod.VCYCLE,
+                                   period=S.period, stride=S.stride)
+        f = _dev(synth.coefficients(S.N, 60 + p))
+        b = torch.empty_like(f)
+        S.rhs_from_coeffs(f, b)
+        u0 = synth.initial_guess(S.N, 70 + p)
+        ud = _dev(u0)
+        cyc, rel, _, ok = S.solve(b, ud, tol=1e-8, max_cycles=40)
+        assert ok and rel <= 1e-8 and 3 <= cyc <= 20
+        bh = _host(b)
+        r_end = np.linalg.norm(O.residual(_host(ud), bh))
+        r_0 = np.linalg.norm(O.residual(u0, bh))
+        assert r_end <= 1.0001e-8 * r_0, (prec, r_end / r_0)
+        cycles[prec] = cyc
+        S.close()
+    assert abs(cycles[iga2l.FP64] - cycles[iga2l.MIXED_FP32]) <= 1
