@@ -107,3 +107,33 @@ def test_concurrent_handles_match_sequential(precision):
         c, rel, _, ok = out[k]
         assert ok and c == seq[k][1] and rel == seq[k][2], k
         assert torch.equal(us[k], seq[k][0]), k
+
+
+def test_full_size_batch_residuals(oracle_mod):
+    """The 256-problem workload (m in {64, 128, 256, 512}, p in {2, 3, 4}, seeded; 26.7M
+    DOFs), mixed precision with autotuned schedules and concurrent groups: every problem
+    converges, and its residual re-evaluated by the oracle meets the 1e-8 rule."""
+    nprob = 256
+    z = synth.splitmix64(synth.BASE_SEED + 4, 2 * nprob)
+    ms = np.array([64, 128, 256, 512])[(z[0::2] % np.uint64(4)).astype(int)]
+    ps = np.array([2, 3, 4])[(z[1::2] % np.uint64(3)).astype(int)]
+    problems = [(int(p), int(m)) for p, m in zip(ps, ms)]
+    BS = BatchedSolver(problems, precision=iga2l.MIXED_FP32, autotune=True)
+    f = [torch.tensor(synth.coefficients((m + p - 2) ** 2, 1000 + i), device="cuda") for i, (p, m) in enumerate(problems)]
+    u0 = [torch.tensor(synth.initial_guess((m + p - 2) ** 2, 2000 + i), device="cuda")
+          for i, (p, m) in enumerate(problems)]
+    b = BS.rhs_from_coeffs(BS.pack(f))
+    u = BS.pack(u0)
+    cycles, relres, ok = BS.solve(b, u, tol=1e-8)
+    assert ok and max(cycles) <= 20 and max(relres) <= 1e-8
+    bs, us = BS.unpack(b), BS.unpack(u)
+    oracles = {}
+    for i, (p, m) in enumerate(problems):
+        if (p, m) not in oracles:
+            oracles[(p, m)] = oracle_mod.Problem(2, p, m, sched=oracle_mod.LATTICE, coarse=oracle_mod.VCYCLE)
+        O = oracles[(p, m)]
+        bh = bs[i].cpu().numpy()
+        r_end = np.linalg.norm(O.residual(us[i].cpu().numpy(), bh))
+        r_0 = np.linalg.norm(O.residual(u0[i].cpu().numpy(), bh))
+        assert r_end <= 1.0001e-8 * r_0, (i, p, m, r_end / r_0)
+    BS.close()
