@@ -108,7 +108,9 @@ int iga2l_assemble_batch(int p, int m, int nbatch, const iga2l_options *opt, iga
  * after each cycle a device kernel counts the cycle for each unfinished problem and
  * retires the problems whose relative residual is <= tol; retired problems are
  * skipped by every later kernel, so each problem's iterates and cycle count equal
- * those of a single solve.  The host polls the number of unfinished problems every
+ * those of a single solve.  With CUDA graphs on (the default) the cycles run inside
+ * one graph whose WHILE node that kernel stops once no problem is unfinished or
+ * max_cycles ran; otherwise the host polls the number of unfinished problems every
  * 4 cycles.  cycles (int) and relres (double) are host arrays of nbatch entries.
  * Returns IGA2L_OK when all converged, IGA2L_NOT_CONVERGED at the cycle cap,
  * IGA2L_ERR_NONFINITE if a norm is not finite. */
