@@ -47,11 +47,13 @@ SCHED_CASES = [
     (2, 4, 12, 2, 7, 7, 2),
     (2, 2, 20, 2, 5, 5, 2),
     (2, 5, 15, 2, 10, 10, 3),
-    # the tile sides the GPU kernels compile (20 for p = 2, 5; 21 for p = 3, 4), with
+    # the tile sides the GPU kernels compile (20 for p = 2, 5; 21 for p = 3, 4; 22 for p = 6), with
     # at least two tiles of one phase
     (2, 2, 44, 2, 20, 5, 2),
     (2, 3, 45, 2, 21, 7, 2),
+    (2, 4, 44, 2, 21, 7, 2),
     (2, 5, 45, 2, 20, 10, 3),
+    (2, 6, 44, 2, 22, 11, 4),
     (3, 2, 8, 1, 0, 5, 2),
     (3, 3, 9, 2, 7, 7, 2),
     (3, 2, 12, 2, 5, 5, 2),   # 3D tile side = period, two tiles of one phase per axis
