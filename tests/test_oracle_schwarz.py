@@ -140,3 +140,30 @@ def test_block_size_table(oracle_mod):
         if p.startswith("_"):
             continue
         assert oracle_mod.block_size(int(p)) == s
+
+
+@pytest.mark.parametrize("p,tile", [(3, 7), (4, 7)])
+def test_tile3d_phases_are_coupling_free_at_size(oracle_mod, p, tile):
+    """The 3D TILE sides the GPU compiles (7 for p = 3, 4) on a grid with several tiles of
+    one phase per axis (29-31 DOFs per axis; the dense check above is too large here):
+    within a colour, any two clipped blocks are more than p apart along some axis, so
+    neither shares a DOF with nor reads a DOF of the other (A couples DOFs at most p apart
+    per axis, the 1D bands having half-width p)."""
+    m = 28
+    n = m + p - 2
+    s = oracle_mod.block_size(p)
+    r = (s - 1) // 2
+    colour, order, ncol = oracle_mod.schedule(3, n, s, p, 2, tile, 7, 2)
+    assert sorted(order.tolist()) == list(range(n ** 3))
+    idx = np.arange(n ** 3)
+    cx, cy, cz = idx % n, (idx // n) % n, idx // (n * n)
+    lo = np.stack([np.maximum(c - r, 0) for c in (cx, cy, cz)], axis=1)
+    hi = np.stack([np.minimum(c + r, n - 1) for c in (cx, cy, cz)], axis=1)
+    for col in np.unique(colour):
+        cent = np.nonzero(colour == col)[0]
+        a_lo, a_hi = lo[cent], hi[cent]
+        # pairwise: separated by more than p along at least one axis
+        sep = (a_lo[:, None, :] > a_hi[None, :, :] + p) | (a_lo[None, :, :] > a_hi[:, None, :] + p)
+        ok = sep.any(axis=2)
+        np.fill_diagonal(ok, True)
+        assert ok.all(), (col, cent[np.argwhere(~ok)[0]])
