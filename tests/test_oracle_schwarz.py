@@ -54,6 +54,9 @@ SCHED_CASES = [
     (2, 4, 44, 2, 21, 7, 2),
     (2, 5, 45, 2, 20, 10, 3),
     (2, 6, 44, 2, 22, 11, 4),
+    # the default LATTICE colourings of the 7x7 blocks (p = 7, 8)
+    (2, 7, 44, 1, 0, 14, 5),
+    (2, 8, 50, 1, 0, 17, 4),
     (3, 2, 8, 1, 0, 5, 2),
     (3, 3, 9, 2, 7, 7, 2),
     (3, 2, 12, 2, 5, 5, 2),   # 3D tile side = period, two tiles of one phase per axis
