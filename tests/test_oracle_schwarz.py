@@ -94,7 +94,8 @@ def test_schedule_rejects_short_period(oracle_mod):
 
 
 @pytest.mark.parametrize("dim,p,m,kind,tile", [(2, 2, 6, 0, 0), (2, 2, 8, 1, 0), (2, 3, 9, 2, 7),
-                                               (2, 5, 5, 1, 0), (3, 2, 4, 1, 0), (3, 3, 3, 0, 0)])
+                                               (2, 5, 5, 1, 0), (2, 6, 6, 1, 0), (2, 7, 6, 1, 0),
+                                               (2, 8, 6, 0, 0), (3, 2, 4, 1, 0), (3, 3, 3, 0, 0)])
 def test_schwarz_matches_product_formula(oracle_mod, dim, p, m, kind, tile):
     """u_new - u* = prod_j (I - V_j^T A_j^{-1} V_j A) (u - u*), blocks in schedule order."""
     A, K, M = _dense_A(oracle_mod, dim, p, m)
