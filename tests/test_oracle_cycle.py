@@ -42,7 +42,8 @@ def _block(dim, n, c, r):
     return np.array(out)
 
 
-@pytest.mark.parametrize("dim,p,m,kind", [(2, 2, 8, 1), (2, 3, 8, 2), (2, 5, 6, 1), (3, 2, 4, 1)])
+@pytest.mark.parametrize("dim,p,m,kind", [(2, 2, 8, 1), (2, 3, 8, 2), (2, 5, 6, 1), (2, 6, 8, 1), (2, 7, 8, 1),
+                                          (3, 2, 4, 1)])
 def test_cycle_matches_dense_error_propagation(oracle_mod, dim, p, m, kind):
     """e_new = (I - R^T A_c^{-1} R A) S_E e with exact coarse solve (Sections 3.1, 3.3, 4.1)."""
     P = oracle_mod.Problem(dim, p, m, sched=kind, tile=7, coarse=oracle_mod.EXACT)
