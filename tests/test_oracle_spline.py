@@ -101,7 +101,7 @@ def _cardinal(n, x, deriv=0):
     return tot / factorial(n)
 
 
-@pytest.mark.parametrize("p", range(1, 7))
+@pytest.mark.parametrize("p", range(1, 9))
 def test_interior_rows_match_cardinal_closed_form(oracle_mod, p):
     """Interior rows of M and K are Toeplitz: M_k = h B_{2p+1}(k), K_k = -B''_{2p+1}(k)/h."""
     m = 4 * p + 8

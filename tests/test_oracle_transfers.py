@@ -29,7 +29,7 @@ def _mixed_mass_scipy(p, plow, m, xi_p, xi_l):
     return (Bl * ws) @ Bp.T
 
 
-@pytest.mark.parametrize("p", [2, 3, 5])
+@pytest.mark.parametrize("p", [2, 3, 5, 6, 7, 8])
 def test_mixed_mass_against_scipy(oracle_mod, p):
     m = 9
     Mx = oracle_mod.mixed_mass_1d(p, 1, m)
@@ -65,7 +65,7 @@ def test_galerkin_identity_degree1(oracle_mod, mc):
     assert np.allclose(S.T @ Mh @ S, M2, atol=1e-16)
 
 
-@pytest.mark.parametrize("p", [2, 3, 4, 5])
+@pytest.mark.parametrize("p", [2, 3, 4, 5, 6, 7, 8])
 def test_restriction_composition(oracle_mod, p):
     m = 16
     Mx = _mixed_mass_scipy(p, 1, m, oracle_mod.knots(p, m), oracle_mod.knots(1, m))
