@@ -142,7 +142,7 @@ def _l2_error(oracle_mod, p, m, u):
     return np.sqrt(np.einsum("a,b,ab->", ws, ws, (U - ex) ** 2))
 
 
-@pytest.mark.parametrize("p", [2, 3])
+@pytest.mark.parametrize("p", [2, 3, 4, 5])
 def test_l2_convergence_rate(oracle_mod, p):
     """Section 5.1 problem: -Lap u = 2 pi^2 sin sin; Galerkin error O(h^{p+1})."""
     errs = []
