@@ -241,7 +241,11 @@ int iga2l_residual_norm2_noalloc(int p, int n, const double *Kb, const double *M
                                  const double *u, const double *b, double *d,
                                  double *norm2, void *stream);
 
+/* Releases everything the handle owns (device tables and workspace, captured CUDA
+ * graphs, its capture stream, pinned host buffers).  NULL is allowed.  The caller
+ * makes sure no work of the handle is still running on the GPU. */
 void iga2l_destroy(iga2l_handle h);
+/* Static text of a return code (never NULL). */
 const char *iga2l_strerror(int code);
 /* Detail of the last error on the calling host thread ("" if none). */
 const char *iga2l_last_error(void);
