@@ -115,6 +115,16 @@ int  or_n(const or_problem *P);          /* DOFs per axis */
 int  or_nc(const or_problem *P);         /* second-level DOFs per axis */
 long long or_ndofs(const or_problem *P); /* n^d */
 
+/* Pinned by (problem level): or_residual = b - (explicit Kronecker A) u; or_smooth =
+ * the product formula above for the problem's schedule; or_restrict / or_prolong_add =
+ * Kronecker products of or_restriction_1d and their adjointness; or_coarse_solve =
+ * the dense Cholesky solve (exact kind) or a V(1,1) that is symmetric and contracts
+ * (V-cycle kind); or_cycle = the dense (I - R^T A_c^{-1} R A) S_E on tiny grids;
+ * or_cycle_adjoint = <C x, y> = <x, C^T y> and the dense C^T; or_solve = the stopping
+ * rule and the Section 5.1 manufactured solution reached to 1e-8.  In 3D (the paper is
+ * 2D only) these are pinned by the same mathematics and parity is unpinned by the
+ * paper (no 3D numbers exist); the paper's tables pin the 2D method only softly, its
+ * three-colour ordering being unavailable. */
 void   or_residual(const or_problem *P, const double *u, const double *b, double *d);
 double or_norm2(long long N, const double *v);
 void   or_smooth(const or_problem *P, const double *b, double *u);          /* Schwarz step */
