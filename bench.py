@@ -8,13 +8,16 @@ cycle) run to ||b - A u|| <= 1e-8 ||b - A u_0|| on the 2D Poisson problem with
 Inputs are synthetic and seeded: f has i.i.d. uniform[-1,1] B-spline
 coefficients, b = (M (x) M) f, u_0 is i.i.d. uniform[-1,1] (SplitMix64).
 
-value  = sum_p N_p / step time, inputs resident in HBM, L2 flushed before every solve.
+value  = sum_p N_p / step time, inputs resident in HBM, L2 flushed before every solve;
+         each solve is one iga2l_solve(f) call (b = (M (x) M) f formed by the library).
 e2e    = the same through the public API with host buffers: H2D of f and u_0,
-         b = (M (x) M) f, solve, D2H of u, all inside the timed region.
+         iga2l_solve(f), D2H of u, all inside the timed region.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
-N > 1 runs as one process per GPU under torchrun; every rank solves the same
-workload independently (replicas, weak scaling, no collective on the data path).
+N > 1 runs as one process per GPU: under torchrun as launched, or, when started
+without a torchrun environment, bench.py starts N ranks itself through
+torch.distributed.run.  Every rank solves the same workload independently
+(replicas, weak scaling, no collective on the data path).
 """
 from __future__ import annotations
 
@@ -246,13 +249,13 @@ def run_reference(args):
 
 
 
-def _time_solve(S, b, u0, u, tol, stream, flush):
+def _time_solve(S, f, u0, u, tol, stream, flush):
     flush.fill_(1.0)
     u.copy_(u0)
     import torch
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    c, rel, _, ok = S.solve(b, u, tol=tol)
+    c, rel, _, ok = S.solve(f, u, tol=tol)
     e1.record(stream)
     e1.synchronize()
     if not ok:
@@ -260,7 +263,7 @@ def _time_solve(S, b, u0, u, tol, stream, flush):
     return e0.elapsed_time(e1), c
 
 
-def concurrent_step(solvers, bs, us, u0s, flush, stream, streams, tol):
+def concurrent_step(solvers, fs, us, u0s, flush, stream, streams, tol):
     """The four independent solves of one step at once: each on its own CUDA stream,
     driven by its own host thread (the library's calls release the GIL), L2 flushed
     once before the step.  Returns (ms, cycles per degree)."""
@@ -277,7 +280,7 @@ def concurrent_step(solvers, bs, us, u0s, flush, stream, streams, tol):
         try:
             s = streams[p]
             s.wait_event(e0)
-            c, rel, _, ok = solvers[p].solve(bs[p], us[p], tol=tol, stream=s)
+            c, rel, _, ok = solvers[p].solve(fs[p], us[p], tol=tol, stream=s)
             if not ok:
                 raise RuntimeError(f"p={p} did not converge (rel {rel:.3e})")
             out[p] = c
@@ -311,12 +314,10 @@ def bench_3d(args, dev):
                        ("mixed_fp32_boundary", iga2l.MIXED_FP32_ALL)):
         S = iga2l.Solver(p, m, dim=3, period=7, stride=2, precision=prec)
         f = torch.tensor(synth.coefficients(S.N, synth.BASE_SEED + 3), device=dev)
-        b = torch.empty_like(f)
-        S.rhs_from_coeffs(f, b)
         u0 = torch.tensor(synth.initial_guess(S.N, synth.BASE_SEED + 4), device=dev)
         u = torch.empty_like(u0)
-        _time_solve(S, b, u0, u, TOL, stream, flush)
-        runs = [_time_solve(S, b, u0, u, TOL, stream, flush) for _ in range(2)]
+        _time_solve(S, f, u0, u, TOL, stream, flush)
+        runs = [_time_solve(S, f, u0, u, TOL, stream, flush) for _ in range(2)]
         ms = min(r[0] for r in runs)
         out[name] = {"value": S.N / (ms * 1e-3), "unit": "DOF/s", "ms": ms, "cycles": runs[-1][1]}
         S.close()
@@ -340,12 +341,10 @@ def bench_high_degree(args, dev):
                                   ("mixed", iga2l.MIXED_FP32, iga2l.SCHED_TILE if p <= 6 else iga2l.SCHED_LATTICE)):
             S = iga2l.Solver(p, M_ELEM, precision=prec, schedule=sched)
             f = torch.tensor(synth.coefficients(S.N, synth.BASE_SEED + 10 + p), device=dev)
-            b = torch.empty_like(f)
-            S.rhs_from_coeffs(f, b)
             u0 = torch.tensor(synth.initial_guess(S.N, synth.BASE_SEED + 20 + p), device=dev)
             u = torch.empty_like(u0)
-            _time_solve(S, b, u0, u, TOL, stream, flush)
-            runs = [_time_solve(S, b, u0, u, TOL, stream, flush) for _ in range(2)]
+            _time_solve(S, f, u0, u, TOL, stream, flush)
+            runs = [_time_solve(S, f, u0, u, TOL, stream, flush) for _ in range(2)]
             ms = min(r[0] for r in runs)
             row[name] = {"value": S.N / (ms * 1e-3), "unit": "DOF/s", "ms": ms, "cycles": runs[-1][1],
                          "schedule": "TILE" if sched == iga2l.SCHED_TILE else "LATTICE"}
@@ -370,7 +369,7 @@ def bench_batched(args, dev):
     BS = BatchedSolver(problems, precision=iga2l.MIXED_FP32, autotune=True)
     f = [torch.tensor(synth.coefficients((m + p - 2) ** 2, 1000 + i), device=dev) for i, (p, m) in enumerate(problems)]
     u0 = [torch.tensor(synth.initial_guess((m + p - 2) ** 2, 2000 + i), device=dev) for i, (p, m) in enumerate(problems)]
-    b = BS.rhs_from_coeffs(BS.pack(f))
+    fp = BS.pack(f)
     u0p = BS.pack(u0)
     ndofs = sum(BS.dofs)
     times = []
@@ -378,7 +377,7 @@ def bench_batched(args, dev):
         u = [t.clone() for t in u0p]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        cycles, relres, ok = BS.solve(b, u, tol=TOL)
+        cycles, relres, ok = BS.solve(fp, u, tol=TOL)
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t0)
         if not ok:
@@ -398,12 +397,14 @@ def run_gpu(args):
     import torch
 
     rank, local, ws = dist_setup("nccl")
+    if ws != args.gpus:
+        raise SystemExit(f"bench.py: --gpus {args.gpus} but the world size is {ws}")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     from paper_2009_01499_gb300 import iga2l, synth
 
     iga2l.load()
-    solvers, bs, u0s, us, fhost, u0host, uhost = {}, {}, {}, {}, {}, {}, {}
+    solvers, fs, bs, u0s, us, fhost, u0host, uhost = {}, {}, {}, {}, {}, {}, {}, {}
     setup_ms = {}
     for p in DEGREES:
         q, g = COLOURING[p]
@@ -415,8 +416,8 @@ def run_gpu(args):
         sf, su = seeds(p)
         f = torch.tensor(synth.coefficients(S.N, sf), device=dev)
         b = torch.empty_like(f)
-        S.rhs_from_coeffs(f, b)
-        solvers[p], bs[p] = S, b
+        S.rhs_from_coeffs(f, b)      # b only for the sweep timing below; solves take f
+        solvers[p], fs[p], bs[p] = S, f, b
         u0s[p] = torch.tensor(synth.initial_guess(S.N, su), device=dev)
         us[p] = torch.empty_like(u0s[p])
         fhost[p] = torch.tensor(synth.coefficients(S.N, sf)).pin_memory()
@@ -433,7 +434,7 @@ def run_gpu(args):
             us[p].copy_(u0s[p])
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            c, rel, _, ok = solvers[p].solve(bs[p], us[p], tol=TOL)
+            c, rel, _, ok = solvers[p].solve(fs[p], us[p], tol=TOL)
             e1.record(stream)
             e1.synchronize()
             if not ok:
@@ -465,8 +466,8 @@ def run_gpu(args):
     # the same step with the four solves running concurrently (one stream and host thread each)
     cstreams = {p: torch.cuda.Stream(dev) for p in DEGREES}
     for _ in range(args.warmup):
-        concurrent_step(solvers, bs, us, u0s, flush, stream, cstreams, TOL)
-    cms = [concurrent_step(solvers, bs, us, u0s, flush, stream, cstreams, TOL)[0] for _ in range(args.steps)]
+        concurrent_step(solvers, fs, us, u0s, flush, stream, cstreams, TOL)
+    cms = [concurrent_step(solvers, fs, us, u0s, flush, stream, cstreams, TOL)[0] for _ in range(args.steps)]
     c_ms = allmax(statistics.mean(cms), ws, dev)
     concurrent = {"value": ws * ndofs / (c_ms * 1e-3), "unit": "DOF/s", "ms_per_step": c_ms,
                   "note": "the step's four independent solves on four streams at once (L2 flushed once per step)"}
@@ -485,8 +486,7 @@ def run_gpu(args):
             e0.record(stream)
             f_dev.copy_(fhost[p], non_blocking=True)
             us[p].copy_(u0host[p], non_blocking=True)
-            S.rhs_from_coeffs(f_dev, bs[p])
-            S.solve(bs[p], us[p], tol=TOL)
+            S.solve(f_dev, us[p], tol=TOL)
             uhost[p].copy_(us[p], non_blocking=True)
             e1.record(stream)
             e1.synchronize()
@@ -517,7 +517,7 @@ def run_gpu(args):
                     us[p].copy_(u0s[p])
                     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                     e0.record(stream)
-                    c, rel, _, ok = msolv[p].solve(bs[p], us[p], tol=TOL)
+                    c, rel, _, ok = msolv[p].solve(fs[p], us[p], tol=TOL)
                     e1.record(stream)
                     e1.synchronize()
                     if not ok:
@@ -530,8 +530,8 @@ def run_gpu(args):
                 mstep()
             mms = allmax(statistics.mean([mstep() for _ in range(args.steps)]), ws, dev)
             for _ in range(args.warmup):
-                concurrent_step(msolv, bs, us, u0s, flush, stream, cstreams, TOL)
-            mcms = allmax(statistics.mean([concurrent_step(msolv, bs, us, u0s, flush, stream, cstreams, TOL)[0]
+                concurrent_step(msolv, fs, us, u0s, flush, stream, cstreams, TOL)
+            mcms = allmax(statistics.mean([concurrent_step(msolv, fs, us, u0s, flush, stream, cstreams, TOL)[0]
                                            for _ in range(args.steps)]), ws, dev)
             out = {"value": ws * ndofs / (mms * 1e-3), "unit": "DOF/s", "ms_per_step": mms,
                    "speedup_vs_fp64": ms_step / mms,
@@ -649,16 +649,58 @@ def run_profile_step(args):
         S = iga2l.Solver(p, m, dim=dim, precision=prec, schedule=sched, graphs=0, **col)
         sf, su = seeds(p)
         f = torch.tensor(synth.coefficients(S.N, sf), device=dev)
-        b = torch.empty_like(f)
-        S.rhs_from_coeffs(f, b)
         u0 = torch.tensor(synth.initial_guess(S.N, su), device=dev)
         u = torch.empty_like(u0)
         for _ in range(args.warmup + 1):
             u.copy_(u0)
-            cyc, rel, _, ok = S.solve(b, u, tol=TOL)
+            cyc, rel, _, ok = S.solve(f, u, tol=TOL)
         torch.cuda.synchronize()
         print(f"p={p} m={m} dim={dim}: {cyc} cycles, rel {rel:.3e}, converged {ok}", flush=True)
         S.close()
+
+
+def _free_port():
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        return sk.getsockname()[1]
+
+
+def relaunch_as_ranks(args, argv):
+    """--gpus N > 1 without a torchrun environment: start N ranks (one process per GPU)
+    through torch.distributed.run on this node and return its exit status."""
+    if not args.launch_check and args.impl == "gpu":
+        import torch
+        have = torch.cuda.device_count() if torch.cuda.is_available() else 0
+        if have < args.gpus:
+            raise SystemExit(f"bench.py: --gpus {args.gpus} requested but only {have} GPU(s) are visible")
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes", "1", "--nproc-per-node", str(args.gpus),
+           "--master-addr", "127.0.0.1", "--master-port", str(_free_port()), os.path.abspath(__file__)] + argv
+    return subprocess.call(cmd)
+
+
+def run_launch_check(args):
+    """Launcher check without GPU work: every rank joins the process group (gloo without
+    CUDA), reports a per-rank time, and rank 0 prints the job line with the world size."""
+    backend = "nccl" if args.impl == "gpu" and _cuda_ok() else "gloo"
+    rank, local, ws = dist_setup(backend)
+    if ws != args.gpus:
+        raise SystemExit(f"bench.py: --gpus {args.gpus} but the world size is {ws}")
+    barrier(ws)
+    ms = allmax(1.0 + rank, ws)
+    if rank == 0:
+        print(json.dumps({"launch_check": True, "n_gpus": ws, "ms_per_step": ms, "backend": backend}), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def _cuda_ok():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
 
 
 def main():
@@ -677,7 +719,17 @@ def main():
     ap.add_argument("--profile-p", type=int, default=0)
     ap.add_argument("--profile-precision", choices=["fp64", "mixed", "mixed_all", "mixed_tf32"], default="fp64",
                     help="form profiled by --profile-step (the benchmark's schedule for it)")
-    args = ap.parse_args()
+    ap.add_argument("--launch-check", action="store_true",
+                    help="start the ranks and report the world size, without GPU work (launcher test)")
+    argv = sys.argv[1:]
+    args = ap.parse_args(argv)
+    if args.gpus < 1:
+        ap.error("--gpus must be >= 1")
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        sys.exit(relaunch_as_ranks(args, argv))
+    if args.launch_check:
+        run_launch_check(args)
+        return
     if args.profile_step:
         run_profile_step(args)
         return

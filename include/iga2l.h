@@ -63,6 +63,16 @@ extern "C" {
 /* second-level solver */
 #define IGA2L_COARSE_EXACT 0
 #define IGA2L_COARSE_VCYCLE 1
+/* right-hand side given to iga2l_solve / iga2l_solve_batch: the B-spline coefficients f
+ * of the source (Section 2: b_p = (f, phi_i), formed on the device as (M(x)M) f), or the
+ * load vector b_p itself */
+#define IGA2L_RHS_COEFFS 0
+#define IGA2L_RHS_IS_LOAD 1
+/* test_flags bits (testing the error paths only; never set in production use):
+ * the tensor-core colour kernel does not issue the bulk copy of its block operator, so
+ * its bounded wait for that copy runs out (no copy and no MMA is ever in flight), the
+ * kernel skips its blocks and the call returns IGA2L_ERR_DEVICE_TIMEOUT */
+#define IGA2L_TEST_SKIP_OPERATOR_COPY 1
 
 typedef struct iga2l_solver *iga2l_handle;
 
@@ -77,10 +87,16 @@ typedef struct {
     int block_side;  /* Schwarz block side s (0 = the paper's choice for p, Section 4.3) */
     int max_cycles;  /* default cap for iga2l_solve when its max_cycles <= 0 */
     int graphs;      /* 1: replay cycles as captured CUDA graphs (default); 0: plain launches */
+    int rhs;         /* IGA2L_RHS_COEFFS (default) or IGA2L_RHS_IS_LOAD: what iga2l_solve and
+                        iga2l_solve_batch read from their right-hand-side argument */
+    int test_flags;  /* 0, or IGA2L_TEST_* bits (error-path tests only) */
+    long long wait_budget_cycles;   /* SM clock cycles a bounded device wait may spin before the
+                        kernel gives up, records the failure and returns (the call then reports
+                        IGA2L_ERR_DEVICE_TIMEOUT); 0 = 2^31 (about 1 s at 2 GHz) */
 } iga2l_options;
 
 /* Fills the defaults: FP64, LATTICE, V(1,1), the paper's block side, 100 cycles,
- * graphs on. */
+ * graphs on, right-hand side given as coefficients, default wait budget. */
 void iga2l_default_options(iga2l_options *opt);
 
 /* Builds the solver for degree p (2..8 in 2D, 2..4 in 3D), m elements per axis,
@@ -104,7 +120,9 @@ int iga2l_assemble(int p, int m, int dim, const iga2l_options *opt, iga2l_handle
  * with a norm are single-problem entry points and return IGA2L_ERR_INVALID_ARG. */
 int iga2l_assemble_batch(int p, int m, int nbatch, const iga2l_options *opt, iga2l_handle *out);
 
-/* Solves every problem of a batch to its own tolerance (Section 5 stopping rule):
+/* Solves every problem of a batch to its own tolerance (Section 5 stopping rule);
+ * `rhs` holds every problem's coefficient vector f (or load vector b with options.rhs =
+ * IGA2L_RHS_IS_LOAD), as iga2l_solve:
  * after each cycle a device kernel counts the cycle for each unfinished problem and
  * retires the problems whose relative residual is <= tol; retired problems are
  * skipped by every later kernel, so each problem's iterates and cycle count equal
@@ -114,7 +132,7 @@ int iga2l_assemble_batch(int p, int m, int nbatch, const iga2l_options *opt, iga
  * 4 cycles.  cycles (int) and relres (double) are host arrays of nbatch entries.
  * Returns IGA2L_OK when all converged, IGA2L_NOT_CONVERGED at the cycle cap,
  * IGA2L_ERR_NONFINITE if a norm is not finite. */
-int iga2l_solve_batch(iga2l_handle h, const double *b, double tol, int max_cycles, double *u, int *cycles,
+int iga2l_solve_batch(iga2l_handle h, const double *rhs, double tol, int max_cycles, double *u, int *cycles,
                       double *relres, void *stream);
 
 /* Sizes: total fine DOFs, DOFs per axis, total and per-axis second-level DOFs.
@@ -165,17 +183,27 @@ int iga2l_cycle(iga2l_handle h, double *u, const double *b, void *stream);
  * Schwarz step.  Its approximate inverse is the transpose of iga2l_cycle's. */
 int iga2l_cycle_adjoint(iga2l_handle h, double *u, const double *b, void *stream);
 
-/* Cycles from the guess in u until ||b - A u||_2 <= tol ||b - A u_0||_2
- * (Section 5 stopping rule) or max_cycles (<= 0: the handle's default).
- * Writes the cycle count, the final relative residual and, if hist is not
- * NULL, the relative residual after every cycle (host array of max_cycles).
+/* Solves A_p u_p = b_p (Section 2) from the guess in u: cycles until
+ * ||b - A u||_2 <= tol ||b - A u_0||_2 (Section 5 stopping rule) or max_cycles (<= 0: the
+ * handle's default).  `rhs` is the source's B-spline coefficient vector f (n^d device
+ * doubles; b_p = (f, phi_i) = (M(x)M[(x)M]) f is formed on the device into the handle's
+ * workspace first), or b_p itself when the handle was built with options.rhs =
+ * IGA2L_RHS_IS_LOAD.  Writes the cycle count, the final relative residual and, if hist is
+ * not NULL, the relative residual after every cycle (host array of max_cycles).
  * Returns IGA2L_OK, IGA2L_NOT_CONVERGED or an error (IGA2L_ERR_NONFINITE if a
- * residual norm is not finite).  With CUDA graphs on (the default) and max_cycles
+ * residual norm is not finite; IGA2L_ERR_DEVICE_TIMEOUT if a bounded device wait gave
+ * up, u then holds unspecified values).  With CUDA graphs on (the default) and max_cycles
  * <= 1024 the cycles and their stopping test run on the device (one graph whose
  * WHILE node repeats cycle + check), and the call synchronises the stream twice
  * (initial residual, result); otherwise once per cycle.  Same results either way. */
-int iga2l_solve(iga2l_handle h, const double *b, double tol, int max_cycles, double *u,
+int iga2l_solve(iga2l_handle h, const double *rhs, double tol, int max_cycles, double *u,
                 int *cycles, double *relres, double *hist, void *stream);
+
+/* iga2l_solve with the load vector b_p given directly (whatever options.rhs says): for
+ * right-hand sides that are not a spline, e.g. b_p = (f, phi_i) of a closed-form f by
+ * quadrature (Section 5.1).  Same arguments, results and errors otherwise. */
+int iga2l_solve_load(iga2l_handle h, const double *b, double tol, int max_cycles, double *u,
+                     int *cycles, double *relres, double *hist, void *stream);
 
 /* Solve of A_p lambda = g with the transposed cycle (A_p is symmetric, so the
  * limit is A_p^{-1} g; the iterates are those of the adjoint iteration).  Always
@@ -236,7 +264,9 @@ int iga2l_host_restriction(int p, int m, double *R);
  * (cudaGetSymbolAddress) with the device current; make that first call before
  * any stream capture.  Every call shares the array: each call overwrites the
  * partials it reads, so nothing has to be cleared, but calls that overlap on the
- * GPU (other streams, other threads) race on it. */
+ * GPU (other streams, other threads) race on it.  The looked-up address belongs to
+ * the device's current context: after cudaDeviceReset on a device it is stale, so this
+ * entry point must not be called again on that device in the same process. */
 int iga2l_residual_norm2_noalloc(int p, int n, const double *Kb, const double *Mb,
                                  const double *u, const double *b, double *d,
                                  double *norm2, void *stream);

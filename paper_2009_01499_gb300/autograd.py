@@ -32,7 +32,7 @@ class BumpSolve(torch.autograd.Function):
         solver.bump_load(th, width, b)
         u = torch.zeros_like(b)
         if mode == "adjoint":
-            cyc, rel, _, ok = solver.solve(b, u, tol=tol, max_cycles=200)
+            cyc, rel, _, ok = solver.solve_load(b, u, tol=tol, max_cycles=200)
             if not ok:
                 raise RuntimeError(f"forward solve did not reach {tol:g} (rel {rel:.3e})")
         else:

@@ -61,7 +61,7 @@ def autotune_schedule(p: int, m: int, precision: int, cache_path: str | None = N
             u = u0.clone()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            S.solve(b, u, tol=1e-8)
+            S.solve_load(b, u, tol=1e-8)
             e1.record()
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
@@ -84,7 +84,7 @@ class BatchedSolver:
     """Independent 2D problems given as a list of (p, m), solved group by group."""
 
     def __init__(self, problems, precision: int = iga2l.MIXED_FP32, autotune: bool = True,
-                 cache_path: str | None = None, schedule: int | None = None):
+                 cache_path: str | None = None, schedule: int | None = None, rhs_is_load: bool = False):
         self.problems = list(problems)
         self.precision = precision
         groups: "OrderedDict[tuple, list]" = OrderedDict()
@@ -96,7 +96,7 @@ class BatchedSolver:
                 autotune_schedule(p, m, precision, cache_path) if autotune else iga2l.SCHED_LATTICE)
             q, g = COLOURING[p]
             h = iga2l.Solver(p, m, nbatch=len(members), batch=True, period=q, stride=g, precision=precision,
-                             schedule=sched)
+                             schedule=sched, rhs=iga2l.RHS_IS_LOAD if rhs_is_load else iga2l.RHS_COEFFS)
             self.groups.append({"p": p, "m": m, "members": members, "handle": h, "schedule": sched,
                                 "stream": torch.cuda.Stream()})
         self.dofs = [(m + p - 2) ** 2 for p, m in self.problems]
@@ -125,8 +125,10 @@ class BatchedSolver:
             g["stream"].synchronize()
         return b_packed
 
-    def solve(self, b_packed, u_packed, tol: float = 1e-8, max_cycles: int = 0):
-        """Solves all groups concurrently in place; returns (cycles, relres, converged) per problem."""
+    def solve(self, rhs_packed, u_packed, tol: float = 1e-8, max_cycles: int = 0):
+        """Solves all groups concurrently in place; rhs_packed holds the coefficient vectors f
+        of every problem (load vectors b with rhs_is_load=True).  Returns (cycles, relres,
+        converged) per problem."""
         cycles = [0] * len(self.problems)
         relres = [0.0] * len(self.problems)
         ok = [True]
@@ -145,7 +147,7 @@ class BatchedSolver:
         cur = torch.cuda.current_stream()
         for g in self.groups:
             g["stream"].wait_stream(cur)
-        threads = [threading.Thread(target=run, args=(g, b, u)) for g, b, u in zip(self.groups, b_packed, u_packed)]
+        threads = [threading.Thread(target=run, args=(g, b, u)) for g, b, u in zip(self.groups, rhs_packed, u_packed)]
         for t in threads:
             t.start()
         for t in threads:

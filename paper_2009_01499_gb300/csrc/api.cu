@@ -338,6 +338,15 @@ iga2l_solver::SolveGraph *solve_graph(iga2l_handle h, double *u, const double *b
     return &h->solve_graphs.back();
 }
 
+// b_p = (f, phi_i) of a source given by its B-spline coefficients f (Section 2), into the
+// handle's right-hand-side buffer (every problem of a batch)
+int load_from_coeffs(iga2l_handle h, const double *f, const double *u, cudaStream_t st)
+{
+    if (!f || !u) return fail(IGA2L_ERR_INVALID_ARG, "null vector");
+    if (f == h->rhsb) return fail(IGA2L_ERR_INVALID_ARG, "aliased vector");
+    return finish(launch_mass2(*h, f, h->rhsb, st), "right-hand side from coefficients");
+}
+
 int solve_impl(iga2l_handle h, const double *b, double tol, int max_cycles, double *u, int *cycles,
                double *relres, double *hist, void *stream, bool adjoint)
 {
@@ -438,6 +447,9 @@ void iga2l_default_options(iga2l_options *opt)
     opt->coarse = IGA2L_COARSE_VCYCLE;
     opt->max_cycles = 100;
     opt->graphs = 1;
+    opt->rhs = IGA2L_RHS_COEFFS;
+    opt->test_flags = 0;
+    opt->wait_budget_cycles = 0;
 }
 
 }  // extern "C"
@@ -471,6 +483,11 @@ static int assemble_impl(int p, int m, int dim, int nbatch, bool batch, const ig
     }
     if (opt.coarse != IGA2L_COARSE_VCYCLE && opt.coarse != IGA2L_COARSE_EXACT)
         return fail(IGA2L_ERR_INVALID_ARG, "unknown coarse solver");
+    if (opt.rhs != IGA2L_RHS_COEFFS && opt.rhs != IGA2L_RHS_IS_LOAD)
+        return fail(IGA2L_ERR_INVALID_ARG, "rhs must be IGA2L_RHS_COEFFS or IGA2L_RHS_IS_LOAD");
+    if (opt.test_flags & ~IGA2L_TEST_SKIP_OPERATOR_COPY) return fail(IGA2L_ERR_INVALID_ARG, "unknown test flag");
+    if (opt.wait_budget_cycles < 0) return fail(IGA2L_ERR_INVALID_ARG, "wait_budget_cycles must be >= 0");
+    if (opt.wait_budget_cycles == 0) opt.wait_budget_cycles = 1LL << 31;
     const int s = opt.block_side > 0 ? opt.block_side : default_block_side(p);
     if (!((s == 3 && p <= 4) || (s == 5 && (p == 5 || p == 6)) || (s == 7 && (p == 7 || p == 8))))
         return fail(IGA2L_ERR_UNSUPPORTED, "block side not compiled for this degree");
@@ -636,6 +653,7 @@ static int assemble_impl(int p, int m, int dim, int nbatch, bool batch, const ig
     S->npart = residual_partials(*S);
     const size_t B = (size_t)nbatch;   // every per-problem buffer holds nbatch problems
     if ((ce = alloc(S, &S->d, B * S->N)) != cudaSuccess || (ce = alloc(S, &S->bwork, B * S->N)) != cudaSuccess ||
+        (ce = alloc(S, &S->rhsb, B * S->N)) != cudaSuccess ||
         (ce = alloc(S, &S->t, B * (dim == 3 ? (size_t)n * n * S->nc : (size_t)n * S->nc))) != cudaSuccess ||
         (ce = alloc(S, &S->t2, B * (dim == 3 ? (size_t)n * S->nc * S->nc : (size_t)n * S->nc))) != cudaSuccess ||
         (ce = alloc(S, &S->dc, B * S->Nc)) != cudaSuccess || (ce = alloc(S, &S->ec, B * S->Nc)) != cudaSuccess ||
@@ -794,16 +812,21 @@ int iga2l_assemble_batch(int p, int m, int nbatch, const iga2l_options *opt, iga
     return assemble_impl(p, m, 2, nbatch, true, opt, out);
 }
 
-int iga2l_solve_batch(iga2l_handle h, const double *b, double tol, int max_cycles, double *u, int *cycles,
+int iga2l_solve_batch(iga2l_handle h, const double *rhs, double tol, int max_cycles, double *u, int *cycles,
                       double *relres, void *stream)
 {
     int rc = check_handle(h);
     if (rc != IGA2L_OK) return rc;
-    if (!b || !u || !cycles || !relres) return fail(IGA2L_ERR_INVALID_ARG, "null argument");
+    if (!rhs || !u || !cycles || !relres) return fail(IGA2L_ERR_INVALID_ARG, "null argument");
     if (!(tol >= 0.0)) return fail(IGA2L_ERR_INVALID_ARG, "tol must be >= 0");
     if (!h->active) return fail(IGA2L_ERR_INVALID_ARG, "handle is not a batch (iga2l_assemble_batch)");
     if (max_cycles <= 0) max_cycles = h->opt.max_cycles;
     cudaStream_t st = as_stream(stream);
+    const double *b = rhs;
+    if (h->opt.rhs == IGA2L_RHS_COEFFS) {   // every problem's b = (M (x) M) f
+        if ((rc = load_from_coeffs(h, rhs, u, st)) != IGA2L_OK) return rc;
+        b = h->rhsb;
+    }
     const int nb = h->nbatch;
     // initial residuals of every problem (all active while they are computed)
     std::vector<int> ones(nb, 1);
@@ -955,8 +978,22 @@ int iga2l_cycle_adjoint(iga2l_handle h, double *u, const double *b, void *stream
     return run_cycle(h, u, b, as_stream(stream), true);
 }
 
-int iga2l_solve(iga2l_handle h, const double *b, double tol, int max_cycles, double *u, int *cycles,
+int iga2l_solve(iga2l_handle h, const double *rhs, double tol, int max_cycles, double *u, int *cycles,
                 double *relres, double *hist, void *stream)
+{
+    int rc = check_handle(h);
+    if (rc != IGA2L_OK) return rc;
+    if (h->active) return fail(IGA2L_ERR_INVALID_ARG, "single-problem entry point on a batch handle");
+    const double *b = rhs;
+    if (h->opt.rhs == IGA2L_RHS_COEFFS) {   // b_p = (f, phi_i) = (M (x) M [(x) M]) f
+        if ((rc = load_from_coeffs(h, rhs, u, as_stream(stream))) != IGA2L_OK) return rc;
+        b = h->rhsb;
+    }
+    return solve_impl(h, b, tol, max_cycles, u, cycles, relres, hist, stream, false);
+}
+
+int iga2l_solve_load(iga2l_handle h, const double *b, double tol, int max_cycles, double *u, int *cycles,
+                     double *relres, double *hist, void *stream)
 {
     int rc = check_handle(h);
     if (rc != IGA2L_OK) return rc;

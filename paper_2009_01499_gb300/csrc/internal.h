@@ -108,7 +108,8 @@ struct Solver {
     double *part = nullptr;      // per-CTA partial sums of squares
     unsigned int *rcount = nullptr;   // per problem: residual CTAs done (fused norm), re-armed to 0
     int npart = 0;
-    double *bwork = nullptr;     // b built from coefficients in solve paths
+    double *bwork = nullptr;     // scratch of the 3D mass apply
+    double *rhsb = nullptr;      // b = (M (x) M) f of a solve given the coefficients f
     MixedState mx;
     // differentiable source (2D): 1D quadrature tables, nq = p+3 points per element
     int nq = 0;

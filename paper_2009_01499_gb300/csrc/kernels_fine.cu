@@ -918,28 +918,27 @@ __global__ void k_prolong_y(int n, int nc, int wc, const T *__restrict__ Cb,
     else u[k] += (TU)acc;
 }
 
-// b[j][i] = sum_b M[j][b] sum_a M[i][a] f[j+b-p][i+a-p]
-template <int P>
-__global__ void k_mass2d(int n, const double *__restrict__ Mb, const double *__restrict__ f,
-                         double *__restrict__ b, long long vec)
+// One 1D pass of b = (M (x) M) f: along y (AXIS 1, out[j][i] = sum_b M[j][b] in[j+b-p][i])
+// or along x (AXIS 0, out[j][i] = sum_a M[i][a] in[j][i+a-p]); the two passes make
+// 2(2p+1) multiply-adds per DOF instead of (2p+1)^2.
+template <int P, int AXIS>
+__global__ void k_mass_pass(int n, const double *__restrict__ Mb, const double *__restrict__ in,
+                            double *__restrict__ out, long long vec)
 {
     constexpr int W = 2 * P + 1;
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
     if (i >= n) return;
-    f += blockIdx.z * vec;
-    b += blockIdx.z * vec;
+    in += blockIdx.z * vec;
+    out += blockIdx.z * vec;
+    const int r = AXIS == 0 ? i : j;
+    const double *row = Mb + (size_t)r * W;
     double acc = 0.0;
-    for (int bb = 0; bb < W; ++bb) {
-        const int jj = j + bb - P;
-        if (jj < 0 || jj >= n) continue;
-        double s = 0.0;
-        for (int aa = 0; aa < W; ++aa) {
-            const int ii = i + aa - P;
-            if (ii >= 0 && ii < n) s = fma(Mb[(size_t)i * W + aa], f[(size_t)jj * n + ii], s);
-        }
-        acc = fma(Mb[(size_t)j * W + bb], s, acc);
+#pragma unroll
+    for (int a = 0; a < W; ++a) {
+        const int k = r + a - P;
+        if (k >= 0 && k < n) acc = fma(__ldg(&row[a]), AXIS == 0 ? in[(size_t)j * n + k] : in[(size_t)k * n + i], acc);
     }
-    b[(size_t)j * n + i] = acc;
+    out[(size_t)j * n + i] = acc;
 }
 
 // norm2 != nullptr (with part): the squared norm of every problem is finished inside the
@@ -1392,18 +1391,19 @@ cudaError_t launch_inner_update(const Solver &S, double *u, cudaStream_t st)
 cudaError_t launch_mass2(const Solver &S, const double *f, double *b, cudaStream_t st)
 {
     if (S.dim == 3) return launch3d_mass(S, f, b, st);
+    // y pass into the workspace d, then the x pass into b
     dim3 grd((S.n + 127) / 128, S.n, S.nbatch);
     switch (S.p) {
-    case 2: k_mass2d<2><<<grd, 128, 0, st>>>(S.n, S.Mb, f, b, S.N); break;
-    case 3: k_mass2d<3><<<grd, 128, 0, st>>>(S.n, S.Mb, f, b, S.N); break;
-    case 4: k_mass2d<4><<<grd, 128, 0, st>>>(S.n, S.Mb, f, b, S.N); break;
-    case 5: k_mass2d<5><<<grd, 128, 0, st>>>(S.n, S.Mb, f, b, S.N); break;
-    case 6: k_mass2d<6><<<grd, 128, 0, st>>>(S.n, S.Mb, f, b, S.N); break;
-    case 7: k_mass2d<7><<<grd, 128, 0, st>>>(S.n, S.Mb, f, b, S.N); break;
-    case 8: k_mass2d<8><<<grd, 128, 0, st>>>(S.n, S.Mb, f, b, S.N); break;
+#define IGA2L_MASS(PP)                                                                           \
+    case PP:                                                                                     \
+        k_mass_pass<PP, 1><<<grd, 128, 0, st>>>(S.n, S.Mb, f, S.d, S.N);                         \
+        k_mass_pass<PP, 0><<<grd, 128, 0, st>>>(S.n, S.Mb, S.d, b, S.N);                         \
+        break;
+    IGA2L_MASS(2) IGA2L_MASS(3) IGA2L_MASS(4) IGA2L_MASS(5) IGA2L_MASS(6) IGA2L_MASS(7) IGA2L_MASS(8)
+#undef IGA2L_MASS
     default: return cudaErrorInvalidValue;
     }
-    count_launches(1);
+    count_launches(2);
     return cudaGetLastError();
 }
 

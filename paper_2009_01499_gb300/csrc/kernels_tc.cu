@@ -57,6 +57,22 @@ __device__ __forceinline__ float to_tf32(float x)
     return __uint_as_float(r);
 }
 
+// Waits for phase `parity` of an mbarrier for at most `budget` SM clock cycles; returns
+// whether the phase completed.
+__device__ __forceinline__ int mbar_wait_bounded(uint32_t bar, uint32_t parity, long long budget)
+{
+    const long long t0 = clock64();
+    uint32_t ok = 0;
+    do {
+        asm volatile("{\n .reg .pred q;\n mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, q;\n}"
+                     : "=r"(ok)
+                     : "r"(bar), "r"(parity)
+                     : "memory");
+    } while (!ok && clock64() - t0 < budget);
+    return (int)ok;
+}
+
 // shared-memory matrix descriptor: start, leading / stride byte offsets, version 1, no swizzle
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
 {
@@ -76,7 +92,8 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int m, int n)
 template <int P, int S>
 __global__ void __launch_bounds__(512)
 k_schwarz_tc(int n, int q, int ox, int oy, int ix0, int iy0, int nix, int niy, int bpc, const float *__restrict__ gtc,
-             const float *__restrict__ b, float *__restrict__ u, int *__restrict__ status)
+             const float *__restrict__ b, float *__restrict__ u, int *__restrict__ status, long long budget,
+             int skip_copy)
 {
     using G = TcGeom<P, S>;
     constexpr int SS = G::SS, R = G::R, PW = G::PW, KU = G::KU, KP = G::KP, NP = G::NP, M = G::M;
@@ -86,6 +103,8 @@ k_schwarz_tc(int n, int q, int ox, int oy, int ix0, int iy0, int nix, int niy, i
     float *sG = reinterpret_cast<float *>(tc_smem + G::XB);
     uint64_t *mbar = reinterpret_cast<uint64_t *>(tc_smem + G::XB + G::GB);   // [0]: MMA, [1]: copy of G
     uint32_t *tslot = reinterpret_cast<uint32_t *>(tc_smem + G::XB + G::GB + 16);
+    __shared__ int s_mma;   // 1: the operator landed and the MMA chain was issued
+    const long long drain = budget > (1LL << 31) ? budget : (1LL << 31);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     // bpc (<= M) blocks per CTA, chosen so that the grid covers the SMs once; rows beyond are zero
     const int nblk = nix * niy, m0 = blockIdx.x * bpc;
@@ -97,10 +116,11 @@ k_schwarz_tc(int n, int q, int ox, int oy, int ix0, int iy0, int nix, int niy, i
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&mbar[1])),
                      "r"((uint32_t)G::GB)
                      : "memory");
-        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                         smem_addr(sG)),
-                     "l"(gtc), "r"((uint32_t)G::GB), "r"(smem_addr(&mbar[1]))
-                     : "memory");
+        if (!skip_copy)   // (error-path tests leave the copy out, so its wait runs out)
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                             smem_addr(sG)),
+                         "l"(gtc), "r"((uint32_t)G::GB), "r"(smem_addr(&mbar[1]))
+                         : "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)),
@@ -147,13 +167,14 @@ k_schwarz_tc(int n, int q, int ox, int oy, int ix0, int iy0, int nix, int niy, i
     const uint32_t tmem = *tslot;
     if (tid == 0) {
         // G has landed (bounded wait), then the MMA chain
-        uint32_t gready = 0;
-        for (int it = 0; it < (1 << 22) && !gready; ++it)
-            asm volatile("{\n .reg .pred q;\n mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n"
-                         " selp.u32 %0, 1, 0, q;\n}"
-                         : "=r"(gready)
-                         : "r"(smem_addr(&mbar[1])), "r"(0)
-                         : "memory");
+        int gready = mbar_wait_bounded(smem_addr(&mbar[1]), 0, budget);
+        if (!gready) {
+            atomicAdd(status, 1);
+            // a copy still in flight must land before the CTA may exit (bounded again, by
+            // at least the default budget whatever the caller chose)
+            if (!skip_copy) mbar_wait_bounded(smem_addr(&mbar[1]), 0, drain);
+        }
+        s_mma = gready;
         if (gready) {
             constexpr uint32_t idesc = idesc_tf32(M, NP);
             const uint32_t xa = smem_addr(sX), ga = smem_addr(sG);
@@ -169,21 +190,20 @@ k_schwarz_tc(int n, int q, int ox, int oy, int ix0, int iy0, int nix, int niy, i
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                              smem_addr(&mbar[0]))
                          : "memory");
-        } else {
-            atomicAdd(status, 1);
-            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&mbar[0])) : "memory");
         }
     }
-    // bounded wait for the MMA chain (phase 0 of the barrier)
+    __syncthreads();
+    // bounded wait for the MMA chain (phase 0 of the barrier); if it gives up, the chain
+    // must still finish before the tensor memory is released (bounded again)
     uint32_t done = 0;
-    for (int it = 0; it < (1 << 22) && !done; ++it)
-        asm volatile("{\n .reg .pred q;\n mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n"
-                     " selp.u32 %0, 1, 0, q;\n}"
-                     : "=r"(done)
-                     : "r"(smem_addr(&mbar[0])), "r"(0)
-                     : "memory");
-    done = __all_sync(0xffffffffu, done);   // tcgen05.ld below is warp-collective
-    if (!done && lane == 0) atomicAdd(status, 1);
+    if (s_mma) {
+        done = mbar_wait_bounded(smem_addr(&mbar[0]), 0, budget);
+        done = __all_sync(0xffffffffu, done);   // tcgen05.ld below is warp-collective
+        if (!done) {
+            if (lane == 0) atomicAdd(status, 1);
+            mbar_wait_bounded(smem_addr(&mbar[0]), 0, drain);
+        }
+    }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (done && (warp >> 2) * 8 < NP) {
         // warps w, w + 4, ... read the rows of TMEM sub-partition w % 4, each a slice of the
@@ -240,7 +260,9 @@ cudaError_t launch_tc_p(const Solver &S_, int ox, int oy, int ix0, int iy0, int 
     if (bpc > G::M) bpc = G::M;
     if (bpc < 1) bpc = 1;
     k_schwarz_tc<P, S><<<(nblk + bpc - 1) / bpc, 512, G::smem, st>>>(S_.n, S_.q, ox, oy, ix0, iy0, nix, niy, bpc,
-                                                                     S_.mx.gtc, b, u, S_.mx.tc_status);
+                                                                     S_.mx.gtc, b, u, S_.mx.tc_status,
+                                                                     S_.opt.wait_budget_cycles,
+                                                                     (S_.opt.test_flags & IGA2L_TEST_SKIP_OPERATOR_COPY) != 0);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -145,8 +145,10 @@ extern "C" int iga2l_residual_norm2_noalloc(int p, int n, const double *Kb, cons
         set_last_error("residual_norm2_noalloc: p must be 2..5, n >= 1 and Kb, Mb, u, b, norm2 non-null");
         return IGA2L_ERR_INVALID_ARG;
     }
-    const long long nparts = (long long)((n + kNoAllocTX - 1) / kNoAllocTX) * ((n + kNoAllocTY - 1) / kNoAllocTY);
-    if (nparts > kNoAllocMaxPartials) {
+    // sizes checked in 64-bit arithmetic, so that no n near INT_MAX can wrap around
+    const long long nl = n;
+    const long long nparts = ((nl + kNoAllocTX - 1) / kNoAllocTX) * ((nl + kNoAllocTY - 1) / kNoAllocTY);
+    if (nl > 4096 || nparts > kNoAllocMaxPartials) {
         set_last_error("residual_norm2_noalloc: n = " + std::to_string(n) +
                        " exceeds the fixed scratch (at most 4096 DOFs per axis)");
         return IGA2L_ERR_INVALID_ARG;

@@ -20,6 +20,8 @@ ERR_INVALID_ARG, ERR_CUDA, ERR_DEVICE_TIMEOUT, ERR_NONFINITE, ERR_UNSUPPORTED = 
 FP64, MIXED_FP32, MIXED_FP32_ALL, MIXED_TF32 = 0, 1, 2, 3
 SCHED_LATTICE, SCHED_TILE = 1, 2
 COARSE_EXACT, COARSE_VCYCLE = 0, 1
+RHS_COEFFS, RHS_IS_LOAD = 0, 1
+TEST_SKIP_OPERATOR_COPY = 1
 
 # Every exported symbol of include/iga2l.h.
 EXPORTS = (
@@ -30,14 +32,15 @@ EXPORTS = (
     "iga2l_host_bands", "iga2l_host_restriction", "iga2l_destroy", "iga2l_strerror",
     "iga2l_last_error", "iga2l_kernel_launches", "iga2l_residual_norm2_noalloc",
     "iga2l_cycles", "iga2l_unrolled_backward", "iga2l_bump_load", "iga2l_bump_grad",
-    "iga2l_assemble_batch", "iga2l_solve_batch", "iga2l_schedule_info",
+    "iga2l_assemble_batch", "iga2l_solve_batch", "iga2l_schedule_info", "iga2l_solve_load",
 )
 
 
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("schedule", ctypes.c_int), ("tile", ctypes.c_int),
                 ("period", ctypes.c_int), ("stride", ctypes.c_int), ("coarse", ctypes.c_int),
-                ("block_side", ctypes.c_int), ("max_cycles", ctypes.c_int), ("graphs", ctypes.c_int)]
+                ("block_side", ctypes.c_int), ("max_cycles", ctypes.c_int), ("graphs", ctypes.c_int),
+                ("rhs", ctypes.c_int), ("test_flags", ctypes.c_int), ("wait_budget_cycles", ctypes.c_longlong)]
 
 
 class IgaError(RuntimeError):
@@ -83,6 +86,8 @@ def load(build_if_missing: bool = True):
             "iga2l_cycle_adjoint": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
             "iga2l_solve": (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.c_int, _vp, _ip, _dp,
                                            _dp, _vp]),
+            "iga2l_solve_load": (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.c_int, _vp, _ip, _dp,
+                                                _dp, _vp]),
             "iga2l_adjoint_solve": (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.c_int, _vp,
                                                    _ip, _dp, _vp]),
             "iga2l_rhs_from_coeffs": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
@@ -249,16 +254,24 @@ class Solver:
                                                _stream(stream)))
 
     # --- solves -------------------------------------------------------------
-    def solve(self, b, u, tol=1e-8, max_cycles=0, stream=None):
-        """Cycles in place on u; returns (cycles, relres, history, converged)."""
+    def _solve(self, fn, rhs, u, tol, max_cycles, stream):
         cap = max_cycles if max_cycles > 0 else self.options.max_cycles
         hist = np.zeros(cap)
         cyc, rel = ctypes.c_int(0), ctypes.c_double(0.0)
-        rc = _check(self._lib.iga2l_solve(self._h, _ptr(b, numel=self.N), float(tol), cap,
-                                          _ptr(u, numel=self.N), ctypes.byref(cyc), ctypes.byref(rel),
-                                          hist.ctypes.data_as(_dp), _stream(stream)),
+        rc = _check(fn(self._h, _ptr(rhs, numel=self.N), float(tol), cap, _ptr(u, numel=self.N),
+                       ctypes.byref(cyc), ctypes.byref(rel), hist.ctypes.data_as(_dp), _stream(stream)),
                     allow_not_converged=True)
         return cyc.value, rel.value, hist[: cyc.value].copy(), rc == OK
+
+    def solve(self, f, u, tol=1e-8, max_cycles=0, stream=None):
+        """Solve A u = b with b = (f, phi_i) of the source given by its B-spline coefficients f
+        (or b itself on a handle built with rhs=RHS_IS_LOAD); cycles in place on u.
+        Returns (cycles, relres, history, converged)."""
+        return self._solve(self._lib.iga2l_solve, f, u, tol, max_cycles, stream)
+
+    def solve_load(self, b, u, tol=1e-8, max_cycles=0, stream=None):
+        """Solve A u = b for a load vector b given directly; as solve() otherwise."""
+        return self._solve(self._lib.iga2l_solve_load, b, u, tol, max_cycles, stream)
 
     def adjoint_solve(self, g, lam, tol=1e-8, max_cycles=0, stream=None):
         cyc, rel = ctypes.c_int(0), ctypes.c_double(0.0)
@@ -268,12 +281,13 @@ class Solver:
                     allow_not_converged=True)
         return cyc.value, rel.value, rc == OK
 
-    def solve_batch(self, b, u, tol=1e-8, max_cycles=0, stream=None):
-        """All problems of a batch handle to tol; returns (cycles[], relres[], converged)."""
+    def solve_batch(self, rhs, u, tol=1e-8, max_cycles=0, stream=None):
+        """All problems of a batch handle to tol; rhs holds every problem's coefficient vector f
+        (or load vector b with rhs=RHS_IS_LOAD).  Returns (cycles[], relres[], converged)."""
         nb = self.nbatch
         cyc = (ctypes.c_int * nb)()
         rel = np.zeros(nb)
-        rc = _check(self._lib.iga2l_solve_batch(self._h, _ptr(b, numel=nb * self.N), float(tol), int(max_cycles),
+        rc = _check(self._lib.iga2l_solve_batch(self._h, _ptr(rhs, numel=nb * self.N), float(tol), int(max_cycles),
                                                 _ptr(u, numel=nb * self.N), cyc, rel.ctypes.data_as(_dp),
                                                 _stream(stream)), allow_not_converged=True)
         return np.array(cyc[:], dtype=np.int64), rel, rc == OK

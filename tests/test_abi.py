@@ -36,6 +36,28 @@ def test_error_strings_and_options():
     assert o.coarse == iga2l.COARSE_VCYCLE and o.max_cycles == 100
 
 
+def test_options_struct_layout_matches_the_header(tmp_path):
+    """The binding's ctypes Options has the size and field offsets of iga2l_options."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    fields = [f for f, _ in iga2l.Options._fields_]
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "iga2l.h"\nint main(void){\n'
+                   '  printf("%zu\\n", sizeof(iga2l_options));\n'
+                   + "".join(f'  printf("%zu\\n", offsetof(iga2l_options, {f}));\n' for f in fields)
+                   + "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert out[0] == ctypes.sizeof(iga2l.Options)
+    assert out[1:] == [getattr(iga2l.Options, f).offset for f in fields]
+    o = iga2l.default_options()
+    assert o.rhs == iga2l.RHS_COEFFS and o.test_flags == 0 and o.wait_budget_cycles == 0
+
+
 def test_assemble_rejects_bad_arguments_before_touching_the_gpu():
     lib = iga2l.load()
     h = ctypes.c_void_p()
@@ -47,6 +69,10 @@ def test_assemble_rejects_bad_arguments_before_touching_the_gpu():
     assert lib.iga2l_assemble(2, 32, 2, ctypes.byref(bad), ctypes.byref(h)) == iga2l.ERR_INVALID_ARG
     bad = iga2l.default_options(period=6, stride=2)   # gcd(g, q) != 1
     assert lib.iga2l_assemble(2, 32, 2, ctypes.byref(bad), ctypes.byref(h)) == iga2l.ERR_INVALID_ARG
+    for kw in ({"rhs": 2}, {"test_flags": 8}, {"wait_budget_cycles": -5}):
+        bad = iga2l.default_options(**kw)
+        assert lib.iga2l_assemble(2, 32, 2, ctypes.byref(bad), ctypes.byref(h)) == iga2l.ERR_INVALID_ARG, kw
+        assert not h.value
 
 
 @pytest.mark.parametrize("p", [1, 2, 3, 4, 5])

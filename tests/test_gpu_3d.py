@@ -101,12 +101,12 @@ def test_mixed_3d_matches_fp64_gpu():
     A.rhs_from_coeffs(f, b)
     u0 = _dev(synth.initial_guess(A.N, 42))
     ua, ub = u0.clone(), u0.clone()
-    ca, ra, _, oka = A.solve(b, ua, tol=1e-8)
-    cb, rb, _, okb = B.solve(b, ub, tol=1e-8)
+    ca, ra, _, oka = A.solve_load(b, ua, tol=1e-8)
+    cb, rb, _, okb = B.solve_load(b, ub, tol=1e-8)
     assert oka and okb and abs(ca - cb) <= 1 and 3 <= ca <= 20
     ua, ub = u0.clone(), u0.clone()
-    A.solve(b, ua, tol=1e-12, max_cycles=60)
-    B.solve(b, ub, tol=1e-12, max_cycles=60)
+    A.solve_load(b, ua, tol=1e-12, max_cycles=60)
+    B.solve_load(b, ub, tol=1e-12, max_cycles=60)
     err = float(torch.linalg.norm(ua - ub) / torch.linalg.norm(ua))
     assert err <= 1e-8, err
 
@@ -159,11 +159,11 @@ def test_mixed_tile_3d_matches_oracle(oracle_mod, precision):
     S.rhs_from_coeffs(_dev(f), bd)
     b = _host(bd)
     ud = _dev(u0)
-    c, _, _, ok = S.solve(bd, ud, tol=1e-8, max_cycles=40)
+    c, _, _, ok = S.solve_load(bd, ud, tol=1e-8, max_cycles=40)
     uo, co, _, _, oko = O.solve(b, u0, tol=1e-8, maxc=40)
     assert ok and oko and abs(c - co) <= 1, (c, co)
     ud = _dev(u0)
-    S.solve(bd, ud, tol=1e-12, max_cycles=60)
+    S.solve_load(bd, ud, tol=1e-12, max_cycles=60)
     uo, _, _, _, oko = O.solve(b, u0, tol=1e-12, maxc=60)
     err = np.linalg.norm(_host(ud) - uo) / np.linalg.norm(uo)
     assert err <= 1e-8, err
@@ -184,7 +184,7 @@ def test_full_size_3d_solves(oracle_mod):
         S.rhs_from_coeffs(f, b)
         u0 = synth.initial_guess(S.N, 52)
         ud = _dev(u0)
-        cyc, rel, _, ok = S.solve(b, ud, tol=1e-8, max_cycles=40)
+        cyc, rel, _, ok = S.solve_load(b, ud, tol=1e-8, max_cycles=40)
         assert ok and rel <= 1e-8 and 3 <= cyc <= 20
         bh = _host(b)
         r_end = np.linalg.norm(O.residual(_host(ud), bh))

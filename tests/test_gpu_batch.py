@@ -19,7 +19,8 @@ COLOURING = {2: (5, 2), 3: (7, 2), 4: (7, 2)}
 def test_batch_equals_single_solves(precision, sched):
     p, m, nb = 3, 64, 6
     q, g = COLOURING[p]
-    B = iga2l.Solver(p, m, nbatch=nb, period=q, stride=g, precision=precision, schedule=sched)
+    B = iga2l.Solver(p, m, nbatch=nb, period=q, stride=g, precision=precision, schedule=sched,
+                     rhs=iga2l.RHS_IS_LOAD)
     S = iga2l.Solver(p, m, period=q, stride=g, precision=precision, schedule=sched)
     f = torch.tensor(np.concatenate([synth.coefficients(S.N, 100 + k) for k in range(nb)]), device="cuda")
     # problem 2 gets a zero right-hand side and guess: done before any cycle
@@ -35,7 +36,7 @@ def test_batch_equals_single_solves(precision, sched):
         sl = slice(k * S.N, (k + 1) * S.N)
         us = u0[sl].clone()
         bs = b[sl].clone()
-        c1, r1, _, ok1 = S.solve(bs, us, tol=1e-8)
+        c1, r1, _, ok1 = S.solve_load(bs, us, tol=1e-8)
         assert ok1 and c1 == cyc[k], (k, c1, cyc[k])
         assert torch.equal(us, ub[sl]), k
         if c1:
@@ -49,7 +50,7 @@ def test_uneven_groups_match_single_solves():
     u0 = [torch.tensor(synth.initial_guess((m + p - 2) ** 2, 400 + i), device="cuda") for i, (p, m) in enumerate(problems)]
     b = BS.rhs_from_coeffs(BS.pack(f))
     u = BS.pack(u0)
-    cycles, relres, ok = BS.solve(b, u, tol=1e-8)
+    cycles, relres, ok = BS.solve(BS.pack(f), u, tol=1e-8)   # coefficients f (the default)
     torch.cuda.synchronize()
     assert ok
     ub = BS.unpack(u)
@@ -60,7 +61,7 @@ def test_uneven_groups_match_single_solves():
         S = iga2l.Solver(p, m, period=q, stride=gg, precision=iga2l.MIXED_FP32, schedule=g["schedule"])
         for i in g["members"]:
             us = u0[i].clone()
-            c1, r1, _, ok1 = S.solve(bb[i].clone(), us, tol=1e-8)
+            c1, r1, _, ok1 = S.solve_load(bb[i].clone(), us, tol=1e-8)
             assert ok1 and c1 == cycles[i] and torch.equal(us, ub[i]), (i, c1, cycles[i])
         S.close()
     BS.close()
@@ -85,7 +86,7 @@ def test_concurrent_handles_match_sequential(precision):
     seq = []
     for S, b, u0 in zip(solvers, bs, u0s):
         u = u0.clone()
-        c, rel, _, ok = S.solve(b, u, tol=1e-8)
+        c, rel, _, ok = S.solve_load(b, u, tol=1e-8)
         assert ok
         seq.append((u, c, rel))
     torch.cuda.synchronize()
@@ -95,7 +96,7 @@ def test_concurrent_handles_match_sequential(precision):
     out = [None] * len(probs)
 
     def run(k):
-        out[k] = solvers[k].solve(bs[k], us[k], tol=1e-8, stream=streams[k])
+        out[k] = solvers[k].solve_load(bs[k], us[k], tol=1e-8, stream=streams[k])
 
     threads = [threading.Thread(target=run, args=(k,)) for k in range(len(probs))]
     for t in threads:
@@ -124,7 +125,7 @@ def test_full_size_batch_residuals(oracle_mod):
           for i, (p, m) in enumerate(problems)]
     b = BS.rhs_from_coeffs(BS.pack(f))
     u = BS.pack(u0)
-    cycles, relres, ok = BS.solve(b, u, tol=1e-8)
+    cycles, relres, ok = BS.solve(BS.pack(f), u, tol=1e-8)
     assert ok and max(cycles) <= 20 and max(relres) <= 1e-8
     bs, us = BS.unpack(b), BS.unpack(u)
     oracles = {}

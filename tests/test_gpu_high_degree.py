@@ -123,7 +123,7 @@ def test_solve_counts_and_mixed_high_p(oracle_mod, p):
     S.rhs_from_coeffs(_dev(f), bd)
     b = _host(bd)
     ud = _dev(u0)
-    cyc, rel, hist, ok = S.solve(bd, ud, tol=1e-8, max_cycles=40)
+    cyc, rel, hist, ok = S.solve_load(bd, ud, tol=1e-8, max_cycles=40)
     uo, cyc_o, rel_o, hist_o, ok_o = O.solve(b, u0, tol=1e-8, maxc=40)
     assert ok and ok_o and cyc == cyc_o
     assert np.linalg.norm(_host(ud) - uo) <= fp64_tol(oracle_mod, p, m) * np.linalg.norm(uo)
@@ -136,11 +136,11 @@ def test_solve_counts_and_mixed_high_p(oracle_mod, p):
     for prec, sched in modes:
         X, _ = _pair(oracle_mod, p, m, sched=sched, precision=prec)
         um = _dev(u0)
-        c, _, _, okm = X.solve(bd, um, tol=1e-8, max_cycles=40)
+        c, _, _, okm = X.solve_load(bd, um, tol=1e-8, max_cycles=40)
         if sched == "lattice":
             assert okm and abs(c - cyc_o) <= 1, (prec, c, cyc_o)
         um = _dev(u0)
-        c, _, _, okm = X.solve(bd, um, tol=1e-15, max_cycles=200)
+        c, _, _, okm = X.solve_load(bd, um, tol=1e-15, max_cycles=200)
         assert okm
         err = np.linalg.norm(_host(um) - ref) / np.linalg.norm(ref)
         assert err <= 1e-8, (prec, err)
@@ -173,7 +173,7 @@ def test_full_size_high_degree_solves(oracle_mod, p):
         S.rhs_from_coeffs(f, b)
         u0 = synth.initial_guess(S.N, 70 + p)
         ud = _dev(u0)
-        cyc, rel, _, ok = S.solve(b, ud, tol=1e-8, max_cycles=40)
+        cyc, rel, _, ok = S.solve_load(b, ud, tol=1e-8, max_cycles=40)
         assert ok and rel <= 1e-8 and 3 <= cyc <= 20
         bh = _host(b)
         r_end = np.linalg.norm(O.residual(_host(ud), bh))

@@ -84,7 +84,7 @@ def test_mixed_refinement_reaches_fp64_solution(oracle_mod, p, precision, sched)
     assert ok_s
     # the metric's stopping rule
     ud = _dev(u0)
-    cyc, rel, hist, ok = S.solve(bd, ud, tol=1e-8, max_cycles=40)
+    cyc, rel, hist, ok = S.solve_load(bd, ud, tol=1e-8, max_cycles=40)
     uo, cyc_o, rel_o, hist_o, ok_o = O.solve(b, u0, tol=1e-8, maxc=40)
     assert ok and ok_o and abs(cyc - cyc_o) <= 1, (cyc, cyc_o)
     r = np.linalg.norm(O.residual(_host(ud), b)) / np.linalg.norm(O.residual(u0, b))
@@ -96,7 +96,7 @@ def test_mixed_refinement_reaches_fp64_solution(oracle_mod, p, precision, sched)
     assert err_mixed <= factor * err_fp64 + 1e-14 * np.linalg.norm(ustar)
     # refinement continued to a 1e-12 residual
     ud = _dev(u0)
-    cyc, rel, hist, ok = S.solve(bd, ud, tol=1e-12, max_cycles=60)
+    cyc, rel, hist, ok = S.solve_load(bd, ud, tol=1e-12, max_cycles=60)
     uo, cyc_o, rel_o, hist_o, ok_o = O.solve(b, u0, tol=1e-12, maxc=60)
     assert ok and ok_o and abs(cyc - cyc_o) <= 1
     err = np.linalg.norm(_host(ud) - uo) / np.linalg.norm(uo)
@@ -115,12 +115,12 @@ def test_mixed_full_size_matches_fp64_gpu():
     A.rhs_from_coeffs(f, b)
     u0 = _dev(synth.initial_guess(A.N, 8))
     ua, ub = u0.clone(), u0.clone()
-    ca, ra, _, oka = A.solve(b, ua, tol=1e-8)
-    cb, rb, _, okb = B.solve(b, ub, tol=1e-8)
+    ca, ra, _, oka = A.solve_load(b, ua, tol=1e-8)
+    cb, rb, _, okb = B.solve_load(b, ub, tol=1e-8)
     assert oka and okb and abs(ca - cb) <= 1
     ua, ub = u0.clone(), u0.clone()
-    A.solve(b, ua, tol=1e-12, max_cycles=60)
-    B.solve(b, ub, tol=1e-12, max_cycles=60)
+    A.solve_load(b, ua, tol=1e-12, max_cycles=60)
+    B.solve_load(b, ub, tol=1e-12, max_cycles=60)
     err = float(torch.linalg.norm(ua - ub) / torch.linalg.norm(ua))
     assert err <= 1e-8, err
 

@@ -151,11 +151,40 @@ def test_solve_matches_oracle_counts(oracle_mod, p):
     b = (M @ f.reshape(S.n, S.n) @ M.T).ravel()
     _close(_host(bd), b)
     ud = _dev(u0)
-    cyc, rel, hist, ok = S.solve(bd, ud, tol=1e-8, max_cycles=40)
+    cyc, rel, hist, ok = S.solve_load(bd, ud, tol=1e-8, max_cycles=40)
     uo, cyc_o, rel_o, hist_o, ok_o = O.solve(b, u0, tol=1e-8, maxc=40)
     assert ok and ok_o and cyc == cyc_o
     assert np.allclose(hist, hist_o, rtol=1e-6, atol=0)
     assert np.linalg.norm(_host(ud) - uo) <= TOL * np.linalg.norm(uo)
+
+
+@pytest.mark.parametrize("p", [2, 5])
+def test_solve_takes_coefficients(oracle_mod, p):
+    """iga2l_solve(f): the right-hand side is the source's B-spline coefficient vector f,
+    b = (f, phi_i) = (M x M) f is formed by the library (Section 2); cycle counts and the
+    converged solution match the oracle solving with its own (M x M) f, and the iterates
+    equal iga2l_solve_load given the library's b bit for bit."""
+    m = 96
+    S, O = _pair(oracle_mod, p, m)
+    f, u0 = _inputs(S.N, 900 + p)
+    K, M = oracle_mod.assemble_1d(p, m)
+    b = (M @ f.reshape(S.n, S.n) @ M.T).ravel()
+    ud = _dev(u0)
+    cyc, rel, hist, ok = S.solve(_dev(f), ud, tol=1e-8, max_cycles=40)
+    uo, cyc_o, rel_o, hist_o, ok_o = O.solve(b, u0, tol=1e-8, maxc=40)
+    assert ok and ok_o and cyc == cyc_o
+    assert np.allclose(hist, hist_o, rtol=1e-6, atol=0)
+    assert np.linalg.norm(_host(ud) - uo) <= TOL * np.linalg.norm(uo)
+    bd = torch.empty(S.N, dtype=torch.float64, device="cuda")
+    S.rhs_from_coeffs(_dev(f), bd)
+    ul = _dev(u0)
+    cl, rl, hl, okl = S.solve_load(bd, ul, tol=1e-8, max_cycles=40)
+    assert okl and cl == cyc and np.array_equal(hl, hist) and torch.equal(ul, ud)
+    # a handle built with rhs = IGA2L_RHS_IS_LOAD reads b from iga2l_solve
+    Sl = iga2l.Solver(p, m, period=S.period, stride=S.stride, rhs=iga2l.RHS_IS_LOAD)
+    ub = _dev(u0)
+    cb, rb, hb, okb = Sl.solve(bd, ub, tol=1e-8, max_cycles=40)
+    assert okb and cb == cyc and np.array_equal(hb, hist) and torch.equal(ub, ud)
 
 
 def test_adjoint_cycle_identity(oracle_mod):
@@ -200,7 +229,7 @@ def test_full_size_cycle_and_solve(oracle_mod, p):
         uo = O.cycle(u0, b)
         assert np.linalg.norm(_host(ud) - uo) <= TOL * np.linalg.norm(uo)
     ud = _dev(u0)
-    cyc, rel, hist, ok = S.solve(bd, ud, tol=1e-8, max_cycles=40)
+    cyc, rel, hist, ok = S.solve_load(bd, ud, tol=1e-8, max_cycles=40)
     assert ok and rel <= 1e-8 and 3 <= cyc <= 20
     r_end = np.linalg.norm(O.residual(_host(ud), b))
     r_0 = np.linalg.norm(O.residual(u0, b))
@@ -219,10 +248,10 @@ def test_invalid_calls_raise_before_launch():
     b = torch.zeros(S.N, dtype=torch.float64, device="cuda")
     b[3] = float("nan")
     with pytest.raises(iga2l.IgaError) as ei:
-        S.solve(b, torch.zeros_like(b))
+        S.solve_load(b, torch.zeros_like(b))
     assert ei.value.code == iga2l.ERR_NONFINITE
     # zero right-hand side and guess: converged with zero cycles
-    cyc, rel, hist, ok = S.solve(torch.zeros_like(b), torch.zeros_like(b))
+    cyc, rel, hist, ok = S.solve_load(torch.zeros_like(b), torch.zeros_like(b))
     assert ok and cyc == 0
 
 
@@ -239,8 +268,8 @@ def test_graph_replay_matches_plain_launches(oracle_mod):
         B.cycle(ub, b)
     assert torch.equal(ua, ub)
     ua2, ub2 = _dev(u0), _dev(u0)
-    ca, ra, ha, _ = A.solve(b, ua2, tol=1e-9)
-    cb, rb, hb, _ = B.solve(b, ub2, tol=1e-9)
+    ca, ra, ha, _ = A.solve_load(b, ua2, tol=1e-9)
+    cb, rb, hb, _ = B.solve_load(b, ub2, tol=1e-9)
     assert ca == cb and np.array_equal(ha, hb) and torch.equal(ua2, ub2)
     n0 = iga2l.kernel_launches()
     A.cycle(ua, b)

@@ -40,3 +40,21 @@ def test_two_rank_max_and_rank0_only():
     out = mgr.dict()
     mp.spawn(_worker, args=(ws, _free_port(), out), nprocs=ws, join=True)
     assert out[0] == 11.0 and out[1] == 11.0
+
+
+def test_bench_gpus_2_starts_two_ranks_itself():
+    """python bench.py --gpus 2 without a torchrun environment launches 2 ranks (here on
+    CPU with gloo, no GPU work) and rank 0 reports n_gpus = 2."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = {k: v for k, v in os.environ.items() if k not in ("WORLD_SIZE", "RANK", "LOCAL_RANK",
+                                                               "MASTER_ADDR", "MASTER_PORT")}
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    res = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--gpus", "2", "--launch-check"],
+                         capture_output=True, text=True, timeout=300, env=env, cwd=root)
+    assert res.returncode == 0, res.stderr[-2000:]
+    lines = [json.loads(x) for x in res.stdout.splitlines() if x.startswith("{")]
+    assert len(lines) == 1, res.stdout
+    assert lines[0]["n_gpus"] == 2 and lines[0]["ms_per_step"] == 2.0 and lines[0]["backend"] == "gloo"
