@@ -643,10 +643,15 @@ def run_profile_step(args):
     m = args.profile_m or (128 if dim == 3 else M_ELEM)
     prec = {"fp64": iga2l.FP64, "mixed": iga2l.MIXED_FP32, "mixed_all": iga2l.MIXED_FP32_ALL,
             "mixed_tf32": iga2l.MIXED_TF32}[args.profile_precision]
-    sched = iga2l.SCHED_LATTICE if (prec in (iga2l.FP64, iga2l.MIXED_TF32) or dim == 3) else iga2l.SCHED_TILE
+    if args.profile_schedule:
+        sched = iga2l.SCHED_TILE if args.profile_schedule == "tile" else iga2l.SCHED_LATTICE
+    else:
+        sched = iga2l.SCHED_LATTICE if (prec in (iga2l.FP64, iga2l.MIXED_TF32) or dim == 3) else iga2l.SCHED_TILE
+    sweep = {"auto": iga2l.SWEEP_AUTO, "per_colour": iga2l.SWEEP_PER_COLOUR,
+             "persistent": iga2l.SWEEP_PERSISTENT}[args.profile_sweep]
     for p in degrees:
         col = {"period": COLOURING[p][0], "stride": COLOURING[p][1]} if p in COLOURING else {}   # else the default
-        S = iga2l.Solver(p, m, dim=dim, precision=prec, schedule=sched, graphs=0, **col)
+        S = iga2l.Solver(p, m, dim=dim, precision=prec, schedule=sched, graphs=0, sweep=sweep, **col)
         sf, su = seeds(p)
         f = torch.tensor(synth.coefficients(S.N, sf), device=dev)
         u0 = torch.tensor(synth.initial_guess(S.N, su), device=dev)
@@ -719,6 +724,10 @@ def main():
     ap.add_argument("--profile-p", type=int, default=0)
     ap.add_argument("--profile-precision", choices=["fp64", "mixed", "mixed_all", "mixed_tf32"], default="fp64",
                     help="form profiled by --profile-step (the benchmark's schedule for it)")
+    ap.add_argument("--profile-schedule", choices=["lattice", "tile"], default=None,
+                    help="schedule profiled by --profile-step (default: the benchmark's for the form)")
+    ap.add_argument("--profile-sweep", choices=["auto", "per_colour", "persistent"], default="auto",
+                    help="FP32 inner sweep kernel profiled by --profile-step")
     ap.add_argument("--launch-check", action="store_true",
                     help="start the ranks and report the world size, without GPU work (launcher test)")
     argv = sys.argv[1:]

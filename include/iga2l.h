@@ -68,11 +68,24 @@ extern "C" {
  * load vector b_p itself */
 #define IGA2L_RHS_COEFFS 0
 #define IGA2L_RHS_IS_LOAD 1
+/* sweep: how the Schwarz step of the FP32 inner cycle runs in the LATTICE order.  AUTO
+ * picks the persistent form for 5x5 and 7x7 blocks where it is available (2D
+ * single-problem handles with IGA2L_MIXED_FP32 or IGA2L_MIXED_FP32_ALL) and one launch
+ * per colour elsewhere;
+ * PERSISTENT asks for it (IGA2L_ERR_UNSUPPORTED where it is not available).  Both give
+ * the same iterates up to FP32 rounding order. */
+#define IGA2L_SWEEP_AUTO 0
+#define IGA2L_SWEEP_PER_COLOUR 1
+#define IGA2L_SWEEP_PERSISTENT 2
 /* test_flags bits (testing the error paths only; never set in production use):
  * the tensor-core colour kernel does not issue the bulk copy of its block operator, so
  * its bounded wait for that copy runs out (no copy and no MMA is ever in flight), the
  * kernel skips its blocks and the call returns IGA2L_ERR_DEVICE_TIMEOUT */
 #define IGA2L_TEST_SKIP_OPERATOR_COPY 1
+/* the persistent sweep's first CTA never raises its progress counter, so its neighbours'
+ * bounded waits run out (nothing asynchronous is in flight); the call returns
+ * IGA2L_ERR_DEVICE_TIMEOUT */
+#define IGA2L_TEST_WITHHOLD_PROGRESS 2
 
 typedef struct iga2l_solver *iga2l_handle;
 
@@ -89,6 +102,10 @@ typedef struct {
     int graphs;      /* 1: replay cycles as captured CUDA graphs (default); 0: plain launches */
     int rhs;         /* IGA2L_RHS_COEFFS (default) or IGA2L_RHS_IS_LOAD: what iga2l_solve and
                         iga2l_solve_batch read from their right-hand-side argument */
+    int sweep;       /* IGA2L_SWEEP_AUTO (default), _PER_COLOUR or _PERSISTENT: the FP32 inner
+                        sweep as one persistent launch (all colours; every CTA owns a region,
+                        neighbours exchange their boundary bands through L2 under bounded
+                        waits) or one launch per colour */
     int test_flags;  /* 0, or IGA2L_TEST_* bits (error-path tests only) */
     long long wait_budget_cycles;   /* SM clock cycles a bounded device wait may spin before the
                         kernel gives up, records the failure and returns (the call then reports

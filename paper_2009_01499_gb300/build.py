@@ -36,7 +36,8 @@ def sources():
 def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
-    deps = sources() + glob.glob(os.path.join(CSRC, "*.h")) + [os.path.join(ROOT, "include", "iga2l.h")]
+    deps = (sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh"))
+            + [os.path.join(ROOT, "include", "iga2l.h")])
     return max(os.path.getmtime(p) for p in deps) > os.path.getmtime(LIB)
 
 

@@ -52,6 +52,7 @@ struct iga2l_solver : public Solver {
     };
     std::vector<SolveGraph> solve_graphs;
     bool solve_graph_failed = false;   // the driver refused one: use the host-driven loop
+    bool cycle_graph_failed = false;   // the driver refused to capture a cycle: plain launches
     SolveCtl *ctl = nullptr, *ctl_host = nullptr;   // device / pinned host copy
     double *dev_hist = nullptr, *host_hist = nullptr;
 };
@@ -210,7 +211,8 @@ int enqueue_cycle(iga2l_handle h, double *u, const double *b, cudaStream_t st, b
 int run_cycle_graph(iga2l_handle h, double *u, const double *b, cudaStream_t st, bool adjoint, bool norm)
 {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (!h->opt.graphs || cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+    if (!h->opt.graphs || h->cycle_graph_failed || cudaStreamIsCapturing(st, &cs) != cudaSuccess ||
+        cs != cudaStreamCaptureStatusNone)
         return enqueue_cycle(h, u, b, st, adjoint, norm);   // plain launches (or the caller is capturing)
     const int kind = (adjoint ? 1 : 0) | (norm ? 2 : 0) | (h->mx.enabled ? 4 : 0);
     iga2l_solver::CycleGraph *g = nullptr;
@@ -227,8 +229,13 @@ int run_cycle_graph(iga2l_handle h, double *u, const double *b, cudaStream_t st,
         g_capturing = false;
         cudaGraph_t graph = nullptr;
         e = cudaStreamEndCapture(h->cap_stream, &graph);
-        if (rc != IGA2L_OK) { if (graph) cudaGraphDestroy(graph); return rc; }
-        if (e != cudaSuccess) return cuda_fail(e, "end capture");
+        if (rc != IGA2L_OK || e != cudaSuccess) {
+            // the driver refused to capture one of the cycle's launches: plain launches from now on
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            h->cycle_graph_failed = true;
+            return enqueue_cycle(h, u, b, st, adjoint, norm);
+        }
         size_t nn = 0;
         cudaGraphGetNodes(graph, nullptr, &nn);
         std::vector<cudaGraphNode_t> nodes(nn);
@@ -420,13 +427,16 @@ int solve_impl(iga2l_handle h, const double *b, double tol, int max_cycles, doub
     if (cycles) *cycles = k;
     if (relres) *relres = rel;
     if (status != IGA2L_OK) g_last_error = "cycle cap reached";
-    if (h->mx.tc_status) {   // a tensor-core wait that gave up left its blocks uncorrected
+    if (h->wait_status) {   // a bounded device wait that gave up left blocks uncorrected
         int bad = 0;
-        cudaError_t e = cudaMemcpy(&bad, h->mx.tc_status, sizeof(int), cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) return cuda_fail(e, "tensor-core status");
+        cudaError_t e = cudaMemcpyAsync(&bad, h->wait_status, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "wait status");
         if (bad) {
-            cudaMemset(h->mx.tc_status, 0, sizeof(int));
-            return fail(IGA2L_ERR_DEVICE_TIMEOUT, "a tensor-core MMA wait gave up");
+            e = cudaMemsetAsync(h->wait_status, 0, sizeof(int), st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) return cuda_fail(e, "wait status");
+            return fail(IGA2L_ERR_DEVICE_TIMEOUT, "a bounded device wait gave up (the results are not valid)");
         }
     }
     return status;
@@ -448,6 +458,7 @@ void iga2l_default_options(iga2l_options *opt)
     opt->max_cycles = 100;
     opt->graphs = 1;
     opt->rhs = IGA2L_RHS_COEFFS;
+    opt->sweep = IGA2L_SWEEP_AUTO;
     opt->test_flags = 0;
     opt->wait_budget_cycles = 0;
 }
@@ -483,9 +494,12 @@ static int assemble_impl(int p, int m, int dim, int nbatch, bool batch, const ig
     }
     if (opt.coarse != IGA2L_COARSE_VCYCLE && opt.coarse != IGA2L_COARSE_EXACT)
         return fail(IGA2L_ERR_INVALID_ARG, "unknown coarse solver");
+    if (opt.sweep != IGA2L_SWEEP_AUTO && opt.sweep != IGA2L_SWEEP_PER_COLOUR && opt.sweep != IGA2L_SWEEP_PERSISTENT)
+        return fail(IGA2L_ERR_INVALID_ARG, "unknown sweep kernel choice");
     if (opt.rhs != IGA2L_RHS_COEFFS && opt.rhs != IGA2L_RHS_IS_LOAD)
         return fail(IGA2L_ERR_INVALID_ARG, "rhs must be IGA2L_RHS_COEFFS or IGA2L_RHS_IS_LOAD");
-    if (opt.test_flags & ~IGA2L_TEST_SKIP_OPERATOR_COPY) return fail(IGA2L_ERR_INVALID_ARG, "unknown test flag");
+    if (opt.test_flags & ~(IGA2L_TEST_SKIP_OPERATOR_COPY | IGA2L_TEST_WITHHOLD_PROGRESS))
+        return fail(IGA2L_ERR_INVALID_ARG, "unknown test flag");
     if (opt.wait_budget_cycles < 0) return fail(IGA2L_ERR_INVALID_ARG, "wait_budget_cycles must be >= 0");
     if (opt.wait_budget_cycles == 0) opt.wait_budget_cycles = 1LL << 31;
     const int s = opt.block_side > 0 ? opt.block_side : default_block_side(p);
@@ -630,7 +644,8 @@ static int assemble_impl(int p, int m, int dim, int nbatch, bool batch, const ig
             k1[a] = ref.Kb[(size_t)xr * W + a] / mref;   // h K_row, h = 1 / mref
             m1[a] = ref.Mb[(size_t)xr * W + a] * mref;   // M_row / h
         }
-        if ((ce = upload_interior_rows(p, k1.data(), m1.data())) != cudaSuccess) {
+        if ((ce = upload_interior_rows(p, k1.data(), m1.data())) != cudaSuccess ||
+            (ce = upload_persist_rows(p, k1.data(), m1.data())) != cudaSuccess) {
             release(S);
             return cuda_fail(ce, "constant 1D rows upload");
         }
@@ -660,6 +675,15 @@ static int assemble_impl(int p, int m, int dim, int nbatch, bool batch, const ig
         (ce = alloc(S, &S->part, B * S->npart)) != cudaSuccess || (ce = alloc(S, &S->dev_norm, B)) != cudaSuccess) {
         release(S);
         return cuda_fail(ce, "workspace allocation");
+    }
+    {   // status word of the bounded device waits
+        void *pw = nullptr;
+        if ((ce = cudaMalloc(&pw, sizeof(int))) != cudaSuccess ||
+            (S->allocs.push_back(pw), ce = cudaMemset(pw, 0, sizeof(int))) != cudaSuccess) {
+            release(S);
+            return cuda_fail(ce, "status word");
+        }
+        S->wait_status = static_cast<int *>(pw);
     }
     {   // completion counters of the fused residual norm, zero between launches
         void *pc = nullptr;
@@ -767,15 +791,37 @@ static int assemble_impl(int p, int m, int dim, int nbatch, bool batch, const ig
                                      binv.begin() + (size_t)(interior + 1) * SS * SS);
             std::vector<float> g;
             build_gtc(*S, ainv, g, X.gtc_n, X.gtc_k);
-            void *pst = nullptr;
-            if ((ce = upload(S, &X.gtc, g)) != cudaSuccess || (ce = cudaMalloc(&pst, sizeof(int))) != cudaSuccess ||
-                (S->allocs.push_back(pst), ce = cudaMemset(pst, 0, sizeof(int))) != cudaSuccess) {
+            if ((ce = upload(S, &X.gtc, g)) != cudaSuccess) {
                 release(S);
                 return cuda_fail(ce, "tensor-core operator upload");
             }
-            X.tc_status = static_cast<int *>(pst);
         }
         X.enabled = true;
+        // the persistent LATTICE sweep of the inner cycle (one launch per sweep)
+        if (dim == 2 && !batch && opt.schedule == IGA2L_SCHED_LATTICE && opt.precision != IGA2L_MIXED_TF32 &&
+            opt.sweep != IGA2L_SWEEP_PER_COLOUR) {
+            void *pp = nullptr;
+            if ((ce = cudaMalloc(&pp, sizeof(unsigned int) * 4096)) != cudaSuccess) {
+                release(S);
+                return cuda_fail(ce, "progress counters");
+            }
+            S->allocs.push_back(pp);
+            S->progress = static_cast<unsigned int *>(pp);
+            if (!persist_setup(*S) && opt.sweep == IGA2L_SWEEP_PERSISTENT) {
+                release(S);
+                return fail(IGA2L_ERR_UNSUPPORTED, "no resident launch plan for the persistent sweep");
+            }
+            // AUTO: measured at 1024^2 (GB300), one persistent launch beats one launch per
+            // colour for 5x5 and 7x7 blocks (q^2 >= 100 colours: 10.9 against 12.9 ms per p = 5
+            // solve) and loses for 3x3 blocks (its colour-to-colour hand-off between
+            // neighbouring CTAs costs about 4.4 us, more than a launch)
+            if (opt.sweep == IGA2L_SWEEP_AUTO && S->s < 5) S->pgx = 0;
+        }
+    }
+    if (opt.sweep == IGA2L_SWEEP_PERSISTENT && S->pgx == 0) {
+        release(S);
+        return fail(IGA2L_ERR_UNSUPPORTED,
+                    "the persistent sweep needs a 2D single-problem handle, IGA2L_MIXED_FP32 or _FP32_ALL, LATTICE");
     }
     if (batch) {
         void *pa = nullptr, *pc = nullptr, *pn = nullptr;

@@ -65,7 +65,6 @@ struct MixedState {
     // to TF32) in the tensor-core operand layout, gtc_n x gtc_k (block DOFs x [b_B; u_patch])
     float *gtc = nullptr;
     int gtc_n = 0, gtc_k = 0;
-    int *tc_status = nullptr;   // device: bounded waits of the tensor-core kernel that gave up
     // IGA2L_MIXED_FP32 / TF32: the FP64 block inverses as unevaluated pairs binv + binv_lo
     // (binv_lo = fl32(B - binv)), for the compensated FP32 application in the TILE kernel
     float *binv_lo = nullptr;
@@ -117,6 +116,10 @@ struct Solver {
     double *adj1 = nullptr, *adj2 = nullptr, *adj3 = nullptr;   // backward workspace (N each)
     double *gbuf = nullptr;      // per-bump 1D loads and their centre derivatives
     int gcap = 0;                // bumps gbuf can hold
+    unsigned int *progress = nullptr;   // persistent sweep: colours finished per CTA
+    int *wait_status = nullptr;         // device: bounded waits that gave up (tensor-core, persistent)
+    int pgx = 0, pgy = 0, prx = 0, pry = 0;   // persistent sweep: regions per axis, largest sides
+    unsigned psmem = 0;                       // (pgx = 0: per-colour launches)
     std::vector<void *> allocs;
     // FP64 inverses of the boundary block classes for the FP32 Schwarz kernels, or null
     // when those are applied in FP32 too (IGA2L_MIXED_FP32_ALL)
@@ -261,6 +264,11 @@ cudaError_t launch3d_inner_update(const Solver &S, double *u, cudaStream_t st);
 void tc_interior_rect(const Solver &S, int o, int nb, int &i0, int &ni);
 cudaError_t launch_schwarz_tc(const Solver &S, int ox, int oy, int ix0, int iy0, int nix, int niy, const float *b,
                               float *u, cudaStream_t st);
+// persistent LATTICE sweep of the FP32 inner cycle (kernels_persist.cu): plans the launch
+// (false: not available for this handle, per-colour launches are used) and runs one sweep
+bool persist_setup(Solver &S);
+cudaError_t launch_schwarz_persist(const Solver &S, float *u, const float *b, bool reverse, cudaStream_t st);
+cudaError_t upload_persist_rows(int p, const double *k1, const double *m1);
 // host: G of the interior block in the operand layout (kernels_tc.cu)
 void build_gtc(const Solver &S, const std::vector<double> &binv_interior, std::vector<float> &g, int &nrows,
                int &kcols);

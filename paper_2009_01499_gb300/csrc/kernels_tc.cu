@@ -260,7 +260,7 @@ cudaError_t launch_tc_p(const Solver &S_, int ox, int oy, int ix0, int iy0, int 
     if (bpc > G::M) bpc = G::M;
     if (bpc < 1) bpc = 1;
     k_schwarz_tc<P, S><<<(nblk + bpc - 1) / bpc, 512, G::smem, st>>>(S_.n, S_.q, ox, oy, ix0, iy0, nix, niy, bpc,
-                                                                     S_.mx.gtc, b, u, S_.mx.tc_status,
+                                                                     S_.mx.gtc, b, u, S_.wait_status,
                                                                      S_.opt.wait_budget_cycles,
                                                                      (S_.opt.test_flags & IGA2L_TEST_SKIP_OPERATOR_COPY) != 0);
     count_launches(1);

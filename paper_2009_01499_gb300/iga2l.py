@@ -21,7 +21,8 @@ FP64, MIXED_FP32, MIXED_FP32_ALL, MIXED_TF32 = 0, 1, 2, 3
 SCHED_LATTICE, SCHED_TILE = 1, 2
 COARSE_EXACT, COARSE_VCYCLE = 0, 1
 RHS_COEFFS, RHS_IS_LOAD = 0, 1
-TEST_SKIP_OPERATOR_COPY = 1
+SWEEP_AUTO, SWEEP_PER_COLOUR, SWEEP_PERSISTENT = 0, 1, 2
+TEST_SKIP_OPERATOR_COPY, TEST_WITHHOLD_PROGRESS = 1, 2
 
 # Every exported symbol of include/iga2l.h.
 EXPORTS = (
@@ -40,7 +41,7 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("schedule", ctypes.c_int), ("tile", ctypes.c_int),
                 ("period", ctypes.c_int), ("stride", ctypes.c_int), ("coarse", ctypes.c_int),
                 ("block_side", ctypes.c_int), ("max_cycles", ctypes.c_int), ("graphs", ctypes.c_int),
-                ("rhs", ctypes.c_int), ("test_flags", ctypes.c_int), ("wait_budget_cycles", ctypes.c_longlong)]
+                ("rhs", ctypes.c_int), ("sweep", ctypes.c_int), ("test_flags", ctypes.c_int), ("wait_budget_cycles", ctypes.c_longlong)]
 
 
 class IgaError(RuntimeError):

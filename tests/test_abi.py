@@ -69,7 +69,7 @@ def test_assemble_rejects_bad_arguments_before_touching_the_gpu():
     assert lib.iga2l_assemble(2, 32, 2, ctypes.byref(bad), ctypes.byref(h)) == iga2l.ERR_INVALID_ARG
     bad = iga2l.default_options(period=6, stride=2)   # gcd(g, q) != 1
     assert lib.iga2l_assemble(2, 32, 2, ctypes.byref(bad), ctypes.byref(h)) == iga2l.ERR_INVALID_ARG
-    for kw in ({"rhs": 2}, {"test_flags": 8}, {"wait_budget_cycles": -5}):
+    for kw in ({"rhs": 2}, {"test_flags": 8}, {"wait_budget_cycles": -5}, {"sweep": 3}):
         bad = iga2l.default_options(**kw)
         assert lib.iga2l_assemble(2, 32, 2, ctypes.byref(bad), ctypes.byref(h)) == iga2l.ERR_INVALID_ARG, kw
         assert not h.value

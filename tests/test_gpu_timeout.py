@@ -44,6 +44,27 @@ def test_missing_operator_copy_times_out_and_context_survives(oracle_mod):
     T.close()
 
 
+def test_withheld_progress_times_out_and_context_survives():
+    """The persistent sweep: CTA 0 never raises its progress counter, so its neighbours'
+    bounded waits give up, every CTA leaves its colour loop, and the solve reports the
+    timeout; a normal solve right after it converges."""
+    p, m = 3, 64
+    S = iga2l.Solver(p, m, precision=iga2l.MIXED_FP32, sweep=iga2l.SWEEP_PERSISTENT,
+                     test_flags=iga2l.TEST_WITHHOLD_PROGRESS, wait_budget_cycles=200000)
+    f = torch.tensor(synth.coefficients(S.N, 15), device="cuda")
+    u = torch.tensor(synth.initial_guess(S.N, 16), device="cuda")
+    with pytest.raises(iga2l.IgaError) as ei:
+        S.solve(f, u, tol=1e-8, max_cycles=2)
+    assert ei.value.code == iga2l.ERR_DEVICE_TIMEOUT
+    S.close()
+    torch.cuda.synchronize()
+    T = iga2l.Solver(p, m, precision=iga2l.MIXED_FP32, sweep=iga2l.SWEEP_PERSISTENT)
+    u = torch.tensor(synth.initial_guess(T.N, 16), device="cuda")
+    cyc, rel, _, ok = T.solve(f, u, tol=1e-8, max_cycles=40)
+    assert ok and rel <= 1e-8
+    T.close()
+
+
 def test_wait_budget_is_validated():
     with pytest.raises(iga2l.IgaError) as ei:
         iga2l.Solver(2, 48, wait_budget_cycles=-1)
