@@ -102,6 +102,9 @@ typedef struct {
     int graphs;      /* 1: replay cycles as captured CUDA graphs (default); 0: plain launches */
     int rhs;         /* IGA2L_RHS_COEFFS (default) or IGA2L_RHS_IS_LOAD: what iga2l_solve and
                         iga2l_solve_batch read from their right-hand-side argument */
+    int tile_groups; /* TILE: the q^d colours split into this many consecutive groups, each group
+                        running the 2^d tile phases in turn (1 = plain TILE, q^d = the LATTICE
+                        order; 0 = the library default: 4 for p = 6, else 1).  Capped at q^d. */
     int sweep;       /* IGA2L_SWEEP_AUTO (default), _PER_COLOUR or _PERSISTENT: the FP32 inner
                         sweep as one persistent launch (all colours; every CTA owns a region,
                         neighbours exchange their boundary bands through L2 under bounded
@@ -159,8 +162,10 @@ int iga2l_num_dofs(iga2l_handle h, long long *n_total, int *n_axis,
 
 /* The Schwarz schedule the handle runs (Section 3.1.1 colouring, this library's
  * reading): schedule (IGA2L_SCHED_*), colour period q, stride g, TILE side T (0 for
- * LATTICE) and block side s, with every default resolved.  Outputs may be NULL. */
-int iga2l_schedule_info(iga2l_handle h, int *schedule, int *period, int *stride, int *tile, int *block_side);
+ * LATTICE), block side s and the TILE order's colour groups (1 for LATTICE), with every
+ * default resolved.  Outputs may be NULL. */
+int iga2l_schedule_info(iga2l_handle h, int *schedule, int *period, int *stride, int *tile, int *block_side,
+                        int *tile_groups);
 
 /* y = A_p u, A_p = K(x)M + M(x)K (Section 2, tensor-product stiffness). */
 int iga2l_apply_A(iga2l_handle h, const double *u, double *y, void *stream);

@@ -69,6 +69,8 @@ def _load():
             "or_cholesky": (ctypes.c_int, [ctypes.c_int, _dp]),
             "or_cholesky_solve": (None, [ctypes.c_int, _dp, _dp, _dp]),
             "or_setup": (ctypes.c_void_p, [ctypes.c_int] * 10),
+            "or_setup_grouped": (ctypes.c_void_p, [ctypes.c_int] * 11),
+            "or_schedule_grouped": (ctypes.c_int, [ctypes.c_int] * 9 + [_ip, _ip]),
             "or_free": (None, [ctypes.c_void_p]),
             "or_n": (ctypes.c_int, [ctypes.c_void_p]),
             "or_nc": (ctypes.c_int, [ctypes.c_void_p]),
@@ -190,14 +192,15 @@ def default_colouring(p: int, s: int):
 
 
 def schedule(dim: int, n: int, s: int, p: int, kind: int, tile: int = 0,
-             period: int = 0, stride: int = 0):
-    """Colour of every block centre and the processing order."""
+             period: int = 0, stride: int = 0, groups: int = 1):
+    """Colour of every block centre and the processing order (groups: colour groups of
+    the TILE order, or_schedule_grouped)."""
     if kind != LEX and period <= 0:
         period, stride = default_colouring(p, s)
     N = n ** dim
     colour = np.empty(N, dtype=np.int32)
     order = np.empty(N, dtype=np.int32)
-    nc = _load().or_schedule(dim, n, s, p, kind, tile, period, stride, _i(colour), _i(order))
+    nc = _load().or_schedule_grouped(dim, n, s, p, kind, tile, period, stride, groups, _i(colour), _i(order))
     if nc < 0:
         raise ValueError("bad schedule arguments")
     return colour, order, nc
@@ -238,14 +241,16 @@ class Problem:
 
     def __init__(self, dim: int, p: int, m: int, s: int = 0, sched: int = TILE,
                  tile: int = 32, coarse: int = VCYCLE, aggressive: bool = True,
-                 period: int = 0, stride: int = 0):
+                 period: int = 0, stride: int = 0, groups: int = 1):
         lib = _load()
         self._lib = lib
         s_eff = s if s > 0 else block_size(p)
         if period <= 0:
             period, stride = default_colouring(p, s_eff)
         self.period, self.stride = period, stride
-        self._h = lib.or_setup(dim, p, m, s, sched, tile, period, stride, coarse, int(aggressive))
+        self._h = lib.or_setup_grouped(dim, p, m, s, sched, tile, period, stride, groups, coarse,
+                                       int(aggressive))
+        self.groups = groups
         if not self._h:
             raise ValueError(f"oracle setup failed for dim={dim} p={p} m={m} s={s}")
         self.dim, self.p, self.m = dim, p, m

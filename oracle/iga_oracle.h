@@ -88,6 +88,15 @@ void or_apply_A(int dim, int n, int w, const double *K, const double *M,
  * order (ascending colour, then index); returns the number of colours or -1. */
 int or_schedule(int dim, int n, int s, int p, int kind, int tile, int period, int stride,
                 int *colour, int *order);
+/* TILE(T) with the lattice colours split into `groups` consecutive groups (group of
+ * colour rank l: floor(l groups / q^d)): for each group in turn, the 2^d tile phases run
+ * that group's colours.  groups = 1 is TILE(T); groups = q^d runs every colour over all
+ * tiles before the next, the LATTICE order.  Same colour and order outputs as or_schedule
+ * (colour = (group 2^d + tile phase) q^d + lattice colour); the number of colours or -1.
+ * Pinned by: brute-force coupling-freedom of every colour; groups = 1 reproduces
+ * or_schedule's TILE order and groups = q^d its LATTICE order. */
+int or_schedule_grouped(int dim, int n, int s, int p, int kind, int tile, int period, int stride,
+                        int groups, int *colour, int *order);
 
 /* One multiplicative Schwarz step (Section 3.1.1): for every centre c in the
  * given order, B = (c + [-r,r]^d) clipped to the grid, r = (s-1)/2, and
@@ -110,6 +119,9 @@ typedef struct or_problem or_problem;
  * or_block_size(p).  Returns NULL on bad arguments. */
 or_problem *or_setup(int dim, int p, int m, int s, int sched_kind, int tile,
                      int period, int stride, int coarse_kind, int aggressive);
+/* or_setup with a grouped TILE schedule (or_schedule_grouped); groups = 1 is or_setup. */
+or_problem *or_setup_grouped(int dim, int p, int m, int s, int sched_kind, int tile,
+                             int period, int stride, int groups, int coarse_kind, int aggressive);
 void or_free(or_problem *P);
 int  or_n(const or_problem *P);          /* DOFs per axis */
 int  or_nc(const or_problem *P);         /* second-level DOFs per axis */

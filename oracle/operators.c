@@ -88,7 +88,13 @@ static int inv_mod(int g, int q)
 int or_schedule(int dim, int n, int s, int p, int kind, int tile, int period, int stride,
                 int *colour, int *order)
 {
-    if (dim < 2 || dim > 3 || s < 1 || (s % 2) == 0 || n < 1) return -1;
+    return or_schedule_grouped(dim, n, s, p, kind, tile, period, stride, 1, colour, order);
+}
+
+int or_schedule_grouped(int dim, int n, int s, int p, int kind, int tile, int period, int stride,
+                        int groups, int *colour, int *order)
+{
+    if (dim < 2 || dim > 3 || s < 1 || (s % 2) == 0 || n < 1 || groups < 1) return -1;
     const long long N = ipow(n, dim);
     const int q = period;
     if (kind != 0 && (q < s + p || stride < 1 || inv_mod(stride % q, q) < 0)) return -1;
@@ -101,7 +107,8 @@ int or_schedule(int dim, int n, int s, int p, int kind, int tile, int period, in
         ncol = nlat;
     else if (kind == 2) {
         if (tile < q) return -1; /* same-phase tiles must be q-1 or more apart */
-        ncol = ipow(2, dim) * nlat;
+        if (groups > nlat) return -1;
+        ncol = (long long)groups * ipow(2, dim) * nlat;
     } else
         return -1;
 
@@ -121,7 +128,10 @@ int or_schedule(int dim, int n, int s, int p, int kind, int tile, int period, in
                 tp = tp * 2 + ((c[k] / tile) % 2);
                 lc = lc * q + (((c[k] % tile) % q) * ginv) % q;
             }
-            col = tp * nlat + lc;
+            /* colour group of the lattice colour: for each group in turn the 2^d tile
+             * phases run that group's colours */
+            const long long grp = lc * groups / nlat;
+            col = (grp * ipow(2, dim) + tp) * nlat + lc;
         }
         colour[i] = (int)col;
     }
@@ -252,6 +262,12 @@ static double *dense_kron_A(int dim, int n, const double *K, const double *M)
 or_problem *or_setup(int dim, int p, int m, int s, int sched_kind, int tile,
                      int period, int stride, int coarse_kind, int aggressive)
 {
+    return or_setup_grouped(dim, p, m, s, sched_kind, tile, period, stride, 1, coarse_kind, aggressive);
+}
+
+or_problem *or_setup_grouped(int dim, int p, int m, int s, int sched_kind, int tile,
+                             int period, int stride, int groups, int coarse_kind, int aggressive)
+{
     if (dim < 2 || dim > 3 || p < 1 || m < 2) return NULL;
     if (s <= 0) s = or_block_size(p);
     if (s <= 0 || (s % 2) == 0) return NULL;
@@ -268,7 +284,7 @@ or_problem *or_setup(int dim, int p, int m, int s, int sched_kind, int tile,
     P->colour = malloc(sizeof(int) * P->N);
     P->order = malloc(sizeof(int) * P->N);
     P->order_rev = malloc(sizeof(int) * P->N);
-    if (or_schedule(dim, n, s, p, sched_kind, tile, period, stride, P->colour, P->order) < 0) {
+    if (or_schedule_grouped(dim, n, s, p, sched_kind, tile, period, stride, groups, P->colour, P->order) < 0) {
         or_free(P);
         return NULL;
     }

@@ -494,6 +494,7 @@ static int assemble_impl(int p, int m, int dim, int nbatch, bool batch, const ig
     }
     if (opt.coarse != IGA2L_COARSE_VCYCLE && opt.coarse != IGA2L_COARSE_EXACT)
         return fail(IGA2L_ERR_INVALID_ARG, "unknown coarse solver");
+    if (opt.tile_groups < 0 || opt.tile_groups > 1024) return fail(IGA2L_ERR_INVALID_ARG, "tile_groups must be 0..1024");
     if (opt.sweep != IGA2L_SWEEP_AUTO && opt.sweep != IGA2L_SWEEP_PER_COLOUR && opt.sweep != IGA2L_SWEEP_PERSISTENT)
         return fail(IGA2L_ERR_INVALID_ARG, "unknown sweep kernel choice");
     if (opt.rhs != IGA2L_RHS_COEFFS && opt.rhs != IGA2L_RHS_IS_LOAD)
@@ -521,6 +522,9 @@ static int assemble_impl(int p, int m, int dim, int nbatch, bool batch, const ig
     S->nbatch = nbatch;
     S->opt = opt;
     S->q = q; S->g = g % q; S->tile = opt.tile;
+    S->tile_groups = opt.schedule == IGA2L_SCHED_TILE && dim == 2
+                         ? (opt.tile_groups > 0 ? opt.tile_groups : tile_groups_default(p)) : 1;
+    if (S->tile_groups > q * q) S->tile_groups = q * q;
     cudaError_t ce = cudaGetDevice(&S->device);
     if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&S->nsm, cudaDevAttrMultiProcessorCount, S->device);
     if (ce != cudaSuccess) { release(S); return cuda_fail(ce, "cudaGetDevice"); }
@@ -934,9 +938,11 @@ int iga2l_num_dofs(iga2l_handle h, long long *n_total, int *n_axis, long long *n
     return IGA2L_OK;
 }
 
-int iga2l_schedule_info(iga2l_handle h, int *schedule, int *period, int *stride, int *tile, int *block_side)
+int iga2l_schedule_info(iga2l_handle h, int *schedule, int *period, int *stride, int *tile, int *block_side,
+                        int *tile_groups)
 {
     if (!h) return fail(IGA2L_ERR_INVALID_ARG, "null handle");
+    if (tile_groups) *tile_groups = h->opt.schedule == IGA2L_SCHED_TILE ? h->tile_groups : 1;
     if (schedule) *schedule = h->opt.schedule;
     if (period) *period = h->q;
     if (stride) *stride = h->g;

@@ -16,6 +16,10 @@ constexpr int kMaxLevels = 24;
 // of the default colour period, at least 2R + P + 1 so tiles of one phase never interact.
 // The TILE kernel keeps a block in one warp, so it exists for blocks up to 5x5 (p <= 6).
 constexpr int tile_side(int p) { return p == 2 || p == 5 ? 20 : (p == 6 ? 22 : (p <= 4 ? 21 : 0)); }
+// Colour groups of the TILE order by default: degree 6 takes the LATTICE cycle counts with
+// its 121 colours split into 4 groups (each group runs the four tile phases in turn); the
+// other degrees use one group (p = 2, 3, 5 already match LATTICE; no grouping does for p = 4).
+constexpr int tile_groups_default(int p) { return p == 6 ? 4 : 1; }
 // 3D TILE side (3x3x3 blocks, p = 2..4): the default colour period, so a colour has one
 // block per tile; at least 2R + P, so tiles of one phase never interact.
 constexpr int tile_side3d(int p) { return p == 2 ? 5 : 7; }
@@ -86,6 +90,7 @@ struct Solver {
     iga2l_options opt{};
     int device = 0;
     int q = 5, g = 1, tile = 0;
+    int tile_groups = 1;         // TILE: colour groups (each runs the four tile phases)
     int nsm = 1;                 // SMs of the device (launch balancing)
     HostTables ht;
     // device tables

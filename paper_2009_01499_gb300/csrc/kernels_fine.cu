@@ -645,7 +645,7 @@ __device__ __forceinline__ T tile_xpass(const typename Vec2<T>::type *yb, int ey
 // CTA barrier per colour.
 template <int P, int S, int TT, typename T>
 __global__ void __launch_bounds__(TileGeom<P, S, TT>::NT, TileGeom<P, S, TT>::template minb<T>())
-k_schwarz_tile2d(int n, int nbc, int q, int g, int rev, int px, int py, int ntpx,
+k_schwarz_tile2d(int n, int nbc, int q, int g, int rev, int c0, int c1, int px, int py, int ntpx,
                  const T *__restrict__ kband, const T *__restrict__ mband,
                  const T *__restrict__ binv, const float *__restrict__ binv_lo, int interior,
                  T *__restrict__ u, const T *__restrict__ b, BatchRef bt)
@@ -706,14 +706,16 @@ k_schwarz_tile2d(int n, int nbc, int q, int g, int rev, int px, int py, int ntpx
     const int bi = slot % NB1, bj = slot / NB1;
     T2 *ybs = yb + slot * G::YB;
     T *rsb = rs + slot * G::RSS;
-    const int ncol = q * q;
-    // colour c visits offsets ((c mod q) g mod q, (c div q) g mod q), advanced incrementally
-    // the colour loop, compiled twice: FAST (interior tiles: every block of the interior
-    // class and inside the grid) and the general form
+    // colours c0 .. c1 - 1 of the tile's lattice order (all q^2 unless the colours are split
+    // into groups), in reverse with rev; colour c visits offsets ((c mod q) g mod q,
+    // (c div q) g mod q), advanced incrementally.  The colour loop is compiled twice: FAST
+    // (interior tiles: every block of the interior class and inside the grid) and the
+    // general form
+    const int ncol = c1 - c0, cstart = rev ? c1 - 1 : c0;
     auto colours = [&](auto fast_tag) {
         constexpr bool FAST = decltype(fast_tag)::value;
-        int cxr = rev ? q - 1 : 0;
-        int ox = rev ? q - g : 0, oy = ox;
+        int cxr = cstart % q;
+        int ox = (cxr * g) % q, oy = ((cstart / q) * g) % q;
         for (int t = 0; t < ncol; ++t) {
             const int cxl = ox + q * bi, cyl = oy + q * bj;   // tile-local centre
             // (q may exceed the minimum period the slots are laid out for, so some slots
@@ -1040,16 +1042,25 @@ cudaError_t schwarz_tile_p(const Solver &S, const T *kband, const T *mband, cons
     using G = TileGeom<P, SB, TT>;
     const int interior = S.ht.L * S.ht.nbc + S.ht.L;
     const int nt = (S.n + TT - 1) / TT;
-    for (int t = 0; t < 4; ++t) {
-        const int ph = reverse ? 3 - t : t;
-        const int px = ph & 1, py = ph >> 1;
-        const int ntpx = (nt - px + 1) / 2, ntpy = (nt - py + 1) / 2;
-        if (ntpx <= 0 || ntpy <= 0) continue;
-        const cudaError_t err = launch_pdl(k_schwarz_tile2d<P, SB, TT, T>, dim3(ntpx * ntpy, S.nbatch), dim3(G::NT),
-                                           st, S.n, S.ht.nbc, S.q, S.g, reverse ? 1 : 0, px, py, ntpx, kband, mband,
-                                           binv, S.boundary_lo(), interior, u, b, BatchRef{S.active, S.N, 0, 0});
-        count_launches(1);
-        if (err != cudaSuccess) return err;
+    // colour groups: for each group in turn the four tile phases run that group's colours
+    // (group k = lattice colours ceil(k q^2 / G) .. ceil((k + 1) q^2 / G) - 1)
+    const int ncol = S.q * S.q, G_ = S.tile_groups > 1 ? S.tile_groups : 1;
+    for (int kk = 0; kk < G_; ++kk) {
+        const int k = reverse ? G_ - 1 - kk : kk;
+        const int c0 = (k * ncol + G_ - 1) / G_, c1 = ((k + 1) * ncol + G_ - 1) / G_;
+        if (c1 <= c0) continue;
+        for (int t = 0; t < 4; ++t) {
+            const int ph = reverse ? 3 - t : t;
+            const int px = ph & 1, py = ph >> 1;
+            const int ntpx = (nt - px + 1) / 2, ntpy = (nt - py + 1) / 2;
+            if (ntpx <= 0 || ntpy <= 0) continue;
+            const cudaError_t err =
+                launch_pdl(k_schwarz_tile2d<P, SB, TT, T>, dim3(ntpx * ntpy, S.nbatch), dim3(G::NT), st, S.n,
+                           S.ht.nbc, S.q, S.g, reverse ? 1 : 0, c0, c1, px, py, ntpx, kband, mband, binv,
+                           S.boundary_lo(), interior, u, b, BatchRef{S.active, S.N, 0, 0});
+            count_launches(1);
+            if (err != cudaSuccess) return err;
+        }
     }
     return cudaSuccess;
 }

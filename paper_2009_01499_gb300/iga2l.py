@@ -41,7 +41,8 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("schedule", ctypes.c_int), ("tile", ctypes.c_int),
                 ("period", ctypes.c_int), ("stride", ctypes.c_int), ("coarse", ctypes.c_int),
                 ("block_side", ctypes.c_int), ("max_cycles", ctypes.c_int), ("graphs", ctypes.c_int),
-                ("rhs", ctypes.c_int), ("sweep", ctypes.c_int), ("test_flags", ctypes.c_int), ("wait_budget_cycles", ctypes.c_longlong)]
+                ("rhs", ctypes.c_int), ("tile_groups", ctypes.c_int), ("sweep", ctypes.c_int),
+                ("test_flags", ctypes.c_int), ("wait_budget_cycles", ctypes.c_longlong)]
 
 
 class IgaError(RuntimeError):
@@ -75,7 +76,7 @@ def load(build_if_missing: bool = True):
             "iga2l_assemble": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                               ctypes.POINTER(Options), ctypes.POINTER(_vp)]),
             "iga2l_num_dofs": (ctypes.c_int, [_vp, _llp, _ip, _llp, _ip]),
-            "iga2l_schedule_info": (ctypes.c_int, [_vp, _ip, _ip, _ip, _ip, _ip]),
+            "iga2l_schedule_info": (ctypes.c_int, [_vp, _ip, _ip, _ip, _ip, _ip, _ip]),
             "iga2l_apply_A": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
             "iga2l_residual": (ctypes.c_int, [_vp, _vp, _vp, _vp, _dp, _vp]),
             "iga2l_schwarz_sweep": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
@@ -202,10 +203,11 @@ class Solver:
                                         ctypes.byref(nca)))
         self.N, self.n, self.Nc, self.nc = nt.value, na.value, nct.value, nca.value
         self.NB, self.NcB = self.N * nbatch, self.Nc * nbatch   # vector lengths seen by the ABI
-        sc, q, g, t, s = (ctypes.c_int() for _ in range(5))
+        sc, q, g, t, s, tg = (ctypes.c_int() for _ in range(6))
         _check(self._lib.iga2l_schedule_info(h, ctypes.byref(sc), ctypes.byref(q), ctypes.byref(g), ctypes.byref(t),
-                                             ctypes.byref(s)))
+                                             ctypes.byref(s), ctypes.byref(tg)))
         self.schedule, self.period, self.stride, self.tile, self.block_side = sc.value, q.value, g.value, t.value, s.value
+        self.tile_groups = tg.value
 
     def close(self):
         if getattr(self, "_h", None):

@@ -35,7 +35,8 @@ def _pair(oracle_mod, p, m, sched="lattice", precision=iga2l.FP64, coarse="vcycl
     S = iga2l.Solver(p, m, schedule=sg, precision=precision, coarse=cg)
     so = oracle_mod.TILE if sched == "tile" else oracle_mod.LATTICE
     co = oracle_mod.VCYCLE if coarse == "vcycle" else oracle_mod.EXACT
-    O = oracle_mod.Problem(2, p, m, sched=so, tile=S.tile or 32, coarse=co, period=S.period, stride=S.stride)
+    O = oracle_mod.Problem(2, p, m, sched=so, tile=S.tile or 32, coarse=co, period=S.period, stride=S.stride,
+                           groups=S.tile_groups)
     assert S.N == O.N and S.block_side == O.s
     assert (S.period, S.stride) == oracle_mod.DEFAULT_COLOURING[p]
     return S, O
@@ -85,7 +86,7 @@ def test_schwarz_sweep_high_p(oracle_mod, p, sched, reverse):
     ud = _dev(u)
     S.schwarz_sweep(ud, _dev(b), reverse=reverse)
     kind = oracle_mod.TILE if sched == "tile" else oracle_mod.LATTICE
-    _, order, _ = oracle_mod.schedule(2, S.n, O.s, p, kind, S.tile or 32, S.period, S.stride)
+    _, order, _ = oracle_mod.schedule(2, S.n, O.s, p, kind, S.tile or 32, S.period, S.stride, S.tile_groups)
     if reverse:
         order = order[::-1].copy()
     K, M = oracle_mod.assemble_1d(p, m)

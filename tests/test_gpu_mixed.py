@@ -46,7 +46,8 @@ def _pair(oracle_mod, p, m, precision, sched):
         kw["sweep"] = iga2l.SWEEP_PER_COLOUR if sched == "lattice_pc" else iga2l.SWEEP_PERSISTENT
     S = iga2l.Solver(p, m, period=q, stride=g, precision=precision, schedule=sg, **kw)
     so = oracle_mod.TILE if sched == "tile" else oracle_mod.LATTICE
-    O = oracle_mod.Problem(2, p, m, sched=so, tile=S.tile or 32, coarse=oracle_mod.VCYCLE, period=q, stride=g)
+    O = oracle_mod.Problem(2, p, m, sched=so, tile=S.tile or 32, coarse=oracle_mod.VCYCLE, period=q, stride=g,
+                           groups=S.tile_groups)
     return S, O
 
 

@@ -25,7 +25,8 @@ def _pair(oracle_mod, p, m, coarse="vcycle", sched="lattice"):
     sg = iga2l.SCHED_TILE if sched == "tile" else iga2l.SCHED_LATTICE
     so = oracle_mod.TILE if sched == "tile" else oracle_mod.LATTICE
     S = iga2l.Solver(p, m, period=q, stride=g, coarse=cg, schedule=sg)
-    O = oracle_mod.Problem(2, p, m, sched=so, tile=S.tile or 32, coarse=co, period=q, stride=g)
+    O = oracle_mod.Problem(2, p, m, sched=so, tile=S.tile or 32, coarse=co, period=q, stride=g,
+                           groups=S.tile_groups)
     assert S.N == O.N and S.Nc == O.Nc
     assert (S.period, S.stride) == (q, g)
     return S, O
@@ -76,12 +77,36 @@ def test_schwarz_sweep(oracle_mod, p, m, reverse, sched):
     ud = _dev(u)
     S.schwarz_sweep(ud, _dev(b), reverse=reverse)
     kind = oracle_mod.TILE if sched == "tile" else oracle_mod.LATTICE
-    _, order, _ = oracle_mod.schedule(2, S.n, O.s, p, kind, S.tile or 32, *COLOURING[p])
+    _, order, _ = oracle_mod.schedule(2, S.n, O.s, p, kind, S.tile or 32, *COLOURING[p], S.tile_groups)
     if reverse:
         order = order[::-1].copy()
     K, M = oracle_mod.assemble_1d(p, m)
     ref = oracle_mod.schwarz_sweep(2, K, M, p, O.s, order, b, u)
     _close(_host(ud), ref)
+
+
+@pytest.mark.parametrize("p,m,groups", [(2, 100, 2), (2, 100, 7), (3, 108, 3), (4, 92, 2), (5, 132, 4),
+                                        (5, 70, 100)])
+@pytest.mark.parametrize("reverse", [False, True])
+def test_grouped_tile_sweep(oracle_mod, p, m, groups, reverse):
+    """TILE with the colours split into groups (each group runs the four tile phases):
+    FP64 sweep against the oracle's grouped order (or_schedule_grouped), per iterate."""
+    q, g = COLOURING[p]
+    S = iga2l.Solver(p, m, period=q, stride=g, schedule=iga2l.SCHED_TILE, tile_groups=groups)
+    assert S.tile_groups == min(groups, q * q)
+    O = oracle_mod.Problem(2, p, m, sched=oracle_mod.TILE, tile=S.tile, period=q, stride=g, groups=S.tile_groups)
+    b, u = _inputs(S.N, 11 * p + m + groups)
+    ud = _dev(u)
+    S.schwarz_sweep(ud, _dev(b), reverse=reverse)
+    _, order, _ = oracle_mod.schedule(2, S.n, O.s, p, oracle_mod.TILE, S.tile, q, g, S.tile_groups)
+    if reverse:
+        order = order[::-1].copy()
+    K, M = oracle_mod.assemble_1d(p, m)
+    _close(_host(ud), oracle_mod.schwarz_sweep(2, K, M, p, O.s, order, b, u))
+    # a whole grouped cycle against the oracle's
+    ud = _dev(u)
+    S.cycle(ud, _dev(b))
+    _close(_host(ud), O.cycle(u, b))
 
 
 @pytest.mark.parametrize("p,m", CASES)

@@ -171,3 +171,57 @@ def test_tile3d_phases_are_coupling_free_at_size(oracle_mod, p, tile):
         ok = sep.any(axis=2)
         np.fill_diagonal(ok, True)
         assert ok.all(), (col, cent[np.argwhere(~ok)[0]])
+
+
+@pytest.mark.parametrize("dim,p,m,tile,period,stride,groups", [
+    (2, 6, 44, 22, 11, 4, 4),     # the grouped TILE order of degree 6 (4 colour groups)
+    (2, 2, 40, 10, 5, 2, 3),
+    (2, 4, 44, 21, 7, 2, 2),
+])
+def test_grouped_tile_colours_are_coupling_free(oracle_mod, dim, p, m, tile, period, stride, groups):
+    """Every colour of the grouped TILE order is one parallel phase (no shared or read DOF)."""
+    A, _, _ = _dense_A(oracle_mod, dim, p, m)
+    n = m + p - 2
+    s = oracle_mod.block_size(p)
+    r = (s - 1) // 2
+    colour, order, ncol = oracle_mod.schedule(dim, n, s, p, 2, tile, period, stride, groups)
+    nz = A != 0
+    assert sorted(order.tolist()) == list(range(n ** dim))
+    for col in np.unique(colour):
+        cent = np.nonzero(colour == col)[0]
+        blocks = [_block(dim, n, c, r) for c in cent]
+        reads = [np.nonzero(nz[b].any(axis=0))[0] for b in blocks]
+        for a, b in itertools.combinations(range(len(cent)), 2):
+            assert not np.intersect1d(blocks[a], blocks[b]).size
+            assert not np.intersect1d(blocks[a], reads[b]).size
+            assert not np.intersect1d(blocks[b], reads[a]).size
+
+
+@pytest.mark.parametrize("p,n,tile,q,g", [(2, 40, 10, 5, 2), (6, 70, 22, 11, 4), (4, 45, 21, 7, 2)])
+def test_grouped_tile_order_limits_and_definition(oracle_mod, p, n, tile, q, g):
+    """groups = 1 is the TILE order and groups = q^2 the LATTICE order; in between, the
+    order is (colour group, tile phase, lattice colour, index) written out here directly:
+    centre (x, y) has tile phase (x // T) % 2 + 2 ((y // T) % 2), lattice colour l =
+    rank(x mod q) + q rank(y mod q) with rank(o) = o g^-1 mod q (tile sides are multiples
+    of q), and group floor(l groups / q^2)."""
+    s = oracle_mod.block_size(p)
+    _, o_tile, _ = oracle_mod.schedule(2, n, s, p, 2, tile, q, g)
+    _, o_g1, _ = oracle_mod.schedule(2, n, s, p, 2, tile, q, g, 1)
+    assert np.array_equal(o_tile, o_g1)
+    _, o_lat, _ = oracle_mod.schedule(2, n, s, p, 1, 0, q, g)
+    _, o_gq, _ = oracle_mod.schedule(2, n, s, p, 2, tile, q, g, q * q)
+    # both orders visit the lattice colours in the same sequence; inside a colour the
+    # LATTICE order is by index, the grouped one by tile phase then index
+    rank = {o: (o * pow(g, -1, q)) % q for o in range(q)}
+    lat = lambda c: rank[(c % n) % q] + q * rank[(c // n) % q]
+    assert [lat(c) for c in o_gq] == [lat(c) for c in o_lat]
+    for groups in (2, 3, q):
+        _, o, _ = oracle_mod.schedule(2, n, s, p, 2, tile, q, g, groups)
+        key = []
+        for c in range(n * n):
+            x, y = c % n, c // n
+            l = lat(c)
+            tp = (x // tile) % 2 + 2 * ((y // tile) % 2)
+            key.append((l * groups // (q * q), tp, l, c))
+        want = [k[3] for k in sorted(key)]
+        assert o.tolist() == want, groups
