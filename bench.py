@@ -74,6 +74,14 @@ def schwarz_flops_per_dof(p, s, dim=2):
     return 2 * sd * w ** dim + sd + 2 * sd * sd + sd
 
 
+def schwarz_flops_per_dof_f32(p, s):
+    """Algorithmic FP32 flops of one Schwarz block (one per DOF) in the sum-factorised form of
+    the FP32 kernels: y pass 2W s (s + 2p) and x pass 2W s^2 multiply-adds (pairs K, M), the
+    block solve s^4 multiply-adds, one subtraction and one update per block DOF."""
+    w = 2 * p + 1
+    return 2 * (2 * w * s * (s + 2 * p) + 2 * w * s * s + s ** 4) + 2 * s * s
+
+
 def block_side(p):
     return 3 if p <= 4 else 5
 
@@ -501,13 +509,16 @@ def run_gpu(args):
     # mixed precision (FP32 inner cycle, TILE schedule) inside FP64 refinement, same
     # workload and stopping rule: boundary-block inverses applied in FP64 ("mixed") or
     # in FP32 as well ("mixed_fp32_boundary")
-    mixed, mixed_all, mixed_tf32 = None, None, None
+    mixed, mixed_all, mixed_tf32, mixed_same = None, None, None, None
+    # FMA-pipe throughputs of this GPU, measured now (the ALU rooflines' denominators)
+    peaks = {"fp64": iga2l.fma_peak(0), "fp32": iga2l.fma_peak(1), "fp32x2": iga2l.fma_peak(2)}
     if not args.no_mixed:
-        def run_mixed(precision, boundary, schedule=iga2l.SCHED_TILE):
+
+        def run_mixed(precision, boundary, schedules):
             msolv = {}
             for p in DEGREES:
                 q, g = COLOURING[p]
-                msolv[p] = iga2l.Solver(p, M_ELEM, period=q, stride=g, precision=precision, schedule=schedule)
+                msolv[p] = iga2l.Solver(p, M_ELEM, period=q, stride=g, precision=precision, schedule=schedules[p])
             mcyc = {}
 
             def mstep():
@@ -533,22 +544,76 @@ def run_gpu(args):
                 concurrent_step(msolv, fs, us, u0s, flush, stream, cstreams, TOL)
             mcms = allmax(statistics.mean([concurrent_step(msolv, fs, us, u0s, flush, stream, cstreams, TOL)[0]
                                            for _ in range(args.steps)]), ws, dev)
+
+            def sched_name(S):
+                if S.tile:
+                    return f"TILE({S.tile})" + (f"x{S.tile_groups} groups" if S.tile_groups > 1 else "")
+                return "LATTICE"
+
             out = {"value": ws * ndofs / (mms * 1e-3), "unit": "DOF/s", "ms_per_step": mms,
                    "speedup_vs_fp64": ms_step / mms,
                    "dtype": f"f32 inner cycle ({boundary} boundary-block inverses), f64 residual/update/coarsest",
-                   "schedule": {str(p): (f"TILE({msolv[p].tile})" if msolv[p].tile else "LATTICE") for p in DEGREES},
+                   "schedule": {str(p): sched_name(msolv[p]) for p in DEGREES},
                    "cycles": {str(p): mcyc[p] for p in DEGREES},
+                   "cycles_equal_fp64": all(mcyc[p] == cycles[p] for p in DEGREES),
                    "accuracy": "same 1e-8 FP64 residual rule; refined to 1e-12 the solution is within "
                                "1e-8 of the FP64 oracle's (tests/test_gpu_mixed.py)",
                    "concurrent": {"value": ws * ndofs / (mcms * 1e-3), "unit": "DOF/s", "ms_per_step": mcms}}
-            for S in msolv.values():
-                S.close()
-            return out
+            return out, msolv
 
-        mixed = run_mixed(iga2l.MIXED_FP32, "f64")
-        mixed_all = run_mixed(iga2l.MIXED_FP32_ALL, "f32")
+        def sweep_roofline(msolv):
+            """FP32 Schwarz sweep of the inner cycle (iga2l_schwarz_sweep_f32), timed alone with
+            CUDA events on the FP32 copies of the step's vectors (L2-resident, as inside a solve)."""
+            tot_fl, tot_ms, per = 0.0, 0.0, {}
+            for p in DEGREES:
+                S = msolv[p]
+                u32 = u0s[p].float()
+                b32 = bs[p].float()
+                S.schwarz_sweep_f32(u32, b32)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                reps = 5
+                e0.record(stream)
+                for _ in range(reps):
+                    S.schwarz_sweep_f32(u32, b32)
+                e1.record(stream)
+                e1.synchronize()
+                ms = e0.elapsed_time(e1) / reps
+                fl = schwarz_flops_per_dof_f32(p, block_side(p)) * S.N
+                per[str(p)] = {"sweep_ms": round(ms, 4), "gflops": round(fl / ms / 1e6, 1),
+                               "cycles": msolv_cycles[p], "schedule": sched_of[p]}
+                tot_fl += msolv_cycles[p] * fl
+                tot_ms += msolv_cycles[p] * ms
+            ach = tot_fl / tot_ms / 1e6
+            pk = peaks["fp32x2"]
+            return {"bound": "alu", "achieved": round(ach, 1), "peak": round(pk, 1), "unit": "GFLOP/s",
+                    "frac": round(ach / pk, 4), "traffic": None,
+                    "kernel": "FP32 Schwarz sweep of the inner cycle (TILE: k_schwarz_tile2d; LATTICE: one launch per "
+                              "colour or k_schwarz_persist2d)",
+                    "peak_source": "packed FP32 FMA pipe measured in this run (iga2l_fma_peak: dependent-free FMA "
+                                   "loops on every SM)",
+                    "flops": "sum-factorised block residual + block solve per DOF: 2[2W s(s+2p) + 2W s^2 + s^4] "
+                             "+ 2 s^2, W = 2p+1",
+                    "per_degree": per}
+
+        # headline mixed form: per degree the fastest schedule with the FP64 form's cycle counts
+        best = {2: iga2l.SCHED_TILE, 3: iga2l.SCHED_TILE, 4: iga2l.SCHED_LATTICE, 5: iga2l.SCHED_TILE}
+        mixed, msolv = run_mixed(iga2l.MIXED_FP32, "f64", best)
+        msolv_cycles = {p: mixed["cycles"][str(p)] for p in DEGREES}
+        sched_of = mixed["schedule"]
+        mixed["roofline"] = sweep_roofline(msolv)
+        for S in msolv.values():
+            S.close()
+        mixed_all, ms_ = run_mixed(iga2l.MIXED_FP32_ALL, "f32", best)
+        for S in ms_.values():
+            S.close()
+        # the same schedule as the FP64 form (LATTICE for every degree)
+        mixed_same, ms_ = run_mixed(iga2l.MIXED_FP32, "f64", {p: iga2l.SCHED_LATTICE for p in DEGREES})
+        for S in ms_.values():
+            S.close()
         # the interior blocks of every LATTICE colour as a tcgen05 TF32 GEMM
-        mixed_tf32 = run_mixed(iga2l.MIXED_TF32, "f64", iga2l.SCHED_LATTICE)
+        mixed_tf32, ms_ = run_mixed(iga2l.MIXED_TF32, "f64", {p: iga2l.SCHED_LATTICE for p in DEGREES})
+        for S in ms_.values():
+            S.close()
         mixed_tf32["dtype"] = ("tf32 tensor-core interior block solves (tcgen05, f32 accumulation), f32 boundary "
                                "frame, f64 residual/update/coarsest")
 
@@ -590,11 +655,13 @@ def run_gpu(args):
         digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         if rec.get("source_sha256_16") == digest:
             traffic = rec.get("bytes_per_launch")
-    roofline = {"bound": "alu", "achieved": round(achieved, 1), "peak": round(FP64_PEAK_GFLOPS, 1),
-                "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4), "traffic": traffic,
+    pk64 = peaks["fp64"]
+    roofline = {"bound": "alu", "achieved": round(achieved, 1), "peak": round(pk64, 1),
+                "unit": "GFLOP/s", "frac": round(achieved / pk64, 4), "traffic": traffic,
                 "kernel": "k_schwarz_lattice2d (one colour phase per launch)",
-                "peak_source": "FP64 FMA pipe: 2 FMA/clk/SM x 152 SMs x 2070 MHz (derived; a "
-                               "dependent-free FMA loop measured 1256 GFLOP/s on this GB300)",
+                "peak_source": "FP64 FMA pipe measured in this run (iga2l_fma_peak: dependent-free FMA loops on "
+                               f"every SM); unit counts give 2 FMA/clk/SM x 152 SMs x 2070 MHz = "
+                               f"{FP64_PEAK_GFLOPS:.1f}",
                 "per_degree": per_p}
 
     line = {
@@ -612,7 +679,9 @@ def run_gpu(args):
         "gpu_launches": int(launches),
         "roofline": roofline,
         "clocks": clk,
-        "concurrent": concurrent, "mixed": mixed, "mixed_fp32_boundary": mixed_all, "mixed_tf32_tensor_core": mixed_tf32,
+        "concurrent": concurrent, "mixed": mixed, "mixed_fp32_boundary": mixed_all,
+        "mixed_same_schedule_as_fp64": mixed_same, "mixed_tf32_tensor_core": mixed_tf32,
+        "measured_peaks_gflops": peaks or None,
         "other_configs": extra,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

@@ -184,6 +184,12 @@ int iga2l_schwarz_sweep(iga2l_handle h, double *u, const double *b, void *stream
  * approximate inverse; used by the adjoint cycle). */
 int iga2l_schwarz_sweep_reverse(iga2l_handle h, double *u, const double *b, void *stream);
 
+/* The Schwarz step of a mixed-precision handle's inner cycle on FP32 vectors (2D):
+ * u <- u + S_p(b - A_p u) in FP32 arithmetic, with the handle's schedule and sweep kernel
+ * (reverse != 0: colours in reverse).  u, b: n^2 device floats.  For checking and timing
+ * the inner cycle's dominant step; IGA2L_ERR_INVALID_ARG on an FP64 or 3D handle. */
+int iga2l_schwarz_sweep_f32(iga2l_handle h, float *u, const float *b, int reverse, void *stream);
+
 /* d_c = I_{p,h}^{1,2h} d (Sections 3.1.2 and 3.3): lumped L2 projection onto
  * the degree-1 space followed by the degree-1 h -> 2h restriction.  dc has nc^d entries. */
 int iga2l_restrict(iga2l_handle h, const double *d, double *dc, void *stream);
@@ -305,6 +311,13 @@ const char *iga2l_last_error(void);
 /* Number of CUDA kernels this library has launched in this process so far
  * (all handles and threads).  For benchmarks; no GPU work. */
 long long iga2l_kernel_launches(void);
+
+/* For benchmarks (not part of the solver): the throughput of one FMA pipe of the current
+ * device in GFLOP/s (an FMA counts 2 flops), measured with dependent-free FMA loops over
+ * every SM: kind 0 = FP64, 1 = FP32, 2 = packed FP32 pairs (one instruction, two FMAs).
+ * These are the denominators of the ALU rooflines of the FP64 and FP32 kernels.
+ * Allocates 16 bytes for the duration of the call and synchronises `stream`. */
+int iga2l_fma_peak(int kind, double *gflops, void *stream);
 
 #ifdef __cplusplus
 }

@@ -990,6 +990,16 @@ int iga2l_schwarz_sweep_reverse(iga2l_handle h, double *u, const double *b, void
     return finish(launch_schwarz(*h, u, b, true, as_stream(stream)), "reverse schwarz sweep");
 }
 
+int iga2l_schwarz_sweep_f32(iga2l_handle h, float *u, const float *b, int reverse, void *stream)
+{
+    int rc = check_handle(h);
+    if (rc != IGA2L_OK) return rc;
+    if (!u || !b) return fail(IGA2L_ERR_INVALID_ARG, "null vector");
+    if (!h->mx.enabled || h->dim != 2)
+        return fail(IGA2L_ERR_INVALID_ARG, "the FP32 sweep needs a 2D mixed-precision handle");
+    return finish(launch_inner_sweep(*h, u, b, reverse != 0, as_stream(stream)), "FP32 schwarz sweep");
+}
+
 int iga2l_restrict(iga2l_handle h, const double *d, double *dc, void *stream)
 {
     int rc = check_handle(h);

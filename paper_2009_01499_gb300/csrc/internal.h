@@ -232,6 +232,8 @@ cudaError_t launch_outer_residual(const Solver &S, const double *u, const double
 cudaError_t launch_inner_fine(const Solver &S, const float *r32, bool reverse, cudaStream_t st);
 cudaError_t launch_inner_coarse(const Solver &S, cudaStream_t st);
 cudaError_t launch_inner_update(const Solver &S, double *u, cudaStream_t st);
+// the FP32 Schwarz step of the inner cycle on caller vectors (2D)
+cudaError_t launch_inner_sweep(const Solver &S, float *u, const float *b, bool reverse, cudaStream_t st);
 int residual_partials(const Solver &S);
 cudaError_t launch_batch_init(const Solver &S, const double *norm2, double *norm0, int *cycles, double *relres,
                               cudaStream_t st);

@@ -1347,6 +1347,13 @@ cudaError_t launch_inner_fine(const Solver &S, const float *r32, bool reverse, c
     return e;
 }
 
+cudaError_t launch_inner_sweep(const Solver &S, float *u, const float *b, bool reverse, cudaStream_t st)
+{
+    const MixedState &X = S.mx;
+    return S.pgx > 0 ? launch_schwarz_persist(S, u, b, reverse, st)
+                     : schwarz_any<float>(S, X.stencil, X.Kb, X.Mb, X.binv, u, b, reverse, st);
+}
+
 cudaError_t launch_inner_update(const Solver &S, double *u, cudaStream_t st)
 {
     if (S.dim == 3) return launch3d_inner_update(S, u, st);

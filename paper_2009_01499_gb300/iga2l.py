@@ -34,6 +34,7 @@ EXPORTS = (
     "iga2l_last_error", "iga2l_kernel_launches", "iga2l_residual_norm2_noalloc",
     "iga2l_cycles", "iga2l_unrolled_backward", "iga2l_bump_load", "iga2l_bump_grad",
     "iga2l_assemble_batch", "iga2l_solve_batch", "iga2l_schedule_info", "iga2l_solve_load",
+    "iga2l_schwarz_sweep_f32", "iga2l_fma_peak",
 )
 
 
@@ -82,6 +83,7 @@ def load(build_if_missing: bool = True):
             "iga2l_schwarz_sweep": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
             "iga2l_schwarz_sweep_reverse": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
             "iga2l_restrict": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+            "iga2l_schwarz_sweep_f32": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp]),
             "iga2l_prolong_add": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
             "iga2l_coarse_solve": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
             "iga2l_cycle": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
@@ -100,6 +102,7 @@ def load(build_if_missing: bool = True):
             "iga2l_strerror": (ctypes.c_char_p, [ctypes.c_int]),
             "iga2l_last_error": (ctypes.c_char_p, []),
             "iga2l_kernel_launches": (ctypes.c_longlong, []),
+            "iga2l_fma_peak": (ctypes.c_int, [ctypes.c_int, _dp, _vp]),
             "iga2l_cycles": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp]),
             "iga2l_assemble_batch": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                     ctypes.POINTER(Options), ctypes.POINTER(_vp)]),
@@ -147,6 +150,13 @@ def _stream(stream):
 def kernel_launches() -> int:
     """Kernels launched by libiga2l.so in this process so far."""
     return int(load().iga2l_kernel_launches())
+
+
+def fma_peak(kind: int, stream=None) -> float:
+    """Measured FMA-pipe throughput (GFLOP/s): kind 0 FP64, 1 FP32, 2 packed FP32 pairs."""
+    g = ctypes.c_double(0.0)
+    _check(load().iga2l_fma_peak(int(kind), ctypes.byref(g), _stream(stream)))
+    return g.value
 
 
 def default_options(**kw) -> Options:
@@ -235,6 +245,11 @@ class Solver:
     def schwarz_sweep(self, u, b, reverse=False, stream=None):
         fn = self._lib.iga2l_schwarz_sweep_reverse if reverse else self._lib.iga2l_schwarz_sweep
         _check(fn(self._h, _ptr(u, numel=self.NB), _ptr(b, numel=self.NB), _stream(stream)))
+
+    def schwarz_sweep_f32(self, u, b, reverse=False, stream=None):
+        """The inner cycle's FP32 Schwarz step on float32 vectors (mixed-precision handles)."""
+        _check(self._lib.iga2l_schwarz_sweep_f32(self._h, _ptr(u, "float32", self.N), _ptr(b, "float32", self.N),
+                                                 int(bool(reverse)), _stream(stream)))
 
     def restrict(self, d, dc, stream=None):
         _check(self._lib.iga2l_restrict(self._h, _ptr(d, numel=self.NB), _ptr(dc, numel=self.NcB),

@@ -175,3 +175,32 @@ def test_fp32_tile_sweep_matches_fp64_tile_sweep(p):
     B.cycle(ub, f)
     corr = float(torch.linalg.norm(ua - u0))
     assert float(torch.linalg.norm(ua - ub)) <= 1e-5 * corr
+
+
+@pytest.mark.parametrize("p,m,sched,kw", [
+    (2, 100, "tile", {}), (5, 132, "tile", {}), (6, 100, "tile", {}),          # p = 6: four colour groups
+    (3, 96, "lattice", {"sweep": iga2l.SWEEP_PER_COLOUR}), (4, 92, "lattice", {"sweep": iga2l.SWEEP_PER_COLOUR}),
+    (5, 132, "lattice", {"sweep": iga2l.SWEEP_PERSISTENT}), (8, 132, "lattice", {"sweep": iga2l.SWEEP_PERSISTENT}),
+])
+@pytest.mark.parametrize("reverse", [False, True])
+def test_fp32_sweep_entry_point_matches_oracle_order(oracle_mod, p, m, sched, kw, reverse):
+    """iga2l_schwarz_sweep_f32 (the inner cycle's Schwarz step on FP32 vectors) against the
+    oracle's FP64 sweep in the same block order from the same (FP32-representable) inputs:
+    FP32 accuracy relative to the correction."""
+    q, g = oracle_mod.DEFAULT_COLOURING[p]
+    sg = iga2l.SCHED_TILE if sched == "tile" else iga2l.SCHED_LATTICE
+    S = iga2l.Solver(p, m, period=q, stride=g, precision=iga2l.MIXED_FP32, schedule=sg, **kw)
+    u = synth.initial_guess(S.N, 70 + p).astype(np.float32)
+    b = synth.coefficients(S.N, 71 + p).astype(np.float32)
+    ud = torch.tensor(u, device="cuda")
+    S.schwarz_sweep_f32(ud, torch.tensor(b, device="cuda"), reverse=reverse)
+    kind = oracle_mod.TILE if sched == "tile" else oracle_mod.LATTICE
+    _, order, _ = oracle_mod.schedule(2, S.n, S.block_side, p, kind, S.tile or 32, q, g, S.tile_groups)
+    if reverse:
+        order = order[::-1].copy()
+    K, M = oracle_mod.assemble_1d(p, m)
+    ref = oracle_mod.schwarz_sweep(2, K, M, p, S.block_side, order, b.astype(np.float64), u.astype(np.float64))
+    got = _host(ud).astype(np.float64)
+    corr = np.linalg.norm(ref - u)
+    assert np.linalg.norm(got - ref) <= 2e-5 * corr, np.linalg.norm(got - ref) / corr
+    S.close()
