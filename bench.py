@@ -580,7 +580,7 @@ def run_gpu(args):
                 ms = e0.elapsed_time(e1) / reps
                 fl = schwarz_flops_per_dof_f32(p, block_side(p)) * S.N
                 per[str(p)] = {"sweep_ms": round(ms, 4), "gflops": round(fl / ms / 1e6, 1),
-                               "cycles": msolv_cycles[p], "schedule": sched_of[p]}
+                               "cycles": msolv_cycles[p], "schedule": sched_of[str(p)]}
                 tot_fl += msolv_cycles[p] * fl
                 tot_ms += msolv_cycles[p] * ms
             ach = tot_fl / tot_ms / 1e6

@@ -138,49 +138,50 @@ template <>
 __device__ __forceinline__ float2 cmk1<float>(int p, int a) { return c_mk1f[p][a]; }
 
 // d = b - A u  (b != nullptr)  or  d = A u  (b == nullptr), arithmetic in T, output
-// stored as TO; part[cta] = sum of d^2 (in double) when part != nullptr.  A 32 x 8 tile
-// of outputs per CTA with u (tile + halo p) in shared memory and the y-then-x sum
-// factorisation A u = sum_b K_y[b] (sum_a M_x[a] u) + M_y[b] (sum_a K_x[a] u): first the
-// pairs (K_y u, M_y u) of every output row at every window column, then per output the
-// x sums (2(2p+1)(1 + 2p/32) + 2(2p+1) FMAs per output instead of (2p+1)^2).  Interior
-// tiles take the interior 1D rows from constant memory; boundary tiles the 1D rows of
-// their own rows and columns, scaled the same way (h K, M / h).
-template <int P, typename T, typename TO>
-__global__ void __launch_bounds__(kResTX *kResTY)
+// stored as TO; part[cta] = sum of d^2 (in double) when part != nullptr.  A TX x TY tile
+// of outputs per CTA (32 x 8 in FP32, 64 x 8 in FP64) with u (tile + halo p) in shared
+// memory and the y-then-x sum factorisation A u = sum_b K_y[b] (sum_a M_x[a] u) + M_y[b]
+// (sum_a K_x[a] u): first the pairs (K_y u, M_y u) of every output row at every window
+// column, then per output the x sums (2(2p+1)(1 + 2p/TX) + 2(2p+1) FMAs per output instead
+// of (2p+1)^2; in interior tiles the symmetric rows make the y pass p adds and 2(p+1)
+// FMAs per pair).  Interior tiles take the interior 1D rows from constant memory; boundary
+// tiles the 1D rows of their own rows and columns, scaled the same way (h K, M / h).
+template <int P, typename T, typename TO, int TX = kResTX, int TY = kResTY>
+__global__ void __launch_bounds__(TX *TY)
 k_residual2d(int n, const T *__restrict__ kband, const T *__restrict__ mband, const T *__restrict__ u,
              const T *__restrict__ b, TO *__restrict__ d, double *__restrict__ part, unsigned int *__restrict__ done,
              double *__restrict__ norm2, BatchRef bt)
 {
     using T2 = typename Vec2<T>::type;
     constexpr int W = 2 * P + 1;
-    constexpr int SX = kResTX + 2 * P, SY = kResTY + 2 * P;
+    constexpr int SX = TX + 2 * P, SY = TY + 2 * P;
     __shared__ T su[SY][SX];
-    __shared__ T2 yv[kResTY][SX];
-    __shared__ T2 kmy[kResTY][W], mkx[kResTX][W];   // boundary tiles
-    __shared__ double red[kResTX * kResTY / 32];
+    __shared__ T2 yv[TY][SX];
+    __shared__ T2 kmy[TY][W], mkx[TX][W];   // boundary tiles
+    __shared__ double red[TX * TY / 32];
     const int z = blockIdx.z;
-    const int x0 = blockIdx.x * kResTX, y0 = blockIdx.y * kResTY;
-    const int tid = threadIdx.x + kResTX * threadIdx.y;
-    constexpr int NT = kResTX * kResTY;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int tid = threadIdx.x + TX * threadIdx.y;
+    constexpr int NT = TX * TY;
     constexpr int K = (SX * SY + NT - 1) / NT;
-    const bool fast = x0 >= 2 * P - 1 && x0 + kResTX - 1 <= n - 2 * P && y0 >= 2 * P - 1 &&
-                      y0 + kResTY - 1 <= n - 2 * P;
+    const bool fast = x0 >= 2 * P - 1 && x0 + TX - 1 <= n - 2 * P && y0 >= 2 * P - 1 &&
+                      y0 + TY - 1 <= n - 2 * P;
     if (!fast) {   // constant tables: read before the wait
         const T h = T(1) / T(n - P + 2), hinv = T(n - P + 2);
-        for (int t = tid; t < (kResTX + kResTY) * W; t += NT) {
+        for (int t = tid; t < (TX + TY) * W; t += NT) {
             const int row = t / W, a = t - row * W;
-            if (row < kResTY) {
+            if (row < TY) {
                 const int gy = y0 + row;
                 T2 km;
                 km.x = gy < n ? kband[(size_t)gy * W + a] * h : T(0);
                 km.y = gy < n ? mband[(size_t)gy * W + a] * hinv : T(0);
                 kmy[row][a] = km;
             } else {
-                const int gx = x0 + row - kResTY;
+                const int gx = x0 + row - TY;
                 T2 mk;
                 mk.x = gx < n ? mband[(size_t)gx * W + a] * hinv : T(0);
                 mk.y = gx < n ? kband[(size_t)gx * W + a] * h : T(0);
-                mkx[row - kResTY][a] = mk;
+                mkx[row - TY][a] = mk;
             }
         }
     }
@@ -203,12 +204,15 @@ k_residual2d(int n, const T *__restrict__ kband, const T *__restrict__ mband, co
         if (t < SX * SY) su[t / SX][t % SX] = v[k];
     }
     __syncthreads();
-    for (int pt = tid; pt < kResTY * SX; pt += NT) {
+    for (int pt = tid; pt < TY * SX; pt += NT) {
         const int r = pt / SX, c = pt - r * SX;
         T2 y = splat2<T2>(T(0));
         if (fast) {
+            // interior rows are symmetric (k[P - j] = k[P + j], the same for m): the two taps
+            // at distance j share one multiply-add per half of the pair
+            y = fma2(ckm1<T>(P, P), splat2<T2>(su[r + P][c]), y);
 #pragma unroll
-            for (int bb = 0; bb < W; ++bb) y = fma2(ckm1<T>(P, bb), splat2<T2>(su[r + bb][c]), y);
+            for (int j = 1; j <= P; ++j) y = fma2(ckm1<T>(P, P - j), splat2<T2>(su[r + P - j][c] + su[r + P + j][c]), y);
         } else {
 #pragma unroll
             for (int bb = 0; bb < W; ++bb) y = fma2(kmy[r][bb], splat2<T2>(su[r + bb][c]), y);
@@ -239,7 +243,7 @@ k_residual2d(int n, const T *__restrict__ kband, const T *__restrict__ mband, co
         __shared__ bool last;
         if (tid == 0) {
             double tot = 0.0;
-            for (int w = 0; w < kResTX * kResTY / 32; ++w) tot += red[w];
+            for (int w = 0; w < TX * TY / 32; ++w) tot += red[w];
             part[blockIdx.x + gridDim.x * blockIdx.y] = tot;
             last = false;
             if (norm2) {   // the last CTA of this problem to finish sums the partials
@@ -252,7 +256,7 @@ k_residual2d(int n, const T *__restrict__ kband, const T *__restrict__ mband, co
             // fixed-order sum of the partials (deterministic), then re-arm the counter
             __threadfence();
             const int np = gridDim.x * gridDim.y;
-            constexpr int NT = kResTX * kResTY;
+            constexpr int NT = TX * TY;
             __shared__ double sh[NT];
             double acc = 0.0;
             for (int i = tid; i < np; i += NT) acc += __ldcg(&part[i]);
@@ -902,9 +906,11 @@ template <int P, typename T, typename TO>
 cudaError_t residual_p(const Solver &S, const T *kband, const T *mband, const T *u, const T *b, TO *d, double *part,
                        double *norm2, cudaStream_t st)
 {
-    dim3 blk(kResTX, kResTY), grd((S.n + kResTX - 1) / kResTX, (S.n + kResTY - 1) / kResTY, S.nbatch);
-    const cudaError_t err = launch_pdl(k_residual2d<P, T, TO>, grd, blk, st, S.n, kband, mband, u, b, d, part,
-                                       S.rcount, norm2, BatchRef{S.active, S.N, residual_partials(S), 0});
+    // FP64: 64-wide tiles (the y pass's halo columns are 2p / 64 of its work instead of 2p / 32)
+    constexpr int TX = sizeof(T) == sizeof(double) ? 64 : kResTX, TY = kResTY;
+    dim3 blk(TX, TY), grd((S.n + TX - 1) / TX, (S.n + TY - 1) / TY, S.nbatch);
+    const cudaError_t err = launch_pdl(k_residual2d<P, T, TO, TX, TY>, grd, blk, st, S.n, kband, mband, u, b, d,
+                                       part, S.rcount, norm2, BatchRef{S.active, S.N, residual_partials(S), 0});
     count_launches(1);
     return err;
 }
