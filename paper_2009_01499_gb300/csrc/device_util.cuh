@@ -21,36 +21,45 @@ __device__ __forceinline__ double2 fma2(double2 a, double2 b, double2 c)
 }
 template <typename T2>
 __device__ __forceinline__ T2 splat2(decltype(T2::x) v) { T2 r; r.x = v; r.y = v; return r; }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ double2 add2(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 
 // Row e of an FP64 block inverse, held as the FP32 pair hi + lo, times the FP32 block
 // residual r, by Dot2 of Ogita, Rump and Oishi ("Accurate sum and dot product", SIAM J.
 // Sci. Comput. 26(6), 2005): every product split exactly into p + ep (TwoProduct by FMA),
 // every running sum into t + es (TwoSum), the error terms gathered in c; the result is as
 // accurate as the sum computed in about twice the FP32 precision and then rounded once.
-// Two interleaved chains (even and odd f) halve the dependent adds.  Explicit _rn
-// intrinsics keep the compiler from contracting the error-free transformations.
+// Four interleaved chains (f mod 4) quarter the dependent adds.  Explicit _rn intrinsics
+// keep the compiler from contracting the error-free transformations.
+__device__ __forceinline__ void two_sum(float a, float b, float &t, float &e)
+{
+    t = __fadd_rn(a, b);
+    const float z = __fsub_rn(t, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(t, z)), __fsub_rn(b, z));   // a + b = t + e
+}
+
 template <int SS>
 __device__ __forceinline__ float dot2_row(const float *__restrict__ hi, const float *__restrict__ lo,
                                           const float *rv)
 {
-    float s0 = 0.f, s1 = 0.f, c0 = 0.f, c1 = 0.f;
+    float s[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int f = 0; f < SS; ++f) {
-        float &s = (f & 1) ? s1 : s0;
-        float &c = (f & 1) ? c1 : c0;
+        const int k = f & 3;
         const float a = __ldg(&hi[f]), r = rv[f];
         const float p = __fmul_rn(a, r);
         const float ep = __fmaf_rn(a, r, -p);                  // a r = p + ep
-        const float t = __fadd_rn(s, p);
-        const float z = __fsub_rn(t, s);
-        const float es = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));   // s + p = t + es
-        s = t;
-        c = __fmaf_rn(__ldg(&lo[f]), r, __fadd_rn(c, __fadd_rn(ep, es)));
+        float t, es;
+        two_sum(s[k], p, t, es);                               // s + p = t + es
+        s[k] = t;
+        c[k] = __fmaf_rn(__ldg(&lo[f]), r, __fadd_rn(c[k], __fadd_rn(ep, es)));
     }
-    const float t = __fadd_rn(s0, s1);
-    const float z = __fsub_rn(t, s0);
-    const float e = __fadd_rn(__fsub_rn(s0, __fsub_rn(t, z)), __fsub_rn(s1, z));   // s0 + s1 = t + e
-    return __fadd_rn(t, __fadd_rn(e, __fadd_rn(c0, c1)));
+    float t01, e01, t23, e23, t, e;
+    two_sum(s[0], s[1], t01, e01);
+    two_sum(s[2], s[3], t23, e23);
+    two_sum(t01, t23, t, e);
+    const float cc = __fadd_rn(__fadd_rn(c[0], c[1]), __fadd_rn(c[2], c[3]));
+    return __fadd_rn(t, __fadd_rn(e, __fadd_rn(__fadd_rn(e01, e23), cc)));
 }
 
 }  // namespace iga2l

@@ -549,6 +549,10 @@ struct TileGeom {
     static constexpr int YS = S == 5 ? 21 : 19, YB = S * YS;
     static constexpr int RSS = (SS + 3) / 4 * 4;           // residual stride (16-byte loads)
     static constexpr int NB2 = (SS + 1) / 2;               // pairs of one inverse row
+    // one block per warp and 2 WIN <= 32 (5 x 5 blocks): the interior y pass takes two lanes
+    // per window column, rows 0 .. RA - 1 and RA .. S - 1
+    static constexpr bool SPLITY = BPW == 1 && 2 * WIN <= 32;
+    static constexpr int RA = (S + 1) / 2;
     // resident CTAs per SM the register allocation must allow (FP32: a 1024^2 tile phase
     // in one wave; FP64 keeps its registers)
     template <typename T>
@@ -575,27 +579,51 @@ __device__ __forceinline__ void stage_window(T *dst, const T *__restrict__ src, 
     }
 }
 
+// stage_window storing every value twice, as the pair (v, v): the packed FMAs of the y
+// pass then read their splatted operand straight from shared memory
+template <int NT, int ROWLEN, int NELEM, typename T2>
+__device__ __forceinline__ void stage_window_dup(T2 *dst, const decltype(T2::x) *__restrict__ src, int n, int gx0,
+                                                 int gy0, int tid)
+{
+    using T = decltype(T2::x);
+    constexpr int K = (NELEM + NT - 1) / NT;
+    T v[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int i = tid + k * NT;
+        const int gx = gx0 + i % ROWLEN, gy = gy0 + i / ROWLEN;
+        v[k] = (i < NELEM && gx >= 0 && gx < n && gy >= 0 && gy < n) ? src[(size_t)gy * n + gx] : T(0);
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int i = tid + k * NT;
+        if (i < NELEM) dst[i] = splat2<T2>(v[k]);
+    }
+}
+
 // y pass of one block: for window column col (tile-local x = cxl - R - P + col) the
 // column slice rows cyl .. cyl + WIN - 1 of the staged u, then for every block row r
 //   Y[r][col] = (sum_b K_y[b] u(col, row r + b - P), sum_b M_y[b] u(...)).
 // FAST: interior rows (constant 1D rows); else the rows' own 1D rows (km1y: (K, M) pairs).
 template <int P, int S, int TT, bool FAST, typename T>
-__device__ __forceinline__ void tile_ypass(const T *su, int cxl, int cyl, int lane_e, typename Vec2<T>::type *yb,
-                                           const typename Vec2<T>::type *km1y)
+__device__ __forceinline__ void tile_ypass(const typename Vec2<T>::type *su, int cxl, int cyl, int lane_e,
+                                           typename Vec2<T>::type *yb, const typename Vec2<T>::type *km1y)
 {
     using G = TileGeom<P, S, TT>;
     using T2 = typename Vec2<T>::type;
     constexpr int W = G::W, WIN = G::WIN, SW = G::SW;
     for (int col = lane_e; FAST && col < WIN; col += G::SS) {
         {
-            T v[WIN];
+            // su holds (v, v) pairs; interior rows are symmetric, so the taps at distance j
+            // from the row's centre share one packed multiply-add on their packed sum
+            T2 v[WIN];
 #pragma unroll
             for (int k = 0; k < WIN; ++k) v[k] = su[(cyl + k) * SW + cxl + col];
 #pragma unroll
             for (int r = 0; r < S; ++r) {
-                T2 y = splat2<T2>(T(0));
+                T2 y = fma2(ckm1<T>(P, P), v[r + P], splat2<T2>(T(0)));
 #pragma unroll
-                for (int bb = 0; bb < W; ++bb) y = fma2(ckm1<T>(P, bb), splat2<T2>(v[r + bb]), y);
+                for (int j = 1; j <= P; ++j) y = fma2(ckm1<T>(P, P - j), add2(v[r + P - j], v[r + P + j]), y);
                 yb[r * G::YS + col] = y;
             }
         }
@@ -606,12 +634,55 @@ __device__ __forceinline__ void tile_ypass(const T *su, int cxl, int cyl, int la
         for (int pt = lane_e; pt < S * WIN; pt += G::SS) {
             const int r = pt / WIN, col = pt - r * WIN;
             const T2 *kr = km1y + (cyl + r) * W;
-            const T *uc = su + (cyl + r) * SW + cxl + col;
+            const T2 *uc = su + (cyl + r) * SW + cxl + col;
             T2 y = splat2<T2>(T(0));
 #pragma unroll
-            for (int bb = 0; bb < W; ++bb) y = fma2(kr[bb], splat2<T2>(uc[bb * SW]), y);
+            for (int bb = 0; bb < W; ++bb) y = fma2(kr[bb], uc[bb * SW], y);
             yb[r * G::YS + col] = y;
         }
+    }
+}
+
+// y pass with two lanes per window column (SPLITY): lane l < WIN takes rows 0 .. RA - 1 of
+// column l, lane WIN + l rows RA .. S - 1.  FASTROW: interior rows (symmetric constant
+// rows); otherwise every row's own (K, M) pairs from km1y, read by all lanes at once.
+template <int P, int S, int TT, bool FASTROW, typename T>
+__device__ __forceinline__ void tile_ypass_split(const typename Vec2<T>::type *su, int cxl, int cyl, int lane,
+                                                 typename Vec2<T>::type *yb, const typename Vec2<T>::type *km1y)
+{
+    using G = TileGeom<P, S, TT>;
+    using T2 = typename Vec2<T>::type;
+    constexpr int W = G::W, WIN = G::WIN, SW = G::SW, RA = G::RA, RB = S - RA;
+    if (lane >= 2 * WIN) return;
+    const int half = lane >= WIN, col = lane - half * WIN, r0 = half ? RA : 0;
+    const T2 *up = su + (cyl + r0) * SW + cxl + col;
+    T2 v[RA + 2 * P];
+#pragma unroll
+    for (int k = 0; k < RB + 2 * P; ++k) v[k] = up[k * SW];
+    if (!half)
+#pragma unroll
+        for (int k = RB + 2 * P; k < RA + 2 * P; ++k) v[k] = up[k * SW];
+    T2 *yo = yb + r0 * G::YS + col;
+#pragma unroll
+    for (int r = 0; r < RA; ++r) {
+        if (half && r >= RB) break;
+        T2 y;
+        if constexpr (FASTROW) {
+            y = fma2(ckm1<T>(P, P), v[r + P], splat2<T2>(T(0)));
+#pragma unroll
+            for (int j = 1; j <= P; ++j) y = fma2(ckm1<T>(P, P - j), add2(v[r + P - j], v[r + P + j]), y);
+        } else {
+            const T2 *kr = km1y + (cyl + r0 + r) * W;
+            T2 y1 = splat2<T2>(T(0));
+            y = y1;
+#pragma unroll
+            for (int bb = 0; bb < W; ++bb) {
+                T2 &acc = (bb & 1) ? y1 : y;
+                acc = fma2(kr[bb], v[r + bb], acc);
+            }
+            y = add2(y, y1);
+        }
+        yo[r * G::YS] = y;
     }
 }
 
@@ -624,9 +695,14 @@ __device__ __forceinline__ T tile_xpass(const typename Vec2<T>::type *yb, int ey
     using T2 = typename Vec2<T>::type;
     constexpr int W = G::W;
     const T2 *y = yb + ey * G::YS + ex;
-    T2 s = splat2<T2>(T(0));
+    // two accumulators (even and odd taps): half the dependent chain
+    T2 s0 = splat2<T2>(T(0)), s1 = s0;
 #pragma unroll
-    for (int a = 0; a < W; ++a) s = fma2(FAST ? cmk1<T>(P, a) : mk1x[xrow * W + a], y[a], s);
+    for (int a = 0; a < W; ++a) {
+        T2 &s = (a & 1) ? s1 : s0;
+        s = fma2(FAST ? cmk1<T>(P, a) : mk1x[xrow * W + a], y[a], s);
+    }
+    const T2 s = add2(s0, s1);
     return s.x + s.y;
 }
 
@@ -659,7 +735,7 @@ k_schwarz_tile2d(int n, int nbc, int q, int g, int rev, int c0, int c1, int px, 
     constexpr int W = G::W, SS = G::SS, R = G::R, H = G::H, L = P - 1 + R;
     constexpr int SW = G::SW, BW = G::BW, NB1 = G::NB1, NT = G::NT;
     constexpr int PCI = 2 * P - 1;   // first interior row class
-    __shared__ T su[SW * SW];
+    __shared__ T2 su[SW * SW];   // u as (u, u) pairs
     __shared__ T sb[BW * BW];
     __shared__ __align__(16) T rs[G::NBLK * G::RSS];
     __shared__ T2 yb[G::NBLK * G::YB];
@@ -704,7 +780,7 @@ k_schwarz_tile2d(int n, int nbc, int q, int g, int rev, int c0, int c1, int px, 
     if (bt.active && !bt.active[blockIdx.y]) return;
     u += blockIdx.y * bt.vec;
     b += blockIdx.y * bt.vec;
-    stage_window<NT, SW, SW * SW>(su, u, n, x0 - H, y0 - H, tid);
+    stage_window_dup<NT, SW, SW * SW>(su, u, n, x0 - H, y0 - H, tid);
     stage_window<NT, BW, BW * BW>(sb, b, n, x0 - R, y0 - R, tid);
     __syncthreads();
     const int bi = slot % NB1, bj = slot / NB1;
@@ -729,9 +805,18 @@ k_schwarz_tile2d(int n, int nbc, int q, int g, int rev, int c0, int c1, int px, 
             // are the block's rows / columns all of the interior class?
             const bool yint = FAST || (y0 + cyl - R >= PCI && y0 + cyl + R <= n - 2 * P);
             const bool xint = FAST || (x0 + cxl - R >= PCI && x0 + cxl + R <= n - 2 * P);
-            if (act) {
-                if (yint) tile_ypass<P, S, TT, true>(su, cxl, cyl, e, ybs, km1y);
-                else tile_ypass<P, S, TT, false>(su, cxl, cyl, e, ybs, km1y);
+            if constexpr (G::SPLITY) {
+                // the whole warp works on its block's y pass (interior rows); lanes past the
+                // block's S^2 carry another slot number, so the warp's own block is used
+                const int ws = tid >> 5, wcx = ox + q * (ws % NB1), wcy = oy + q * (ws / NB1);
+                if (ws < G::NBLK && wcx < tw && wcy < th) {
+                    const bool wyint = FAST || (y0 + wcy - R >= PCI && y0 + wcy + R <= n - 2 * P);
+                    if (wyint) tile_ypass_split<P, S, TT, true, T>(su, wcx, wcy, lane, yb + ws * G::YB, km1y);
+                    else tile_ypass_split<P, S, TT, false, T>(su, wcx, wcy, lane, yb + ws * G::YB, km1y);
+                }
+            } else if (act) {
+                if (yint) tile_ypass<P, S, TT, true, T>(su, cxl, cyl, e, ybs, km1y);
+                else tile_ypass<P, S, TT, false, T>(su, cxl, cyl, e, ybs, km1y);
             }
             __syncwarp();
             const int gx = x0 + lx, gy = y0 + ly;
@@ -752,10 +837,15 @@ k_schwarz_tile2d(int n, int nbc, int q, int g, int rev, int c0, int c1, int px, 
                 }
                 T ev = T(0);
                 if (cls == interior) {
-                    T2 acc2 = splat2<T2>(T(0));
+                    // two pair accumulators: four independent chains
+                    T2 acc0 = splat2<T2>(T(0)), acc1 = acc0;
                     const T2 *r2 = reinterpret_cast<const T2 *>(rsb);   // 16-byte aligned, zero padded
     #pragma unroll
-                    for (int k = 0; k < G::NB2; ++k) acc2 = fma2(brow[k], r2[k], acc2);
+                    for (int k = 0; k < G::NB2; ++k) {
+                        T2 &acc = (k & 1) ? acc1 : acc0;
+                        acc = fma2(brow[k], r2[k], acc);
+                    }
+                    const T2 acc2 = add2(acc0, acc1);
                     ev = acc2.x + acc2.y;
                 } else if (sizeof(T) == sizeof(double) || !binv_lo) {
                     const T *Bi = binv + ((size_t)cls * SS + e) * SS;
@@ -772,7 +862,10 @@ k_schwarz_tile2d(int n, int nbc, int q, int g, int rev, int c0, int c1, int px, 
                     for (int k = 0; k < G::NB2; ++k) { const T2 v = r2[k]; rv[2 * k] = v.x; rv[2 * k + 1] = v.y; }
                     ev = dot2_row<SS>(binv + row, binv_lo + row, rv);
                 }
-                if (in) su[(ly + H) * SW + (lx + H)] += ev;
+                if (in) {
+                    T2 &ref = su[(ly + H) * SW + (lx + H)];
+                    ref = splat2<T2>(ref.x + ev);
+                }
             }
             __syncthreads();
             if (!rev) {
@@ -788,7 +881,7 @@ k_schwarz_tile2d(int n, int nbc, int q, int g, int rev, int c0, int c1, int px, 
     else colours(std::false_type{});
     for (int i = tid; i < BW * BW; i += NT) {
         const int gx = x0 - R + i % BW, gy = y0 - R + i / BW;
-        if (gx >= 0 && gx < n && gy >= 0 && gy < n) u[(size_t)gy * n + gx] = su[(i / BW + P) * SW + (i % BW + P)];
+        if (gx >= 0 && gx < n && gy >= 0 && gy < n) u[(size_t)gy * n + gx] = su[(i / BW + P) * SW + (i % BW + P)].x;
     }
 }
 
