@@ -70,6 +70,9 @@ def _load():
             "or_cholesky_solve": (None, [ctypes.c_int, _dp, _dp, _dp]),
             "or_setup": (ctypes.c_void_p, [ctypes.c_int] * 10),
             "or_setup_grouped": (ctypes.c_void_p, [ctypes.c_int] * 11),
+            "or_setup_plow": (ctypes.c_void_p, [ctypes.c_int] * 12),
+            "or_embed_spline": (None, [ctypes.c_int, ctypes.c_int, _dp]),
+            "or_restriction_plow": (None, [ctypes.c_int] * 4 + [_dp]),
             "or_schedule_grouped": (ctypes.c_int, [ctypes.c_int] * 9 + [_ip, _ip]),
             "or_free": (None, [ctypes.c_void_p]),
             "or_n": (ctypes.c_int, [ctypes.c_void_p]),
@@ -168,6 +171,20 @@ def restriction_1d(p: int, m: int, aggressive: bool = True) -> np.ndarray:
     return R
 
 
+def embed_spline(plow: int, mc: int) -> np.ndarray:
+    """Degree-plow embedding of the 2h space into the h space (or_embed_spline)."""
+    S = np.empty((2 * mc + plow - 2, mc + plow - 2))
+    _load().or_embed_spline(plow, mc, _d(S))
+    return S
+
+
+def restriction_plow(p: int, plow: int, m: int, aggressive: bool = True) -> np.ndarray:
+    rows = (m // 2 if aggressive else m) + plow - 2
+    R = np.empty((rows, m + p - 2))
+    _load().or_restriction_plow(p, plow, m, int(aggressive), _d(R))
+    return R
+
+
 def block_size(p: int) -> int:
     return _load().or_block_size(p)
 
@@ -241,16 +258,16 @@ class Problem:
 
     def __init__(self, dim: int, p: int, m: int, s: int = 0, sched: int = TILE,
                  tile: int = 32, coarse: int = VCYCLE, aggressive: bool = True,
-                 period: int = 0, stride: int = 0, groups: int = 1):
+                 period: int = 0, stride: int = 0, groups: int = 1, plow: int = 1):
         lib = _load()
         self._lib = lib
         s_eff = s if s > 0 else block_size(p)
         if period <= 0:
             period, stride = default_colouring(p, s_eff)
         self.period, self.stride = period, stride
-        self._h = lib.or_setup_grouped(dim, p, m, s, sched, tile, period, stride, groups, coarse,
-                                       int(aggressive))
-        self.groups = groups
+        self._h = lib.or_setup_plow(dim, p, m, s, sched, tile, period, stride, groups, coarse,
+                                    int(aggressive), plow)
+        self.groups, self.plow = groups, plow
         if not self._h:
             raise ValueError(f"oracle setup failed for dim={dim} p={p} m={m} s={s}")
         self.dim, self.p, self.m = dim, p, m

@@ -61,6 +61,20 @@ void or_load_1d(int p, int m, int kind, const double *par, int nq, double *g);
  * (2mc-1) x (mc-1).  Pinned by: [1/2,1,1/2] stencil, Galerkin identity. */
 void or_embed_p1(int mc, double *S);
 
+/* Embedding of the restricted degree-plow spline space on mc elements into the one on
+ * 2 mc elements, S = (M_fine)^{-1} (phi_fine, phi_coarse) (exact: nested spaces).
+ * (2mc + plow - 2) x (mc + plow - 2).  Pinned by: equal to or_embed_p1 for plow = 1; the
+ * quadratic subdivision weights (1/4, 3/4, 3/4, 1/4) in the interior; Galerkin identities
+ * S^T M_f S = M_c and S^T K_f S = K_c. */
+void or_embed_spline(int plow, int mc, double *S);
+
+/* Restriction of Section 3.1.2 with row-sum lumping to degree plow (1 or 2):
+ * aggressive=0: R = D^{-1} M_p^plow, (m+plow-2) x n; aggressive=1: R = S^T D^{-1} M_p^plow,
+ * (m/2+plow-2) x n, S the degree-plow 2h -> h embedding.  D = row sums of the restricted
+ * degree-plow mass.  Pinned by: scipy mixed mass, interior row sums 1, equal to
+ * or_restriction_1d for plow = 1, the dense two-level cycle with it. */
+void or_restriction_plow(int p, int plow, int m, int aggressive, double *R);
+
 /* Restriction of Section 3.1.2 with row-sum lumping, plow = 1:
  * aggressive=0: R = D^{-1} M_p^1, (m-1) x n   (same mesh h, Section 3.1.2)
  * aggressive=1: R = S^T D^{-1} M_p^1, (m/2-1) x n   (degree p -> 1, then h -> 2h,
@@ -122,6 +136,12 @@ or_problem *or_setup(int dim, int p, int m, int s, int sched_kind, int tile,
 /* or_setup with a grouped TILE schedule (or_schedule_grouped); groups = 1 is or_setup. */
 or_problem *or_setup_grouped(int dim, int p, int m, int s, int sched_kind, int tile,
                              int period, int stride, int groups, int coarse_kind, int aggressive);
+/* The same with a second level of degree plow (1 or 2, Section 3: the "linear or
+ * quadratic" coarse discretisation): the restriction or_restriction_plow and the Galerkin
+ * degree-plow matrix on the second-level mesh.  plow = 2 takes the exact second-level
+ * solve only (coarse_kind 0; the V(1,1) of Section 3.2 is for the degree-1 hierarchy). */
+or_problem *or_setup_plow(int dim, int p, int m, int s, int sched_kind, int tile, int period, int stride,
+                          int groups, int coarse_kind, int aggressive, int plow);
 void or_free(or_problem *P);
 int  or_n(const or_problem *P);          /* DOFs per axis */
 int  or_nc(const or_problem *P);         /* second-level DOFs per axis */

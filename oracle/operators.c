@@ -268,6 +268,13 @@ or_problem *or_setup(int dim, int p, int m, int s, int sched_kind, int tile,
 or_problem *or_setup_grouped(int dim, int p, int m, int s, int sched_kind, int tile,
                              int period, int stride, int groups, int coarse_kind, int aggressive)
 {
+    return or_setup_plow(dim, p, m, s, sched_kind, tile, period, stride, groups, coarse_kind, aggressive, 1);
+}
+
+or_problem *or_setup_plow(int dim, int p, int m, int s, int sched_kind, int tile, int period, int stride,
+                          int groups, int coarse_kind, int aggressive, int plow)
+{
+    if (plow < 1 || plow > 2 || (plow == 2 && coarse_kind != 0)) return NULL;
     if (dim < 2 || dim > 3 || p < 1 || m < 2) return NULL;
     if (s <= 0) s = or_block_size(p);
     if (s <= 0 || (s % 2) == 0) return NULL;
@@ -290,11 +297,11 @@ or_problem *or_setup_grouped(int dim, int p, int m, int s, int sched_kind, int t
     }
     for (long long i = 0; i < P->N; ++i) P->order_rev[i] = P->order[P->N - 1 - i];
 
-    /* second level: degree 1 on h (m elements) or on 2h (m/2 elements) */
+    /* second level: degree plow on h (m elements) or on 2h (m/2 elements) */
     const int m0 = aggressive ? m / 2 : m;
-    P->nc = m0 - 1;
+    P->nc = m0 + plow - 2;
     P->R = malloc(sizeof(double) * (size_t)P->nc * n);
-    or_restriction_1d(p, m, aggressive, P->R);
+    or_restriction_plow(p, plow, m, aggressive, P->R);
     P->Rlo = malloc(sizeof(int) * P->nc); P->Rhi = malloc(sizeof(int) * P->nc);
     P->Clo = malloc(sizeof(int) * n); P->Chi = malloc(sizeof(int) * n);
     for (int I = 0; I < P->nc; ++I) {
@@ -315,11 +322,11 @@ or_problem *or_setup_grouped(int dim, int p, int m, int s, int sched_kind, int t
     int ml = m0, L = 0;
     for (;;) {
         P->ml[L] = ml;
-        P->nl[L] = ml - 1;
-        const int nn = ml - 1;
+        P->nl[L] = ml + plow - 2;
+        const int nn = ml + plow - 2;
         P->Kl[L] = malloc(sizeof(double) * nn * nn);
         P->Ml[L] = malloc(sizeof(double) * nn * nn);
-        or_assemble_1d(1, ml, 0, P->Kl[L], P->Ml[L]);
+        or_assemble_1d(plow, ml, 0, P->Kl[L], P->Ml[L]);
         ++L;
         if (coarse_kind == 0 || ml <= 8 || (ml % 2) != 0 || L >= OR_MAXLEV) break;
         ml /= 2;

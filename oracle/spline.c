@@ -225,18 +225,60 @@ void or_embed_p1(int mc, double *S)
     free(dN);
 }
 
+/* Embedding of the restricted degree-plow space on mc elements into the one on 2 mc
+ * elements (Section 4.1: the standard transfer between spline spaces of equal degree):
+ * the coarse space is a subspace of the fine one, so the coefficients are its L2
+ * projection, S = (M_f)^{-1} (phi_f, phi_c), exact up to rounding.  Each fine element lies
+ * inside one coarse element, where both bases are polynomials of degree plow, so plow + 1
+ * Gauss points are exact.  (2 mc + plow - 2) x (mc + plow - 2). */
+void or_embed_spline(int plow, int mc, double *S)
+{
+    const int mf = 2 * mc, nf = mf + plow - 2, nc = mc + plow - 2;
+    const int nq = plow + 1;
+    double *Kf = malloc(sizeof(double) * (size_t)nf * nf), *Mf = malloc(sizeof(double) * (size_t)nf * nf);
+    double *B = calloc((size_t)nf * nc, sizeof(double));
+    double *gx = malloc(sizeof(double) * nq), *gw = malloc(sizeof(double) * nq);
+    double *xq = malloc(sizeof(double) * nq), *wq = malloc(sizeof(double) * nq);
+    double *Nf = malloc(sizeof(double) * (mf + plow)), *Nc = malloc(sizeof(double) * (mc + plow));
+    double *dtmp = malloc(sizeof(double) * (mf + plow));
+    or_assemble_1d(plow, mf, 0, Kf, Mf);
+    or_gauss(nq, gx, gw);
+    for (int e = 0; e < mf; ++e) {
+        element_points(mf, e, nq, gx, gw, xq, wq);
+        for (int q = 0; q < nq; ++q) {
+            or_basis_eval(plow, mf, xq[q], Nf, dtmp);
+            or_basis_eval(plow, mc, xq[q], Nc, dtmp);
+            for (int i = 0; i < nf; ++i) {
+                if (Nf[i + 1] == 0.0) continue;
+                for (int I = 0; I < nc; ++I) B[(size_t)i * nc + I] += wq[q] * Nf[i + 1] * Nc[I + 1];
+            }
+        }
+    }
+    /* S = M_f^{-1} B, column by column (dense Cholesky: test-size problems only) */
+    or_cholesky(nf, Mf);
+    double *col = malloc(sizeof(double) * nf), *x = malloc(sizeof(double) * nf);
+    for (int I = 0; I < nc; ++I) {
+        for (int i = 0; i < nf; ++i) col[i] = B[(size_t)i * nc + I];
+        or_cholesky_solve(nf, Mf, col, x);
+        for (int i = 0; i < nf; ++i) S[(size_t)i * nc + I] = x[i];
+    }
+    free(Kf); free(Mf); free(B); free(gx); free(gw); free(xq); free(wq); free(Nf); free(Nc); free(dtmp);
+    free(col); free(x);
+}
+
 /* Section 3.1.2: I_p^{plow} = (M_plow^plow)^{-1} M_p^{plow} with the inverse replaced by
  * the inverse of the row-sum lumped mass; Section 3.3 composes it with the
- * h -> 2h restriction S^T of the degree-1 spaces. */
-void or_restriction_1d(int p, int m, int aggressive, double *R)
+ * h -> 2h restriction S^T of the degree-plow spaces (the degree-1 embedding is the nodal
+ * one, or_embed_p1; degree 2 uses or_embed_spline).  (mr + plow - 2) x n rows, mr = m or m/2. */
+void or_restriction_plow(int p, int plow, int m, int aggressive, double *R)
 {
-    const int n = m + p - 2, n1 = m - 1;
+    const int n = m + p - 2, n1 = m + plow - 2;
     double *Mx = malloc(sizeof(double) * (size_t)n1 * n);
     double *K1 = malloc(sizeof(double) * (size_t)n1 * n1);
     double *M1 = malloc(sizeof(double) * (size_t)n1 * n1);
-    or_mixed_mass_1d(p, 1, m, Mx);
-    or_assemble_1d(1, m, 0, K1, M1);
-    /* Rp = D^{-1} M_p^1 with D_ii = sum_j (M_1^1)_ij */
+    or_mixed_mass_1d(p, plow, m, Mx);
+    or_assemble_1d(plow, m, 0, K1, M1);
+    /* Rp = D^{-1} M_p^plow with D_ii = sum_j (M_plow^plow)_ij */
     for (int i = 0; i < n1; ++i) {
         double D = 0.0;
         for (int j = 0; j < n1; ++j) D += M1[(size_t)i * n1 + j];
@@ -245,9 +287,10 @@ void or_restriction_1d(int p, int m, int aggressive, double *R)
     if (!aggressive) {
         memcpy(R, Mx, sizeof(double) * (size_t)n1 * n);
     } else {
-        const int mc = m / 2, nc = mc - 1;
+        const int mc = m / 2, nc = mc + plow - 2;
         double *S = malloc(sizeof(double) * (size_t)n1 * nc);
-        or_embed_p1(mc, S);
+        if (plow == 1) or_embed_p1(mc, S);
+        else or_embed_spline(plow, mc, S);
         for (int I = 0; I < nc; ++I)
             for (int j = 0; j < n; ++j) {
                 double acc = 0.0;
@@ -260,4 +303,9 @@ void or_restriction_1d(int p, int m, int aggressive, double *R)
     free(Mx);
     free(K1);
     free(M1);
+}
+
+void or_restriction_1d(int p, int m, int aggressive, double *R)
+{
+    or_restriction_plow(p, 1, m, aggressive, R);
 }

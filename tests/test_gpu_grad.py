@@ -120,3 +120,62 @@ def test_config4_full_size_gradient():
                   - _loss(S, _dev(tm), ut, "unrolled", ncycles=40).item()) / (2 * h)
         assert abs(g[idx] - fd) <= 1e-5 * max(1.0, abs(fd)), (idx, g[idx], fd)
     assert torch.isfinite(gu).all()
+
+
+def _dense_A_and_mass(oracle_mod, p, m):
+    K, M = oracle_mod.assemble_1d(p, m)
+    return np.kron(K, M) + np.kron(M, K), np.kron(M, M)
+
+
+@pytest.mark.parametrize("mode", ["adjoint", "unrolled"])
+def test_coefficient_gradient_matches_oracle_and_finite_differences(oracle_mod, mode):
+    """dL/df through CoeffSolve (b = (M x M) f, Section 2), L = 0.5 ||u - u_t||^2:
+    adjoint mode against the dense (M x M) A^{-1} (u - u_t); unrolled mode against
+    (M x M) C_K^T (u_K - u_t) with C_K the oracle's K-cycle map b -> u_K built column by
+    column; both against central differences of the GPU map."""
+    from paper_2009_01499_gb300.autograd import coeff_solve, load_solve
+    p, m, K = 2, 12, 6
+    S = iga2l.Solver(p, m, period=5, stride=2, coarse=iga2l.COARSE_EXACT)
+    O = oracle_mod.Problem(2, p, m, sched=oracle_mod.LATTICE, coarse=oracle_mod.EXACT, period=5, stride=2)
+    N = S.N
+    A, MM = _dense_A_and_mass(oracle_mod, p, m)
+    f = synth.coefficients(N, 61)
+    ut = synth.uniform_pm1(62, N)
+    fd = _dev(f).requires_grad_(True)
+    u = coeff_solve(fd, S, mode=mode, tol=1e-13, ncycles=K)
+    loss = 0.5 * torch.sum((u - _dev(ut)) ** 2)
+    loss.backward()
+    g = fd.grad.cpu().numpy()
+    if mode == "adjoint":
+        uo = np.linalg.solve(A, MM @ f)
+        ref = MM @ np.linalg.solve(A, uo - ut)
+    else:
+        CK = np.zeros((N, N))
+        for j in range(N):
+            e = np.zeros(N)
+            e[j] = 1.0
+            x = np.zeros(N)
+            for _ in range(K):
+                x = O.cycle(x, e)
+            CK[:, j] = x
+        uk = CK @ (MM @ f)
+        ref = MM @ (CK.T @ (uk - ut))
+    assert np.abs(g - ref).max() <= 1e-10 * np.abs(ref).max()
+    # central differences of the GPU map along two random directions
+    rng = np.random.default_rng(63)
+    for _ in range(2):
+        v = rng.standard_normal(N)
+        h = 1e-6
+        lp = float(0.5 * torch.sum((coeff_solve(_dev(f + h * v), S, mode=mode, tol=1e-13, ncycles=K) - _dev(ut)) ** 2))
+        lm = float(0.5 * torch.sum((coeff_solve(_dev(f - h * v), S, mode=mode, tol=1e-13, ncycles=K) - _dev(ut)) ** 2))
+        fdv = (lp - lm) / (2 * h)
+        assert abs(fdv - float(np.dot(g, v))) <= 1e-6 * max(1.0, abs(fdv))
+    # the load-vector form gives dL/db = lambda, and (M x M) lambda = dL/df
+    bd = torch.empty(N, dtype=torch.float64, device="cuda")
+    S.rhs_from_coeffs(_dev(f), bd)
+    bd.requires_grad_(True)
+    u2 = load_solve(bd, S, mode=mode, tol=1e-13, ncycles=K)
+    (0.5 * torch.sum((u2 - _dev(ut)) ** 2)).backward()
+    lam = bd.grad.cpu().numpy()
+    assert np.abs(MM @ lam - g).max() <= 1e-12 * np.abs(g).max()
+    S.close()
