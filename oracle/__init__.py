@@ -21,6 +21,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liboracle.so")
+_SO_OMP = os.path.join(_BUILD, "liboracle_omp.so")
 _SRCS = [os.path.join(_HERE, f) for f in ("spline.c", "operators.c")]
 _HDR = os.path.join(_HERE, "iga_oracle.h")
 _lock = threading.Lock()
@@ -34,25 +35,34 @@ _ip = ctypes.POINTER(ctypes.c_int)
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle into ``oracle/_build/liboracle.so`` (if stale)."""
+    """Compile the oracle into ``oracle/_build/liboracle.so`` and its OpenMP build
+    ``liboracle_omp.so`` (if stale)."""
     os.makedirs(_BUILD, exist_ok=True)
     newest = max(os.path.getmtime(p) for p in _SRCS + [_HDR])
-    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= newest:
-        return _SO
-    tmp = _SO + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-           "-shared", "-o", tmp] + _SRCS + ["-lm"]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, _SO)
+    for so, extra in ((_SO, []), (_SO_OMP, ["-fopenmp"])):
+        if not force and os.path.exists(so) and os.path.getmtime(so) >= newest:
+            continue
+        tmp = so + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", *extra,
+               "-shared", "-o", tmp] + _SRCS + ["-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, so)
     return _SO
 
 
-def _load():
-    global _lib
+_lib_omp = None
+
+
+def _load(threaded: bool = False):
+    """The plain oracle, or its OpenMP build (identical results) when threaded."""
+    global _lib, _lib_omp
     with _lock:
-        if _lib is not None:
+        if threaded and _lib_omp is not None:
+            return _lib_omp
+        if not threaded and _lib is not None:
             return _lib
-        lib = ctypes.CDLL(build())
+        build()
+        lib = ctypes.CDLL(_SO_OMP if threaded else _SO)
         sig = {
             "or_knots": (None, [ctypes.c_int, ctypes.c_int, _dp]),
             "or_basis_eval": (None, [ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp, _dp]),
@@ -90,11 +100,16 @@ def _load():
             "or_solve": (ctypes.c_int, [ctypes.c_void_p, _dp, ctypes.c_double, ctypes.c_int,
                                         ctypes.c_int, _dp, _ip, _dp, _dp]),
         }
+        sig["or_set_threads"] = (None, [ctypes.c_int])
+        sig["or_threads"] = (ctypes.c_int, [])
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
             fn.restype = res
             fn.argtypes = args
-        _lib = lib
+        if threaded:
+            _lib_omp = lib
+        else:
+            _lib = lib
         return lib
 
 
@@ -258,8 +273,13 @@ class Problem:
 
     def __init__(self, dim: int, p: int, m: int, s: int = 0, sched: int = TILE,
                  tile: int = 32, coarse: int = VCYCLE, aggressive: bool = True,
-                 period: int = 0, stride: int = 0, groups: int = 1, plow: int = 1):
-        lib = _load()
+                 period: int = 0, stride: int = 0, groups: int = 1, plow: int = 1, threads: int = 1):
+        """threads > 1: the OpenMP build of the oracle with that many threads (results
+        identical to the sequential oracle)."""
+        lib = _load(threaded=threads > 1)
+        if threads > 1:
+            lib.or_set_threads(int(threads))
+        self.threads = lib.or_threads()
         self._lib = lib
         s_eff = s if s > 0 else block_size(p)
         if period <= 0:

@@ -119,6 +119,14 @@ int or_schedule_grouped(int dim, int n, int s, int p, int kind, int tile, int pe
 void or_schwarz_sweep(int dim, int n, int w, int s, const double *K, const double *M,
                       const int *order, const double *b, double *u);
 
+/* Threads of the parallel loops.  The oracle is also built with OpenMP (a second shared
+ * object): the blocks of one Schwarz colour, the points of one Gauss-Seidel sub-lattice
+ * and the outputs of the stencil and transfer loops are independent, so they are split
+ * over threads with results identical to the sequential run, bit for bit (sums are never
+ * split).  Without OpenMP these are no-ops and or_threads() is 1. */
+void or_set_threads(int nthreads);
+int or_threads(void);
+
 /* Dense Cholesky A = L L^T in place (lower triangle); returns 0 or -1 (not SPD). */
 int or_cholesky(int N, double *A);
 void or_cholesky_solve(int N, const double *L, const double *b, double *x);

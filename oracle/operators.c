@@ -70,8 +70,9 @@ void or_apply_A(int dim, int n, int w, const double *K, const double *M,
                 const double *u, double *y)
 {
     const long long N = ipow(n, dim);
-    int x[3];
+    #pragma omp parallel for schedule(static)
     for (long long i = 0; i < N; ++i) {
+        int x[3];
         coords(dim, n, i, x);
         y[i] = a_row_apply(dim, n, w, K, M, x, u);
     }
@@ -178,48 +179,106 @@ void or_cholesky_solve(int N, const double *L, const double *b, double *x)
     free(y);
 }
 
+/* Scratch of one Schwarz block solve (s^d unknowns at most). */
+typedef struct {
+    long long *gidx;
+    int *gco;
+    double *AB, *rB, *eB;
+} block_scratch;
+
+static void scratch_alloc(block_scratch *w, int nbmax)
+{
+    w->gidx = malloc(sizeof(long long) * nbmax);
+    w->gco = malloc(sizeof(int) * 3 * nbmax);
+    w->AB = malloc(sizeof(double) * nbmax * nbmax);
+    w->rB = malloc(sizeof(double) * nbmax);
+    w->eB = malloc(sizeof(double) * nbmax);
+}
+
+static void scratch_free(block_scratch *w)
+{
+    free(w->gidx); free(w->gco); free(w->AB); free(w->rB); free(w->eB);
+}
+
+/* Section 3.1.1, one block: B_p^j = the s^d box around centre c clipped to the grid,
+ * u_B += (A_B)^{-1} (b - A u)_B with A_B = V A V^T by Cholesky. */
+static void schwarz_block(int dim, int n, int w, int s, const double *K, const double *M, int centre,
+                          const double *b, double *u, block_scratch *ws)
+{
+    const int r = (s - 1) / 2;
+    int c[3];
+    coords(dim, n, centre, c);
+    /* grid points of the box, lexicographic, x fastest */
+    int nb = 0;
+    const int oz0 = dim == 3 ? -r : 0, oz1 = dim == 3 ? r : 0;
+    for (int oz = oz0; oz <= oz1; ++oz)
+        for (int oy = -r; oy <= r; ++oy)
+            for (int ox = -r; ox <= r; ++ox) {
+                const int x = c[0] + ox, y = c[1] + oy, z = c[2] + oz;
+                if (x < 0 || x >= n || y < 0 || y >= n || z < 0 || z >= (dim == 3 ? n : 1)) continue;
+                ws->gco[3 * nb] = x;
+                ws->gco[3 * nb + 1] = y;
+                ws->gco[3 * nb + 2] = z;
+                ws->gidx[nb] = x + (long long)n * (y + (long long)n * z);
+                ++nb;
+            }
+    /* A_p^{B_j} = V A V^T and the block residual V (b - A u) */
+    for (int a = 0; a < nb; ++a) {
+        for (int e = 0; e < nb; ++e)
+            ws->AB[a * nb + e] = a_entry(dim, n, K, M, &ws->gco[3 * a], &ws->gco[3 * e]);
+        ws->rB[a] = b[ws->gidx[a]] - a_row_apply(dim, n, w, K, M, &ws->gco[3 * a], u);
+    }
+    or_cholesky(nb, ws->AB);
+    or_cholesky_solve(nb, ws->AB, ws->rB, ws->eB);
+    for (int a = 0; a < nb; ++a) u[ws->gidx[a]] += ws->eB[a];
+}
+
 /* Section 3.1.1: one multiplicative Schwarz iteration, blocks visited in the
  * given order; block j is the s^d box around its grid point clipped to the grid. */
 void or_schwarz_sweep(int dim, int n, int w, int s, const double *K, const double *M,
                       const int *order, const double *b, double *u)
 {
     const long long N = ipow(n, dim);
-    const int r = (s - 1) / 2;
-    const int nbmax = (int)ipow(s, dim);
-    long long *gidx = malloc(sizeof(long long) * nbmax);
-    int *gco = malloc(sizeof(int) * 3 * nbmax);
-    double *AB = malloc(sizeof(double) * nbmax * nbmax);
-    double *rB = malloc(sizeof(double) * nbmax), *eB = malloc(sizeof(double) * nbmax);
-
-    for (long long t = 0; t < N; ++t) {
-        int c[3];
-        coords(dim, n, order[t], c);
-        /* B_p^j: grid points of the box, lexicographic, x fastest */
-        int nb = 0;
-        const int oz0 = dim == 3 ? -r : 0, oz1 = dim == 3 ? r : 0;
-        for (int oz = oz0; oz <= oz1; ++oz)
-            for (int oy = -r; oy <= r; ++oy)
-                for (int ox = -r; ox <= r; ++ox) {
-                    const int x = c[0] + ox, y = c[1] + oy, z = c[2] + oz;
-                    if (x < 0 || x >= n || y < 0 || y >= n || z < 0 || z >= (dim == 3 ? n : 1)) continue;
-                    gco[3 * nb] = x;
-                    gco[3 * nb + 1] = y;
-                    gco[3 * nb + 2] = z;
-                    gidx[nb] = x + (long long)n * (y + (long long)n * z);
-                    ++nb;
-                }
-        /* A_p^{B_j} = V A V^T and the block residual V (b - A u) */
-        for (int a = 0; a < nb; ++a) {
-            for (int e = 0; e < nb; ++e)
-                AB[a * nb + e] = a_entry(dim, n, K, M, &gco[3 * a], &gco[3 * e]);
-            rB[a] = b[gidx[a]] - a_row_apply(dim, n, w, K, M, &gco[3 * a], u);
-        }
-        or_cholesky(nb, AB);
-        or_cholesky_solve(nb, AB, rB, eB);
-        for (int a = 0; a < nb; ++a) u[gidx[a]] += eB[a];
-    }
-    free(gidx); free(gco); free(AB); free(rB); free(eB);
+    block_scratch ws;
+    scratch_alloc(&ws, (int)ipow(s, dim));
+    for (long long t = 0; t < N; ++t) schwarz_block(dim, n, w, s, K, M, order[t], b, u, &ws);
+    scratch_free(&ws);
 }
+
+/* The same sweep with the colour of every centre known: each run of consecutive
+ * same-coloured centres in the order is one set of blocks that share no DOF and read
+ * none another writes, so with OpenMP the blocks of a run are solved by several threads
+ * at once; the result is the sequential sweep's, bit for bit. */
+static void schwarz_sweep_colours(int dim, int n, int w, int s, const double *K, const double *M,
+                                  const int *order, const int *colour, const double *b, double *u)
+{
+    const long long N = ipow(n, dim);
+    const int nbmax = (int)ipow(s, dim);
+    long long t0 = 0;
+    while (t0 < N) {
+        long long t1 = t0 + 1;
+        while (t1 < N && colour[order[t1]] == colour[order[t0]]) ++t1;
+        #pragma omp parallel
+        {
+            block_scratch ws;
+            scratch_alloc(&ws, nbmax);
+            #pragma omp for schedule(static)
+            for (long long t = t0; t < t1; ++t) schwarz_block(dim, n, w, s, K, M, order[t], b, u, &ws);
+            scratch_free(&ws);
+        }
+        t0 = t1;
+    }
+}
+
+/* Threads used by the parallel loops (only in the OpenMP build of the oracle). */
+#ifdef _OPENMP
+#include <omp.h>
+void or_set_threads(int nthreads) { if (nthreads > 0) omp_set_num_threads(nthreads); }
+int or_threads(void) { return omp_get_max_threads(); }
+#else
+void or_set_threads(int nthreads) { (void)nthreads; }
+int or_threads(void) { return 1; }
+#endif
 
 /* ------------------------------------------------------------------------ */
 
@@ -366,12 +425,13 @@ double or_norm2(long long N, const double *v)
 void or_residual(const or_problem *P, const double *u, const double *b, double *d)
 {
     or_apply_A(P->dim, P->n, P->w, P->K, P->M, u, d);
+    #pragma omp parallel for schedule(static)
     for (long long i = 0; i < P->N; ++i) d[i] = b[i] - d[i];
 }
 
 void or_smooth(const or_problem *P, const double *b, double *u)
 {
-    or_schwarz_sweep(P->dim, P->n, P->w, P->s, P->K, P->M, P->order, b, u);
+    schwarz_sweep_colours(P->dim, P->n, P->w, P->s, P->K, P->M, P->order, P->colour, b, u);
 }
 
 /* d_c = (R (x) R [(x) R]) d, Kronecker product of the 1D restriction. */
@@ -380,6 +440,7 @@ void or_restrict(const or_problem *P, const double *d, double *dc)
     const int n = P->n, nc = P->nc, dim = P->dim;
     const double *R = P->R;
     const int Z = dim == 3 ? nc : 1;
+    #pragma omp parallel for collapse(2) schedule(static)
     for (int K3 = 0; K3 < Z; ++K3)
         for (int J = 0; J < nc; ++J)
             for (int I = 0; I < nc; ++I) {
@@ -402,6 +463,7 @@ void or_prolong_add(const or_problem *P, const double *ec, double *u)
     const int n = P->n, nc = P->nc, dim = P->dim;
     const double *R = P->R;
     const int Z = dim == 3 ? n : 1;
+    #pragma omp parallel for collapse(2) schedule(static)
     for (int k = 0; k < Z; ++k)
         for (int j = 0; j < n; ++j)
             for (int i = 0; i < n; ++i) {
@@ -434,10 +496,12 @@ static void gs_level(const or_problem *P, int l, const double *rhs, double *e, i
     const long long Nl = ipow(nn, dim);
     const int ncol = 1 << dim;
     const int *seq = dim == 2 ? gs_seq2 : gs_seq3;
-    int x[3];
     for (int t = 0; t < ncol; ++t) {
         const int col = seq[forward ? t : ncol - 1 - t];
+        /* the points of one sub-lattice do not couple: relaxed by several threads at once */
+        #pragma omp parallel for schedule(static)
         for (long long i = 0; i < Nl; ++i) {
+            int x[3];
             coords(dim, nn, i, x);
             int c = (x[0] & 1) | ((x[1] & 1) << 1) | (dim == 3 ? ((x[2] & 1) << 2) : 0);
             if (c != col) continue;
@@ -454,8 +518,9 @@ static void level_restrict(const or_problem *P, int l, const double *r, double *
     const int dim = P->dim, nf = P->nl[l], nc = P->nl[l + 1];
     const double *S = P->Sl[l];
     const long long Nc = ipow(nc, dim);
-    int X[3];
+    #pragma omp parallel for schedule(static)
     for (long long Ic = 0; Ic < Nc; ++Ic) {
+        int X[3];
         coords(dim, nc, Ic, X);
         double acc = 0.0;
         /* column I of S is nonzero only on rows 2I .. 2I+2 */
@@ -476,8 +541,9 @@ static void level_prolong_add(const or_problem *P, int l, const double *ec, doub
     const int dim = P->dim, nf = P->nl[l], nc = P->nl[l + 1];
     const double *S = P->Sl[l];
     const long long Nf = ipow(nf, dim);
-    int x[3];
+    #pragma omp parallel for schedule(static)
     for (long long i = 0; i < Nf; ++i) {
+        int x[3];
         coords(dim, nf, i, x);
         double acc = 0.0;
         /* row x of S is nonzero only on columns (x-2)/2 .. x/2 (rounded inward) */
@@ -549,7 +615,7 @@ void or_cycle(const or_problem *P, const double *b, double *u)
 void or_cycle_adjoint(const or_problem *P, const double *b, double *u)
 {
     coarse_correction(P, b, u);
-    or_schwarz_sweep(P->dim, P->n, P->w, P->s, P->K, P->M, P->order_rev, b, u);
+    schwarz_sweep_colours(P->dim, P->n, P->w, P->s, P->K, P->M, P->order_rev, P->colour, b, u);
 }
 
 /* Section 5: random initial guess, stop when the initial residual is reduced by tol. */
