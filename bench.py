@@ -51,6 +51,8 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.json")
 ORACLE_CYCLES = os.path.join(ROOT, "tests", "golden", "oracle_cycles_m1024.json")
 # FP64 pipe of GB300: 2 FP64 FMA per clock per SM, 152 SMs, 2070 MHz maximum SM clock
 FP64_PEAK_GFLOPS = 2 * 2 * 152 * 2.070
+# FP32 pipe of GB300: 128 FP32 FMA per clock per SM
+FP32_PEAK_GFLOPS = 128 * 2 * 152 * 2.070
 
 
 def seeds(p):
@@ -382,8 +384,10 @@ def bench_high_degree(args, dev):
 
 
 def bench_batched(args, dev):
-    """256 independent 2D problems, m from {64,128,256,512} and p from {2,3,4} by seed, mixed
-    precision, autotuned schedules, concurrent groups, to 1e-8."""
+    """256 independent 2D problems, m from {64,128,256,512} and p from {2,3,4} by seed, solved
+    to 1e-8 in the mixed form and in FP64, each with autotuned schedules and concurrent
+    groups; device time between two events on the launching stream (the groups' streams
+    wait on the first and are joined before the second)."""
     import numpy as np
     import torch
     from paper_2009_01499_gb300 import iga2l, synth
@@ -393,30 +397,41 @@ def bench_batched(args, dev):
     ms_choice = np.array([64, 128, 256, 512])[(z[0::2] % np.uint64(4)).astype(int)]
     ps = np.array([2, 3, 4])[(z[1::2] % np.uint64(3)).astype(int)]
     problems = [(int(p), int(m)) for p, m in zip(ps, ms_choice)]
-    BS = BatchedSolver(problems, precision=iga2l.MIXED_FP32, autotune=True)
     f = [torch.tensor(synth.coefficients((m + p - 2) ** 2, 1000 + i), device=dev) for i, (p, m) in enumerate(problems)]
     u0 = [torch.tensor(synth.initial_guess((m + p - 2) ** 2, 2000 + i), device=dev) for i, (p, m) in enumerate(problems)]
-    fp = BS.pack(f)
-    u0p = BS.pack(u0)
-    ndofs = sum(BS.dofs)
-    times = []
-    for it in range(3):
-        u = [t.clone() for t in u0p]
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        cycles, relres, ok = BS.solve(fp, u, tol=TOL)
-        torch.cuda.synchronize()
-        times.append(time.perf_counter() - t0)
-        if not ok:
-            raise RuntimeError("batched solve did not converge")
-    sec = min(times[1:])
+    stream = torch.cuda.current_stream(dev)
     out = {"workload": "256 independent 2D Poisson problems, m uniform in {64,128,256,512}, p uniform in "
-                       "{2,3,4} (seeded), uniform[-1,1] coefficients of f, mixed precision, to 1e-8",
-           "value": ndofs / sec, "unit": "DOF/s", "dofs": ndofs, "seconds": sec, "groups": len(BS.groups),
-           "cycles_max": int(max(cycles)), "schedules": {f"p{g['p']}m{g['m']}": ("TILE" if g["schedule"] == 2 else "LATTICE")
-                                                       for g in BS.groups},
-           "timing": "host wall clock around the whole batch (groups on concurrent streams)"}
-    BS.close()
+                       "{2,3,4} (seeded), uniform[-1,1] coefficients of f, to 1e-8",
+           "timing": "CUDA events on the launching stream around the whole batch (groups on concurrent streams)"}
+    for name, prec in (("mixed", iga2l.MIXED_FP32), ("fp64", iga2l.FP64)):
+        BS = BatchedSolver(problems, precision=prec, autotune=True)
+        fp = BS.pack(f)
+        u0p = BS.pack(u0)
+        ndofs = sum(BS.dofs)
+        times, cycles = [], None
+        for it in range(3):
+            u = [t.clone() for t in u0p]
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            cycles, relres, ok = BS.solve(fp, u, tol=TOL)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            if not ok:
+                raise RuntimeError(f"batched {name} solve did not converge")
+        ms = min(times[1:])
+        out[name] = {"value": ndofs / (ms * 1e-3), "unit": "DOF/s", "dofs": ndofs, "ms": ms,
+                     "groups": len(BS.groups), "cycles_max": int(max(cycles)), "cycles": [int(c) for c in cycles],
+                     "schedules": {f"p{g['p']}m{g['m']}": ("TILE" + (f"x{g['tile_groups']}" if g["tile_groups"] > 1
+                                                                     else "") if g["schedule"] == 2 else "LATTICE")
+                                   for g in BS.groups}}
+        BS.close()
+    out["value"] = out["mixed"]["value"]
+    out["unit"] = "DOF/s"
+    out["speedup_mixed_vs_fp64"] = out["fp64"]["ms"] / out["mixed"]["ms"]
+    out["cycles_equal"] = out["mixed"]["cycles"] == out["fp64"]["cycles"]
+    for name in ("mixed", "fp64"):
+        out[name].pop("cycles")
     return out
 
 # ---------------------------------------------------------------------------- gpu arm
@@ -603,13 +618,15 @@ def run_gpu(args):
                 tot_fl += msolv_cycles[p] * fl
                 tot_ms += msolv_cycles[p] * ms
             ach = tot_fl / tot_ms / 1e6
-            pk = peaks["fp32x2"]
+            pk = FP32_PEAK_GFLOPS
             return {"bound": "alu", "achieved": round(ach, 1), "peak": round(pk, 1), "unit": "GFLOP/s",
                     "frac": round(ach / pk, 4), "traffic": None,
                     "kernel": "FP32 Schwarz sweep of the inner cycle (TILE: k_schwarz_tile2d; LATTICE: one launch per "
                               "colour or k_schwarz_persist2d)",
-                    "peak_source": "packed FP32 FMA pipe measured in this run (iga2l_fma_peak: dependent-free FMA "
-                                   "loops on every SM)",
+                    "peak_source": "FP32 FMA pipe from unit counts: 128 FMA/clk/SM x 152 SMs x 2070 MHz (the "
+                                   "packed pair instruction issues two of them); dependent-free FMA loops measured "
+                                   f"{peaks['fp32']:.0f} (scalar) and {peaks['fp32x2']:.0f} (pairs) GFLOP/s in this "
+                                   "run (iga2l_fma_peak)",
                     "flops": "sum-factorised block residual + block solve per DOF: 2[2W s(s+2p) + 2W s^2 + s^4] "
                              "+ 2 s^2, W = 2p+1",
                     "per_degree": per}
@@ -674,13 +691,12 @@ def run_gpu(args):
         digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         if rec.get("source_sha256_16") == digest:
             traffic = rec.get("bytes_per_launch")
-    pk64 = peaks["fp64"]
-    roofline = {"bound": "alu", "achieved": round(achieved, 1), "peak": round(pk64, 1),
-                "unit": "GFLOP/s", "frac": round(achieved / pk64, 4), "traffic": traffic,
+    roofline = {"bound": "alu", "achieved": round(achieved, 1), "peak": round(FP64_PEAK_GFLOPS, 1),
+                "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4), "traffic": traffic,
                 "kernel": "k_schwarz_lattice2d (one colour phase per launch)",
-                "peak_source": "FP64 FMA pipe measured in this run (iga2l_fma_peak: dependent-free FMA loops on "
-                               f"every SM); unit counts give 2 FMA/clk/SM x 152 SMs x 2070 MHz = "
-                               f"{FP64_PEAK_GFLOPS:.1f}",
+                "peak_source": "FP64 FMA pipe from unit counts: 2 FMA/clk/SM x 152 SMs x 2070 MHz (ncu reports "
+                               "the same 2 FP64 FMA per SM and cycle); a dependent-free FMA loop measured "
+                               f"{peaks['fp64']:.1f} GFLOP/s in this run (iga2l_fma_peak)",
                 "per_degree": per_p}
 
     line = {

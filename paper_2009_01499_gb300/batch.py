@@ -4,10 +4,11 @@ Problems are grouped by (p, m); each group is one batch handle of the library
 (shared tables, one launch per step for the whole group, converged problems
 masked on the device, cycles replayed from captured CUDA graphs).  Groups run
 concurrently, each on its own CUDA stream driven by its own host thread (the
-library's calls release the GIL).  For every group the schedule (LATTICE or
-TILE(32) colouring of the Schwarz step) is chosen by timing a seeded probe
-solve with each candidate; choices are cached per (device, p, m, precision),
-in memory and optionally in a JSON file.
+library's calls release the GIL).  For every group the schedule of the Schwarz step
+(LATTICE, or TILE with its colours in 1, 2 or 4 groups) is chosen by timing a seeded
+probe solve to 1e-8 with each candidate, so a candidate that costs cycles loses what it
+saves per cycle; choices are cached per (device, p, m, precision), in memory and
+optionally in a JSON file.
 
 This module is host orchestration only: all arithmetic runs in libiga2l.so.
 """
@@ -23,7 +24,8 @@ import torch
 from . import iga2l, synth
 
 COLOURING = {2: (5, 2), 3: (7, 2), 4: (7, 2), 5: (10, 3), 6: (11, 4), 7: (14, 5), 8: (17, 4)}
-CANDIDATES = (iga2l.SCHED_LATTICE, iga2l.SCHED_TILE)
+# (schedule, TILE colour groups); TILE is compiled for blocks up to 5x5 (p <= 6)
+CANDIDATES = ((iga2l.SCHED_LATTICE, 0), (iga2l.SCHED_TILE, 1), (iga2l.SCHED_TILE, 2), (iga2l.SCHED_TILE, 4))
 _cache: dict = {}
 _cache_lock = threading.Lock()
 
@@ -33,8 +35,9 @@ def _key(p, m, precision):
     return f"{name}|p={p}|m={m}|prec={precision}"
 
 
-def autotune_schedule(p: int, m: int, precision: int, cache_path: str | None = None, reps: int = 2) -> int:
-    """Fastest schedule (time to a 1e-8 residual on a seeded probe problem)."""
+def autotune_schedule(p: int, m: int, precision: int, cache_path: str | None = None, reps: int = 2):
+    """Fastest (schedule, TILE colour groups) by the time to a 1e-8 residual on a seeded
+    probe problem of the same (p, m)."""
     key = _key(p, m, precision)
     with _cache_lock:
         if key in _cache:
@@ -48,10 +51,10 @@ def autotune_schedule(p: int, m: int, precision: int, cache_path: str | None = N
                 return _cache[key]
     q, g = COLOURING[p]
     best, best_ms = None, float("inf")
-    for sched in CANDIDATES:
+    for sched, groups in CANDIDATES:
         if sched == iga2l.SCHED_TILE and p > 6:   # TILE is compiled for blocks up to 5x5
             continue
-        S = iga2l.Solver(p, m, period=q, stride=g, precision=precision, schedule=sched)
+        S = iga2l.Solver(p, m, period=q, stride=g, precision=precision, schedule=sched, tile_groups=groups)
         f = torch.tensor(synth.coefficients(S.N, 77), device="cuda")
         b = torch.empty_like(f)
         S.rhs_from_coeffs(f, b)
@@ -68,7 +71,7 @@ def autotune_schedule(p: int, m: int, precision: int, cache_path: str | None = N
         ms = min(times[1:])
         S.close()
         if ms < best_ms:
-            best, best_ms = sched, ms
+            best, best_ms = [sched, groups], ms
     with _cache_lock:
         _cache[key] = best
         if cache_path:
@@ -92,13 +95,18 @@ class BatchedSolver:
             groups.setdefault((p, m), []).append(idx)
         self.groups = []
         for (p, m), members in groups.items():
-            sched = schedule if schedule is not None else (
-                autotune_schedule(p, m, precision, cache_path) if autotune else iga2l.SCHED_LATTICE)
+            if schedule is not None:
+                sched, groups_ = schedule, 0
+            elif autotune:
+                sched, groups_ = autotune_schedule(p, m, precision, cache_path)
+            else:
+                sched, groups_ = iga2l.SCHED_LATTICE, 0
             q, g = COLOURING[p]
             h = iga2l.Solver(p, m, nbatch=len(members), batch=True, period=q, stride=g, precision=precision,
-                             schedule=sched, rhs=iga2l.RHS_IS_LOAD if rhs_is_load else iga2l.RHS_COEFFS)
+                             schedule=sched, tile_groups=groups_,
+                             rhs=iga2l.RHS_IS_LOAD if rhs_is_load else iga2l.RHS_COEFFS)
             self.groups.append({"p": p, "m": m, "members": members, "handle": h, "schedule": sched,
-                                "stream": torch.cuda.Stream()})
+                                "tile_groups": h.tile_groups, "stream": torch.cuda.Stream()})
         self.dofs = [(m + p - 2) ** 2 for p, m in self.problems]
 
     def pack(self, vectors):

@@ -58,7 +58,8 @@ def test_uneven_groups_match_single_solves():
     for g in BS.groups:
         p, m = g["p"], g["m"]
         q, gg = COLOURING[p]
-        S = iga2l.Solver(p, m, period=q, stride=gg, precision=iga2l.MIXED_FP32, schedule=g["schedule"])
+        S = iga2l.Solver(p, m, period=q, stride=gg, precision=iga2l.MIXED_FP32, schedule=g["schedule"],
+                         tile_groups=g["tile_groups"])
         for i in g["members"]:
             us = u0[i].clone()
             c1, r1, _, ok1 = S.solve_load(bb[i].clone(), us, tol=1e-8)
