@@ -76,6 +76,21 @@ def schwarz_flops_per_dof(p, s, dim=2):
     return 2 * sd * w ** dim + sd + 2 * sd * sd + sd
 
 
+def kernel_source_digest(relpath, function):
+    """Hash of one kernel's definition text (from its name at the start of a line to the
+    closing brace at the start of a line): a traffic record stays valid while that text
+    is unchanged."""
+    try:
+        text = open(os.path.join(ROOT, relpath)).read()
+    except OSError:
+        return None
+    start = text.find("\n" + function + "(")
+    if start < 0:
+        return None
+    end = text.find("\n}\n", start)
+    return hashlib.sha256(text[start:end].encode()).hexdigest()[:16] if end > 0 else None
+
+
 def schwarz_flops_per_dof_f32(p, s):
     """Algorithmic FP32 flops of one Schwarz block (one per DOF) in the sum-factorised form of
     the FP32 kernels: y pass 2W s (s + 2p) and x pass 2W s^2 multiply-adds (pairs K, M), the
@@ -687,9 +702,7 @@ def run_gpu(args):
     traffic = None
     if os.path.exists(TRAFFIC_FILE):
         rec = json.load(open(TRAFFIC_FILE))
-        src = os.path.join(ROOT, "paper_2009_01499_gb300", "csrc", "kernels_fine.cu")
-        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        if rec.get("source_sha256_16") == digest:
+        if rec.get("kernel_source_sha256_16") == kernel_source_digest(rec.get("source", ""), rec.get("function", "")):
             traffic = rec.get("bytes_per_launch")
     roofline = {"bound": "alu", "achieved": round(achieved, 1), "peak": round(FP64_PEAK_GFLOPS, 1),
                 "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4), "traffic": traffic,
@@ -755,7 +768,10 @@ def run_profile_step(args):
     m = args.profile_m or (128 if dim == 3 else M_ELEM)
     prec = {"fp64": iga2l.FP64, "mixed": iga2l.MIXED_FP32, "mixed_all": iga2l.MIXED_FP32_ALL,
             "mixed_tf32": iga2l.MIXED_TF32}[args.profile_precision]
-    if args.profile_schedule:
+    best = {2: iga2l.SCHED_TILE, 3: iga2l.SCHED_TILE, 4: iga2l.SCHED_LATTICE, 5: iga2l.SCHED_TILE}
+    if args.profile_schedule == "best":     # the benchmark's mixed schedules per degree
+        sched = None
+    elif args.profile_schedule:
         sched = iga2l.SCHED_TILE if args.profile_schedule == "tile" else iga2l.SCHED_LATTICE
     else:
         sched = iga2l.SCHED_LATTICE if (prec in (iga2l.FP64, iga2l.MIXED_TF32) or dim == 3) else iga2l.SCHED_TILE
@@ -763,7 +779,8 @@ def run_profile_step(args):
              "persistent": iga2l.SWEEP_PERSISTENT}[args.profile_sweep]
     for p in degrees:
         col = {"period": COLOURING[p][0], "stride": COLOURING[p][1]} if p in COLOURING else {}   # else the default
-        S = iga2l.Solver(p, m, dim=dim, precision=prec, schedule=sched, graphs=0, sweep=sweep, **col)
+        sch = sched if sched is not None else best.get(p, iga2l.SCHED_LATTICE)
+        S = iga2l.Solver(p, m, dim=dim, precision=prec, schedule=sch, graphs=0, sweep=sweep, **col)
         sf, su = seeds(p)
         f = torch.tensor(synth.coefficients(S.N, sf), device=dev)
         u0 = torch.tensor(synth.initial_guess(S.N, su), device=dev)
@@ -836,7 +853,7 @@ def main():
     ap.add_argument("--profile-p", type=int, default=0)
     ap.add_argument("--profile-precision", choices=["fp64", "mixed", "mixed_all", "mixed_tf32"], default="fp64",
                     help="form profiled by --profile-step (the benchmark's schedule for it)")
-    ap.add_argument("--profile-schedule", choices=["lattice", "tile"], default=None,
+    ap.add_argument("--profile-schedule", choices=["lattice", "tile", "best"], default=None,
                     help="schedule profiled by --profile-step (default: the benchmark's for the form)")
     ap.add_argument("--profile-sweep", choices=["auto", "per_colour", "persistent"], default="auto",
                     help="FP32 inner sweep kernel profiled by --profile-step")

@@ -303,52 +303,91 @@ __device__ __forceinline__ void frame_block(int f, int nbx, int ix0, int iy0, in
     i = f % nbx;
 }
 
+// Resident CTAs per SM the register allocation must allow, so that a 1024^2 colour (4.1 to
+// 7.7 CTAs of 256 threads per SM for p = 2..6) runs in one wave
+constexpr int lattice_sf_minb(int p) { return p == 2 ? 8 : (p == 3 ? 6 : (p == 4 ? 7 : (p <= 6 ? 5 : 4))); }
+
 template <int P, int S, typename T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, lattice_sf_minb(P))
 k_schwarz_lattice2d_sf(int n, int nbc, int q, int ox, int oy, int nbx, int ix0, int iy0, int nix, int niy,
                        int nblocks,
                        const T *__restrict__ kband, const T *__restrict__ mband,
-                       const T *__restrict__ binv, const double *__restrict__ binv64, int interior,
-                       const int *__restrict__ bcls, T *__restrict__ u, const T *__restrict__ b, BatchRef bt)
+                       const T *__restrict__ binv, const float *__restrict__ binv_lo, int interior,
+                       T *__restrict__ u, const T *__restrict__ b, BatchRef bt)
 {
     using T2 = typename Vec2<T>::type;
     constexpr int W = 2 * P + 1, SS = S * S, R = (S - 1) / 2, WIN = S + 2 * P, PCI = 2 * P - 1;
-    constexpr int NT = 256, NB = NT / WIN;
-    __shared__ T2 yb[NB][S][WIN];
+    constexpr int NT = 256, NB = NT / WIN, YS = WIN | 1, L = P - 1 + R;
+    __shared__ T2 yb[NB][S][YS];
     __shared__ T rs[NB][SS];
+    __shared__ T sub[NB][SS];   // u at the block's DOFs (from the window columns)
+    __shared__ T sbb[NB][SS];   // b at the block's DOFs
     __shared__ T sbi[SS * SS];
+    __shared__ int scx[NB], scy[NB], scls[NB];   // block centres and classes (cls < 0: no block)
     const int tid = threadIdx.x;
     for (int i = tid; i < SS * SS; i += NT) sbi[i] = binv[(size_t)interior * SS * SS + i];   // constant table
+    const int blk0 = blockIdx.x * NB;
+    if (tid < NB) {   // the CTA's blocks, once (frame_block divides by the colour's row length)
+        const int blk = blk0 + tid;
+        int cls = -1, cx = 0, cy = 0;
+        if (blk < nblocks) {
+            int bi_, bj_;
+            frame_block(blk, nbx, ix0, iy0, nix, niy, bi_, bj_);
+            cx = ox + q * bi_;
+            cy = oy + q * bj_;
+            const int bx = cx < L ? cx : (cx > n - 1 - L ? 2 * L - (n - 1 - cx) : L);
+            const int by = cy < L ? cy : (cy > n - 1 - L ? 2 * L - (n - 1 - cy) : L);
+            cls = by * nbc + bx;
+        }
+        scx[tid] = cx;
+        scy[tid] = cy;
+        scls[tid] = cls;
+    }
     pdl_wait();
     if (bt.active && !bt.active[blockIdx.y]) return;
     u += blockIdx.y * bt.vec;
     b += blockIdx.y * bt.vec;
-    const int blk0 = blockIdx.x * NB;
-    // 1. y pass
+    __syncthreads();
+    const T h = T(1) / T(n - P + 2), hinv = T(n - P + 2);   // boundary rows and columns only
+    // 1. thread (block j, window column c): the column's WIN values of u and, for the block's
+    //    own columns, its S values of b -- every global load of the launch in one round trip --
+    //    then the pairs (sum_b K_y[b] u, sum_b M_y[b] u) of the block's S rows
     if (tid < NB * WIN) {
-        const int j = tid / WIN, c = tid - j * WIN, blk = blk0 + j;
-        if (blk < nblocks) {
-            int bi_, bj_;
-            frame_block(blk, nbx, ix0, iy0, nix, niy, bi_, bj_);
-            const int cx = ox + q * bi_, cy = oy + q * bj_;
+        const int j = tid / WIN, c = tid - j * WIN;
+        if (scls[j] >= 0) {
+            const int cx = scx[j], cy = scy[j];
             const int x = cx - R - P + c;
-            const bool xin = x >= 0 && x < n;
-            T v[WIN];
+            const bool xin = x >= 0 && x < n, own = c >= P && c < P + S;
+            T v[WIN], bv[S];
 #pragma unroll
             for (int k = 0; k < WIN; ++k) {
                 const int y = cy - R - P + k;
                 v[k] = (xin && y >= 0 && y < n) ? u[(size_t)y * n + x] : T(0);
             }
+#pragma unroll
+            for (int r = 0; r < S; ++r) {
+                const int y = cy - R + r;
+                bv[r] = (own && xin && y >= 0 && y < n) ? b[(size_t)y * n + x] : T(0);
+            }
+            if (own)
+#pragma unroll
+                for (int r = 0; r < S; ++r) {
+                    sub[j][r * S + c - P] = v[P + r];
+                    sbb[j][r * S + c - P] = bv[r];
+                }
             const bool yint = cy - R >= PCI && cy + R <= n - 2 * P;
 #pragma unroll
             for (int r = 0; r < S; ++r) {
-                T2 acc = splat2<T2>(T(0));
+                T2 acc;
                 if (yint) {
+                    // interior rows are symmetric: the taps at distance jj share one multiply-add
+                    acc = fma2(ckm1<T>(P, P), splat2<T2>(v[r + P]), splat2<T2>(T(0)));
 #pragma unroll
-                    for (int bb = 0; bb < W; ++bb) acc = fma2(ckm1<T>(P, bb), splat2<T2>(v[r + bb]), acc);
+                    for (int jj = 1; jj <= P; ++jj)
+                        acc = fma2(ckm1<T>(P, P - jj), splat2<T2>(v[r + P - jj] + v[r + P + jj]), acc);
                 } else {
+                    acc = splat2<T2>(T(0));
                     const int gy = cy - R + r;
-                    const T h = T(1) / T(n - P + 2), hinv = T(n - P + 2);   // boundary rows only
                     if (gy >= 0 && gy < n) {
 #pragma unroll
                         for (int bb = 0; bb < W; ++bb) {
@@ -364,64 +403,65 @@ k_schwarz_lattice2d_sf(int n, int nbc, int q, int ox, int oy, int nbx, int ix0, 
         }
     }
     __syncthreads();
-    // 2. x pass and block residuals
+    // 2. x pass and block residuals (shared memory only)
     for (int o = tid; o < NB * SS; o += NT) {
-        const int j = o / SS, e = o - j * SS, blk = blk0 + j;
-        if (blk >= nblocks) continue;
-        int bi_, bj_;
-        frame_block(blk, nbx, ix0, iy0, nix, niy, bi_, bj_);
-        const int cx = ox + q * bi_, cy = oy + q * bj_;
-        const int ey = e / S, ex = e - ey * S;
+        const int j = o / SS, e = o - j * SS, ey = e / S, ex = e - ey * S;
+        if (scls[j] < 0) continue;
+        const int cx = scx[j], cy = scy[j];
         const int x = cx - R + ex, y = cy - R + ey;
         T r = T(0);
         if (x >= 0 && x < n && y >= 0 && y < n) {
             const bool xint = cx - R >= PCI && cx + R <= n - 2 * P;
-            T2 acc = splat2<T2>(T(0));
+            T2 a0 = splat2<T2>(T(0)), a1 = a0;
             if (xint) {
 #pragma unroll
-                for (int a = 0; a < W; ++a) acc = fma2(cmk1<T>(P, a), yb[j][ey][ex + a], acc);
+                for (int a = 0; a < W; ++a) {
+                    T2 &acc = (a & 1) ? a1 : a0;
+                    acc = fma2(cmk1<T>(P, a), yb[j][ey][ex + a], acc);
+                }
             } else {
-                const T h = T(1) / T(n - P + 2), hinv = T(n - P + 2);   // boundary columns only
 #pragma unroll
                 for (int a = 0; a < W; ++a) {
                     T2 mk;
                     mk.x = mband[(size_t)x * W + a] * hinv;
                     mk.y = kband[(size_t)x * W + a] * h;
+                    T2 &acc = (a & 1) ? a1 : a0;
                     acc = fma2(mk, yb[j][ey][ex + a], acc);
                 }
             }
-            r = b[(size_t)y * n + x] - (acc.x + acc.y);
+            const T2 acc = add2(a0, a1);
+            r = sbb[j][e] - (acc.x + acc.y);
         }
         rs[j][e] = r;
     }
     __syncthreads();
-    // 3. block solves
+    // 3. block solves: interior class from shared memory, boundary classes from their own
+    //    inverse (FP64 rows as FP32 pairs by compensated arithmetic when binv_lo is given)
     for (int o = tid; o < NB * SS; o += NT) {
-        const int j = o / SS, e = o - j * SS, blk = blk0 + j;
-        if (blk >= nblocks) continue;
-        int bi_, bj_;
-        frame_block(blk, nbx, ix0, iy0, nix, niy, bi_, bj_);
-        const int cx = ox + q * bi_, cy = oy + q * bj_;
-        const int x = cx - R + e % S, y = cy - R + e / S;
+        const int j = o / SS, e = o - j * SS;
+        const int cls = scls[j];
+        if (cls < 0) continue;
+        const int x = scx[j] - R + e % S, y = scy[j] - R + e / S;
         if (x < 0 || x >= n || y < 0 || y >= n) continue;
-        const int cls = bcls[cy] * nbc + bcls[cx];
         T ev = T(0);
         if (cls == interior) {
             const T *Bi = sbi + e * SS;
+            T e1 = T(0);
 #pragma unroll
-            for (int f = 0; f < SS; ++f) ev = fma(Bi[f], rs[j][f], ev);
-        } else if (sizeof(T) == sizeof(double) || !binv64) {
+            for (int f = 0; f < SS; ++f) {
+                T &acc = (f & 1) ? e1 : ev;
+                acc = fma(Bi[f], rs[j][f], acc);
+            }
+            ev += e1;
+        } else if (sizeof(T) == sizeof(double) || !binv_lo) {
             const T *Bi = binv + ((size_t)cls * SS + e) * SS;
 #pragma unroll
             for (int f = 0; f < SS; ++f) ev = fma(__ldg(&Bi[f]), rs[j][f], ev);
-        } else {
-            const double *Bi = binv64 + ((size_t)cls * SS + e) * SS;
-            double ed[4] = {0.0, 0.0, 0.0, 0.0};
-#pragma unroll
-            for (int f = 0; f < SS; ++f) ed[f & 3] = fma(__ldg(&Bi[f]), (double)rs[j][f], ed[f & 3]);
-            ev = (T)((ed[0] + ed[1]) + (ed[2] + ed[3]));
+        } else if constexpr (sizeof(T) == sizeof(float)) {
+            const size_t row = ((size_t)cls * SS + e) * SS;
+            ev = dot2_row<SS>(binv + row, binv_lo + row, &rs[j][0]);
         }
-        u[(size_t)y * n + x] += ev;
+        u[(size_t)y * n + x] = sub[j][e] + ev;
     }
 }
 
@@ -806,6 +846,7 @@ k_schwarz_tile2d(int n, int nbc, int q, int g, int rev, int c0, int c1, int px, 
             const bool yint = FAST || (y0 + cyl - R >= PCI && y0 + cyl + R <= n - 2 * P);
             const bool xint = FAST || (x0 + cxl - R >= PCI && x0 + cxl + R <= n - 2 * P);
             if constexpr (G::SPLITY) {
+                (void)yint;
                 // the whole warp works on its block's y pass (interior rows); lanes past the
                 // block's S^2 carry another slot number, so the warp's own block is used
                 const int ws = tid >> 5, wcx = ox + q * (ws % NB1), wcy = oy + q * (ws / NB1);
@@ -1118,7 +1159,7 @@ cudaError_t schwarz_lattice_p(const Solver &S, const T *stencil, const T *kband,
             if (nframe <= 0) continue;
             err = launch_pdl(k_schwarz_lattice2d_sf<P, SB, T>, dim3((nframe + NBSF - 1) / NBSF, S.nbatch), dim3(256),
                              st, S.n, S.ht.nbc, q, ox, oy, nbx, ix0, iy0, nix, niy, nframe, kband, mband, binv,
-                             S.boundary64(), interior, (const int *)S.bcls, u, b, BatchRef{S.active, S.N, 0, 0});
+                             S.boundary_lo(), interior, u, b, BatchRef{S.active, S.N, 0, 0});
         } else {
             const int bpc = lattice_bpc((long long)nblocks * S.nbatch, SB * SB, S.nsm);
             if constexpr (SB >= 7)   // sum factorisation pays once the block is as wide as the stencil
