@@ -55,7 +55,9 @@ extern "C" {
 #define IGA2L_MIXED_FP32_ALL 2
 /* IGA2L_MIXED_FP32 with the interior blocks of every LATTICE colour computed as one
  * tensor-core GEMM (tcgen05, TF32 operands, FP32 accumulation): e_B = [A_B^-1 | -A_B^-1
- * A_(B,patch)] [b_B ; u_patch]; 2D, LATTICE schedule, p <= 6 */
+ * A_(B,patch)] [b_B ; u_patch], the colour's other (boundary) blocks in FP32 in the same
+ * launch; single 2D problems, LATTICE schedule, p <= 5 (IGA2L_ERR_UNSUPPORTED otherwise, or
+ * when the lattice period makes a CTA's tile of 128 blocks exceed the shared memory) */
 #define IGA2L_MIXED_TF32 3
 /* schedule: colour classes of the multiplicative Schwarz step */
 #define IGA2L_SCHED_LATTICE 1

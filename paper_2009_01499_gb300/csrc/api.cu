@@ -480,8 +480,8 @@ static int assemble_impl(int p, int m, int dim, int nbatch, bool batch, const ig
     if (opt.precision != IGA2L_FP64 && opt.precision != IGA2L_MIXED_FP32 && opt.precision != IGA2L_MIXED_FP32_ALL &&
         opt.precision != IGA2L_MIXED_TF32)
         return fail(IGA2L_ERR_UNSUPPORTED, "precision not available");
-    if (opt.precision == IGA2L_MIXED_TF32 && (dim != 2 || opt.schedule != IGA2L_SCHED_LATTICE || p > kTcMaxP))
-        return fail(IGA2L_ERR_UNSUPPORTED, "the tensor-core form is compiled for 2D, LATTICE, p <= 6");
+    if (opt.precision == IGA2L_MIXED_TF32 && (dim != 2 || batch || opt.schedule != IGA2L_SCHED_LATTICE || p > kTcMaxP))
+        return fail(IGA2L_ERR_UNSUPPORTED, "the tensor-core form is compiled for single 2D problems, LATTICE, p <= 5");
     if (opt.schedule != IGA2L_SCHED_LATTICE && opt.schedule != IGA2L_SCHED_TILE)
         return fail(IGA2L_ERR_UNSUPPORTED, "schedule not available");
     if (dim == 3 && opt.schedule == IGA2L_SCHED_TILE) {
@@ -798,6 +798,11 @@ static int assemble_impl(int p, int m, int dim, int nbatch, bool batch, const ig
             if ((ce = upload(S, &X.gtc, g)) != cudaSuccess) {
                 release(S);
                 return cuda_fail(ce, "tensor-core operator upload");
+            }
+            std::string why;
+            if (!tc_colour_prepare(*S, why)) {
+                release(S);
+                return fail(IGA2L_ERR_UNSUPPORTED, why.c_str());
             }
         }
         X.enabled = true;

@@ -266,11 +266,11 @@ cudaError_t launch3d_inner_fine(const Solver &S, const float *r32, cudaStream_t 
 cudaError_t launch3d_inner_coarse(const Solver &S, cudaStream_t st);
 cudaError_t launch3d_inner_update(const Solver &S, double *u, cudaStream_t st);
 // tensor-core Schwarz (kernels_tc.cu): the colour's block-index range [i0, i0 + ni) along one
-// axis whose blocks (and their patches) see only interior rows, and one colour's interior
-// rectangle of blocks as a TF32 GEMM on tcgen05 (2D, p <= 6)
+// axis whose blocks (and their patches) see only interior rows
 void tc_interior_rect(const Solver &S, int o, int nb, int &i0, int &ni);
-cudaError_t launch_schwarz_tc(const Solver &S, int ox, int oy, int ix0, int iy0, int nix, int niy, const float *b,
-                              float *u, cudaStream_t st);
+// checks that the tensor-core colour step's shared memory (set by the lattice period q) fits
+// the device and allows it for the kernel (kernels_fine.cu); false: not available
+bool tc_colour_prepare(const Solver &S, std::string &why);
 // persistent LATTICE sweep of the FP32 inner cycle (kernels_persist.cu): plans the launch
 // (false: not available for this handle, per-colour launches are used) and runs one sweep
 bool persist_setup(Solver &S);
@@ -279,7 +279,7 @@ cudaError_t upload_persist_rows(int p, const double *k1, const double *m1);
 // host: G of the interior block in the operand layout (kernels_tc.cu)
 void build_gtc(const Solver &S, const std::vector<double> &binv_interior, std::vector<float> &g, int &nrows,
                int &kcols);
-constexpr int kTcMaxP = 6;
+constexpr int kTcMaxP = 5;
 
 // The interior 1D rows k = h K_row, m = M_row / h of degree p (h-independent) into
 // constant memory; written once per device and degree.

@@ -18,10 +18,12 @@
 #include <cuda_runtime.h>
 
 #include <mutex>
+#include <string>
 #include <type_traits>
 
 #include "device_util.cuh"
 #include "internal.h"
+#include "tc_util.cuh"
 
 namespace iga2l {
 
@@ -307,26 +309,45 @@ __device__ __forceinline__ void frame_block(int f, int nbx, int ix0, int iy0, in
 // 7.7 CTAs of 256 threads per SM for p = 2..6) runs in one wave
 constexpr int lattice_sf_minb(int p) { return p == 2 ? 8 : (p == 3 ? 6 : (p == 4 ? 7 : (p <= 6 ? 5 : 4))); }
 
-template <int P, int S, typename T>
-__global__ void __launch_bounds__(256, lattice_sf_minb(P))
-k_schwarz_lattice2d_sf(int n, int nbc, int q, int ox, int oy, int nbx, int ix0, int iy0, int nix, int niy,
-                       int nblocks,
-                       const T *__restrict__ kband, const T *__restrict__ mband,
-                       const T *__restrict__ binv, const float *__restrict__ binv_lo, int interior,
-                       T *__restrict__ u, const T *__restrict__ b, BatchRef bt)
+// Shared memory of one CTA of the per-colour FP32 step (NT threads).
+template <int P, int S, typename T, int NT>
+struct SfSmem {
+    using T2 = typename Vec2<T>::type;
+    static constexpr int SS = S * S, WIN = S + 2 * P, NB = NT / WIN, YS = WIN | 1;
+    T2 yb[NB][S][YS];
+    T rs[NB][SS];
+    T sub[NB][SS];   // u at the block's DOFs (from the window columns)
+    T sbb[NB][SS];   // b at the block's DOFs
+    T sbi[SS * SS];
+    int scx[NB], scy[NB], scls[NB];   // block centres and classes (cls < 0: no block)
+};
+
+// The work of one CTA of a colour phase: blocks vb NB .. vb NB + NB - 1 of the colour (in the
+// numbering of frame_block, which skips the rectangle [ix0, ix0 + nix) x [iy0, iy0 + niy)).
+// All NT threads call it; `pre` runs between the constant-table reads and the first
+// dependent read (the programmatic-launch wait) and returns whether the CTA goes on (the
+// same answer in every thread).
+template <int P, int S, typename T, int NT, typename Pre>
+__device__ __forceinline__ void schwarz_sf_cta(SfSmem<P, S, T, NT> &sm, int vb, int n, int nbc, int q, int ox,
+                                               int oy, int nbx, int ix0, int iy0, int nix, int niy, int nblocks,
+                                               const T *__restrict__ kband, const T *__restrict__ mband,
+                                               const T *__restrict__ binv, const float *__restrict__ binv_lo,
+                                               int interior, T *__restrict__ u, const T *__restrict__ b, Pre pre)
 {
     using T2 = typename Vec2<T>::type;
     constexpr int W = 2 * P + 1, SS = S * S, R = (S - 1) / 2, WIN = S + 2 * P, PCI = 2 * P - 1;
-    constexpr int NT = 256, NB = NT / WIN, YS = WIN | 1, L = P - 1 + R;
-    __shared__ T2 yb[NB][S][YS];
-    __shared__ T rs[NB][SS];
-    __shared__ T sub[NB][SS];   // u at the block's DOFs (from the window columns)
-    __shared__ T sbb[NB][SS];   // b at the block's DOFs
-    __shared__ T sbi[SS * SS];
-    __shared__ int scx[NB], scy[NB], scls[NB];   // block centres and classes (cls < 0: no block)
+    constexpr int NB = SfSmem<P, S, T, NT>::NB, L = P - 1 + R;
+    auto &yb = sm.yb;
+    auto &rs = sm.rs;
+    auto &sub = sm.sub;
+    auto &sbb = sm.sbb;
+    auto &sbi = sm.sbi;
+    auto &scx = sm.scx;
+    auto &scy = sm.scy;
+    auto &scls = sm.scls;
     const int tid = threadIdx.x;
     for (int i = tid; i < SS * SS; i += NT) sbi[i] = binv[(size_t)interior * SS * SS + i];   // constant table
-    const int blk0 = blockIdx.x * NB;
+    const int blk0 = vb * NB;
     if (tid < NB) {   // the CTA's blocks, once (frame_block divides by the colour's row length)
         const int blk = blk0 + tid;
         int cls = -1, cx = 0, cy = 0;
@@ -343,10 +364,7 @@ k_schwarz_lattice2d_sf(int n, int nbc, int q, int ox, int oy, int nbx, int ix0, 
         scy[tid] = cy;
         scls[tid] = cls;
     }
-    pdl_wait();
-    if (bt.active && !bt.active[blockIdx.y]) return;
-    u += blockIdx.y * bt.vec;
-    b += blockIdx.y * bt.vec;
+    if (!pre()) return;
     __syncthreads();
     const T h = T(1) / T(n - P + 2), hinv = T(n - P + 2);   // boundary rows and columns only
     // 1. thread (block j, window column c): the column's WIN values of u and, for the block's
@@ -462,6 +480,281 @@ k_schwarz_lattice2d_sf(int n, int nbc, int q, int ox, int oy, int nbx, int ix0, 
             ev = dot2_row<SS>(binv + row, binv_lo + row, &rs[j][0]);
         }
         u[(size_t)y * n + x] = sub[j][e] + ev;
+    }
+}
+
+template <int P, int S, typename T>
+__global__ void __launch_bounds__(256, lattice_sf_minb(P))
+k_schwarz_lattice2d_sf(int n, int nbc, int q, int ox, int oy, int nbx, int ix0, int iy0, int nix, int niy,
+                       int nblocks,
+                       const T *__restrict__ kband, const T *__restrict__ mband,
+                       const T *__restrict__ binv, const float *__restrict__ binv_lo, int interior,
+                       T *__restrict__ u, const T *__restrict__ b, BatchRef bt)
+{
+    __shared__ SfSmem<P, S, T, 256> sm;
+    u += blockIdx.y * bt.vec;
+    b += blockIdx.y * bt.vec;
+    schwarz_sf_cta<P, S, T, 256>(sm, blockIdx.x, n, nbc, q, ox, oy, nbx, ix0, iy0, nix, niy, nblocks, kband, mband,
+                                 binv, binv_lo, interior, u, b, [&] {
+                                     pdl_wait();
+                                     return !(bt.active && !bt.active[blockIdx.y]);
+                                 });
+}
+
+// One LATTICE colour of the FP32 inner cycle with the interior blocks on the tensor cores
+// (IGA2L_MIXED_TF32).  The grid's first nfc CTAs take the colour's frame (the blocks outside
+// the interior rectangle) with the SIMT step above; each other CTA takes a TBX x TBY tile of
+// the interior rectangle (M = 128 blocks) and computes its corrections as D = X G^T:
+//   * G (NP x KP, built on the host in the operand layout) arrives by one bulk asynchronous
+//     copy (cp.async.bulk, completion on an mbarrier), issued before the wait for the
+//     previous grid since G is constant;
+//   * the region of u the tile's patches cover (RW x RH, coalesced rows) and the blocks' b
+//     values are read once; X = [b_B ; u_patch] is built from shared memory in 16-byte
+//     pieces (four consecutive k of one row), rounded to TF32;
+//   * one thread issues the tcgen05.mma chain (kind::tf32, FP32 accumulator in tensor
+//     memory) and commits it to a second mbarrier; both waits are bounded;
+//   * each block's row of D is read back (tcgen05.ld) and u = u_old + e is written, u_old
+//     from the staged region.
+// Blocks of one colour share no DOF and read no DOF another writes, so all CTAs run
+// independently.
+struct TcColourArgs {
+    int n, nbc, q, ox, oy, nbx, ix0, iy0, nix, niy, ntx, nfc, nframe, interior, skip_copy;
+    long long budget;
+    const float *kband, *mband, *binv, *binv_lo, *gtc, *b;
+    float *u;
+    int *status;
+};
+
+constexpr int tc_colour_minb(int p) { return p == 2 ? 3 : (p == 5 ? 1 : 2); }
+
+template <int P, int S>
+__global__ void __launch_bounds__(256, tc_colour_minb(P)) k_schwarz_tc_colour(const TcColourArgs a)
+{
+    using G = TcGeom<P, S>;
+    constexpr int SS = G::SS, R = G::R, KU = G::KU, KP = G::KP, NP = G::NP, M = G::M;
+    constexpr int TBX = G::TBX, TBY = G::TBY;
+    constexpr int NT = 256, NWARP = NT / 32;
+    extern __shared__ __align__(1024) unsigned char dyn[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if ((int)blockIdx.x < a.nfc) {   // frame blocks: the SIMT step
+        auto &sm = *reinterpret_cast<SfSmem<P, S, float, NT> *>(dyn);
+        schwarz_sf_cta<P, S, float, NT>(sm, blockIdx.x, a.n, a.nbc, a.q, a.ox, a.oy, a.nbx, a.ix0, a.iy0, a.nix,
+                                        a.niy, a.nframe, a.kband, a.mband, a.binv, a.binv_lo, a.interior, a.u, a.b,
+                                        [] {
+                                            pdl_wait();
+                                            return true;
+                                        });
+        return;
+    }
+    float *sX = reinterpret_cast<float *>(dyn);
+    float *sG = reinterpret_cast<float *>(dyn + G::XB);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(dyn + G::XB + G::GB);   // [0]: MMA, [1]: copy of G
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(dyn + G::XB + G::GB + 16);
+    int *s_mma = reinterpret_cast<int *>(dyn + G::XB + G::GB + 20);   // 1: G landed, the chain was issued
+    int *sOff = reinterpret_cast<int *>(dyn + G::XB + G::GB + G::BARB);   // patch column k -> region offset
+    int *sRb = sOff + KP;                                                 // block row r -> region offset
+    float *sR = reinterpret_cast<float *>(sRb + M);                       // the region of u
+    const int n = a.n, q = a.q, RW = G::RW(q), RH = G::RH(q);
+    const int t = blockIdx.x - a.nfc, tx = t % a.ntx, ty = t / a.ntx;
+    const int bi0 = a.ix0 + TBX * tx, bj0 = a.iy0 + TBY * ty;   // the tile's first block (lattice indices)
+    const int vx = min(TBX, a.ix0 + a.nix - bi0), vy = min(TBY, a.iy0 + a.niy - bj0);   // valid blocks
+    const int gx0 = a.ox + q * bi0 - R - P, gy0 = a.oy + q * bj0 - R - P;            // region origin (>= 0)
+    const long long drain = a.budget > (1LL << 31) ? a.budget : (1LL << 31);
+    pdl_wait();
+    // every global load first (b at the blocks' DOFs, then the region of u), the set-up while
+    // they are in flight, then the stores to shared memory
+    // RB: region loads per thread and batch (one batch for the region of the default period)
+    constexpr int NBV = (M * SS + NT - 1) / NT, RB = P == 2 ? 14 : (P == 3 ? 26 : 28);
+    float bv[NBV];
+#pragma unroll
+    for (int i = 0; i < NBV; ++i) {
+        const int idx = tid + NT * i, r = idx / SS, k = idx - r * SS;
+        const int tbx = r % TBX, tby = r / TBX;
+        float v = 0.f;
+        if (idx < M * SS && tbx < vx && tby < vy)
+            v = __ldg(&a.b[(size_t)(gy0 + q * tby + P + k / S) * n + (gx0 + q * tbx + P + k % S)]);
+        bv[i] = v;
+    }
+    const int nreg = RW * RH;
+    const float rcp = 1.0f / (float)RW;   // exact quotient: idx < 2^16 and RW < 2^9
+    auto load_region = [&](int base, float (&v)[RB]) {
+#pragma unroll
+        for (int i = 0; i < RB; ++i) {
+            const int idx = base + NT * i;
+            const int ry = (int)(((float)idx + 0.5f) * rcp), rx = idx - ry * RW;
+            const int gy = gy0 + ry, gx = gx0 + rx;
+            v[i] = (idx < nreg && gy < n && gx < n) ? a.u[(size_t)gy * n + gx] : 0.f;
+        }
+    };
+    float rv[RB];
+    load_region(tid, rv);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar[1])));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&mbar[1])),
+                     "r"((uint32_t)G::GB)
+                     : "memory");
+        if (!a.skip_copy)   // (error-path tests leave the copy out, so its wait runs out)
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                             smem_addr(sG)),
+                         "l"(a.gtc), "r"((uint32_t)G::GB), "r"(smem_addr(&mbar[1]))
+                         : "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)),
+                     "r"(G::TCOLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    for (int k = tid; k < KP; k += NT) {
+        const int j = k - SS;
+        sOff[k] = (k >= SS && k < KU) ? (j / G::PW) * RW + (j % G::PW) : 0;
+    }
+    for (int r = tid; r < M; r += NT) sRb[r] = q * (r / TBX) * RW + q * (r % TBX);
+#pragma unroll
+    for (int i = 0; i < RB; ++i)
+        if (tid + NT * i < nreg) sR[tid + NT * i] = rv[i];
+    for (int base = tid + NT * RB; base < nreg; base += NT * RB) {   // regions above NT RB floats
+        load_region(base, rv);
+#pragma unroll
+        for (int i = 0; i < RB; ++i)
+            if (base + NT * i < nreg) sR[base + NT * i] = rv[i];
+    }
+#pragma unroll
+    for (int i = 0; i < NBV; ++i) {
+        const int idx = tid + NT * i, r = idx / SS, k = idx - r * SS;
+        if (idx < M * SS) sX[tc_off(r, k, KP)] = to_tf32(bv[i]);
+    }
+    __syncthreads();
+    // X's patch columns.  16-byte pieces k = 4 kq .. 4 kq + 3 of one row hold u only for kq in
+    // [KQ0, KQ1): warp w builds the 8-row groups w, w + 8 (lane = 8 (kq mod 4) + row in group),
+    // U pieces at a time with their loads first.  The pieces that mix b and u, or u and the
+    // zero padding, element by element: thread (row, half) one row's head or tail.
+    {
+        constexpr int KQ0 = (SS + 3) / 4, KQ1 = KU / 4, NQ = KQ1 - KQ0, NIT = (NQ + 3) / 4, U = 4;
+        const int r8 = lane & 7, kql = lane >> 3;
+        const int4 *off4 = reinterpret_cast<const int4 *>(sOff);
+#pragma unroll 1
+        for (int rg = warp; rg < M / 8; rg += NWARP) {
+            const int r = rg * 8 + r8;
+            const float *__restrict__ src = sR + sRb[r];
+            float *__restrict__ dst = sX + tc_off(r, 0, KP);
+#pragma unroll
+            for (int i0 = 0; i0 < NIT; i0 += U) {
+                float4 x[U];
+#pragma unroll
+                for (int i = 0; i < U; ++i) {
+                    const int kq = KQ0 + kql + 4 * (i0 + i);
+                    if (i0 + i < NIT && kq < KQ1) {
+                        const int4 o = off4[kq];
+                        x[i] = make_float4(src[o.x], src[o.y], src[o.z], src[o.w]);
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < U; ++i) {
+                    const int kq = KQ0 + kql + 4 * (i0 + i);
+                    if (i0 + i < NIT && kq < KQ1)
+                        *reinterpret_cast<float4 *>(dst + kq * 32) =
+                            make_float4(to_tf32(x[i].x), to_tf32(x[i].y), to_tf32(x[i].z), to_tf32(x[i].w));
+                }
+            }
+        }
+        constexpr int NH = 4 * KQ0 - SS, NTL = KP - 4 * KQ1;
+        static_assert(NT == 2 * M, "one thread per row and half");
+        const int r = tid & (M - 1);
+        const float *src = sR + sRb[r];
+        if (tid < M) {
+#pragma unroll
+            for (int i = 0; i < NH; ++i) sX[tc_off(r, SS + i, KP)] = to_tf32(src[sOff[SS + i]]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < NTL; ++i) {
+                const int k = 4 * KQ1 + i;
+                sX[tc_off(r, k, KP)] = k < KU ? to_tf32(src[sOff[k]]) : 0.f;
+            }
+        }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic-proxy writes -> MMA reads
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+    if (tid == 0) {
+        // G has landed (bounded wait), then the MMA chain
+        const int gready = mbar_wait_bounded(smem_addr(&mbar[1]), 0, a.budget);
+        if (!gready) {
+            atomicAdd(a.status, 1);
+            // a copy still in flight must land before the CTA may exit (bounded again, by
+            // at least the default budget whatever the caller chose)
+            if (!a.skip_copy) mbar_wait_bounded(smem_addr(&mbar[1]), 0, drain);
+        }
+        *s_mma = gready;
+        if (gready) {
+            constexpr uint32_t idesc = idesc_tf32(M, NP);
+            const uint32_t xa = smem_addr(sX), ga = smem_addr(sG);
+#pragma unroll 1
+            for (int s = 0; s < KP / 8; ++s) {
+                const uint64_t da = smem_desc(xa + s * 2 * G::LBO, G::LBO, G::SBO);
+                const uint64_t db = smem_desc(ga + s * 2 * G::LBO, G::LBO, G::SBO);
+                const uint32_t acc = s > 0 ? 1u : 0u;
+                asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                             " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+                             "l"(da), "l"(db), "r"(idesc), "r"(acc));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_addr(&mbar[0]))
+                         : "memory");
+        }
+    }
+    __syncthreads();
+    // bounded wait for the MMA chain (phase 0 of the barrier); if it gives up, the chain
+    // must still finish before the tensor memory is released (bounded again)
+    uint32_t done = 0;
+    if (*s_mma) {
+        done = mbar_wait_bounded(smem_addr(&mbar[0]), 0, a.budget);
+        done = __all_sync(0xffffffffu, done);   // tcgen05.ld below is warp-collective
+        if (!done) {
+            if (lane == 0) atomicAdd(a.status, 1);
+            mbar_wait_bounded(smem_addr(&mbar[0]), 0, drain);
+        }
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // warp w reads the rows of tensor-memory sub-partition w % 4 (one block per lane), column
+    // slices w / 4, w / 4 + 2, ... of 8; the tensor memory is released before the stores
+    constexpr int NCS = (NP / 8 + 1) / 2;   // slices per warp
+    const int sub = warp & 3, r = sub * 32 + lane;
+    uint32_t d[NCS][8];
+    if (done) {
+#pragma unroll
+        for (int j = 0; j < NCS; ++j) {
+            const int cs = (warp >> 2) + 2 * j;
+            if (cs < NP / 8) {
+                const uint32_t taddr = tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(cs * 8);
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                             : "=r"(d[j][0]), "=r"(d[j][1]), "=r"(d[j][2]), "=r"(d[j][3]), "=r"(d[j][4]),
+                               "=r"(d[j][5]), "=r"(d[j][6]), "=r"(d[j][7])
+                             : "r"(taddr));
+            }
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(G::TCOLS));
+    const int tbx = r % TBX, tby = r / TBX;
+    if (done && tbx < vx && tby < vy) {
+        const float *uo = sR + sRb[r] + P * RW + P;   // u_old at the block's first DOF
+        float *ug = a.u + (size_t)(gy0 + q * tby + P) * n + (gx0 + q * tbx + P);
+#pragma unroll
+        for (int j = 0; j < NCS; ++j) {
+            const int cs = (warp >> 2) + 2 * j;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int e = cs * 8 + i, ey = e / S, ex = e - ey * S;
+                if (cs < NP / 8 && e < SS) ug[(size_t)ey * n + ex] = uo[ey * RW + ex] + __uint_as_float(d[j][i]);
+            }
+        }
     }
 }
 
@@ -1118,6 +1411,81 @@ cudaError_t launch_lattice_pd(const Solver &S, int q, int ox, int oy, int nbx, i
                       binv, (const int *)S.bcls, u, b, BatchRef{S.active, S.N, 0, 0});
 }
 
+// the colour's dynamic shared memory: the tensor-core tile or the SIMT frame step
+template <int P, int S>
+size_t tc_colour_smem(int q)
+{
+    const size_t a = TcGeom<P, S>::smem(q), b = sizeof(SfSmem<P, S, float, 256>);
+    return a > b ? a : b;
+}
+
+template <int P, int S>
+cudaError_t launch_tc_colour(const Solver &S_, int ox, int oy, int nbx, int nby, const float *kband,
+                             const float *mband, const float *binv, int interior, float *u, const float *b,
+                             cudaStream_t st)
+{
+    using G = TcGeom<P, S>;
+    int ix0 = 0, nix = 0, iy0 = 0, niy = 0;
+    tc_interior_rect(S_, ox, nbx, ix0, nix);
+    tc_interior_rect(S_, oy, nby, iy0, niy);
+    if (nix <= 0 || niy <= 0) ix0 = iy0 = nix = niy = 0;   // no interior block: all frame
+    const int ntx = (nix + G::TBX - 1) / G::TBX, nty = (niy + G::TBY - 1) / G::TBY;
+    const int nframe = nbx * nby - nix * niy;
+    constexpr int NB = SfSmem<P, S, float, 256>::NB;
+    const int nfc = (nframe + NB - 1) / NB, grid = nfc + ntx * nty;
+    if (grid == 0) return cudaSuccess;
+    TcColourArgs a;
+    a.n = S_.n;
+    a.nbc = S_.ht.nbc;
+    a.q = S_.q;
+    a.ox = ox;
+    a.oy = oy;
+    a.nbx = nbx;
+    a.ix0 = ix0;
+    a.iy0 = iy0;
+    a.nix = nix;
+    a.niy = niy;
+    a.ntx = ntx > 0 ? ntx : 1;
+    a.nfc = nfc;
+    a.nframe = nframe;
+    a.interior = interior;
+    a.skip_copy = (S_.opt.test_flags & IGA2L_TEST_SKIP_OPERATOR_COPY) != 0;
+    a.budget = S_.opt.wait_budget_cycles;
+    a.kband = kband;
+    a.mband = mband;
+    a.binv = binv;
+    a.binv_lo = S_.boundary_lo();
+    a.gtc = S_.mx.gtc;
+    a.b = b;
+    a.u = u;
+    a.status = S_.wait_status;
+    return launch_pdl_smem(k_schwarz_tc_colour<P, S>, dim3(grid), dim3(256), tc_colour_smem<P, S>(S_.q), st, a);
+}
+
+template <int P, int S>
+bool tc_colour_prepare_p(const Solver &S_, std::string &why)
+{
+    int optin = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, S_.device);
+    const size_t need = tc_colour_smem<P, S>(S_.q);
+    using G = TcGeom<P, S>;
+    // the region's row index is taken from a float reciprocal, exact while RW < 2^9 and the
+    // element index < 2^16
+    const bool shape_ok = G::RW(S_.q) < 512 && G::RW(S_.q) * G::RH(S_.q) + 256 * 32 < 65536;
+    if (e != cudaSuccess || need > (size_t)optin || !shape_ok) {
+        why = "tensor-core colour step: " + std::to_string(need) + " bytes of shared memory for lattice period " +
+              std::to_string(S_.q) + " exceed the device's " + std::to_string(optin);
+        return false;
+    }
+    // the largest allowance: handles with other periods share the kernel
+    e = cudaFuncSetAttribute(k_schwarz_tc_colour<P, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e != cudaSuccess) {
+        why = std::string("tensor-core colour step: ") + cudaGetErrorString(e);
+        return false;
+    }
+    return true;
+}
+
 template <int P, int SB, typename T>
 cudaError_t schwarz_lattice_p(const Solver &S, const T *stencil, const T *kband, const T *mband, const T *binv, T *u,
                               const T *b, bool reverse, cudaStream_t st)
@@ -1141,25 +1509,16 @@ cudaError_t schwarz_lattice_p(const Solver &S, const T *stencil, const T *kband,
         if (nblocks <= 0) continue;
         cudaError_t err;
         if constexpr (SF) {
-            // interior blocks of the colour as one tensor-core GEMM (IGA2L_MIXED_TF32), the
-            // frame of the other blocks here
-            int ix0 = 0, iy0 = 0, nix = 0, niy = 0;
-            if (S.mx.gtc) {
-                tc_interior_rect(S, ox, nbx, ix0, nix);
-                tc_interior_rect(S, oy, nby, iy0, niy);
-                if (nix > 0 && niy > 0) {
-                    err = launch_schwarz_tc(S, ox, oy, ix0, iy0, nix, niy, reinterpret_cast<const float *>(b),
-                                            reinterpret_cast<float *>(u), st);
-                    if (err != cudaSuccess) return err;
-                } else {
-                    nix = niy = 0;
-                }
+            if (S.mx.gtc) {   // IGA2L_MIXED_TF32: interior blocks on the tensor cores, same launch
+                if constexpr (P <= kTcMaxP)
+                    err = launch_tc_colour<P, SB>(S, ox, oy, nbx, nby, kband, mband, binv, interior, u, b, st);
+                else
+                    err = cudaErrorInvalidValue;
+            } else {
+                err = launch_pdl(k_schwarz_lattice2d_sf<P, SB, T>, dim3((nblocks + NBSF - 1) / NBSF, S.nbatch),
+                                 dim3(256), st, S.n, S.ht.nbc, q, ox, oy, nbx, 0, 0, 0, 0, nblocks, kband, mband, binv,
+                                 S.boundary_lo(), interior, u, b, BatchRef{S.active, S.N, 0, 0});
             }
-            const int nframe = nblocks - nix * niy;
-            if (nframe <= 0) continue;
-            err = launch_pdl(k_schwarz_lattice2d_sf<P, SB, T>, dim3((nframe + NBSF - 1) / NBSF, S.nbatch), dim3(256),
-                             st, S.n, S.ht.nbc, q, ox, oy, nbx, ix0, iy0, nix, niy, nframe, kband, mband, binv,
-                             S.boundary_lo(), interior, u, b, BatchRef{S.active, S.N, 0, 0});
         } else {
             const int bpc = lattice_bpc((long long)nblocks * S.nbatch, SB * SB, S.nsm);
             if constexpr (SB >= 7)   // sum factorisation pays once the block is as wide as the stencil
@@ -1485,6 +1844,17 @@ cudaError_t launch_inner_fine(const Solver &S, const float *r32, bool reverse, c
     if (e == cudaSuccess) e = residual_any<float, float>(S, X.Kb, X.Mb, X.delta, r32, X.d, nullptr, st);
     if (e == cudaSuccess) e = restrict_any<float>(S, X.Rb, X.d, X.t, X.dc, st);
     return e;
+}
+
+bool tc_colour_prepare(const Solver &S, std::string &why)
+{
+    switch (S.p) {
+    case 2: return tc_colour_prepare_p<2, 3>(S, why);
+    case 3: return tc_colour_prepare_p<3, 3>(S, why);
+    case 4: return tc_colour_prepare_p<4, 3>(S, why);
+    case 5: return tc_colour_prepare_p<5, 5>(S, why);
+    default: why = "the tensor-core colour step is compiled for p = 2..5"; return false;
+    }
 }
 
 cudaError_t launch_inner_sweep(const Solver &S, float *u, const float *b, bool reverse, cudaStream_t st)

@@ -132,8 +132,6 @@ def test_solve_counts_and_mixed_high_p(oracle_mod, p):
     assert ok_r
     modes = [(iga2l.MIXED_FP32, "tile" if p <= 6 else "lattice"),
              (iga2l.MIXED_FP32_ALL, "tile" if p <= 6 else "lattice")]
-    if p <= 6:
-        modes.append((iga2l.MIXED_TF32, "lattice"))   # tensor-core form (compiled for p <= 6)
     for prec, sched in modes:
         X, _ = _pair(oracle_mod, p, m, sched=sched, precision=prec)
         um = _dev(u0)
@@ -151,9 +149,10 @@ def test_tile_rejected_for_7x7_blocks():
     with pytest.raises(iga2l.IgaError) as ei:
         iga2l.Solver(7, 40, schedule=iga2l.SCHED_TILE)
     assert ei.value.code == iga2l.ERR_UNSUPPORTED
-    with pytest.raises(iga2l.IgaError) as ei:   # the tensor-core form: 2D, LATTICE, p <= 6
-        iga2l.Solver(7, 40, precision=iga2l.MIXED_TF32)
-    assert ei.value.code == iga2l.ERR_UNSUPPORTED
+    for p in (6, 7):   # the tensor-core form: single 2D problems, LATTICE, p <= 5
+        with pytest.raises(iga2l.IgaError) as ei:
+            iga2l.Solver(p, 40, precision=iga2l.MIXED_TF32)
+        assert ei.value.code == iga2l.ERR_UNSUPPORTED
 
 
 @pytest.mark.parametrize("p", [6, 7, 8])
