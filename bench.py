@@ -438,7 +438,9 @@ def bench_batched(args, dev):
         out[name] = {"value": ndofs / (ms * 1e-3), "unit": "DOF/s", "dofs": ndofs, "ms": ms,
                      "groups": len(BS.groups), "cycles_max": int(max(cycles)), "cycles": [int(c) for c in cycles],
                      "schedules": {f"p{g['p']}m{g['m']}": ("TILE" + (f"x{g['tile_groups']}" if g["tile_groups"] > 1
-                                                                     else "") if g["schedule"] == 2 else "LATTICE")
+                                                                     else "")
+                                                            + (" work-list" if g["sweep"] == iga2l.SWEEP_WORK_LIST
+                                                               else "") if g["schedule"] == 2 else "LATTICE")
                                    for g in BS.groups}}
         BS.close()
     out["value"] = out["mixed"]["value"]

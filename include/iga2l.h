@@ -79,14 +79,22 @@ extern "C" {
 #define IGA2L_SWEEP_AUTO 0
 #define IGA2L_SWEEP_PER_COLOUR 1
 #define IGA2L_SWEEP_PERSISTENT 2
+/* WORK_LIST (TILE schedule, 2D, any precision, single or batch handles): the whole TILE sweep
+ * of every problem of the handle in one launch.  CTAs claim (colour group, tile phase,
+ * problem, tile) items in sweep order; a tile starts once every tile of its problem's
+ * previous phase has finished (a bounded device wait, IGA2L_ERR_DEVICE_TIMEOUT when it gives
+ * up).  Iterates are bitwise those of one launch per tile phase (PER_COLOUR and AUTO with the
+ * TILE schedule). */
+#define IGA2L_SWEEP_WORK_LIST 3
 /* test_flags bits (testing the error paths only; never set in production use):
  * the tensor-core colour kernel does not issue the bulk copy of its block operator, so
  * its bounded wait for that copy runs out (no copy and no MMA is ever in flight), the
  * kernel skips its blocks and the call returns IGA2L_ERR_DEVICE_TIMEOUT */
 #define IGA2L_TEST_SKIP_OPERATOR_COPY 1
 /* the persistent sweep's first CTA never raises its progress counter, so its neighbours'
- * bounded waits run out (nothing asynchronous is in flight); the call returns
- * IGA2L_ERR_DEVICE_TIMEOUT */
+ * bounded waits run out (nothing asynchronous is in flight); in the work-list TILE sweep no
+ * finished tile is counted, so the first wait for a previous phase runs out; the call
+ * returns IGA2L_ERR_DEVICE_TIMEOUT */
 #define IGA2L_TEST_WITHHOLD_PROGRESS 2
 
 typedef struct iga2l_solver *iga2l_handle;
@@ -107,10 +115,11 @@ typedef struct {
     int tile_groups; /* TILE: the q^d colours split into this many consecutive groups, each group
                         running the 2^d tile phases in turn (1 = plain TILE, q^d = the LATTICE
                         order; 0 = the library default: 4 for p = 6, else 1).  Capped at q^d. */
-    int sweep;       /* IGA2L_SWEEP_AUTO (default), _PER_COLOUR or _PERSISTENT: the FP32 inner
-                        sweep as one persistent launch (all colours; every CTA owns a region,
-                        neighbours exchange their boundary bands through L2 under bounded
-                        waits) or one launch per colour */
+    int sweep;       /* IGA2L_SWEEP_AUTO (default), _PER_COLOUR, _PERSISTENT or _WORK_LIST: with
+                        LATTICE, the FP32 inner sweep as one persistent launch (all colours;
+                        every CTA owns a region, neighbours exchange their boundary bands
+                        through L2 under bounded waits) or one launch per colour; with TILE,
+                        the work-list sweep (_WORK_LIST) or one launch per tile phase */
     int test_flags;  /* 0, or IGA2L_TEST_* bits (error-path tests only) */
     long long wait_budget_cycles;   /* SM clock cycles a bounded device wait may spin before the
                         kernel gives up, records the failure and returns (the call then reports

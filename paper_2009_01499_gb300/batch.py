@@ -5,10 +5,11 @@ Problems are grouped by (p, m); each group is one batch handle of the library
 masked on the device, cycles replayed from captured CUDA graphs).  Groups run
 concurrently, each on its own CUDA stream driven by its own host thread (the
 library's calls release the GIL).  For every group the schedule of the Schwarz step
-(LATTICE, or TILE with its colours in 1, 2 or 4 groups) is chosen by timing a seeded
-probe solve to 1e-8 with each candidate, so a candidate that costs cycles loses what it
-saves per cycle; choices are cached per (device, p, m, precision), in memory and
-optionally in a JSON file.
+(LATTICE, or TILE with its colours in 1, 2 or 4 groups, each TILE form either one launch
+per tile phase or the work-list sweep: one launch per sweep over every problem's tiles)
+is chosen by timing a seeded probe batch of the group's size to 1e-8 with each candidate,
+so a candidate that costs cycles loses what it saves per cycle; choices are cached per
+(device, p, m, precision, batch size), in memory and optionally in a JSON file.
 
 This module is host orchestration only: all arithmetic runs in libiga2l.so.
 """
@@ -19,59 +20,66 @@ import os
 import threading
 from collections import OrderedDict
 
+import numpy as np
 import torch
 
 from . import iga2l, synth
 
 COLOURING = {2: (5, 2), 3: (7, 2), 4: (7, 2), 5: (10, 3), 6: (11, 4), 7: (14, 5), 8: (17, 4)}
-# (schedule, TILE colour groups); TILE is compiled for blocks up to 5x5 (p <= 6)
-CANDIDATES = ((iga2l.SCHED_LATTICE, 0), (iga2l.SCHED_TILE, 1), (iga2l.SCHED_TILE, 2), (iga2l.SCHED_TILE, 4))
+# (schedule, TILE colour groups, sweep form); TILE is compiled for blocks up to 5x5 (p <= 6)
+CANDIDATES = tuple([(iga2l.SCHED_LATTICE, 0, iga2l.SWEEP_AUTO)] +
+                   [(iga2l.SCHED_TILE, gr, sw) for sw in (iga2l.SWEEP_AUTO, iga2l.SWEEP_WORK_LIST) for gr in (1, 2, 4)])
 _cache: dict = {}
 _cache_lock = threading.Lock()
 
 
-def _key(p, m, precision):
+def _key(p, m, precision, nbatch):
     name = torch.cuda.get_device_name() if torch.cuda.is_available() else "cpu"
-    return f"{name}|p={p}|m={m}|prec={precision}"
+    return f"{name}|p={p}|m={m}|prec={precision}|nbatch={nbatch}"
 
 
-def autotune_schedule(p: int, m: int, precision: int, cache_path: str | None = None, reps: int = 2):
-    """Fastest (schedule, TILE colour groups) by the time to a 1e-8 residual on a seeded
-    probe problem of the same (p, m)."""
-    key = _key(p, m, precision)
+def autotune_schedule(p: int, m: int, precision: int, cache_path: str | None = None, reps: int = 2,
+                      nbatch: int = 1):
+    """Fastest (schedule, TILE colour groups, sweep form) by the time to a 1e-8 residual of a
+    seeded probe batch of nbatch problems of the same (p, m) (one problem: a single-problem
+    handle): the latency of small grids and the throughput of large batches pick differently."""
+    key = _key(p, m, precision, nbatch)
     with _cache_lock:
-        if key in _cache:
+        if key in _cache and len(_cache[key]) == 3:
             return _cache[key]
         if cache_path and os.path.exists(cache_path):
             try:
                 _cache.update(json.load(open(cache_path)))
             except (OSError, ValueError):
                 pass
-            if key in _cache:
+            if key in _cache and len(_cache[key]) == 3:
                 return _cache[key]
     q, g = COLOURING[p]
     best, best_ms = None, float("inf")
-    for sched, groups in CANDIDATES:
+    for sched, groups, sweep in CANDIDATES:
         if sched == iga2l.SCHED_TILE and p > 6:   # TILE is compiled for blocks up to 5x5
             continue
-        S = iga2l.Solver(p, m, period=q, stride=g, precision=precision, schedule=sched, tile_groups=groups)
-        f = torch.tensor(synth.coefficients(S.N, 77), device="cuda")
-        b = torch.empty_like(f)
-        S.rhs_from_coeffs(f, b)
-        u0 = torch.tensor(synth.initial_guess(S.N, 78), device="cuda")
+        S = iga2l.Solver(p, m, period=q, stride=g, precision=precision, schedule=sched, tile_groups=groups,
+                         sweep=sweep, nbatch=nbatch, batch=nbatch > 1)
+        N = (m + p - 2) ** 2
+        f = torch.tensor(np.concatenate([synth.coefficients(N, 77 + k) for k in range(nbatch)]), device="cuda")
+        u0 = torch.tensor(np.concatenate([synth.initial_guess(N, 78 + k) for k in range(nbatch)]), device="cuda")
         times = []
         for _ in range(reps + 1):
             u = u0.clone()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            S.solve_load(b, u, tol=1e-8)
+            if nbatch > 1:
+                S.solve_batch(f, u, tol=1e-8)
+            else:
+                S.solve(f, u, tol=1e-8)
             e1.record()
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
         ms = min(times[1:])
         S.close()
         if ms < best_ms:
-            best, best_ms = [sched, groups], ms
+            best, best_ms = [sched, groups, sweep], ms
     with _cache_lock:
         _cache[key] = best
         if cache_path:
@@ -87,7 +95,8 @@ class BatchedSolver:
     """Independent 2D problems given as a list of (p, m), solved group by group."""
 
     def __init__(self, problems, precision: int = iga2l.MIXED_FP32, autotune: bool = True,
-                 cache_path: str | None = None, schedule: int | None = None, rhs_is_load: bool = False):
+                 cache_path: str | None = None, schedule: int | None = None, rhs_is_load: bool = False,
+                 sweep: int = iga2l.SWEEP_AUTO):
         self.problems = list(problems)
         self.precision = precision
         groups: "OrderedDict[tuple, list]" = OrderedDict()
@@ -96,17 +105,17 @@ class BatchedSolver:
         self.groups = []
         for (p, m), members in groups.items():
             if schedule is not None:
-                sched, groups_ = schedule, 0
+                sched, groups_, sweep_ = schedule, 0, sweep
             elif autotune:
-                sched, groups_ = autotune_schedule(p, m, precision, cache_path)
+                sched, groups_, sweep_ = autotune_schedule(p, m, precision, cache_path, nbatch=len(members))
             else:
-                sched, groups_ = iga2l.SCHED_LATTICE, 0
+                sched, groups_, sweep_ = iga2l.SCHED_LATTICE, 0, iga2l.SWEEP_AUTO
             q, g = COLOURING[p]
             h = iga2l.Solver(p, m, nbatch=len(members), batch=True, period=q, stride=g, precision=precision,
-                             schedule=sched, tile_groups=groups_,
+                             schedule=sched, tile_groups=groups_, sweep=sweep_,
                              rhs=iga2l.RHS_IS_LOAD if rhs_is_load else iga2l.RHS_COEFFS)
             self.groups.append({"p": p, "m": m, "members": members, "handle": h, "schedule": sched,
-                                "tile_groups": h.tile_groups, "stream": torch.cuda.Stream()})
+                                "tile_groups": h.tile_groups, "sweep": sweep_, "stream": torch.cuda.Stream()})
         self.dofs = [(m + p - 2) ** 2 for p, m in self.problems]
 
     def pack(self, vectors):

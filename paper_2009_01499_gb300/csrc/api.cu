@@ -354,6 +354,22 @@ int load_from_coeffs(iga2l_handle h, const double *f, const double *u, cudaStrea
     return finish(launch_mass2(*h, f, h->rhsb, st), "right-hand side from coefficients");
 }
 
+// IGA2L_ERR_DEVICE_TIMEOUT (and the flag cleared) when a bounded device wait gave up since the
+// last check: blocks or tiles were left uncorrected
+int wait_status_check(iga2l_handle h, cudaStream_t st)
+{
+    if (!h->wait_status) return IGA2L_OK;
+    int bad = 0;
+    cudaError_t e = cudaMemcpyAsync(&bad, h->wait_status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "wait status");
+    if (!bad) return IGA2L_OK;
+    e = cudaMemsetAsync(h->wait_status, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "wait status");
+    return fail(IGA2L_ERR_DEVICE_TIMEOUT, "a bounded device wait gave up (the results are not valid)");
+}
+
 int solve_impl(iga2l_handle h, const double *b, double tol, int max_cycles, double *u, int *cycles,
                double *relres, double *hist, void *stream, bool adjoint)
 {
@@ -427,18 +443,7 @@ int solve_impl(iga2l_handle h, const double *b, double tol, int max_cycles, doub
     if (cycles) *cycles = k;
     if (relres) *relres = rel;
     if (status != IGA2L_OK) g_last_error = "cycle cap reached";
-    if (h->wait_status) {   // a bounded device wait that gave up left blocks uncorrected
-        int bad = 0;
-        cudaError_t e = cudaMemcpyAsync(&bad, h->wait_status, sizeof(int), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) return cuda_fail(e, "wait status");
-        if (bad) {
-            e = cudaMemsetAsync(h->wait_status, 0, sizeof(int), st);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-            if (e != cudaSuccess) return cuda_fail(e, "wait status");
-            return fail(IGA2L_ERR_DEVICE_TIMEOUT, "a bounded device wait gave up (the results are not valid)");
-        }
-    }
+    if ((rc = wait_status_check(h, st)) != IGA2L_OK) return rc;
     return status;
 }
 
@@ -495,8 +500,11 @@ static int assemble_impl(int p, int m, int dim, int nbatch, bool batch, const ig
     if (opt.coarse != IGA2L_COARSE_VCYCLE && opt.coarse != IGA2L_COARSE_EXACT)
         return fail(IGA2L_ERR_INVALID_ARG, "unknown coarse solver");
     if (opt.tile_groups < 0 || opt.tile_groups > 1024) return fail(IGA2L_ERR_INVALID_ARG, "tile_groups must be 0..1024");
-    if (opt.sweep != IGA2L_SWEEP_AUTO && opt.sweep != IGA2L_SWEEP_PER_COLOUR && opt.sweep != IGA2L_SWEEP_PERSISTENT)
+    if (opt.sweep != IGA2L_SWEEP_AUTO && opt.sweep != IGA2L_SWEEP_PER_COLOUR && opt.sweep != IGA2L_SWEEP_PERSISTENT &&
+        opt.sweep != IGA2L_SWEEP_WORK_LIST)
         return fail(IGA2L_ERR_INVALID_ARG, "unknown sweep kernel choice");
+    if (opt.sweep == IGA2L_SWEEP_WORK_LIST && (dim != 2 || opt.schedule != IGA2L_SCHED_TILE))
+        return fail(IGA2L_ERR_UNSUPPORTED, "the work-list sweep runs the 2D TILE schedule");
     if (opt.rhs != IGA2L_RHS_COEFFS && opt.rhs != IGA2L_RHS_IS_LOAD)
         return fail(IGA2L_ERR_INVALID_ARG, "rhs must be IGA2L_RHS_COEFFS or IGA2L_RHS_IS_LOAD");
     if (opt.test_flags & ~(IGA2L_TEST_SKIP_OPERATOR_COPY | IGA2L_TEST_WITHHOLD_PROGRESS))
@@ -827,6 +835,21 @@ static int assemble_impl(int p, int m, int dim, int nbatch, bool batch, const ig
             if (opt.sweep == IGA2L_SWEEP_AUTO && S->s < 5) S->pgx = 0;
         }
     }
+    if (opt.sweep == IGA2L_SWEEP_WORK_LIST) {   // the TILE sweep as one work-list launch
+        void *pc = nullptr;
+        const size_t groups = S->tile_groups > 1 ? (size_t)S->tile_groups : 1;   // as the sweep runs them
+        S->tile_work_ctas = tile_work_ctas(*S);
+        if (S->tile_work_ctas <= 0) {
+            release(S);
+            return fail(IGA2L_ERR_UNSUPPORTED, "no resident launch plan for the work-list sweep");
+        }
+        if ((ce = cudaMalloc(&pc, sizeof(unsigned int) * (1 + (size_t)nbatch * 4 * groups))) != cudaSuccess) {
+            release(S);
+            return cuda_fail(ce, "work-list counters");
+        }
+        S->allocs.push_back(pc);
+        S->tile_ctr = static_cast<unsigned int *>(pc);
+    }
     if (opt.sweep == IGA2L_SWEEP_PERSISTENT && S->pgx == 0) {
         release(S);
         return fail(IGA2L_ERR_UNSUPPORTED,
@@ -927,6 +950,7 @@ int iga2l_solve_batch(iga2l_handle h, const double *rhs, double tol, int max_cyc
     if (e == cudaSuccess) e = cudaMemcpyAsync(&left, h->bcount, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "batch results");
+    if ((rc = wait_status_check(h, st)) != IGA2L_OK) return rc;
     for (int k = 0; k < nb; ++k)
         if (!std::isfinite(relres[k])) return fail(IGA2L_ERR_NONFINITE, "a residual norm is not finite");
     if (left > 0) { g_last_error = "cycle cap reached"; return IGA2L_NOT_CONVERGED; }

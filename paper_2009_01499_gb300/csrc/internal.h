@@ -122,6 +122,9 @@ struct Solver {
     double *gbuf = nullptr;      // per-bump 1D loads and their centre derivatives
     int gcap = 0;                // bumps gbuf can hold
     unsigned int *progress = nullptr;   // persistent sweep: colours finished per CTA
+    unsigned int *tile_ctr = nullptr;   // work-list TILE sweep: item counter + tiles finished per
+                                        // (problem, phase); null: one launch per tile phase
+    int tile_work_ctas = 0;             // work-list TILE sweep: resident CTAs (its grid)
     int *wait_status = nullptr;         // device: bounded waits that gave up (tensor-core, persistent)
     int pgx = 0, pgy = 0, prx = 0, pry = 0;   // persistent sweep: regions per axis, largest sides
     unsigned psmem = 0;                       // (pgx = 0: per-colour launches)
@@ -271,6 +274,8 @@ void tc_interior_rect(const Solver &S, int o, int nb, int &i0, int &ni);
 // checks that the tensor-core colour step's shared memory (set by the lattice period q) fits
 // the device and allows it for the kernel (kernels_fine.cu); false: not available
 bool tc_colour_prepare(const Solver &S, std::string &why);
+// resident CTAs of the work-list TILE sweep for this handle's degree and precision (0: none)
+int tile_work_ctas(const Solver &S);
 // persistent LATTICE sweep of the FP32 inner cycle (kernels_persist.cu): plans the launch
 // (false: not available for this handle, per-colour launches are used) and runs one sweep
 bool persist_setup(Solver &S);

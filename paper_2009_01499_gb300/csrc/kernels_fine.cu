@@ -17,6 +17,7 @@
 // GB300 the FP64 kernels are bound by the FP64 pipe, not by HBM.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <mutex>
 #include <string>
 #include <type_traits>
@@ -890,6 +891,10 @@ struct TileGeom {
     // in one wave; FP64 keeps its registers)
     template <typename T>
     static constexpr int minb() { return sizeof(T) == sizeof(double) ? 1 : (NT >= 128 ? 5 : 4); }
+    // the work-list form keeps the per-phase kernel's residency (its item loop would otherwise
+    // take more registers)
+    template <typename T>
+    static constexpr int minb_work() { return sizeof(T) == sizeof(double) ? 1 : (NT >= 128 ? 5 : 8); }
 };
 
 // Stages a (tile-local, zero outside the grid) window into shared memory with all loads
@@ -914,7 +919,7 @@ __device__ __forceinline__ void stage_window(T *dst, const T *__restrict__ src, 
 
 // stage_window storing every value twice, as the pair (v, v): the packed FMAs of the y
 // pass then read their splatted operand straight from shared memory
-template <int NT, int ROWLEN, int NELEM, typename T2>
+template <int NT, int ROWLEN, int NELEM, typename T2, bool L2ONLY = false>
 __device__ __forceinline__ void stage_window_dup(T2 *dst, const decltype(T2::x) *__restrict__ src, int n, int gx0,
                                                  int gy0, int tid)
 {
@@ -925,7 +930,11 @@ __device__ __forceinline__ void stage_window_dup(T2 *dst, const decltype(T2::x) 
     for (int k = 0; k < K; ++k) {
         const int i = tid + k * NT;
         const int gx = gx0 + i % ROWLEN, gy = gy0 + i / ROWLEN;
-        v[k] = (i < NELEM && gx >= 0 && gx < n && gy >= 0 && gy < n) ? src[(size_t)gy * n + gx] : T(0);
+        const bool in = i < NELEM && gx >= 0 && gx < n && gy >= 0 && gy < n;
+        if constexpr (L2ONLY)   // written by other CTAs of the same launch: not through L1
+            v[k] = in ? __ldcg(&src[(size_t)gy * n + gx]) : T(0);
+        else
+            v[k] = in ? src[(size_t)gy * n + gx] : T(0);
     }
 #pragma unroll
     for (int k = 0; k < K; ++k) {
@@ -1056,25 +1065,41 @@ __device__ __forceinline__ T tile_xpass(const typename Vec2<T>::type *yb, int ey
 // registers; boundary classes with their FP64 inverse, in compensated FP32 arithmetic)
 // and adds the result to u in shared memory.  One
 // CTA barrier per colour.
+// Shared memory of one CTA of the TILE step.
 template <int P, int S, int TT, typename T>
-__global__ void __launch_bounds__(TileGeom<P, S, TT>::NT, TileGeom<P, S, TT>::template minb<T>())
-k_schwarz_tile2d(int n, int nbc, int q, int g, int rev, int c0, int c1, int px, int py, int ntpx,
-                 const T *__restrict__ kband, const T *__restrict__ mband,
-                 const T *__restrict__ binv, const float *__restrict__ binv_lo, int interior,
-                 T *__restrict__ u, const T *__restrict__ b, BatchRef bt)
+struct TileSmem {
+    using G = TileGeom<P, S, TT>;
+    using T2 = typename Vec2<T>::type;
+    T2 su[G::SW * G::SW];   // u as (u, u) pairs
+    T sb[G::BW * G::BW];
+    __align__(16) T rs[G::NBLK * G::RSS];
+    T2 yb[G::NBLK * G::YB];
+    T2 km1y[G::BW * G::W], mk1x[G::BW * G::W];   // boundary tiles: (K, M) of rows, (M, K) of columns
+};
+
+// One tile of one TILE phase (tile index ti of the phase's ntpx-wide grid of tiles).  `pre`
+// runs after the constant-table reads, before the first read of u or b, and returns whether
+// the CTA goes on (the same answer in every thread).  L2ONLY: u is read past L1 (other CTAs
+// of the same launch wrote it).
+template <int P, int S, int TT, typename T, bool L2ONLY, typename Pre>
+__device__ __forceinline__ void schwarz_tile_cta(TileSmem<P, S, TT, T> &sm, int ti, int n, int nbc, int q, int g,
+                                                 int rev, int c0, int c1, int px, int py, int ntpx,
+                                                 const T *__restrict__ kband, const T *__restrict__ mband,
+                                                 const T *__restrict__ binv, const float *__restrict__ binv_lo,
+                                                 int interior, T *__restrict__ u, const T *__restrict__ b, Pre pre)
 {
     using G = TileGeom<P, S, TT>;
     using T2 = typename Vec2<T>::type;
     constexpr int W = G::W, SS = G::SS, R = G::R, H = G::H, L = P - 1 + R;
     constexpr int SW = G::SW, BW = G::BW, NB1 = G::NB1, NT = G::NT;
     constexpr int PCI = 2 * P - 1;   // first interior row class
-    __shared__ T2 su[SW * SW];   // u as (u, u) pairs
-    __shared__ T sb[BW * BW];
-    __shared__ __align__(16) T rs[G::NBLK * G::RSS];
-    __shared__ T2 yb[G::NBLK * G::YB];
-    __shared__ T2 km1y[BW * W], mk1x[BW * W];   // boundary tiles: (K, M) of rows, (M, K) of columns
+    T2 *su = sm.su;
+    T *sb = sm.sb;
+    T *rs = sm.rs;
+    T2 *yb = sm.yb;
+    T2 *km1y = sm.km1y, *mk1x = sm.mk1x;
     const int tid = threadIdx.x;
-    const int x0 = (px + 2 * (blockIdx.x % ntpx)) * TT, y0 = (py + 2 * (blockIdx.x / ntpx)) * TT;
+    const int x0 = (px + 2 * (ti % ntpx)) * TT, y0 = (py + 2 * (ti / ntpx)) * TT;
     const int tw = min(TT, n - x0), th = min(TT, n - y0);   // centres of this tile
     const bool fast = x0 - R >= PCI && x0 + TT - 1 + R <= n - 2 * P && y0 - R >= PCI &&
                       y0 + TT - 1 + R <= n - 2 * P;
@@ -1109,11 +1134,8 @@ k_schwarz_tile2d(int n, int nbc, int q, int g, int rev, int c0, int c1, int px, 
         brow[k].x = role ? __ldg(&binv[base + 2 * k]) : T(0);
         brow[k].y = (role && 2 * k + 1 < SS) ? __ldg(&binv[base + 2 * k + 1]) : T(0);
     }
-    pdl_wait();
-    if (bt.active && !bt.active[blockIdx.y]) return;
-    u += blockIdx.y * bt.vec;
-    b += blockIdx.y * bt.vec;
-    stage_window_dup<NT, SW, SW * SW>(su, u, n, x0 - H, y0 - H, tid);
+    if (!pre()) return;
+    stage_window_dup<NT, SW, SW * SW, T2, L2ONLY>(su, u, n, x0 - H, y0 - H, tid);
     stage_window<NT, BW, BW * BW>(sb, b, n, x0 - R, y0 - R, tid);
     __syncthreads();
     const int bi = slot % NB1, bj = slot / NB1;
@@ -1216,6 +1238,127 @@ k_schwarz_tile2d(int n, int nbc, int q, int g, int rev, int c0, int c1, int px, 
     for (int i = tid; i < BW * BW; i += NT) {
         const int gx = x0 - R + i % BW, gy = y0 - R + i / BW;
         if (gx >= 0 && gx < n && gy >= 0 && gy < n) u[(size_t)gy * n + gx] = su[(i / BW + P) * SW + (i % BW + P)].x;
+    }
+}
+
+template <int P, int S, int TT, typename T>
+__global__ void __launch_bounds__(TileGeom<P, S, TT>::NT, TileGeom<P, S, TT>::template minb<T>())
+k_schwarz_tile2d(int n, int nbc, int q, int g, int rev, int c0, int c1, int px, int py, int ntpx,
+                 const T *__restrict__ kband, const T *__restrict__ mband,
+                 const T *__restrict__ binv, const float *__restrict__ binv_lo, int interior,
+                 T *__restrict__ u, const T *__restrict__ b, BatchRef bt)
+{
+    __shared__ TileSmem<P, S, TT, T> sm;
+    u += blockIdx.y * bt.vec;
+    b += blockIdx.y * bt.vec;
+    schwarz_tile_cta<P, S, TT, T, false>(sm, blockIdx.x, n, nbc, q, g, rev, c0, c1, px, py, ntpx, kband, mband, binv,
+                                         binv_lo, interior, u, b, [&] {
+                                             pdl_wait();
+                                             return !(bt.active && !bt.active[blockIdx.y]);
+                                         });
+}
+
+__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// The TILE sweep of every problem of a handle in one launch (a work list).  Items are
+// (colour group, tile phase, problem, tile) in sweep order, claimed one at a time from a
+// counter: item ids grow with the sweep order, so an item waits only for items claimed
+// before it by CTAs that are running, and the launch cannot deadlock.  A tile starts once
+// every tile of its problem's previous phase has finished (a per-problem, per-phase
+// counter raised by each finished tile after a device-scope fence; the wait is bounded by
+// `budget` cycles and gives up at once after any failure).  u is read past L1, since other
+// SMs wrote it during the launch.  The counters are zeroed on the stream before the
+// launch.  withhold (tests only): finished tiles are not counted, so the first wait runs
+// out.
+struct TileWorkArgs {
+    int n, nbc, q, g, rev, interior, nbatch, groups, withhold;
+    int tiles[4], ntpx[4];   // tiles and tiles per row of phase (px, py) = (t & 1, t >> 1)
+    long long per_group;     // items per colour group: nbatch (tiles[0] + ... + tiles[3])
+    long long total;
+    unsigned *ctr;           // [0]: next item; [1 + problem * 4 groups + phase]: finished tiles
+    const int *active;
+    size_t vec;
+    int *status;
+    long long budget;
+};
+
+template <int P, int S, int TT, typename T>
+__global__ void __launch_bounds__(TileGeom<P, S, TT>::NT, TileGeom<P, S, TT>::template minb_work<T>())
+k_schwarz_tile2d_work(const __grid_constant__ TileWorkArgs a, const T *__restrict__ kband,
+                      const T *__restrict__ mband, const T *__restrict__ binv, const float *__restrict__ binv_lo,
+                      T *__restrict__ u, const T *__restrict__ b)
+{
+    __shared__ TileSmem<P, S, TT, T> sm;
+    __shared__ long long s_item;
+    __shared__ int s_go;
+    const int ncol = a.q * a.q, nph = 4 * a.groups;
+    pdl_wait();
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(a.ctr, 1u);
+        __syncthreads();
+        const long long item = s_item;
+        if (item >= a.total) break;
+        // decode: colour group and phase in sweep order, then problem and tile
+        const int kseq = (int)(item / a.per_group);
+        long long rem = item - (long long)kseq * a.per_group;
+        int tseq = 0, ph = a.rev ? 3 : 0;
+        while (tseq < 3 && rem >= (long long)a.nbatch * a.tiles[ph]) {
+            rem -= (long long)a.nbatch * a.tiles[ph];
+            ++tseq;
+            ph = a.rev ? 3 - tseq : tseq;
+        }
+        const int i = (int)(rem / a.tiles[ph]), ti = (int)(rem - (long long)i * a.tiles[ph]);
+        const int k = a.rev ? a.groups - 1 - kseq : kseq, phi = 4 * kseq + tseq;
+        const int c0 = (k * ncol + a.groups - 1) / a.groups, c1 = ((k + 1) * ncol + a.groups - 1) / a.groups;
+        unsigned *done = a.ctr + 1 + (size_t)i * nph;
+        // the most recent earlier phase of the sweep that has tiles (every item counts when it
+        // is done, tiles of converged problems and empty colour groups included)
+        int wph = -1, wtiles = 0;
+        for (int pp = phi - 1; pp >= 0 && wph < 0; --pp) {
+            const int pt = pp & 3, pph = a.rev ? 3 - pt : pt;
+            if (a.tiles[pph] > 0) {
+                wph = pp;
+                wtiles = a.tiles[pph];
+            }
+        }
+        if (!(a.active && !a.active[i]) && c1 > c0) {
+            schwarz_tile_cta<P, S, TT, T, true>(
+                sm, ti, a.n, a.nbc, a.q, a.g, a.rev, c0, c1, ph & 1, ph >> 1, a.ntpx[ph], kband, mband, binv, binv_lo,
+                a.interior, u + (size_t)i * a.vec, b + (size_t)i * a.vec, [&] {
+                    if (threadIdx.x == 0) {
+                        int go = 1;
+                        if (wph >= 0) {
+                            // relaxed polls (an acquire per poll would also drop the SM's L1
+                            // lines that co-resident tiles are using), one acquire fence after
+                            const long long t0 = clock64();
+                            bool ok = ld_relaxed_u32(done + wph) >= (unsigned)wtiles;
+                            while (!ok && *(volatile int *)a.status == 0 && clock64() - t0 < a.budget) {
+                                __nanosleep(64);
+                                ok = ld_relaxed_u32(done + wph) >= (unsigned)wtiles;
+                            }
+                            asm volatile("fence.acq_rel.gpu;" ::: "memory");
+                            if (!ok) {
+                                atomicAdd(a.status, 1);
+                                go = 0;
+                            }
+                        }
+                        s_go = go;
+                    }
+                    __syncthreads();
+                    return s_go != 0;
+                });
+        }
+        __syncthreads();   // the tile's writes of u, before it counts as finished
+        if (threadIdx.x == 0 && !a.withhold) {
+            __threadfence();
+            atomicAdd(done + phi, 1u);
+        }
+        __syncthreads();   // shared memory and s_item are reused by the next item
     }
 }
 
@@ -1533,10 +1676,57 @@ cudaError_t schwarz_lattice_p(const Solver &S, const T *stencil, const T *kband,
     return cudaSuccess;
 }
 
+// the TILE sweep as one work-list launch over every problem of the handle
+template <int P, int SB, typename T>
+cudaError_t schwarz_tile_work_p(const Solver &S, const T *kband, const T *mband, const T *binv, T *u, const T *b,
+                                bool reverse, cudaStream_t st)
+{
+    constexpr int TT = tile_side(P);
+    using G = TileGeom<P, SB, TT>;
+    const int nt = (S.n + TT - 1) / TT;
+    TileWorkArgs a;
+    a.n = S.n;
+    a.nbc = S.ht.nbc;
+    a.q = S.q;
+    a.g = S.g;
+    a.rev = reverse ? 1 : 0;
+    a.interior = S.ht.L * S.ht.nbc + S.ht.L;
+    a.nbatch = S.nbatch;
+    a.groups = S.tile_groups > 1 ? S.tile_groups : 1;
+    a.withhold = (S.opt.test_flags & IGA2L_TEST_WITHHOLD_PROGRESS) != 0;
+    long long per = 0, widest = 0;
+    for (int t = 0; t < 4; ++t) {
+        const int ntpx = (nt - (t & 1) + 1) / 2, ntpy = (nt - (t >> 1) + 1) / 2;
+        a.ntpx[t] = ntpx > 0 ? ntpx : 1;
+        a.tiles[t] = ntpx > 0 && ntpy > 0 ? ntpx * ntpy : 0;
+        per += a.tiles[t];
+        widest = std::max(widest, (long long)a.tiles[t] * S.nbatch);
+    }
+    a.per_group = per * S.nbatch;
+    a.total = a.per_group * a.groups;
+    if (a.total > (1LL << 31)) return cudaErrorInvalidValue;   // the item counter is 32-bit
+    a.ctr = S.tile_ctr;
+    a.active = S.active;
+    a.vec = S.N;
+    a.status = S.wait_status;
+    a.budget = S.opt.wait_budget_cycles;
+    cudaError_t e = cudaMemsetAsync(S.tile_ctr, 0, sizeof(unsigned) * (1 + (size_t)S.nbatch * 4 * a.groups), st);
+    if (e != cudaSuccess) return e;
+    // no more CTAs than the largest phase has items: otherwise the CTAs that start last claim
+    // the next phase's items at once and the SMs they sit on run fewer tiles of this phase
+    // while others run more (measured: p = 5 phase 0 at 1024^2 took 195 us against 153)
+    const long long grid = std::min(widest, (long long)S.tile_work_ctas);
+    if (grid <= 0) return cudaSuccess;
+    k_schwarz_tile2d_work<P, SB, TT, T><<<(unsigned)grid, G::NT, 0, st>>>(a, kband, mband, binv, S.boundary_lo(), u, b);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 template <int P, int SB, typename T>
 cudaError_t schwarz_tile_p(const Solver &S, const T *kband, const T *mband, const T *binv, T *u, const T *b,
                            bool reverse, cudaStream_t st)
 {
+    if (S.tile_ctr) return schwarz_tile_work_p<P, SB, T>(S, kband, mband, binv, u, b, reverse, st);
     constexpr int TT = tile_side(P);
     using G = TileGeom<P, SB, TT>;
     const int interior = S.ht.L * S.ht.nbc + S.ht.L;
@@ -1844,6 +2034,34 @@ cudaError_t launch_inner_fine(const Solver &S, const float *r32, bool reverse, c
     if (e == cudaSuccess) e = residual_any<float, float>(S, X.Kb, X.Mb, X.delta, r32, X.d, nullptr, st);
     if (e == cudaSuccess) e = restrict_any<float>(S, X.Rb, X.d, X.t, X.dc, st);
     return e;
+}
+
+namespace {
+template <int P, int SB>
+int tile_work_ctas_p(const Solver &S)
+{
+    constexpr int TT = tile_side(P);
+    using G = TileGeom<P, SB, TT>;
+    int per_sm = 0;
+    cudaError_t e;
+    if (S.mx.enabled)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_schwarz_tile2d_work<P, SB, TT, float>, G::NT, 0);
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_schwarz_tile2d_work<P, SB, TT, double>, G::NT, 0);
+    return e == cudaSuccess ? per_sm * S.nsm : 0;
+}
+}  // namespace
+
+int tile_work_ctas(const Solver &S)
+{
+    switch (S.p) {
+    case 2: return tile_work_ctas_p<2, 3>(S);
+    case 3: return tile_work_ctas_p<3, 3>(S);
+    case 4: return tile_work_ctas_p<4, 3>(S);
+    case 5: return tile_work_ctas_p<5, 5>(S);
+    case 6: return tile_work_ctas_p<6, 5>(S);
+    default: return 0;
+    }
 }
 
 bool tc_colour_prepare(const Solver &S, std::string &why)

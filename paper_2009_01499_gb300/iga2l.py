@@ -21,7 +21,7 @@ FP64, MIXED_FP32, MIXED_FP32_ALL, MIXED_TF32 = 0, 1, 2, 3
 SCHED_LATTICE, SCHED_TILE = 1, 2
 COARSE_EXACT, COARSE_VCYCLE = 0, 1
 RHS_COEFFS, RHS_IS_LOAD = 0, 1
-SWEEP_AUTO, SWEEP_PER_COLOUR, SWEEP_PERSISTENT = 0, 1, 2
+SWEEP_AUTO, SWEEP_PER_COLOUR, SWEEP_PERSISTENT, SWEEP_WORK_LIST = 0, 1, 2, 3
 TEST_SKIP_OPERATOR_COPY, TEST_WITHHOLD_PROGRESS = 1, 2
 
 # Every exported symbol of include/iga2l.h.

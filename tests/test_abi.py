@@ -69,10 +69,16 @@ def test_assemble_rejects_bad_arguments_before_touching_the_gpu():
     assert lib.iga2l_assemble(2, 32, 2, ctypes.byref(bad), ctypes.byref(h)) == iga2l.ERR_INVALID_ARG
     bad = iga2l.default_options(period=6, stride=2)   # gcd(g, q) != 1
     assert lib.iga2l_assemble(2, 32, 2, ctypes.byref(bad), ctypes.byref(h)) == iga2l.ERR_INVALID_ARG
-    for kw in ({"rhs": 2}, {"test_flags": 8}, {"wait_budget_cycles": -5}, {"sweep": 3}):
+    for kw in ({"rhs": 2}, {"test_flags": 8}, {"wait_budget_cycles": -5}, {"sweep": 4}):
         bad = iga2l.default_options(**kw)
         assert lib.iga2l_assemble(2, 32, 2, ctypes.byref(bad), ctypes.byref(h)) == iga2l.ERR_INVALID_ARG, kw
         assert not h.value
+    # the work-list sweep runs the 2D TILE schedule only
+    bad = iga2l.default_options(sweep=iga2l.SWEEP_WORK_LIST)
+    assert lib.iga2l_assemble(2, 32, 2, ctypes.byref(bad), ctypes.byref(h)) == iga2l.ERR_UNSUPPORTED
+    bad = iga2l.default_options(sweep=iga2l.SWEEP_WORK_LIST, schedule=iga2l.SCHED_TILE)
+    assert lib.iga2l_assemble(2, 16, 3, ctypes.byref(bad), ctypes.byref(h)) == iga2l.ERR_UNSUPPORTED
+    assert not h.value
 
 
 @pytest.mark.parametrize("p", [1, 2, 3, 4, 5])
