@@ -347,6 +347,17 @@ iga2l_solver::SolveGraph *solve_graph(iga2l_handle h, double *u, const double *b
 
 // b_p = (f, phi_i) of a source given by its B-spline coefficients f (Section 2), into the
 // handle's right-hand-side buffer (every problem of a batch)
+// every ss x ss class matrix of a [class][e][f] table transposed to [class][f][e]
+std::vector<double> transpose_classes(const std::vector<double> &m, int ss)
+{
+    std::vector<double> t(m.size());
+    const size_t sq = (size_t)ss * ss;
+    for (size_t c = 0; c + sq <= m.size(); c += sq)
+        for (int e = 0; e < ss; ++e)
+            for (int f = 0; f < ss; ++f) t[c + (size_t)f * ss + e] = m[c + (size_t)e * ss + f];
+    return t;
+}
+
 int load_from_coeffs(iga2l_handle h, const double *f, const double *u, cudaStream_t st)
 {
     if (!f || !u) return fail(IGA2L_ERR_INVALID_ARG, "null vector");
@@ -667,6 +678,7 @@ static int assemble_impl(int p, int m, int dim, int nbatch, bool batch, const ig
         (ce = upload(S, &S->Mb, ht.Mb)) != cudaSuccess ||
         (ce = upload(S, &S->stencil, stencil)) != cudaSuccess ||
         (ce = upload(S, &S->binv, binv)) != cudaSuccess ||
+        (dim == 2 && (ce = upload(S, &S->binv_t, transpose_classes(binv, SS))) != cudaSuccess) ||
         (ce = upload(S, &S->pcls, pcls)) != cudaSuccess ||
         (ce = upload(S, &S->bcls, bcls)) != cudaSuccess ||
         (ce = upload(S, &S->Rb, ht.Rb)) != cudaSuccess ||
@@ -789,12 +801,24 @@ static int assemble_impl(int p, int m, int dim, int nbatch, bool batch, const ig
                 release(S);
                 return cuda_fail(ce, "mixed-precision level allocation");
             }
+        if (dim == 2 && (ce = upload(S, &X.binv_t, to_f(transpose_classes(binv, SS)))) != cudaSuccess) {
+            release(S);
+            return cuda_fail(ce, "block-inverse upload");
+        }
         if (opt.precision == IGA2L_MIXED_FP32 || opt.precision == IGA2L_MIXED_TF32) {
             std::vector<float> lo(binv.size());
             for (size_t i = 0; i < binv.size(); ++i) lo[i] = (float)(binv[i] - (double)(float)binv[i]);
             if ((ce = upload(S, &X.binv_lo, lo)) != cudaSuccess) {
                 release(S);
                 return cuda_fail(ce, "block-inverse pair upload");
+            }
+            if (dim == 2) {
+                std::vector<double> bt = transpose_classes(binv, SS);
+                for (size_t i = 0; i < bt.size(); ++i) lo[i] = (float)(bt[i] - (double)(float)bt[i]);
+                if ((ce = upload(S, &X.binv_lo_t, lo)) != cudaSuccess) {
+                    release(S);
+                    return cuda_fail(ce, "block-inverse pair upload");
+                }
             }
         }
         if (opt.precision == IGA2L_MIXED_TF32) {

@@ -38,7 +38,8 @@ __device__ __forceinline__ void two_sum(float a, float b, float &t, float &e)
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(t, z)), __fsub_rn(b, z));   // a + b = t + e
 }
 
-template <int SS>
+// (element f of the row at hi[f * STRIDE], lo[f * STRIDE])
+template <int SS, int STRIDE = 1>
 __device__ __forceinline__ float dot2_row(const float *__restrict__ hi, const float *__restrict__ lo,
                                           const float *rv)
 {
@@ -46,13 +47,13 @@ __device__ __forceinline__ float dot2_row(const float *__restrict__ hi, const fl
 #pragma unroll
     for (int f = 0; f < SS; ++f) {
         const int k = f & 3;
-        const float a = __ldg(&hi[f]), r = rv[f];
+        const float a = __ldg(&hi[f * STRIDE]), r = rv[f];
         const float p = __fmul_rn(a, r);
         const float ep = __fmaf_rn(a, r, -p);                  // a r = p + ep
         float t, es;
         two_sum(s[k], p, t, es);                               // s + p = t + es
         s[k] = t;
-        c[k] = __fmaf_rn(__ldg(&lo[f]), r, __fadd_rn(c[k], __fadd_rn(ep, es)));
+        c[k] = __fmaf_rn(__ldg(&lo[f * STRIDE]), r, __fadd_rn(c[k], __fadd_rn(ep, es)));
     }
     float t01, e01, t23, e23, t, e;
     two_sum(s[0], s[1], t01, e01);

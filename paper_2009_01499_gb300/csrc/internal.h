@@ -72,6 +72,9 @@ struct MixedState {
     // IGA2L_MIXED_FP32 / TF32: the FP64 block inverses as unevaluated pairs binv + binv_lo
     // (binv_lo = fl32(B - binv)), for the compensated FP32 application in the TILE kernel
     float *binv_lo = nullptr;
+    // TILE (2D): binv and binv_lo with each class's matrix transposed ([class][f][e]), so that
+    // the lanes of a block, one per row e, read consecutive words
+    float *binv_t = nullptr, *binv_lo_t = nullptr;
     float *r = nullptr;       // outer residual b - A u, computed in FP64, stored in FP32
     float *delta = nullptr;   // correction of the Schwarz step
     float *d = nullptr, *t = nullptr, *t2 = nullptr, *dc = nullptr, *ec = nullptr;
@@ -97,6 +100,7 @@ struct Solver {
     double *Kb = nullptr, *Mb = nullptr;
     double *stencil = nullptr;   // npc^dim classes x (2p+1)^dim coefficients
     double *binv = nullptr;      // nbc^dim classes x S*S, S = s^dim
+    double *binv_t = nullptr;    // TILE (2D): binv with each class transposed ([class][f][e])
     int *pcls = nullptr;         // point class of every row index (n)
     int *bcls = nullptr;         // block class of every centre index (n)
     double *Rb = nullptr, *Cb = nullptr;
@@ -139,6 +143,11 @@ struct Solver {
     const float *boundary_lo() const
     {
         return opt.precision == IGA2L_MIXED_FP32 || opt.precision == IGA2L_MIXED_TF32 ? mx.binv_lo : nullptr;
+    }
+    // the same, transposed per class (the TILE kernels)
+    const float *boundary_lo_t() const
+    {
+        return opt.precision == IGA2L_MIXED_FP32 || opt.precision == IGA2L_MIXED_TF32 ? mx.binv_lo_t : nullptr;
     }
 };
 

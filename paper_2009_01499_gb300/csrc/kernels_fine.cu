@@ -1080,7 +1080,8 @@ struct TileSmem {
 // One tile of one TILE phase (tile index ti of the phase's ntpx-wide grid of tiles).  `pre`
 // runs after the constant-table reads, before the first read of u or b, and returns whether
 // the CTA goes on (the same answer in every thread).  L2ONLY: u is read past L1 (other CTAs
-// of the same launch wrote it).
+// of the same launch wrote it).  binv and binv_lo hold every class's inverse transposed
+// ([class][f][e]): the lanes of a block (one per row e) read consecutive words.
 template <int P, int S, int TT, typename T, bool L2ONLY, typename Pre>
 __device__ __forceinline__ void schwarz_tile_cta(TileSmem<P, S, TT, T> &sm, int ti, int n, int nbc, int q, int g,
                                                  int rev, int c0, int c1, int px, int py, int ntpx,
@@ -1130,9 +1131,9 @@ __device__ __forceinline__ void schwarz_tile_cta(TileSmem<P, S, TT, T> &sm, int 
     T2 brow[G::NB2];
 #pragma unroll
     for (int k = 0; k < G::NB2; ++k) {
-        const size_t base = ((size_t)interior * SS + e) * SS;
-        brow[k].x = role ? __ldg(&binv[base + 2 * k]) : T(0);
-        brow[k].y = (role && 2 * k + 1 < SS) ? __ldg(&binv[base + 2 * k + 1]) : T(0);
+        const size_t base = (size_t)interior * SS * SS + e;
+        brow[k].x = role ? __ldg(&binv[base + (size_t)(2 * k) * SS]) : T(0);
+        brow[k].y = (role && 2 * k + 1 < SS) ? __ldg(&binv[base + (size_t)(2 * k + 1) * SS]) : T(0);
     }
     if (!pre()) return;
     stage_window_dup<NT, SW, SW * SW, T2, L2ONLY>(su, u, n, x0 - H, y0 - H, tid);
@@ -1204,19 +1205,19 @@ __device__ __forceinline__ void schwarz_tile_cta(TileSmem<P, S, TT, T> &sm, int 
                     const T2 acc2 = add2(acc0, acc1);
                     ev = acc2.x + acc2.y;
                 } else if (sizeof(T) == sizeof(double) || !binv_lo) {
-                    const T *Bi = binv + ((size_t)cls * SS + e) * SS;
+                    const T *Bi = binv + (size_t)cls * SS * SS + e;
     #pragma unroll
-                    for (int f = 0; f < SS; ++f) ev = fma(__ldg(&Bi[f]), rsb[f], ev);
+                    for (int f = 0; f < SS; ++f) ev = fma(__ldg(&Bi[(size_t)f * SS]), rsb[f], ev);
                 } else if constexpr (sizeof(T) == sizeof(float)) {
                     // FP64 row of a boundary-class inverse (as the pair binv + binv_lo), applied
                     // in compensated FP32 arithmetic: GB300's FP64 pipe is 1/58 of its FP32
                     // rate, and these rows set the boundary tiles' critical path
-                    const size_t row = ((size_t)cls * SS + e) * SS;
+                    const size_t col = (size_t)cls * SS * SS + e;
                     T rv[2 * G::NB2];
                     const T2 *r2 = reinterpret_cast<const T2 *>(rsb);
     #pragma unroll
                     for (int k = 0; k < G::NB2; ++k) { const T2 v = r2[k]; rv[2 * k] = v.x; rv[2 * k + 1] = v.y; }
-                    ev = dot2_row<SS>(binv + row, binv_lo + row, rv);
+                    ev = dot2_row<SS, SS>(binv + col, binv_lo + col, rv);
                 }
                 if (in) {
                     T2 &ref = su[(ly + H) * SW + (lx + H)];
@@ -1676,6 +1677,14 @@ cudaError_t schwarz_lattice_p(const Solver &S, const T *stencil, const T *kband,
     return cudaSuccess;
 }
 
+// the block inverses transposed per class, as the TILE kernels read them
+template <typename T>
+const T *tile_binv(const Solver &S);
+template <>
+const double *tile_binv<double>(const Solver &S) { return S.binv_t; }
+template <>
+const float *tile_binv<float>(const Solver &S) { return S.mx.binv_t; }
+
 // the TILE sweep as one work-list launch over every problem of the handle
 template <int P, int SB, typename T>
 cudaError_t schwarz_tile_work_p(const Solver &S, const T *kband, const T *mband, const T *binv, T *u, const T *b,
@@ -1717,7 +1726,8 @@ cudaError_t schwarz_tile_work_p(const Solver &S, const T *kband, const T *mband,
     // while others run more (measured: p = 5 phase 0 at 1024^2 took 195 us against 153)
     const long long grid = std::min(widest, (long long)S.tile_work_ctas);
     if (grid <= 0) return cudaSuccess;
-    k_schwarz_tile2d_work<P, SB, TT, T><<<(unsigned)grid, G::NT, 0, st>>>(a, kband, mband, binv, S.boundary_lo(), u, b);
+    k_schwarz_tile2d_work<P, SB, TT, T><<<(unsigned)grid, G::NT, 0, st>>>(a, kband, mband, tile_binv<T>(S),
+                                                                          S.boundary_lo_t(), u, b);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -1745,8 +1755,8 @@ cudaError_t schwarz_tile_p(const Solver &S, const T *kband, const T *mband, cons
             if (ntpx <= 0 || ntpy <= 0) continue;
             const cudaError_t err =
                 launch_pdl(k_schwarz_tile2d<P, SB, TT, T>, dim3(ntpx * ntpy, S.nbatch), dim3(G::NT), st, S.n,
-                           S.ht.nbc, S.q, S.g, reverse ? 1 : 0, c0, c1, px, py, ntpx, kband, mband, binv,
-                           S.boundary_lo(), interior, u, b, BatchRef{S.active, S.N, 0, 0});
+                           S.ht.nbc, S.q, S.g, reverse ? 1 : 0, c0, c1, px, py, ntpx, kband, mband,
+                           tile_binv<T>(S), S.boundary_lo_t(), interior, u, b, BatchRef{S.active, S.N, 0, 0});
             count_launches(1);
             if (err != cudaSuccess) return err;
         }
