@@ -71,9 +71,9 @@ extern "C" {
 #define IGA2L_RHS_COEFFS 0
 #define IGA2L_RHS_IS_LOAD 1
 /* sweep: how the Schwarz step of the FP32 inner cycle runs in the LATTICE order.  AUTO
- * picks the persistent form for 5x5 and 7x7 blocks where it is available (2D
- * single-problem handles with IGA2L_MIXED_FP32 or IGA2L_MIXED_FP32_ALL) and one launch
- * per colour elsewhere;
+ * picks the persistent form for colourings of at least 250 colours (p = 8's default) where
+ * it is available (2D single-problem handles with IGA2L_MIXED_FP32 or IGA2L_MIXED_FP32_ALL)
+ * and one launch per colour elsewhere;
  * PERSISTENT asks for it (IGA2L_ERR_UNSUPPORTED where it is not available).  Both give
  * the same iterates up to FP32 rounding order. */
 #define IGA2L_SWEEP_AUTO 0

@@ -853,10 +853,11 @@ static int assemble_impl(int p, int m, int dim, int nbatch, bool batch, const ig
                 return fail(IGA2L_ERR_UNSUPPORTED, "no resident launch plan for the persistent sweep");
             }
             // AUTO: measured at 1024^2 (GB300), one persistent launch beats one launch per
-            // colour for 5x5 and 7x7 blocks (q^2 >= 100 colours: 10.9 against 12.9 ms per p = 5
-            // solve) and loses for 3x3 blocks (its colour-to-colour hand-off between
-            // neighbouring CTAs costs about 4.4 us, more than a launch)
-            if (opt.sweep == IGA2L_SWEEP_AUTO && S->s < 5) S->pgx = 0;
+            // colour only with the most colours (p = 8, q^2 = 289: 3.85 against 4.23 ms per
+            // sweep); with fewer its colour-to-colour hand-off between neighbouring CTAs (about
+            // 4.4 us) costs more than a launch (p = 5: 1.20 against 1.11 ms, p = 7: 3.35 against
+            // 2.99 ms)
+            if (opt.sweep == IGA2L_SWEEP_AUTO && S->q * S->q < 250) S->pgx = 0;
         }
     }
     if (opt.sweep == IGA2L_SWEEP_WORK_LIST) {   // the TILE sweep as one work-list launch

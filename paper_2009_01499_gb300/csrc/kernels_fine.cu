@@ -325,6 +325,7 @@ struct SfSmem {
 
 // The work of one CTA of a colour phase: blocks vb NB .. vb NB + NB - 1 of the colour (in the
 // numbering of frame_block, which skips the rectangle [ix0, ix0 + nix) x [iy0, iy0 + niy)).
+// binv and binv_lo hold every class's inverse transposed ([class][f][e]).
 // All NT threads call it; `pre` runs between the constant-table reads and the first
 // dependent read (the programmatic-launch wait) and returns whether the CTA goes on (the
 // same answer in every thread).
@@ -347,7 +348,7 @@ __device__ __forceinline__ void schwarz_sf_cta(SfSmem<P, S, T, NT> &sm, int vb, 
     auto &scy = sm.scy;
     auto &scls = sm.scls;
     const int tid = threadIdx.x;
-    for (int i = tid; i < SS * SS; i += NT) sbi[i] = binv[(size_t)interior * SS * SS + i];   // constant table
+    for (int i = tid; i < SS * SS; i += NT) sbi[i] = binv[(size_t)interior * SS * SS + i];   // constant table (transposed)
     const int blk0 = vb * NB;
     if (tid < NB) {   // the CTA's blocks, once (frame_block divides by the colour's row length)
         const int blk = blk0 + tid;
@@ -360,6 +361,15 @@ __device__ __forceinline__ void schwarz_sf_cta(SfSmem<P, S, T, NT> &sm, int vb, 
             const int bx = cx < L ? cx : (cx > n - 1 - L ? 2 * L - (n - 1 - cx) : L);
             const int by = cy < L ? cy : (cy > n - 1 - L ? 2 * L - (n - 1 - cy) : L);
             cls = by * nbc + bx;
+            if (cls != interior) {   // the class's inverse into L1 now, for phase 3
+                constexpr int LINES = (SS * SS * (int)sizeof(T) + 127) / 128;
+                const char *m = reinterpret_cast<const char *>(binv + (size_t)cls * SS * SS);
+                const char *ml = binv_lo ? reinterpret_cast<const char *>(binv_lo + (size_t)cls * SS * SS) : nullptr;
+                for (int l = 0; l < LINES; ++l) {
+                    asm volatile("prefetch.global.L1 [%0];" ::"l"(m + 128 * l));
+                    if (ml) asm volatile("prefetch.global.L1 [%0];" ::"l"(ml + 128 * l));
+                }
+            }
         }
         scx[tid] = cx;
         scy[tid] = cy;
@@ -464,21 +474,21 @@ __device__ __forceinline__ void schwarz_sf_cta(SfSmem<P, S, T, NT> &sm, int vb, 
         if (x < 0 || x >= n || y < 0 || y >= n) continue;
         T ev = T(0);
         if (cls == interior) {
-            const T *Bi = sbi + e * SS;
+            const T *Bi = sbi + e;
             T e1 = T(0);
 #pragma unroll
             for (int f = 0; f < SS; ++f) {
                 T &acc = (f & 1) ? e1 : ev;
-                acc = fma(Bi[f], rs[j][f], acc);
+                acc = fma(Bi[f * SS], rs[j][f], acc);
             }
             ev += e1;
         } else if (sizeof(T) == sizeof(double) || !binv_lo) {
-            const T *Bi = binv + ((size_t)cls * SS + e) * SS;
+            const T *Bi = binv + (size_t)cls * SS * SS + e;
 #pragma unroll
-            for (int f = 0; f < SS; ++f) ev = fma(__ldg(&Bi[f]), rs[j][f], ev);
+            for (int f = 0; f < SS; ++f) ev = fma(__ldg(&Bi[(size_t)f * SS]), rs[j][f], ev);
         } else if constexpr (sizeof(T) == sizeof(float)) {
-            const size_t row = ((size_t)cls * SS + e) * SS;
-            ev = dot2_row<SS>(binv + row, binv_lo + row, &rs[j][0]);
+            const size_t col = (size_t)cls * SS * SS + e;
+            ev = dot2_row<SS, SS>(binv + col, binv_lo + col, &rs[j][0]);
         }
         u[(size_t)y * n + x] = sub[j][e] + ev;
     }
@@ -1523,6 +1533,14 @@ inline int lattice_bpc(long long nblocks, int ss, int nsm)
     return best;
 }
 
+// the block inverses transposed per class, as the TILE and per-colour FP32 kernels read them
+template <typename T>
+const T *tile_binv(const Solver &S);
+template <>
+const double *tile_binv<double>(const Solver &S) { return S.binv_t; }
+template <>
+const float *tile_binv<float>(const Solver &S) { return S.mx.binv_t; }
+
 // launches the compiled variant with bpc blocks per CTA (BPC, BPC / 2 or BPC / 4, the ones
 // lattice_bpc offers)
 template <int P, int SB, int BPC, typename T>
@@ -1597,8 +1615,8 @@ cudaError_t launch_tc_colour(const Solver &S_, int ox, int oy, int nbx, int nby,
     a.budget = S_.opt.wait_budget_cycles;
     a.kband = kband;
     a.mband = mband;
-    a.binv = binv;
-    a.binv_lo = S_.boundary_lo();
+    a.binv = S_.mx.binv_t;
+    a.binv_lo = S_.boundary_lo_t();
     a.gtc = S_.mx.gtc;
     a.b = b;
     a.u = u;
@@ -1660,8 +1678,8 @@ cudaError_t schwarz_lattice_p(const Solver &S, const T *stencil, const T *kband,
                     err = cudaErrorInvalidValue;
             } else {
                 err = launch_pdl(k_schwarz_lattice2d_sf<P, SB, T>, dim3((nblocks + NBSF - 1) / NBSF, S.nbatch),
-                                 dim3(256), st, S.n, S.ht.nbc, q, ox, oy, nbx, 0, 0, 0, 0, nblocks, kband, mband, binv,
-                                 S.boundary_lo(), interior, u, b, BatchRef{S.active, S.N, 0, 0});
+                                 dim3(256), st, S.n, S.ht.nbc, q, ox, oy, nbx, 0, 0, 0, 0, nblocks, kband, mband,
+                                 tile_binv<T>(S), S.boundary_lo_t(), interior, u, b, BatchRef{S.active, S.N, 0, 0});
             }
         } else {
             const int bpc = lattice_bpc((long long)nblocks * S.nbatch, SB * SB, S.nsm);
@@ -1676,14 +1694,6 @@ cudaError_t schwarz_lattice_p(const Solver &S, const T *stencil, const T *kband,
     }
     return cudaSuccess;
 }
-
-// the block inverses transposed per class, as the TILE kernels read them
-template <typename T>
-const T *tile_binv(const Solver &S);
-template <>
-const double *tile_binv<double>(const Solver &S) { return S.binv_t; }
-template <>
-const float *tile_binv<float>(const Solver &S) { return S.mx.binv_t; }
 
 // the TILE sweep as one work-list launch over every problem of the handle
 template <int P, int SB, typename T>

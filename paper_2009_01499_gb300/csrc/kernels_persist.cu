@@ -101,7 +101,8 @@ struct PersistArgs {
     int gx, gy;               // regions per axis
     int rxmax, rymax;         // largest region sides (layout)
     const float *kband, *mband, *binv;
-    const float *binv_lo;     // FP64 boundary inverses as pairs binv + binv_lo (Dot2), or null
+    const float *binv_lo;     // FP64 boundary inverses as pairs binv + binv_lo (Dot2), or null;
+                              // both with every class's matrix transposed ([class][f][e])
     float *u;
     const float *b;
     unsigned int *progress;   // per CTA: colours finished in this launch (zeroed before it)
@@ -169,18 +170,18 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_schwarz_persist2d(const 
             mk1x[i] = make_float2(in ? A.mband[(size_t)gx * W + a] * hinv : 0.f, in ? A.kband[(size_t)gx * W + a] * h : 0.f);
         }
         if constexpr (!G::BREG)
-            for (int i = tid; i < SS * SS; i += NT) bi[i] = A.binv[(size_t)A.interior * SS * SS + i];
+            for (int i = tid; i < SS * SS; i += NT) bi[i] = A.binv[(size_t)A.interior * SS * SS + i];   // transposed
     }
     const int gA = tid / WIN, col = tid - gA * WIN;
     const int gB = tid / SS, e = tid - gB * SS;
     const int ey = e / S, ex = e - ey * S;
     float2 brow[G::BREG ? G::NB2 : 1];
     if constexpr (G::BREG) {
-        const size_t base = ((size_t)A.interior * SS + e) * SS;
+        const size_t base = (size_t)A.interior * SS * SS + e;
 #pragma unroll
         for (int k = 0; k < G::NB2; ++k) {
-            brow[k].x = gB < G::GE ? A.binv[base + 2 * k] : 0.f;
-            brow[k].y = (gB < G::GE && 2 * k + 1 < SS) ? A.binv[base + 2 * k + 1] : 0.f;
+            brow[k].x = gB < G::GE ? A.binv[base + (size_t)(2 * k) * SS] : 0.f;
+            brow[k].y = (gB < G::GE && 2 * k + 1 < SS) ? A.binv[base + (size_t)(2 * k + 1) * SS] : 0.f;
         }
     }
     // windows of u and b (zero outside the grid); the residual padding stays zero
@@ -317,19 +318,19 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_schwarz_persist2d(const 
 #pragma unroll
                         for (int kk = 0; kk < G::NB2; ++kk) acc = fma2(brow[kk], r2[kk], acc);
                     } else {
-                        const float *br = bi + e * SS;
+                        const float *br = bi + e;
 #pragma unroll
-                        for (int f = 0; f < SS; ++f) acc.x = fmaf(br[f], rb[f], acc.x);
+                        for (int f = 0; f < SS; ++f) acc.x = fmaf(br[f * SS], rb[f], acc.x);
                     }
                     ev = acc.x + acc.y;
                 } else if (A.binv_lo) {
-                    const size_t row = ((size_t)cls * SS + e) * SS;
-                    ev = dot2_row<SS>(A.binv + row, A.binv_lo + row, rb);
+                    const size_t col = (size_t)cls * SS * SS + e;
+                    ev = dot2_row<SS, SS>(A.binv + col, A.binv_lo + col, rb);
                 } else {
-                    const float *Bi = A.binv + ((size_t)cls * SS + e) * SS;
+                    const float *Bi = A.binv + (size_t)cls * SS * SS + e;
                     ev = 0.f;
 #pragma unroll
-                    for (int f = 0; f < SS; ++f) ev = fmaf(__ldg(&Bi[f]), rb[f], ev);
+                    for (int f = 0; f < SS; ++f) ev = fmaf(__ldg(&Bi[(size_t)f * SS]), rb[f], ev);
                 }
                 float &ref = su[(y - wy0) * WX + (x - wx0)];
                 const float nv = ref + ev;
@@ -418,8 +419,8 @@ cudaError_t persist_p(const Solver &S_, float *u, const float *b, bool reverse, 
     a.rymax = S_.pry;
     a.kband = S_.mx.Kb;
     a.mband = S_.mx.Mb;
-    a.binv = S_.mx.binv;
-    a.binv_lo = S_.boundary_lo();
+    a.binv = S_.mx.binv_t;
+    a.binv_lo = S_.boundary_lo_t();
     a.u = u;
     a.b = b;
     a.progress = S_.progress;

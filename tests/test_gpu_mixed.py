@@ -26,8 +26,8 @@ def _host(t):
     return t.cpu().numpy()
 
 
-# "lattice": the persistent sweep (one launch, default for single problems); "lattice_pc": one
-# launch per colour; "tile": the TILE order
+# "lattice": the persistent sweep (one launch per sweep); "lattice_pc": one launch per colour;
+# "tile": the TILE order
 MODES = [(iga2l.MIXED_FP32, "lattice"), (iga2l.MIXED_FP32_ALL, "lattice"), (iga2l.MIXED_FP32, "lattice_pc"),
          (iga2l.MIXED_FP32_ALL, "lattice_pc"), (iga2l.MIXED_FP32, "tile"), (iga2l.MIXED_FP32_ALL, "tile"),
          (iga2l.MIXED_TF32, "lattice")]
