@@ -81,9 +81,9 @@ extern "C" {
 #define IGA2L_SWEEP_PERSISTENT 2
 /* WORK_LIST (TILE schedule, 2D, any precision, single or batch handles): the whole TILE sweep
  * of every problem of the handle in one launch.  CTAs claim (colour group, tile phase,
- * problem, tile) items in sweep order; a tile starts once every tile of its problem's
- * previous phase has finished (a bounded device wait, IGA2L_ERR_DEVICE_TIMEOUT when it gives
- * up).  Iterates are bitwise those of one launch per tile phase (PER_COLOUR and AUTO with the
+ * problem, tile) items in sweep order; a tile starts once the earlier occurrences of its own
+ * and its eight neighbouring tile positions have finished (bounded device waits,
+ * IGA2L_ERR_DEVICE_TIMEOUT when one gives up).  Iterates are bitwise those of one launch per tile phase (PER_COLOUR and AUTO with the
  * TILE schedule). */
 #define IGA2L_SWEEP_WORK_LIST 3
 /* test_flags bits (testing the error paths only; never set in production use):

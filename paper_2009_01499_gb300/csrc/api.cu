@@ -862,13 +862,13 @@ static int assemble_impl(int p, int m, int dim, int nbatch, bool batch, const ig
     }
     if (opt.sweep == IGA2L_SWEEP_WORK_LIST) {   // the TILE sweep as one work-list launch
         void *pc = nullptr;
-        const size_t groups = S->tile_groups > 1 ? (size_t)S->tile_groups : 1;   // as the sweep runs them
+        const size_t nt = (size_t)((S->n + tile_side(p) - 1) / tile_side(p));   // tile positions per axis
         S->tile_work_ctas = tile_work_ctas(*S);
         if (S->tile_work_ctas <= 0) {
             release(S);
             return fail(IGA2L_ERR_UNSUPPORTED, "no resident launch plan for the work-list sweep");
         }
-        if ((ce = cudaMalloc(&pc, sizeof(unsigned int) * (1 + (size_t)nbatch * 4 * groups))) != cudaSuccess) {
+        if ((ce = cudaMalloc(&pc, sizeof(unsigned int) * (1 + (size_t)nbatch * nt * nt))) != cudaSuccess) {
             release(S);
             return cuda_fail(ce, "work-list counters");
         }

@@ -126,8 +126,8 @@ struct Solver {
     double *gbuf = nullptr;      // per-bump 1D loads and their centre derivatives
     int gcap = 0;                // bumps gbuf can hold
     unsigned int *progress = nullptr;   // persistent sweep: colours finished per CTA
-    unsigned int *tile_ctr = nullptr;   // work-list TILE sweep: item counter + tiles finished per
-                                        // (problem, phase); null: one launch per tile phase
+    unsigned int *tile_ctr = nullptr;   // work-list TILE sweep: item counter + finished occurrences
+                                        // per (problem, tile position); null: one launch per phase
     int tile_work_ctas = 0;             // work-list TILE sweep: resident CTAs (its grid)
     int *wait_status = nullptr;         // device: bounded waits that gave up (tensor-core, persistent)
     int pgx = 0, pgy = 0, prx = 0, pry = 0;   // persistent sweep: regions per axis, largest sides

@@ -1279,19 +1279,25 @@ __device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned *p)
 // The TILE sweep of every problem of a handle in one launch (a work list).  Items are
 // (colour group, tile phase, problem, tile) in sweep order, claimed one at a time from a
 // counter: item ids grow with the sweep order, so an item waits only for items claimed
-// before it by CTAs that are running, and the launch cannot deadlock.  A tile starts once
-// every tile of its problem's previous phase has finished (a per-problem, per-phase
-// counter raised by each finished tile after a device-scope fence; the wait is bounded by
-// `budget` cycles and gives up at once after any failure).  u is read past L1, since other
-// SMs wrote it during the launch.  The counters are zeroed on the stream before the
-// launch.  withhold (tests only): finished tiles are not counted, so the first wait runs
-// out.
+// before it by CTAs that are running, and the launch cannot deadlock.  A tile reads u within
+// H = R + P of its square and writes within R of it; H + R <= TT, so only its eight
+// neighbouring tiles (and itself, with colour groups) touch the same DOFs.  It therefore
+// starts once the earlier occurrences of those nine tile positions in the sweep order have
+// finished: a per-problem, per-position counter of finished occurrences, raised after a
+// device-scope fence; each wait is bounded by `budget` cycles and gives up at once after
+// any failure.  Every pair of tiles that touch the same DOFs keeps the order of one launch
+// per phase, so the iterates are bitwise those of that form, while the tiles of a phase no
+// longer wait for its slowest (boundary) tiles unless they are neighbours.  u is read past
+// L1, since other SMs wrote it during the launch.  The counters are zeroed on the stream
+// before the launch.  withhold (tests only): finished tiles are not counted, so the first
+// wait runs out.
 struct TileWorkArgs {
-    int n, nbc, q, g, rev, interior, nbatch, groups, withhold;
+    int n, nbc, q, g, rev, interior, nbatch, groups, withhold, nt;
     int tiles[4], ntpx[4];   // tiles and tiles per row of phase (px, py) = (t & 1, t >> 1)
     long long per_group;     // items per colour group: nbatch (tiles[0] + ... + tiles[3])
     long long total;
-    unsigned *ctr;           // [0]: next item; [1 + problem * 4 groups + phase]: finished tiles
+    unsigned *ctr;           // [0]: next item; [1 + problem nt^2 + J nt + I]: finished
+                             // occurrences of tile position (I, J)
     const int *active;
     size_t vec;
     int *status;
@@ -1307,7 +1313,7 @@ k_schwarz_tile2d_work(const __grid_constant__ TileWorkArgs a, const T *__restric
     __shared__ TileSmem<P, S, TT, T> sm;
     __shared__ long long s_item;
     __shared__ int s_go;
-    const int ncol = a.q * a.q, nph = 4 * a.groups;
+    const int ncol = a.q * a.q, nt = a.nt;
     pdl_wait();
     for (;;) {
         if (threadIdx.x == 0) s_item = (long long)atomicAdd(a.ctr, 1u);
@@ -1324,40 +1330,42 @@ k_schwarz_tile2d_work(const __grid_constant__ TileWorkArgs a, const T *__restric
             ph = a.rev ? 3 - tseq : tseq;
         }
         const int i = (int)(rem / a.tiles[ph]), ti = (int)(rem - (long long)i * a.tiles[ph]);
-        const int k = a.rev ? a.groups - 1 - kseq : kseq, phi = 4 * kseq + tseq;
+        const int k = a.rev ? a.groups - 1 - kseq : kseq;
         const int c0 = (k * ncol + a.groups - 1) / a.groups, c1 = ((k + 1) * ncol + a.groups - 1) / a.groups;
-        unsigned *done = a.ctr + 1 + (size_t)i * nph;
-        // the most recent earlier phase of the sweep that has tiles (every item counts when it
-        // is done, tiles of converged problems and empty colour groups included)
-        int wph = -1, wtiles = 0;
-        for (int pp = phi - 1; pp >= 0 && wph < 0; --pp) {
-            const int pt = pp & 3, pph = a.rev ? 3 - pt : pt;
-            if (a.tiles[pph] > 0) {
-                wph = pp;
-                wtiles = a.tiles[pph];
-            }
-        }
+        const int I = (ph & 1) + 2 * (ti % a.ntpx[ph]), J = (ph >> 1) + 2 * (ti / a.ntpx[ph]);   // tile position
+        unsigned *done = a.ctr + 1 + (size_t)i * nt * nt;   // (every item counts when it is done,
+                                                            // converged problems' and empty groups' too)
         if (!(a.active && !a.active[i]) && c1 > c0) {
             schwarz_tile_cta<P, S, TT, T, true>(
                 sm, ti, a.n, a.nbc, a.q, a.g, a.rev, c0, c1, ph & 1, ph >> 1, a.ntpx[ph], kband, mband, binv, binv_lo,
                 a.interior, u + (size_t)i * a.vec, b + (size_t)i * a.vec, [&] {
                     if (threadIdx.x == 0) {
+                        // the earlier occurrences of the nine positions: a position of phase tn
+                        // ran kseq times before this colour group, plus once in it if its phase
+                        // comes first in the sweep order; relaxed polls (an acquire per poll
+                        // would also drop the SM's L1 lines that co-resident tiles are using),
+                        // one acquire fence after
                         int go = 1;
-                        if (wph >= 0) {
-                            // relaxed polls (an acquire per poll would also drop the SM's L1
-                            // lines that co-resident tiles are using), one acquire fence after
-                            const long long t0 = clock64();
-                            bool ok = ld_relaxed_u32(done + wph) >= (unsigned)wtiles;
-                            while (!ok && *(volatile int *)a.status == 0 && clock64() - t0 < a.budget) {
-                                __nanosleep(64);
-                                ok = ld_relaxed_u32(done + wph) >= (unsigned)wtiles;
+                        const long long t0 = clock64();
+                        for (int dj = -1; dj <= 1 && go; ++dj)
+                            for (int di = -1; di <= 1 && go; ++di) {
+                                const int In = I + di, Jn = J + dj;
+                                if (In < 0 || In >= nt || Jn < 0 || Jn >= nt) continue;
+                                const int tn = (In & 1) + 2 * (Jn & 1);
+                                const unsigned need = (unsigned)kseq + ((a.rev ? tn > ph : tn < ph) ? 1u : 0u);
+                                if (need == 0) continue;
+                                const unsigned *c = done + (size_t)Jn * nt + In;
+                                bool ok = ld_relaxed_u32(c) >= need;
+                                while (!ok && *(volatile int *)a.status == 0 && clock64() - t0 < a.budget) {
+                                    __nanosleep(64);
+                                    ok = ld_relaxed_u32(c) >= need;
+                                }
+                                if (!ok) {
+                                    atomicAdd(a.status, 1);
+                                    go = 0;
+                                }
                             }
-                            asm volatile("fence.acq_rel.gpu;" ::: "memory");
-                            if (!ok) {
-                                atomicAdd(a.status, 1);
-                                go = 0;
-                            }
-                        }
+                        asm volatile("fence.acq_rel.gpu;" ::: "memory");
                         s_go = go;
                     }
                     __syncthreads();
@@ -1367,7 +1375,7 @@ k_schwarz_tile2d_work(const __grid_constant__ TileWorkArgs a, const T *__restric
         __syncthreads();   // the tile's writes of u, before it counts as finished
         if (threadIdx.x == 0 && !a.withhold) {
             __threadfence();
-            atomicAdd(done + phi, 1u);
+            atomicAdd(done + (size_t)J * nt + I, 1u);
         }
         __syncthreads();   // shared memory and s_item are reused by the next item
     }
@@ -1713,6 +1721,7 @@ cudaError_t schwarz_tile_work_p(const Solver &S, const T *kband, const T *mband,
     a.nbatch = S.nbatch;
     a.groups = S.tile_groups > 1 ? S.tile_groups : 1;
     a.withhold = (S.opt.test_flags & IGA2L_TEST_WITHHOLD_PROGRESS) != 0;
+    a.nt = nt;
     long long per = 0, widest = 0;
     for (int t = 0; t < 4; ++t) {
         const int ntpx = (nt - (t & 1) + 1) / 2, ntpy = (nt - (t >> 1) + 1) / 2;
@@ -1729,7 +1738,7 @@ cudaError_t schwarz_tile_work_p(const Solver &S, const T *kband, const T *mband,
     a.vec = S.N;
     a.status = S.wait_status;
     a.budget = S.opt.wait_budget_cycles;
-    cudaError_t e = cudaMemsetAsync(S.tile_ctr, 0, sizeof(unsigned) * (1 + (size_t)S.nbatch * 4 * a.groups), st);
+    cudaError_t e = cudaMemsetAsync(S.tile_ctr, 0, sizeof(unsigned) * (1 + (size_t)S.nbatch * nt * nt), st);
     if (e != cudaSuccess) return e;
     // no more CTAs than the largest phase has items: otherwise the CTAs that start last claim
     // the next phase's items at once and the SMs they sit on run fewer tiles of this phase

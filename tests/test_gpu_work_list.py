@@ -1,8 +1,9 @@
 """GPU tests of the work-list TILE sweep (IGA2L_SWEEP_WORK_LIST): the whole TILE sweep of
 every problem of a handle in one launch, CTAs claiming (colour group, tile phase, problem,
-tile) items in sweep order and each tile waiting (bounded) for its problem's previous
-phase.  Every tile computes what the same tile computes in one launch per tile phase, after
-the same tiles, so the iterates are bitwise equal to that form's (which the oracle parity
+tile) items in sweep order and each tile waiting (bounded) for the earlier occurrences of
+its own and its eight neighbouring tile positions.  Every pair of tiles that touch the same
+DOFs keeps the order of one launch per tile phase, so the iterates are bitwise equal to that
+form's (which the oracle parity
 tests pin); here: sweeps forward and reverse, whole cycles and solves, FP64 and FP32,
 colour groups, grids with empty tile phases, batches with problems masked mid-solve, and
 the bounded wait running out."""
