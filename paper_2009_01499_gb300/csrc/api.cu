@@ -678,7 +678,7 @@ static int assemble_impl(int p, int m, int dim, int nbatch, bool batch, const ig
         (ce = upload(S, &S->Mb, ht.Mb)) != cudaSuccess ||
         (ce = upload(S, &S->stencil, stencil)) != cudaSuccess ||
         (ce = upload(S, &S->binv, binv)) != cudaSuccess ||
-        (dim == 2 && (ce = upload(S, &S->binv_t, transpose_classes(binv, SS))) != cudaSuccess) ||
+        (ce = upload(S, &S->binv_t, transpose_classes(binv, SD))) != cudaSuccess ||
         (ce = upload(S, &S->pcls, pcls)) != cudaSuccess ||
         (ce = upload(S, &S->bcls, bcls)) != cudaSuccess ||
         (ce = upload(S, &S->Rb, ht.Rb)) != cudaSuccess ||
@@ -801,7 +801,7 @@ static int assemble_impl(int p, int m, int dim, int nbatch, bool batch, const ig
                 release(S);
                 return cuda_fail(ce, "mixed-precision level allocation");
             }
-        if (dim == 2 && (ce = upload(S, &X.binv_t, to_f(transpose_classes(binv, SS)))) != cudaSuccess) {
+        if ((ce = upload(S, &X.binv_t, to_f(transpose_classes(binv, SD)))) != cudaSuccess) {
             release(S);
             return cuda_fail(ce, "block-inverse upload");
         }
@@ -812,13 +812,11 @@ static int assemble_impl(int p, int m, int dim, int nbatch, bool batch, const ig
                 release(S);
                 return cuda_fail(ce, "block-inverse pair upload");
             }
-            if (dim == 2) {
-                std::vector<double> bt = transpose_classes(binv, SS);
-                for (size_t i = 0; i < bt.size(); ++i) lo[i] = (float)(bt[i] - (double)(float)bt[i]);
-                if ((ce = upload(S, &X.binv_lo_t, lo)) != cudaSuccess) {
-                    release(S);
-                    return cuda_fail(ce, "block-inverse pair upload");
-                }
+            std::vector<double> bt = transpose_classes(binv, SD);
+            for (size_t i = 0; i < bt.size(); ++i) lo[i] = (float)(bt[i] - (double)(float)bt[i]);
+            if ((ce = upload(S, &X.binv_lo_t, lo)) != cudaSuccess) {
+                release(S);
+                return cuda_fail(ce, "block-inverse pair upload");
             }
         }
         if (opt.precision == IGA2L_MIXED_TF32) {

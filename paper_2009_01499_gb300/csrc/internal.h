@@ -100,7 +100,7 @@ struct Solver {
     double *Kb = nullptr, *Mb = nullptr;
     double *stencil = nullptr;   // npc^dim classes x (2p+1)^dim coefficients
     double *binv = nullptr;      // nbc^dim classes x S*S, S = s^dim
-    double *binv_t = nullptr;    // TILE (2D): binv with each class transposed ([class][f][e])
+    double *binv_t = nullptr;    // binv with each class transposed ([class][f][e]): TILE and 3D kernels
     int *pcls = nullptr;         // point class of every row index (n)
     int *bcls = nullptr;         // block class of every centre index (n)
     double *Rb = nullptr, *Cb = nullptr;
@@ -138,6 +138,11 @@ struct Solver {
     const double *boundary64() const
     {
         return opt.precision == IGA2L_MIXED_FP32 || opt.precision == IGA2L_MIXED_TF32 ? binv : nullptr;
+    }
+    // the same, transposed per class (the 3D kernels)
+    const double *boundary64_t() const
+    {
+        return opt.precision == IGA2L_MIXED_FP32 || opt.precision == IGA2L_MIXED_TF32 ? binv_t : nullptr;
     }
     // the low halves of the FP32 pairs of those inverses, or null likewise
     const float *boundary_lo() const

@@ -206,16 +206,16 @@ k_schwarz_lattice3d(int n, int nbc, int q, int ox, int oy, int oz, int nbx, int 
         if (gx >= 0 && gx < n && gy >= 0 && gy < n && gz >= 0 && gz < n) {
             const int cls = (bcls[cz] * nbc + bcls[cy]) * nbc + bcls[cx];
             if (sizeof(T) == sizeof(double) || cls == interior || !binv64) {
-                const T *Bi = binv + ((size_t)cls * SS + tid) * SS;
+                const T *Bi = binv + (size_t)cls * SS * SS + tid;
                 T ev = T(0);
 #pragma unroll
-                for (int f = 0; f < SS; ++f) ev = fma(__ldg(&Bi[f]), rs[f], ev);
+                for (int f = 0; f < SS; ++f) ev = fma(__ldg(&Bi[(size_t)f * SS]), rs[f], ev);
                 u[((size_t)gz * n + gy) * n + gx] += ev;
             } else {
-                const double *Bi = binv64 + ((size_t)cls * SS + tid) * SS;
+                const double *Bi = binv64 + (size_t)cls * SS * SS + tid;
                 double ev = 0.0;
 #pragma unroll
-                for (int f = 0; f < SS; ++f) ev = fma(__ldg(&Bi[f]), (double)rs[f], ev);
+                for (int f = 0; f < SS; ++f) ev = fma(__ldg(&Bi[(size_t)f * SS]), (double)rs[f], ev);
                 u[((size_t)gz * n + gy) * n + gx] += (T)ev;
             }
         }
@@ -352,16 +352,16 @@ k_schwarz_lattice3d_mb(int n, int nbc, int q, int ox, int oy, int oz, int nbx, i
         if (blk0 + j >= nblocks || gx < 0 || gx >= n || gy < 0 || gy >= n || gz < 0 || gz >= n) continue;
         const int cls = (bcls[cz] * nbc + bcls[cy]) * nbc + bcls[cx];
         if (sizeof(T) == sizeof(double) || cls == interior || !binv64) {
-            const T *Bi = binv + ((size_t)cls * SS + e) * SS;
+            const T *Bi = binv + (size_t)cls * SS * SS + e;
             T ev = T(0);
 #pragma unroll
-            for (int f = 0; f < SS; ++f) ev = fma(__ldg(&Bi[f]), rs[j][f], ev);
+            for (int f = 0; f < SS; ++f) ev = fma(__ldg(&Bi[(size_t)f * SS]), rs[j][f], ev);
             u[((size_t)gz * n + gy) * n + gx] += ev;
         } else {
-            const double *Bi = binv64 + ((size_t)cls * SS + e) * SS;
+            const double *Bi = binv64 + (size_t)cls * SS * SS + e;
             double ev = 0.0;
 #pragma unroll
-            for (int f = 0; f < SS; ++f) ev = fma(__ldg(&Bi[f]), (double)rs[j][f], ev);
+            for (int f = 0; f < SS; ++f) ev = fma(__ldg(&Bi[(size_t)f * SS]), (double)rs[j][f], ev);
             u[((size_t)gz * n + gy) * n + gx] += (T)ev;
         }
     }
@@ -506,18 +506,18 @@ k_schwarz_tile3d(int n, int nbc, int q, int g, int rev, int px, int py, int pz, 
                             const int cls = (bcls[gcz] * nbc + bcls[gcy]) * nbc + bcls[gcx];
                             T ev = T(0);
                             if (cls == interior) {
-                                const T *Bi = sbi + tid * SS;
+                                const T *Bi = sbi + tid;
 #pragma unroll
-                                for (int f = 0; f < SS; ++f) ev = fma(Bi[f], rs[f], ev);
+                                for (int f = 0; f < SS; ++f) ev = fma(Bi[f * SS], rs[f], ev);
                             } else if (sizeof(T) == sizeof(double) || !binv64) {
-                                const T *Bi = binv + ((size_t)cls * SS + tid) * SS;
+                                const T *Bi = binv + (size_t)cls * SS * SS + tid;
 #pragma unroll
-                                for (int f = 0; f < SS; ++f) ev = fma(__ldg(&Bi[f]), rs[f], ev);
+                                for (int f = 0; f < SS; ++f) ev = fma(__ldg(&Bi[(size_t)f * SS]), rs[f], ev);
                             } else {
-                                const double *Bi = binv64 + ((size_t)cls * SS + tid) * SS;
+                                const double *Bi = binv64 + (size_t)cls * SS * SS + tid;
                                 double ed = 0.0;
 #pragma unroll
-                                for (int f = 0; f < SS; ++f) ed = fma(__ldg(&Bi[f]), (double)rs[f], ed);
+                                for (int f = 0; f < SS; ++f) ed = fma(__ldg(&Bi[(size_t)f * SS]), (double)rs[f], ed);
                                 ev = (T)ed;
                             }
                             su[((cz + P + ez) * SW + cy + P + ey) * SW + cx + P + ex] += ev;
@@ -815,7 +815,7 @@ cudaError_t schwarz_tile3d_p(const Solver &S, const T *Kb, const T *Mb, const T 
         const int ntpx = (nt - px + 1) / 2, ntpy = (nt - py + 1) / 2, ntpz = (nt - pz + 1) / 2;
         if (ntpx <= 0 || ntpy <= 0 || ntpz <= 0) continue;
         k_schwarz_tile3d<P, TT, T><<<ntpx * ntpy * ntpz, 128, G::bytes, st>>>(
-            S.n, nbc, S.q, S.g, reverse ? 1 : 0, px, py, pz, ntpx, ntpy, Kb, Mb, binv, S.boundary64(), interior,
+            S.n, nbc, S.q, S.g, reverse ? 1 : 0, px, py, pz, ntpx, ntpy, Kb, Mb, binv, S.boundary64_t(), interior,
             S.bcls, u, b);
         count_launches(1);
         cudaError_t err = cudaGetLastError();
@@ -842,10 +842,10 @@ cudaError_t schwarz3d_p(const Solver &S, const T *Kb, const T *Mb, const T *binv
         if constexpr (sizeof(T) == sizeof(double)) {
             constexpr int NB = Lattice3dGeom<P, T>::NB;
             k_schwarz_lattice3d_mb<P, T><<<(nblocks + NB - 1) / NB, 256, 0, st>>>(
-                S.n, nbc, q, ox, oy, oz, nbx, nby, nblocks, Kb, Mb, binv, S.boundary64(), interior, S.bcls, u, b);
+                S.n, nbc, q, ox, oy, oz, nbx, nby, nblocks, Kb, Mb, binv, S.boundary64_t(), interior, S.bcls, u, b);
         } else {
             k_schwarz_lattice3d<P, T><<<nblocks, 128, 0, st>>>(S.n, nbc, q, ox, oy, oz, nbx, nby, Kb, Mb, binv,
-                                                                S.boundary64(), interior, S.bcls, u, b);
+                                                                S.boundary64_t(), interior, S.bcls, u, b);
         }
         count_launches(1);
         cudaError_t err = cudaGetLastError();
@@ -911,7 +911,7 @@ cudaError_t launch3d_residual(const Solver &S, const double *u, const double *b,
 
 cudaError_t launch3d_schwarz(const Solver &S, double *u, const double *b, bool reverse, cudaStream_t st)
 {
-    return schwarz3d_any<double>(S, S.Kb, S.Mb, S.binv, u, b, reverse, st);
+    return schwarz3d_any<double>(S, S.Kb, S.Mb, S.binv_t, u, b, reverse, st);
 }
 
 cudaError_t launch3d_restrict(const Solver &S, const double *d, double *dc, cudaStream_t st)
@@ -953,7 +953,7 @@ cudaError_t launch3d_inner_fine(const Solver &S, const float *r32, cudaStream_t 
 {
     const MixedState &X = S.mx;
     cudaError_t e = cudaMemsetAsync(X.delta, 0, sizeof(float) * S.N, st);
-    if (e == cudaSuccess) e = schwarz3d_any<float>(S, X.Kb, X.Mb, X.binv, X.delta, r32, false, st);
+    if (e == cudaSuccess) e = schwarz3d_any<float>(S, X.Kb, X.Mb, X.binv_t, X.delta, r32, false, st);
     if (e == cudaSuccess) e = residual3d_any<float, float>(S, X.Kb, X.Mb, X.delta, r32, X.d, nullptr, st);
     if (e == cudaSuccess) e = restrict3d<float>(S, X.Rb, X.d, X.t, X.t2, X.dc, st);
     return e;
