@@ -1005,8 +1005,11 @@ __device__ __forceinline__ void tile_ypass_split(const typename Vec2<T>::type *s
     using G = TileGeom<P, S, TT>;
     using T2 = typename Vec2<T>::type;
     constexpr int W = G::W, WIN = G::WIN, SW = G::SW, RA = G::RA, RB = S - RA;
-    if (lane >= 2 * WIN) return;
-    const int half = lane >= WIN, col = lane - half * WIN, r0 = half ? RA : 0;
+    // one half of the rows per half-warp (lanes 0 .. WIN - 1 and 16 .. 15 + WIN): a half-warp's
+    // 8-byte loads then read one contiguous row segment (with the halves mixed in one
+    // half-warp, the second half's rows fell on the first half's banks)
+    const int half = lane >> 4, col = lane & 15, r0 = half ? RA : 0;
+    if (col >= WIN) return;
     const T2 *up = su + (cyl + r0) * SW + cxl + col;
     T2 v[RA + 2 * P];
 #pragma unroll
