@@ -897,6 +897,13 @@ struct TileGeom {
     // per window column, rows 0 .. RA - 1 and RA .. S - 1
     static constexpr bool SPLITY = BPW == 1 && 2 * WIN <= 32;
     static constexpr int RA = (S + 1) / 2;
+    // row stride of the staged u: with SPLITY the two halves of a warp read rows RA apart, so
+    // the stride is padded until those rows' banks (4-byte words) do not overlap
+    static constexpr int swp(int w)
+    {
+        return !SPLITY || ((RA * w) % 32 >= WIN && (RA * w) % 32 <= 32 - WIN) ? w : swp(w + 1);
+    }
+    static constexpr int SWP = swp(SW);
     // resident CTAs per SM the register allocation must allow (FP32: a 1024^2 tile phase
     // in one wave; FP64 keeps its registers)
     template <typename T>
@@ -909,31 +916,9 @@ struct TileGeom {
 
 // Stages a (tile-local, zero outside the grid) window into shared memory with all loads
 // of a thread issued before its stores.
-template <int NT, int ROWLEN, int NELEM, typename T>
+template <int NT, int ROWLEN, int NELEM, typename T, bool L2ONLY = false, int DSTROW = ROWLEN>
 __device__ __forceinline__ void stage_window(T *dst, const T *__restrict__ src, int n, int gx0, int gy0, int tid)
 {
-    constexpr int K = (NELEM + NT - 1) / NT;
-    T v[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const int i = tid + k * NT;
-        const int gx = gx0 + i % ROWLEN, gy = gy0 + i / ROWLEN;
-        v[k] = (i < NELEM && gx >= 0 && gx < n && gy >= 0 && gy < n) ? src[(size_t)gy * n + gx] : T(0);
-    }
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const int i = tid + k * NT;
-        if (i < NELEM) dst[i] = v[k];
-    }
-}
-
-// stage_window storing every value twice, as the pair (v, v): the packed FMAs of the y
-// pass then read their splatted operand straight from shared memory
-template <int NT, int ROWLEN, int NELEM, typename T2, bool L2ONLY = false>
-__device__ __forceinline__ void stage_window_dup(T2 *dst, const decltype(T2::x) *__restrict__ src, int n, int gx0,
-                                                 int gy0, int tid)
-{
-    using T = decltype(T2::x);
     constexpr int K = (NELEM + NT - 1) / NT;
     T v[K];
 #pragma unroll
@@ -949,7 +934,7 @@ __device__ __forceinline__ void stage_window_dup(T2 *dst, const decltype(T2::x) 
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         const int i = tid + k * NT;
-        if (i < NELEM) dst[i] = splat2<T2>(v[k]);
+        if (i < NELEM) dst[DSTROW == ROWLEN ? i : (i / ROWLEN) * DSTROW + i % ROWLEN] = v[k];
     }
 }
 
@@ -958,24 +943,25 @@ __device__ __forceinline__ void stage_window_dup(T2 *dst, const decltype(T2::x) 
 //   Y[r][col] = (sum_b K_y[b] u(col, row r + b - P), sum_b M_y[b] u(...)).
 // FAST: interior rows (constant 1D rows); else the rows' own 1D rows (km1y: (K, M) pairs).
 template <int P, int S, int TT, bool FAST, typename T>
-__device__ __forceinline__ void tile_ypass(const typename Vec2<T>::type *su, int cxl, int cyl, int lane_e,
+__device__ __forceinline__ void tile_ypass(const T *su, int cxl, int cyl, int lane_e,
                                            typename Vec2<T>::type *yb, const typename Vec2<T>::type *km1y)
 {
     using G = TileGeom<P, S, TT>;
     using T2 = typename Vec2<T>::type;
-    constexpr int W = G::W, WIN = G::WIN, SW = G::SW;
+    constexpr int W = G::W, WIN = G::WIN, SW = G::SWP;   // (SW: the staged u's row stride)
     for (int col = lane_e; FAST && col < WIN; col += G::SS) {
         {
-            // su holds (v, v) pairs; interior rows are symmetric, so the taps at distance j
-            // from the row's centre share one packed multiply-add on their packed sum
-            T2 v[WIN];
+            // interior rows are symmetric, so the taps at distance j from the row's centre
+            // share one packed multiply-add (K, M) on their sum, held as a (v, v) pair
+            T v[WIN];
 #pragma unroll
             for (int k = 0; k < WIN; ++k) v[k] = su[(cyl + k) * SW + cxl + col];
 #pragma unroll
             for (int r = 0; r < S; ++r) {
-                T2 y = fma2(ckm1<T>(P, P), v[r + P], splat2<T2>(T(0)));
+                T2 y = fma2(ckm1<T>(P, P), splat2<T2>(v[r + P]), splat2<T2>(T(0)));
 #pragma unroll
-                for (int j = 1; j <= P; ++j) y = fma2(ckm1<T>(P, P - j), add2(v[r + P - j], v[r + P + j]), y);
+                for (int j = 1; j <= P; ++j)
+                    y = fma2(ckm1<T>(P, P - j), splat2<T2>(v[r + P - j] + v[r + P + j]), y);
                 yb[r * G::YS + col] = y;
             }
         }
@@ -986,10 +972,10 @@ __device__ __forceinline__ void tile_ypass(const typename Vec2<T>::type *su, int
         for (int pt = lane_e; pt < S * WIN; pt += G::SS) {
             const int r = pt / WIN, col = pt - r * WIN;
             const T2 *kr = km1y + (cyl + r) * W;
-            const T2 *uc = su + (cyl + r) * SW + cxl + col;
+            const T *uc = su + (cyl + r) * SW + cxl + col;
             T2 y = splat2<T2>(T(0));
 #pragma unroll
-            for (int bb = 0; bb < W; ++bb) y = fma2(kr[bb], uc[bb * SW], y);
+            for (int bb = 0; bb < W; ++bb) y = fma2(kr[bb], splat2<T2>(uc[bb * SW]), y);
             yb[r * G::YS + col] = y;
         }
     }
@@ -999,19 +985,19 @@ __device__ __forceinline__ void tile_ypass(const typename Vec2<T>::type *su, int
 // column l, lane WIN + l rows RA .. S - 1.  FASTROW: interior rows (symmetric constant
 // rows); otherwise every row's own (K, M) pairs from km1y, read by all lanes at once.
 template <int P, int S, int TT, bool FASTROW, typename T>
-__device__ __forceinline__ void tile_ypass_split(const typename Vec2<T>::type *su, int cxl, int cyl, int lane,
+__device__ __forceinline__ void tile_ypass_split(const T *su, int cxl, int cyl, int lane,
                                                  typename Vec2<T>::type *yb, const typename Vec2<T>::type *km1y)
 {
     using G = TileGeom<P, S, TT>;
     using T2 = typename Vec2<T>::type;
-    constexpr int W = G::W, WIN = G::WIN, SW = G::SW, RA = G::RA, RB = S - RA;
+    constexpr int W = G::W, WIN = G::WIN, SW = G::SWP, RA = G::RA, RB = S - RA;   // (SW: row stride)
     // one half of the rows per half-warp (lanes 0 .. WIN - 1 and 16 .. 15 + WIN): a half-warp's
     // 8-byte loads then read one contiguous row segment (with the halves mixed in one
     // half-warp, the second half's rows fell on the first half's banks)
     const int half = lane >> 4, col = lane & 15, r0 = half ? RA : 0;
     if (col >= WIN) return;
-    const T2 *up = su + (cyl + r0) * SW + cxl + col;
-    T2 v[RA + 2 * P];
+    const T *up = su + (cyl + r0) * SW + cxl + col;
+    T v[RA + 2 * P];
 #pragma unroll
     for (int k = 0; k < RB + 2 * P; ++k) v[k] = up[k * SW];
     if (!half)
@@ -1023,9 +1009,10 @@ __device__ __forceinline__ void tile_ypass_split(const typename Vec2<T>::type *s
         if (half && r >= RB) break;
         T2 y;
         if constexpr (FASTROW) {
-            y = fma2(ckm1<T>(P, P), v[r + P], splat2<T2>(T(0)));
+            y = fma2(ckm1<T>(P, P), splat2<T2>(v[r + P]), splat2<T2>(T(0)));
 #pragma unroll
-            for (int j = 1; j <= P; ++j) y = fma2(ckm1<T>(P, P - j), add2(v[r + P - j], v[r + P + j]), y);
+            for (int j = 1; j <= P; ++j)
+                y = fma2(ckm1<T>(P, P - j), splat2<T2>(v[r + P - j] + v[r + P + j]), y);
         } else {
             const T2 *kr = km1y + (cyl + r0 + r) * W;
             T2 y1 = splat2<T2>(T(0));
@@ -1033,7 +1020,7 @@ __device__ __forceinline__ void tile_ypass_split(const typename Vec2<T>::type *s
 #pragma unroll
             for (int bb = 0; bb < W; ++bb) {
                 T2 &acc = (bb & 1) ? y1 : y;
-                acc = fma2(kr[bb], v[r + bb], acc);
+                acc = fma2(kr[bb], splat2<T2>(v[r + bb]), acc);
             }
             y = add2(y, y1);
         }
@@ -1083,7 +1070,8 @@ template <int P, int S, int TT, typename T>
 struct TileSmem {
     using G = TileGeom<P, S, TT>;
     using T2 = typename Vec2<T>::type;
-    T2 su[G::SW * G::SW];   // u as (u, u) pairs
+    T su[G::SW * G::SWP];   // u, rows G::SWP apart (the y passes form the (u, u) pairs of the
+                            // packed FMAs in registers)
     T sb[G::BW * G::BW];
     __align__(16) T rs[G::NBLK * G::RSS];
     T2 yb[G::NBLK * G::YB];
@@ -1107,7 +1095,7 @@ __device__ __forceinline__ void schwarz_tile_cta(TileSmem<P, S, TT, T> &sm, int 
     constexpr int W = G::W, SS = G::SS, R = G::R, H = G::H, L = P - 1 + R;
     constexpr int SW = G::SW, BW = G::BW, NB1 = G::NB1, NT = G::NT;
     constexpr int PCI = 2 * P - 1;   // first interior row class
-    T2 *su = sm.su;
+    T *su = sm.su;
     T *sb = sm.sb;
     T *rs = sm.rs;
     T2 *yb = sm.yb;
@@ -1149,7 +1137,7 @@ __device__ __forceinline__ void schwarz_tile_cta(TileSmem<P, S, TT, T> &sm, int 
         brow[k].y = (role && 2 * k + 1 < SS) ? __ldg(&binv[base + (size_t)(2 * k + 1) * SS]) : T(0);
     }
     if (!pre()) return;
-    stage_window_dup<NT, SW, SW * SW, T2, L2ONLY>(su, u, n, x0 - H, y0 - H, tid);
+    stage_window<NT, SW, SW * SW, T, L2ONLY, G::SWP>(su, u, n, x0 - H, y0 - H, tid);
     stage_window<NT, BW, BW * BW>(sb, b, n, x0 - R, y0 - R, tid);
     __syncthreads();
     const int bi = slot % NB1, bj = slot / NB1;
@@ -1233,8 +1221,8 @@ __device__ __forceinline__ void schwarz_tile_cta(TileSmem<P, S, TT, T> &sm, int 
                     ev = dot2_row<SS, SS>(binv + col, binv_lo + col, rv);
                 }
                 if (in) {
-                    T2 &ref = su[(ly + H) * SW + (lx + H)];
-                    ref = splat2<T2>(ref.x + ev);
+                    T &ref = su[(ly + H) * G::SWP + (lx + H)];
+                    ref = ref + ev;
                 }
             }
             __syncthreads();
@@ -1251,7 +1239,7 @@ __device__ __forceinline__ void schwarz_tile_cta(TileSmem<P, S, TT, T> &sm, int 
     else colours(std::false_type{});
     for (int i = tid; i < BW * BW; i += NT) {
         const int gx = x0 - R + i % BW, gy = y0 - R + i / BW;
-        if (gx >= 0 && gx < n && gy >= 0 && gy < n) u[(size_t)gy * n + gx] = su[(i / BW + P) * SW + (i % BW + P)].x;
+        if (gx >= 0 && gx < n && gy >= 0 && gy < n) u[(size_t)gy * n + gx] = su[(i / BW + P) * G::SWP + (i % BW + P)];
     }
 }
 
