@@ -898,10 +898,15 @@ struct TileGeom {
     static constexpr bool SPLITY = BPW == 1 && 2 * WIN <= 32;
     static constexpr int RA = (S + 1) / 2;
     // row stride of the staged u: with SPLITY the two halves of a warp read rows RA apart, so
-    // the stride is padded until those rows' banks (4-byte words) do not overlap
+    // the stride is padded until those rows' banks (4-byte words) do not overlap; with 3x3
+    // blocks (three per warp, at offsets set by the colour) p = 3 takes 31 for 29: counting the
+    // y pass's bank conflicts over every colour offset and candidate stride gave 20% fewer of
+    // its load wavefronts (measured sweep 170.2 -> 169.4 us: the y pass is a small part of the
+    // kernel's shared-memory traffic), and no better stride for p = 2 or 4
     static constexpr int swp(int w)
     {
-        return !SPLITY || ((RA * w) % 32 >= WIN && (RA * w) % 32 <= 32 - WIN) ? w : swp(w + 1);
+        return !SPLITY ? (P == 3 && S == 3 ? SW + 2 : w)
+                       : ((RA * w) % 32 >= WIN && (RA * w) % 32 <= 32 - WIN) ? w : swp(w + 1);
     }
     static constexpr int SWP = swp(SW);
     // resident CTAs per SM the register allocation must allow (FP32: a 1024^2 tile phase
