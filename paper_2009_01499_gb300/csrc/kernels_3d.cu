@@ -141,6 +141,7 @@ k_schwarz_lattice3d(int n, int nbc, int q, int ox, int oy, int oz, int nbx, int 
     const int cx = ox + q * (blk % nbx), cy = oy + q * ((blk / nbx) % nby), cz = oz + q * (blk / (nbx * nby));
     const int px0 = cx - R - P, py0 = cy - R - P, pz0 = cz - R - P;
     const int tid = threadIdx.x, nth = blockDim.x;
+    pdl_wait();   // the previous colour's writes of u
     for (int i = tid; i < PW * PW * PW; i += nth) {
         const int gx = px0 + i % PW, gy = py0 + (i / PW) % PW, gz = pz0 + i / (PW * PW);
         pu[i] = (gx >= 0 && gx < n && gy >= 0 && gy < n && gz >= 0 && gz < n)
@@ -272,6 +273,7 @@ k_schwarz_lattice3d_mb(int n, int nbc, int q, int ox, int oy, int oz, int nbx, i
         cen[tid][1] = oy + q * ((bi / nbx) % nby);
         cen[tid][2] = oz + q * (bi / (nbx * nby));
     }
+    pdl_wait();   // the previous colour's writes of u
     __syncthreads();
     for (int i = tid; i < NB * PW * PW * PW; i += NT) {
         const int j = i / (PW * PW * PW), k = i - j * (PW * PW * PW);
@@ -418,6 +420,7 @@ k_schwarz_tile3d(int n, int nbc, int q, int g, int rev, int px, int py, int pz, 
               z0 = (pz + 2 * (bx / (ntpx * ntpy))) * TT;
     const int org[3] = {x0, y0, z0};
     const int tw = min(TT, n - x0), th = min(TT, n - y0), td = min(TT, n - z0);
+    pdl_wait();   // the previous phase's writes of u
     for (int i = tid; i < SW * SW * SW; i += NT) {
         const int gx = x0 - H + i % SW, gy = y0 - H + (i / SW) % SW, gz = z0 - H + i / (SW * SW);
         su[i] = (gx >= 0 && gx < n && gy >= 0 && gy < n && gz >= 0 && gz < n) ? u[((size_t)gz * n + gy) * n + gx]
@@ -814,11 +817,10 @@ cudaError_t schwarz_tile3d_p(const Solver &S, const T *Kb, const T *Mb, const T 
         const int px = ph & 1, py = (ph >> 1) & 1, pz = ph >> 2;
         const int ntpx = (nt - px + 1) / 2, ntpy = (nt - py + 1) / 2, ntpz = (nt - pz + 1) / 2;
         if (ntpx <= 0 || ntpy <= 0 || ntpz <= 0) continue;
-        k_schwarz_tile3d<P, TT, T><<<ntpx * ntpy * ntpz, 128, G::bytes, st>>>(
-            S.n, nbc, S.q, S.g, reverse ? 1 : 0, px, py, pz, ntpx, ntpy, Kb, Mb, binv, S.boundary64_t(), interior,
-            S.bcls, u, b);
+        cudaError_t err = launch_pdl_smem(k_schwarz_tile3d<P, TT, T>, dim3(ntpx * ntpy * ntpz), dim3(128), G::bytes,
+                                          st, S.n, nbc, S.q, S.g, reverse ? 1 : 0, px, py, pz, ntpx, ntpy, Kb, Mb,
+                                          binv, S.boundary64_t(), interior, (const int *)S.bcls, u, b);
         count_launches(1);
-        cudaError_t err = cudaGetLastError();
         if (err != cudaSuccess) return err;
     }
     return cudaSuccess;
@@ -839,16 +841,17 @@ cudaError_t schwarz3d_p(const Solver &S, const T *Kb, const T *Mb, const T *binv
         // FP64: several blocks per CTA (175 against 180 ms for the 128^3 p=3 solve); FP32: one
         // block per CTA (the multi-block form was slower, 65.5 against 57.5 ms)
         const int nblocks = nbx * nby * nbz;
+        cudaError_t err;
         if constexpr (sizeof(T) == sizeof(double)) {
             constexpr int NB = Lattice3dGeom<P, T>::NB;
-            k_schwarz_lattice3d_mb<P, T><<<(nblocks + NB - 1) / NB, 256, 0, st>>>(
-                S.n, nbc, q, ox, oy, oz, nbx, nby, nblocks, Kb, Mb, binv, S.boundary64_t(), interior, S.bcls, u, b);
+            err = launch_pdl(k_schwarz_lattice3d_mb<P, T>, dim3((nblocks + NB - 1) / NB), dim3(256), st, S.n, nbc, q,
+                             ox, oy, oz, nbx, nby, nblocks, Kb, Mb, binv, S.boundary64_t(), interior,
+                             (const int *)S.bcls, u, b);
         } else {
-            k_schwarz_lattice3d<P, T><<<nblocks, 128, 0, st>>>(S.n, nbc, q, ox, oy, oz, nbx, nby, Kb, Mb, binv,
-                                                                S.boundary64_t(), interior, S.bcls, u, b);
+            err = launch_pdl(k_schwarz_lattice3d<P, T>, dim3(nblocks), dim3(128), st, S.n, nbc, q, ox, oy, oz, nbx,
+                             nby, Kb, Mb, binv, S.boundary64_t(), interior, (const int *)S.bcls, u, b);
         }
         count_launches(1);
-        cudaError_t err = cudaGetLastError();
         if (err != cudaSuccess) return err;
     }
     return cudaSuccess;
