@@ -394,6 +394,56 @@ def bench_3d(args, dev):
     return out
 
 
+def bench_differentiable(args, dev):
+    """p = 3 on 512^2 elements, f = 16 seeded Gaussian bumps (width 0.05), loss
+    0.5 ||u - u_t||^2: forward solve + gradient w.r.t. the 48 bump parameters, by the adjoint
+    solve (both solves to 1e-12) and by the unrolled 20-cycle backward; device time of one
+    forward + backward each (CUDA events), and a central difference of the 40-cycle map for
+    one parameter beside the adjoint gradient."""
+    import torch
+    from paper_2009_01499_gb300 import iga2l, synth
+    from paper_2009_01499_gb300.autograd import bump_solve
+    p, m, nb, width = 3, 512, 16, 0.05
+    S = iga2l.Solver(p, m, period=7, stride=2)
+    theta0 = synth.bumps(nb, synth.BASE_SEED + 5).ravel()
+    ut = torch.tensor(synth.uniform_pm1(synth.BASE_SEED + 6, S.N), device=dev)
+
+    def loss(th, mode, ncycles=20, tol=1e-12):
+        u = bump_solve(th, S, width, mode=mode, tol=tol, ncycles=ncycles)
+        return 0.5 * torch.sum((u - ut) ** 2)
+
+    out = {"workload": "2D Poisson, p=3 on 512x512 elements, f = 16 seeded Gaussian bumps (width 0.05), loss "
+                       "0.5||u - u_t||^2 with seeded u_t; gradient w.r.t. the 48 bump parameters"}
+    grads = {}
+    for mode in ("adjoint", "unrolled"):
+        times = []
+        for _ in range(3):
+            th = torch.tensor(theta0, device=dev, requires_grad=True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            L = loss(th, mode)
+            L.backward()
+            e1.record()
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            grads[mode] = th.grad.detach().cpu().numpy()
+        out[mode] = {"ms_forward_backward": min(times[1:]), "loss": float(L.item())}
+    idx = 0
+    h = 1e-5 * max(1.0, abs(theta0[idx]))
+    tp, tm = theta0.copy(), theta0.copy()
+    tp[idx] += h
+    tm[idx] -= h
+    with torch.no_grad():
+        fd = (loss(torch.tensor(tp, device=dev), "unrolled", ncycles=40).item()
+              - loss(torch.tensor(tm, device=dev), "unrolled", ncycles=40).item()) / (2 * h)
+    out["adjoint"]["fd_check"] = {"parameter": idx, "gradient": float(grads["adjoint"][idx]), "central_difference": fd,
+                                  "rel_diff": float(abs(grads["adjoint"][idx] - fd) / max(1.0, abs(fd)))}
+    g_a, g_u = grads["adjoint"], grads["unrolled"]
+    out["unrolled"]["rel_diff_to_adjoint"] = float(np.abs(g_u - g_a).max() / np.abs(g_a).max())
+    S.close()
+    return out
+
+
 def bench_high_degree(args, dev):
     """2D, p = 6, 7, 8 on 1024^2 elements (5x5 and 7x7 Schwarz blocks, Sections 4.3, 5.1):
     FP64 (LATTICE) and mixed (TILE for p = 6, LATTICE for 7x7 blocks), to 1e-8."""
@@ -701,6 +751,7 @@ def run_gpu(args):
         extra["3d"] = bench_3d(args, dev)
         extra["batched"] = bench_batched(args, dev)
         extra["high_degree"] = bench_high_degree(args, dev)
+        extra["differentiable"] = bench_differentiable(args, dev)
 
     # roofline of the dominant kernel, the Schwarz colour-phase kernel (FP64 pipe bound)
     sweep_flops, sweep_ms, per_p = 0.0, 0.0, {}
