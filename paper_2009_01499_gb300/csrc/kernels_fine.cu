@@ -104,17 +104,19 @@ k_schwarz_lattice2d(int n, int npc, int nbc, int q, int ox, int oy, int nbx, int
     if (inside) {
         const int cls = bcls[cy] * nbc + bcls[cx];
         const T *rb = rs + lb * SS;
+        // (binv, binv64: every class's inverse transposed, [class][f][e]: the lanes of a block
+        // read consecutive words)
         if (sizeof(T) == sizeof(double) || cls == interior || !binv64) {
-            const T *Bi = binv + ((size_t)cls * SS + e) * SS;
+            const T *Bi = binv + (size_t)cls * SS * SS + e;
             T ev = T(0);
 #pragma unroll
-            for (int f = 0; f < SS; ++f) ev = fma(__ldg(&Bi[f]), rb[f], ev);
+            for (int f = 0; f < SS; ++f) ev = fma(__ldg(&Bi[(size_t)f * SS]), rb[f], ev);
             u[(size_t)y * n + x] += ev;
         } else {
-            const double *Bi = binv64 + ((size_t)cls * SS + e) * SS;
+            const double *Bi = binv64 + (size_t)cls * SS * SS + e;
             double ev = 0.0;
 #pragma unroll
-            for (int f = 0; f < SS; ++f) ev = fma(__ldg(&Bi[f]), (double)rb[f], ev);
+            for (int f = 0; f < SS; ++f) ev = fma(__ldg(&Bi[(size_t)f * SS]), (double)rb[f], ev);
             u[(size_t)y * n + x] += (T)ev;
         }
     }
@@ -869,10 +871,10 @@ k_schwarz_lattice2d_pd(int n, int nbc, int q, int ox, int oy, int nbx, int nbloc
     // 3. block solve
     if (inside) {
         const int cls = bcls[cy] * nbc + bcls[cx];
-        const double *Bi = binv + ((size_t)cls * SS + e) * SS;
+        const double *Bi = binv + (size_t)cls * SS * SS + e;   // (transposed per class)
         double ev = 0.0;
 #pragma unroll
-        for (int f = 0; f < SS; ++f) ev = fma(__ldg(&Bi[f]), rs[lb][f], ev);
+        for (int f = 0; f < SS; ++f) ev = fma(__ldg(&Bi[(size_t)f * SS]), rs[lb][f], ev);
         u[(size_t)y * n + x] += ev;
     }
 }
@@ -1558,8 +1560,8 @@ cudaError_t launch_lattice_direct(const Solver &S, int q, int ox, int oy, int nb
     }
     return launch_pdl(k_schwarz_lattice2d<P, SB, BPC, T>, dim3((nblocks + BPC - 1) / BPC, S.nbatch),
                       dim3((BPC * SB * SB + 31) / 32 * 32), st, S.n, S.ht.npc, S.ht.nbc, q, ox, oy, nbx, nblocks,
-                      stencil, (const int *)S.pcls, binv, S.boundary64(), interior, (const int *)S.bcls, u, b,
-                      BatchRef{S.active, S.N, 0, 0});
+                      stencil, (const int *)S.pcls, tile_binv<T>(S), S.boundary64_t(), interior,
+                      (const int *)S.bcls, u, b, BatchRef{S.active, S.N, 0, 0});
 }
 
 // the FP64 sum-factorised colour kernel (5x5 and 7x7 blocks) with bpc blocks per CTA
@@ -1574,7 +1576,7 @@ cudaError_t launch_lattice_pd(const Solver &S, int q, int ox, int oy, int nbx, i
     }
     return launch_pdl(k_schwarz_lattice2d_pd<P, SB, BPC>, dim3((nblocks + BPC - 1) / BPC, S.nbatch),
                       dim3((BPC * SB * SB + 31) / 32 * 32), st, S.n, S.ht.nbc, q, ox, oy, nbx, nblocks, kband, mband,
-                      binv, (const int *)S.bcls, u, b, BatchRef{S.active, S.N, 0, 0});
+                      S.binv_t, (const int *)S.bcls, u, b, BatchRef{S.active, S.N, 0, 0});
 }
 
 // the colour's dynamic shared memory: the tensor-core tile or the SIMT frame step
