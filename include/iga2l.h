@@ -96,6 +96,12 @@ extern "C" {
  * finished tile is counted, so the first wait for a previous phase runs out; the call
  * returns IGA2L_ERR_DEVICE_TIMEOUT */
 #define IGA2L_TEST_WITHHOLD_PROGRESS 2
+/* every device buffer of the handle is placed between two 4 KiB guard zones: all-ones bytes
+ * (a NaN in FP32 and FP64) around floating-point buffers, zero bytes around integer tables
+ * and counters.  A kernel that reads past the end of a floating-point buffer then meets a
+ * NaN that reaches its results; one that writes past either end of any buffer changes a
+ * zone, which iga2l_guard_check reports.  Results are otherwise unchanged. */
+#define IGA2L_TEST_GUARD_ALLOCS 4
 
 typedef struct iga2l_solver *iga2l_handle;
 
@@ -136,8 +142,11 @@ void iga2l_default_options(iga2l_options *opt);
  * inverses of every block class (Section 3.1.1), the lumped L2-projection
  * restriction composed with h->2h (Sections 3.1.2, 3.3), the degree-1
  * hierarchy (Section 3.2) and the dense inverse of its coarsest level; then one
- * upload.  m must be even and large enough that interior blocks exist
- * (m >= 4p + 4); the colouring must satisfy q >= s+p, gcd(g,q) = 1, T >= q.
+ * upload.  m must be even, at least 4 (the 2h level) and at least p + 1 (n >= 2p - 1: the
+ * boundary row and block classes); on such small grids every block is a boundary block.
+ * 3D handles, IGA2L_MIXED_TF32 and IGA2L_SWEEP_PERSISTENT need m >= 4p + 4 (grids with
+ * interior blocks; AUTO then launches one kernel per colour).  The colouring must satisfy
+ * q >= s+p, gcd(g,q) = 1, T >= q.
  * *out receives the handle (NULL on error).  opt may be NULL (defaults). */
 int iga2l_assemble(int p, int m, int dim, const iga2l_options *opt, iga2l_handle *out);
 
@@ -322,6 +331,12 @@ const char *iga2l_last_error(void);
 /* Number of CUDA kernels this library has launched in this process so far
  * (all handles and threads).  For benchmarks; no GPU work. */
 long long iga2l_kernel_launches(void);
+
+/* For tests: synchronises the device and counts, in *changed, the bytes of the guard zones
+ * of a handle assembled with IGA2L_TEST_GUARD_ALLOCS that no longer hold their fill (0: no
+ * kernel of the handle wrote outside its buffers).  IGA2L_ERR_INVALID_ARG for a handle built
+ * without the flag or a null changed. */
+int iga2l_guard_check(iga2l_handle h, long long *changed);
 
 /* For benchmarks (not part of the solver): the throughput of one FMA pipe of the current
  * device in GFLOP/s (an FMA counts 2 flops), measured with dependent-free FMA loops over

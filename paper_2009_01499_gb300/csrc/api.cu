@@ -8,6 +8,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "internal.h"
@@ -72,26 +73,49 @@ int cuda_fail(cudaError_t e, const char *where)
     return fail(IGA2L_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
+// Every device buffer of a handle comes from here.  Under IGA2L_TEST_GUARD_ALLOCS it sits
+// between two zones of guard_bytes bytes: all-ones (a NaN in FP32 and FP64) around
+// floating-point buffers, so that a kernel reading past either end meets a NaN that reaches
+// its results, and zeros around integer tables and counters, so that a stray read there
+// still yields an in-range index; a stray write changes a zone (iga2l_guard_check).  The
+// zones are a multiple of 256 bytes, so every buffer keeps cudaMalloc's alignment.
+cudaError_t dmalloc(iga2l_solver *S, void **out, size_t bytes, bool floating)
+{
+    if (bytes == 0) bytes = 1;
+    const size_t G = S->guard_bytes;
+    void *base = nullptr;
+    cudaError_t e = cudaMalloc(&base, bytes + 2 * G);
+    if (e != cudaSuccess) return e;
+    S->allocs.push_back(base);
+    char *p = static_cast<char *>(base) + G;
+    if (G) {
+        const unsigned char fill = floating ? 0xFF : 0x00;
+        if ((e = cudaMemset(base, fill, G)) != cudaSuccess || (e = cudaMemset(p + bytes, fill, G)) != cudaSuccess)
+            return e;
+        S->guarded.push_back({p, bytes, fill});
+    }
+    *out = p;
+    return cudaSuccess;
+}
+
 template <typename T>
 cudaError_t upload(iga2l_solver *S, T **dst, const std::vector<T> &src)
 {
     void *p = nullptr;
-    cudaError_t e = cudaMalloc(&p, sizeof(T) * (src.empty() ? 1 : src.size()));
+    cudaError_t e = dmalloc(S, &p, sizeof(T) * src.size(), std::is_floating_point<T>::value);
     if (e != cudaSuccess) return e;
-    S->allocs.push_back(p);
     *dst = static_cast<T *>(p);
     if (src.empty()) return cudaSuccess;
     return cudaMemcpy(p, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice);
 }
 
-cudaError_t alloc(iga2l_solver *S, double **dst, size_t count)
+template <typename T>
+cudaError_t alloc(iga2l_solver *S, T **dst, size_t count)
 {
     void *p = nullptr;
-    cudaError_t e = cudaMalloc(&p, sizeof(double) * (count ? count : 1));
-    if (e != cudaSuccess) return e;
-    S->allocs.push_back(p);
-    *dst = static_cast<double *>(p);
-    return cudaSuccess;
+    cudaError_t e = dmalloc(S, &p, sizeof(T) * count, std::is_floating_point<T>::value);
+    if (e == cudaSuccess) *dst = static_cast<T *>(p);
+    return e;
 }
 
 void release(iga2l_solver *S)
@@ -491,13 +515,21 @@ static int assemble_impl(int p, int m, int dim, int nbatch, bool batch, const ig
     if (dim != 2 && dim != 3) return fail(IGA2L_ERR_INVALID_ARG, "dim must be 2 or 3");
     if (p < 2 || p > kMaxP) return fail(IGA2L_ERR_INVALID_ARG, "p must be in 2..8");
     if (dim == 3 && p > 4) return fail(IGA2L_ERR_UNSUPPORTED, "3D kernels are compiled for p = 2..4");
-    if (m < 4 * p + 4 || (m % 2) != 0)
-        return fail(IGA2L_ERR_INVALID_ARG, "m must be even and >= 4p+4 (aggressive 2h coarsening)");
+    // 2D: the boundary row and block classes need n = m + p - 2 >= 2p - 1 DOFs per axis and
+    // the aggressive 2h level m >= 4, so grids down to every block being a boundary block
+    // are accepted.  The 3D kernels, the tensor-core form and the persistent sweep are built
+    // for grids with interior blocks and rows: m >= 4p + 4.
+    const bool has_interior = m >= 4 * p + 4;
+    if ((m % 2) != 0 || m < 4 || m < p + 1)
+        return fail(IGA2L_ERR_INVALID_ARG, "m must be even, >= 4 and >= p + 1");
+    if (dim == 3 && !has_interior) return fail(IGA2L_ERR_INVALID_ARG, "3D: m must be even and >= 4p+4");
     if (opt.precision != IGA2L_FP64 && opt.precision != IGA2L_MIXED_FP32 && opt.precision != IGA2L_MIXED_FP32_ALL &&
         opt.precision != IGA2L_MIXED_TF32)
         return fail(IGA2L_ERR_UNSUPPORTED, "precision not available");
-    if (opt.precision == IGA2L_MIXED_TF32 && (dim != 2 || batch || opt.schedule != IGA2L_SCHED_LATTICE || p > kTcMaxP))
-        return fail(IGA2L_ERR_UNSUPPORTED, "the tensor-core form is compiled for single 2D problems, LATTICE, p <= 5");
+    if (opt.precision == IGA2L_MIXED_TF32 &&
+        (dim != 2 || batch || opt.schedule != IGA2L_SCHED_LATTICE || p > kTcMaxP || !has_interior))
+        return fail(IGA2L_ERR_UNSUPPORTED,
+                    "the tensor-core form is compiled for single 2D problems, LATTICE, p <= 5, m >= 4p+4");
     if (opt.schedule != IGA2L_SCHED_LATTICE && opt.schedule != IGA2L_SCHED_TILE)
         return fail(IGA2L_ERR_UNSUPPORTED, "schedule not available");
     if (dim == 3 && opt.schedule == IGA2L_SCHED_TILE) {
@@ -516,9 +548,11 @@ static int assemble_impl(int p, int m, int dim, int nbatch, bool batch, const ig
         return fail(IGA2L_ERR_INVALID_ARG, "unknown sweep kernel choice");
     if (opt.sweep == IGA2L_SWEEP_WORK_LIST && (dim != 2 || opt.schedule != IGA2L_SCHED_TILE))
         return fail(IGA2L_ERR_UNSUPPORTED, "the work-list sweep runs the 2D TILE schedule");
+    if (opt.sweep == IGA2L_SWEEP_PERSISTENT && !has_interior)
+        return fail(IGA2L_ERR_UNSUPPORTED, "the persistent sweep needs m >= 4p+4");
     if (opt.rhs != IGA2L_RHS_COEFFS && opt.rhs != IGA2L_RHS_IS_LOAD)
         return fail(IGA2L_ERR_INVALID_ARG, "rhs must be IGA2L_RHS_COEFFS or IGA2L_RHS_IS_LOAD");
-    if (opt.test_flags & ~(IGA2L_TEST_SKIP_OPERATOR_COPY | IGA2L_TEST_WITHHOLD_PROGRESS))
+    if (opt.test_flags & ~(IGA2L_TEST_SKIP_OPERATOR_COPY | IGA2L_TEST_WITHHOLD_PROGRESS | IGA2L_TEST_GUARD_ALLOCS))
         return fail(IGA2L_ERR_INVALID_ARG, "unknown test flag");
     if (opt.wait_budget_cycles < 0) return fail(IGA2L_ERR_INVALID_ARG, "wait_budget_cycles must be >= 0");
     if (opt.wait_budget_cycles == 0) opt.wait_budget_cycles = 1LL << 31;
@@ -540,6 +574,7 @@ static int assemble_impl(int p, int m, int dim, int nbatch, bool batch, const ig
     S->N = (long long)S->n * S->n * (dim == 3 ? S->n : 1);
     S->nbatch = nbatch;
     S->opt = opt;
+    S->guard_bytes = (opt.test_flags & IGA2L_TEST_GUARD_ALLOCS) ? kGuardBytes : 0;
     S->q = q; S->g = g % q; S->tile = opt.tile;
     S->tile_groups = opt.schedule == IGA2L_SCHED_TILE && dim == 2
                          ? (opt.tile_groups > 0 ? opt.tile_groups : tile_groups_default(p)) : 1;
@@ -701,22 +736,18 @@ static int assemble_impl(int p, int m, int dim, int nbatch, bool batch, const ig
         return cuda_fail(ce, "workspace allocation");
     }
     {   // status word of the bounded device waits
-        void *pw = nullptr;
-        if ((ce = cudaMalloc(&pw, sizeof(int))) != cudaSuccess ||
-            (S->allocs.push_back(pw), ce = cudaMemset(pw, 0, sizeof(int))) != cudaSuccess) {
+        if ((ce = alloc(S, &S->wait_status, 1)) != cudaSuccess ||
+            (ce = cudaMemset(S->wait_status, 0, sizeof(int))) != cudaSuccess) {
             release(S);
             return cuda_fail(ce, "status word");
         }
-        S->wait_status = static_cast<int *>(pw);
     }
     {   // completion counters of the fused residual norm, zero between launches
-        void *pc = nullptr;
-        if ((ce = cudaMalloc(&pc, sizeof(unsigned int) * B)) != cudaSuccess ||
-            (S->allocs.push_back(pc), ce = cudaMemset(pc, 0, sizeof(unsigned int) * B)) != cudaSuccess) {
+        if ((ce = alloc(S, &S->rcount, B)) != cudaSuccess ||
+            (ce = cudaMemset(S->rcount, 0, sizeof(unsigned int) * B)) != cudaSuccess) {
             release(S);
             return cuda_fail(ce, "workspace allocation");
         }
-        S->rcount = static_cast<unsigned int *>(pc);
     }
     // differentiable source (2D): quadrature tables and per-bump buffers; backward workspace
     if (dim == 2) {
@@ -756,8 +787,8 @@ static int assemble_impl(int p, int m, int dim, int nbatch, bool batch, const ig
     }
     {
         void *pc = nullptr;
-        if ((ce = cudaMalloc(&pc, sizeof(SolveCtl))) != cudaSuccess ||
-            (S->allocs.push_back(pc), (ce = alloc(S, &S->dev_hist, kSolveHistCap))) != cudaSuccess) {
+        if ((ce = dmalloc(S, &pc, sizeof(SolveCtl), false)) != cudaSuccess ||
+            (ce = alloc(S, &S->dev_hist, kSolveHistCap)) != cudaSuccess) {
             release(S);
             return cuda_fail(ce, "solve control block");
         }
@@ -769,12 +800,7 @@ static int assemble_impl(int p, int m, int dim, int nbatch, bool batch, const ig
         // for boundary classes and the FP64 coarsest inverse for the direct solve)
         MixedState &X = S->mx;
         auto to_f = [](const std::vector<double> &v) { return std::vector<float>(v.begin(), v.end()); };
-        auto allocf = [&](float **dst, size_t count) {
-            void *p = nullptr;
-            cudaError_t e = cudaMalloc(&p, sizeof(float) * (count ? count : 1));
-            if (e == cudaSuccess) { S->allocs.push_back(p); *dst = static_cast<float *>(p); }
-            return e;
-        };
+        auto allocf = [&](float **dst, size_t count) { return alloc(S, dst, count); };
         if ((ce = upload(S, &X.stencil, to_f(stencil))) != cudaSuccess ||
             (ce = upload(S, &X.binv, to_f(binv))) != cudaSuccess ||
             (ce = upload(S, &X.Rb, to_f(ht.Rb))) != cudaSuccess ||
@@ -838,14 +864,11 @@ static int assemble_impl(int p, int m, int dim, int nbatch, bool batch, const ig
         X.enabled = true;
         // the persistent LATTICE sweep of the inner cycle (one launch per sweep)
         if (dim == 2 && !batch && opt.schedule == IGA2L_SCHED_LATTICE && opt.precision != IGA2L_MIXED_TF32 &&
-            opt.sweep != IGA2L_SWEEP_PER_COLOUR) {
-            void *pp = nullptr;
-            if ((ce = cudaMalloc(&pp, sizeof(unsigned int) * 4096)) != cudaSuccess) {
+            opt.sweep != IGA2L_SWEEP_PER_COLOUR && has_interior) {
+            if ((ce = alloc(S, &S->progress, 4096)) != cudaSuccess) {
                 release(S);
                 return cuda_fail(ce, "progress counters");
             }
-            S->allocs.push_back(pp);
-            S->progress = static_cast<unsigned int *>(pp);
             if (!persist_setup(*S) && opt.sweep == IGA2L_SWEEP_PERSISTENT) {
                 release(S);
                 return fail(IGA2L_ERR_UNSUPPORTED, "no resident launch plan for the persistent sweep");
@@ -859,38 +882,30 @@ static int assemble_impl(int p, int m, int dim, int nbatch, bool batch, const ig
         }
     }
     if (opt.sweep == IGA2L_SWEEP_WORK_LIST) {   // the TILE sweep as one work-list launch
-        void *pc = nullptr;
         const size_t nt = (size_t)((S->n + tile_side(p) - 1) / tile_side(p));   // tile positions per axis
         S->tile_work_ctas = tile_work_ctas(*S);
         if (S->tile_work_ctas <= 0) {
             release(S);
             return fail(IGA2L_ERR_UNSUPPORTED, "no resident launch plan for the work-list sweep");
         }
-        if ((ce = cudaMalloc(&pc, sizeof(unsigned int) * (1 + (size_t)nbatch * nt * nt))) != cudaSuccess) {
+        if ((ce = alloc(S, &S->tile_ctr, 1 + (size_t)nbatch * nt * nt)) != cudaSuccess) {
             release(S);
             return cuda_fail(ce, "work-list counters");
         }
-        S->allocs.push_back(pc);
-        S->tile_ctr = static_cast<unsigned int *>(pc);
     }
     if (opt.sweep == IGA2L_SWEEP_PERSISTENT && S->pgx == 0) {
         release(S);
         return fail(IGA2L_ERR_UNSUPPORTED,
-                    "the persistent sweep needs a 2D single-problem handle, IGA2L_MIXED_FP32 or _FP32_ALL, LATTICE");
+                    "the persistent sweep needs a 2D single-problem handle, IGA2L_MIXED_FP32 or _FP32_ALL, LATTICE, "
+                    "m >= 4p+4");
     }
     if (batch) {
-        void *pa = nullptr, *pc = nullptr, *pn = nullptr;
-        if ((ce = cudaMalloc(&pa, sizeof(int) * B)) != cudaSuccess ||
-            (S->allocs.push_back(pa), (ce = cudaMalloc(&pc, sizeof(int) * (B + 1))) != cudaSuccess) ||
-            (S->allocs.push_back(pc), (ce = cudaMalloc(&pn, sizeof(double) * 2 * B)) != cudaSuccess)) {
+        if ((ce = alloc(S, &S->active, B)) != cudaSuccess || (ce = alloc(S, &S->bcycles, B + 1)) != cudaSuccess ||
+            (ce = alloc(S, &S->bnorm0, 2 * B)) != cudaSuccess) {
             release(S);
             return cuda_fail(ce, "batch state");
         }
-        S->allocs.push_back(pn);
-        S->active = static_cast<int *>(pa);
-        S->bcycles = static_cast<int *>(pc);
         S->bcount = S->bcycles + B;
-        S->bnorm0 = static_cast<double *>(pn);
         S->brel = S->bnorm0 + B;
     }
     *out = S;
@@ -1244,5 +1259,26 @@ const char *iga2l_strerror(int code)
 const char *iga2l_last_error(void) { return g_last_error.c_str(); }
 
 long long iga2l_kernel_launches(void) { return launches_so_far(); }
+
+int iga2l_guard_check(iga2l_handle h, long long *changed)
+{
+    int rc = check_handle(h);
+    if (rc != IGA2L_OK) return rc;
+    if (!changed) return fail(IGA2L_ERR_INVALID_ARG, "null output");
+    *changed = 0;
+    if (!h->guard_bytes) return fail(IGA2L_ERR_INVALID_ARG, "the handle was built without IGA2L_TEST_GUARD_ALLOCS");
+    cudaError_t ce = cudaDeviceSynchronize();
+    if (ce != cudaSuccess) return cuda_fail(ce, "guard check");
+    std::vector<unsigned char> zone(h->guard_bytes);
+    long long bad = 0;
+    for (const auto &g : h->guarded)
+        for (const char *z : {g.p - h->guard_bytes, g.p + g.bytes}) {
+            if ((ce = cudaMemcpy(zone.data(), z, zone.size(), cudaMemcpyDeviceToHost)) != cudaSuccess)
+                return cuda_fail(ce, "guard check");
+            for (unsigned char c : zone) bad += c != g.fill;
+        }
+    *changed = bad;
+    return IGA2L_OK;
+}
 
 }  // extern "C"

@@ -12,6 +12,7 @@ namespace iga2l {
 
 constexpr int kMaxP = 8;       // degrees with compiled kernels: 2..8 (2D), 2..4 (3D)
 constexpr int kMaxLevels = 24;
+constexpr size_t kGuardBytes = 4096;   // IGA2L_TEST_GUARD_ALLOCS: zone before and after each buffer
 // Side of the TILE schedule's tiles (block centres) compiled for degree p: a multiple
 // of the default colour period, at least 2R + P + 1 so tiles of one phase never interact.
 // The TILE kernel keeps a block in one warp, so it exists for blocks up to 5x5 (p <= 6).
@@ -133,6 +134,11 @@ struct Solver {
     int pgx = 0, pgy = 0, prx = 0, pry = 0;   // persistent sweep: regions per axis, largest sides
     unsigned psmem = 0;                       // (pgx = 0: per-colour launches)
     std::vector<void *> allocs;
+    // IGA2L_TEST_GUARD_ALLOCS: bytes of the zone before and after every device buffer, and
+    // (buffer, size in bytes, fill byte) of each guarded buffer
+    size_t guard_bytes = 0;
+    struct Guarded { char *p; size_t bytes; unsigned char fill; };
+    std::vector<Guarded> guarded;
     // FP64 inverses of the boundary block classes for the FP32 Schwarz kernels, or null
     // when those are applied in FP32 too (IGA2L_MIXED_FP32_ALL)
     const double *boundary64() const

@@ -220,9 +220,12 @@ int build_host_tables(int p, int m, int s, HostTables &ht, std::string &err)
     bspline_band_1d(p, m, ht.Kb, ht.Mb);
 
     // residual point classes: rows within 2p-1 of a boundary see non-uniform
-    // functions; rows 2p-1 .. n-2p are Toeplitz and share the middle row
+    // functions; rows 2p-1 .. n-2p are Toeplitz and share the middle row.  Row x < 2p-1
+    // has class x, row x > n-2p (and >= 2p-1) class x-n+4p-1, so on grids with fewer than
+    // 4p-1 rows every row keeps its own class and representative (itself), and the classes
+    // no row uses still have a row of the grid as representative when n >= 2p-1
     ht.npc = 4 * p - 1;
-    if (n < ht.npc) {
+    if (n < 2 * p - 1) {
         err = "mesh too small for the residual stencil classes";
         return IGA2L_ERR_INVALID_ARG;
     }
@@ -233,10 +236,13 @@ int build_host_tables(int p, int m, int s, HostTables &ht, std::string &err)
         else ht.pc_rep[c] = c + n - (4 * p - 1);
     }
     // block classes: a block is interior if all its DOFs are uniform functions,
-    // i.e. its centre lies in [L, n-1-L] with L = p-1+r
+    // i.e. its centre lies in [L, n-1-L] with L = p-1+r.  Centre x < L has class x, centre
+    // x > n-1-L (and >= L) class 2L-(n-1-x): with fewer than 2L+1 centres no block is
+    // interior, every block keeps its own class and representative, and the unused middle
+    // class is built from the (boundary) block at n/2
     ht.L = p - 1 + ht.r;
     ht.nbc = 2 * ht.L + 1;
-    if (n < ht.nbc) {
+    if (n < ht.L) {
         err = "mesh too small for the Schwarz block classes";
         return IGA2L_ERR_INVALID_ARG;
     }

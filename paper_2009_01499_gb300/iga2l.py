@@ -22,7 +22,7 @@ SCHED_LATTICE, SCHED_TILE = 1, 2
 COARSE_EXACT, COARSE_VCYCLE = 0, 1
 RHS_COEFFS, RHS_IS_LOAD = 0, 1
 SWEEP_AUTO, SWEEP_PER_COLOUR, SWEEP_PERSISTENT, SWEEP_WORK_LIST = 0, 1, 2, 3
-TEST_SKIP_OPERATOR_COPY, TEST_WITHHOLD_PROGRESS = 1, 2
+TEST_SKIP_OPERATOR_COPY, TEST_WITHHOLD_PROGRESS, TEST_GUARD_ALLOCS = 1, 2, 4
 
 # Every exported symbol of include/iga2l.h.
 EXPORTS = (
@@ -34,7 +34,7 @@ EXPORTS = (
     "iga2l_last_error", "iga2l_kernel_launches", "iga2l_residual_norm2_noalloc",
     "iga2l_cycles", "iga2l_unrolled_backward", "iga2l_bump_load", "iga2l_bump_grad",
     "iga2l_assemble_batch", "iga2l_solve_batch", "iga2l_schedule_info", "iga2l_solve_load",
-    "iga2l_schwarz_sweep_f32", "iga2l_fma_peak",
+    "iga2l_schwarz_sweep_f32", "iga2l_fma_peak", "iga2l_guard_check",
 )
 
 
@@ -102,6 +102,7 @@ def load(build_if_missing: bool = True):
             "iga2l_strerror": (ctypes.c_char_p, [ctypes.c_int]),
             "iga2l_last_error": (ctypes.c_char_p, []),
             "iga2l_kernel_launches": (ctypes.c_longlong, []),
+            "iga2l_guard_check": (ctypes.c_int, [_vp, _llp]),
             "iga2l_fma_peak": (ctypes.c_int, [ctypes.c_int, _dp, _vp]),
             "iga2l_cycles": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp]),
             "iga2l_assemble_batch": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -334,3 +335,10 @@ class Solver:
         M = np.zeros(self.n * w)
         _check(self._lib.iga2l_get_bands(self._h, K.ctypes.data_as(_dp), M.ctypes.data_as(_dp)))
         return K.reshape(self.n, w), M.reshape(self.n, w)
+
+    def guard_check(self) -> int:
+        """Bytes of the handle's guard zones that changed (handles assembled with
+        test_flags=TEST_GUARD_ALLOCS); synchronises the device."""
+        c = ctypes.c_longlong(0)
+        _check(self._lib.iga2l_guard_check(self._h, ctypes.byref(c)))
+        return c.value

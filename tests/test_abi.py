@@ -61,7 +61,8 @@ def test_options_struct_layout_matches_the_header(tmp_path):
 def test_assemble_rejects_bad_arguments_before_touching_the_gpu():
     lib = iga2l.load()
     h = ctypes.c_void_p()
-    for p, m, dim in [(1, 32, 2), (9, 64, 2), (2, 31, 2), (2, 8, 2), (2, 32, 4)]:
+    # m odd, m < 4, m < p + 1 (2D); m < 4p + 4 in 3D
+    for p, m, dim in [(1, 32, 2), (9, 64, 2), (2, 31, 2), (2, 2, 2), (8, 8, 2), (2, 32, 4), (3, 14, 3)]:
         rc = lib.iga2l_assemble(p, m, dim, None, ctypes.byref(h))
         assert rc in (iga2l.ERR_INVALID_ARG, iga2l.ERR_UNSUPPORTED)
         assert not h.value
@@ -79,6 +80,11 @@ def test_assemble_rejects_bad_arguments_before_touching_the_gpu():
     bad = iga2l.default_options(sweep=iga2l.SWEEP_WORK_LIST, schedule=iga2l.SCHED_TILE)
     assert lib.iga2l_assemble(2, 16, 3, ctypes.byref(bad), ctypes.byref(h)) == iga2l.ERR_UNSUPPORTED
     assert not h.value
+    # grids without interior blocks: no tensor-core form and no persistent sweep
+    for kw in ({"precision": iga2l.MIXED_TF32}, {"precision": iga2l.MIXED_FP32, "sweep": iga2l.SWEEP_PERSISTENT}):
+        bad = iga2l.default_options(**kw)
+        assert lib.iga2l_assemble(3, 14, 2, ctypes.byref(bad), ctypes.byref(h)) == iga2l.ERR_UNSUPPORTED, kw
+        assert not h.value
 
 
 @pytest.mark.parametrize("p", [1, 2, 3, 4, 5])
