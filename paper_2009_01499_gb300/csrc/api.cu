@@ -682,8 +682,9 @@ static int assemble_impl(int p, int m, int dim, int nbatch, bool batch, const ig
     if (!cholesky_inverse(S->ndirect, Ad)) { release(S); return fail(IGA2L_ERR_INVALID_ARG, "coarsest matrix not SPD"); }
 
     // the interior stencil of degree p from a reference mesh, so that every handle of
-    // degree p writes identical constant-memory values (2D stencils do not depend on h)
-    if (dim == 2) {
+    // degree p writes identical constant-memory values (2D stencils do not depend on h;
+    // the 3D FP32 colour kernel takes the same h-scaled 1D rows)
+    {
         HostTables ref;
         std::string rerr;
         const int mref = 8 * p + 16;
@@ -695,15 +696,18 @@ static int assemble_impl(int p, int m, int dim, int nbatch, bool batch, const ig
                 sti[(size_t)bb * W + a] = ref.Kb[(size_t)xr * W + a] * ref.Mb[(size_t)xr * W + bb]
                                         + ref.Mb[(size_t)xr * W + a] * ref.Kb[(size_t)xr * W + bb];
         // the handle's own interior class uses the same values
-        double *dst = &stencil[(size_t)((2 * p - 1) * ht.npc + (2 * p - 1)) * W * W];
-        for (int i = 0; i < W * W; ++i) dst[i] = sti[i];
+        if (dim == 2) {
+            double *dst = &stencil[(size_t)((2 * p - 1) * ht.npc + (2 * p - 1)) * W * W];
+            for (int i = 0; i < W * W; ++i) dst[i] = sti[i];
+        }
         std::vector<double> k1(W), m1(W);
         for (int a = 0; a < W; ++a) {
             k1[a] = ref.Kb[(size_t)xr * W + a] / mref;   // h K_row, h = 1 / mref
             m1[a] = ref.Mb[(size_t)xr * W + a] * mref;   // M_row / h
         }
-        if ((ce = upload_interior_rows(p, k1.data(), m1.data())) != cudaSuccess ||
-            (ce = upload_persist_rows(p, k1.data(), m1.data())) != cudaSuccess) {
+        if (dim == 2 ? ((ce = upload_interior_rows(p, k1.data(), m1.data())) != cudaSuccess ||
+                        (ce = upload_persist_rows(p, k1.data(), m1.data())) != cudaSuccess)
+                     : (ce = upload_rows3d(p, k1.data(), m1.data())) != cudaSuccess) {
             release(S);
             return cuda_fail(ce, "constant 1D rows upload");
         }

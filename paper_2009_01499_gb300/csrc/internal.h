@@ -301,6 +301,8 @@ int tile_work_ctas(const Solver &S);
 bool persist_setup(Solver &S);
 cudaError_t launch_schwarz_persist(const Solver &S, float *u, const float *b, bool reverse, cudaStream_t st);
 cudaError_t upload_persist_rows(int p, const double *k1, const double *m1);
+// the same rows (as FP32 pairs (k, m)) for the 3D FP32 colour kernel, degrees 2..4
+cudaError_t upload_rows3d(int p, const double *k1, const double *m1);
 // host: G of the interior block in the operand layout (kernels_tc.cu)
 void build_gtc(const Solver &S, const std::vector<double> &binv_interior, std::vector<float> &g, int &nrows,
                int &kcols);

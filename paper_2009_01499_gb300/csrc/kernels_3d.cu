@@ -14,8 +14,10 @@
 // Templated on the storage type (double: FP64 form; float: inner cycle of the mixed form).
 #include <cuda_runtime.h>
 
+#include <mutex>
 #include <vector>
 
+#include "device_util.cuh"
 #include "internal.h"
 
 namespace iga2l {
@@ -120,105 +122,6 @@ k_residual3d(int n, const T *__restrict__ Kb, const T *__restrict__ Mb, const T 
             double tot = 0.0;
             for (int w = 0; w < nth / 32; ++w) tot += red[w];
             part[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = tot;
-        }
-    }
-}
-
-// One LATTICE colour in 3D, one Schwarz block per CTA (128 threads), block side S = 3.
-template <int P, typename T>
-__global__ void __launch_bounds__(128)
-k_schwarz_lattice3d(int n, int nbc, int q, int ox, int oy, int oz, int nbx, int nby,
-                    const T *__restrict__ Kb, const T *__restrict__ Mb, const T *__restrict__ binv,
-                    const double *__restrict__ binv64, int interior, const int *__restrict__ bcls,
-                    T *__restrict__ u, const T *__restrict__ b)
-{
-    constexpr int S = 3, R = 1, W = 2 * P + 1, SS = S * S * S, PW = S + 2 * P;   // patch side
-    __shared__ T pu[PW * PW * PW];
-    __shared__ T tK[PW * PW * S], tM[PW * PW * S];
-    __shared__ T S1[PW * S * S], MM[PW * S * S];
-    __shared__ T rs[SS];
-    const int blk = blockIdx.x;
-    const int cx = ox + q * (blk % nbx), cy = oy + q * ((blk / nbx) % nby), cz = oz + q * (blk / (nbx * nby));
-    const int px0 = cx - R - P, py0 = cy - R - P, pz0 = cz - R - P;
-    const int tid = threadIdx.x, nth = blockDim.x;
-    pdl_wait();   // the previous colour's writes of u
-    for (int i = tid; i < PW * PW * PW; i += nth) {
-        const int gx = px0 + i % PW, gy = py0 + (i / PW) % PW, gz = pz0 + i / (PW * PW);
-        pu[i] = (gx >= 0 && gx < n && gy >= 0 && gy < n && gz >= 0 && gz < n)
-                    ? u[((size_t)gz * n + gy) * n + gx] : T(0);
-    }
-    __syncthreads();
-    for (int i = tid; i < PW * PW * S; i += nth) {   // x pass: (z, y) patch rows, 3 x outputs
-        const int ex = i % S, r = i / S;
-        const int gx = cx - R + ex;
-        T k = T(0), m = T(0);
-        if (gx >= 0 && gx < n) {
-            const T *kr = Kb + (size_t)gx * W, *mr = Mb + (size_t)gx * W;
-            const T *ur = pu + r * PW + ex;
-#pragma unroll
-            for (int a = 0; a < W; ++a) {
-                k = fma(kr[a], ur[a], k);
-                m = fma(mr[a], ur[a], m);
-            }
-        }
-        tK[i] = k;
-        tM[i] = m;
-    }
-    __syncthreads();
-    for (int i = tid; i < PW * S * S; i += nth) {    // y pass: z patch rows, 3 y x 3 x outputs
-        const int ex = i % S, ey = (i / S) % S, z = i / (S * S);
-        const int gy = cy - R + ey;
-        T s1 = T(0), mm = T(0);
-        if (gy >= 0 && gy < n) {
-            const T *kr = Kb + (size_t)gy * W, *mr = Mb + (size_t)gy * W;
-#pragma unroll
-            for (int bb = 0; bb < W; ++bb) {
-                const int j = (z * PW + ey + bb) * S + ex;
-                s1 = fma(mr[bb], tK[j], s1);
-                s1 = fma(kr[bb], tM[j], s1);
-                mm = fma(mr[bb], tM[j], mm);
-            }
-        }
-        S1[i] = s1;
-        MM[i] = mm;
-    }
-    __syncthreads();
-    if (tid < SS) {                                  // z pass and block residual
-        const int ex = tid % S, ey = (tid / S) % S, ez = tid / (S * S);
-        const int gx = cx - R + ex, gy = cy - R + ey, gz = cz - R + ez;
-        T rv = T(0);
-        if (gx >= 0 && gx < n && gy >= 0 && gy < n && gz >= 0 && gz < n) {
-            const T *kr = Kb + (size_t)gz * W, *mr = Mb + (size_t)gz * W;
-            T acc = T(0);
-#pragma unroll
-            for (int c = 0; c < W; ++c) {
-                const int j = ((ez + c) * S + ey) * S + ex;
-                acc = fma(mr[c], S1[j], acc);
-                acc = fma(kr[c], MM[j], acc);
-            }
-            rv = b[((size_t)gz * n + gy) * n + gx] - acc;
-        }
-        rs[tid] = rv;
-    }
-    __syncthreads();
-    if (tid < SS) {                                  // block solve and update
-        const int ex = tid % S, ey = (tid / S) % S, ez = tid / (S * S);
-        const int gx = cx - R + ex, gy = cy - R + ey, gz = cz - R + ez;
-        if (gx >= 0 && gx < n && gy >= 0 && gy < n && gz >= 0 && gz < n) {
-            const int cls = (bcls[cz] * nbc + bcls[cy]) * nbc + bcls[cx];
-            if (sizeof(T) == sizeof(double) || cls == interior || !binv64) {
-                const T *Bi = binv + (size_t)cls * SS * SS + tid;
-                T ev = T(0);
-#pragma unroll
-                for (int f = 0; f < SS; ++f) ev = fma(__ldg(&Bi[(size_t)f * SS]), rs[f], ev);
-                u[((size_t)gz * n + gy) * n + gx] += ev;
-            } else {
-                const double *Bi = binv64 + (size_t)cls * SS * SS + tid;
-                double ev = 0.0;
-#pragma unroll
-                for (int f = 0; f < SS; ++f) ev = fma(__ldg(&Bi[(size_t)f * SS]), (double)rs[f], ev);
-                u[((size_t)gz * n + gy) * n + gx] += (T)ev;
-            }
         }
     }
 }
@@ -365,6 +268,188 @@ k_schwarz_lattice3d_mb(int n, int nbc, int q, int ox, int oy, int oz, int nbx, i
 #pragma unroll
             for (int f = 0; f < SS; ++f) ev = fma(__ldg(&Bi[(size_t)f * SS]), (double)rs[j][f], ev);
             u[((size_t)gz * n + gy) * n + gx] += (T)ev;
+        }
+    }
+}
+
+// Interior rows of the 1D stiffness and mass matrices scaled to be independent of h
+// (k = h K_row, m = M_row / h), as pairs (k[a], m[a]); degrees 2..4, written once per
+// device and degree.
+__constant__ float2 c3_km[5][9];
+
+// One LATTICE colour in 3D for the FP32 inner cycle: one Schwarz block (S = 3) per warp,
+// WPC blocks per CTA, each warp on its own without CTA barriers.  With the 1D rows scaled
+// as k = h K, m = M / h (interior rows from c3_km, the others from their own band rows):
+//   x pass, a lane per patch row (z', y') with the row's PW values of u in registers:
+//       tK = sum_a k_x[a] u,  tM = sum_a m_x[a] u          (= h K_x u, M_x u / h)
+//   y pass, a lane per (z', x) column of the x pass's output:
+//       S1 = sum_b m_y[b] tK + k_y[b] tM,  MM = sum_b m_y[b] tM   (= S1, MM / h^2)
+//   z pass, a lane per (y, x) column:  acc = sum_c m_z[c] S1 + k_z[c] MM  (= (A u) / h)
+// then r = b - h acc, the block solve e = B^{-1} r (the interior class's inverse staged in
+// shared memory once per CTA; a boundary class's FP64 rows as the FP32 pairs binv + binv_lo
+// applied by compensated (Dot2) arithmetic, or its FP32 rows when binv_lo is null) and
+// u += e.  The arithmetic of the sum factorisation is that of
+// the residual kernels, the h factors regrouped.
+template <int P>
+struct Warp3dGeom {
+    static constexpr int S = 3, R = 1, W = 2 * P + 1, SS = S * S * S, PW = S + 2 * P;
+    static constexpr int NROW = PW * PW;   // patch rows (z', y') of the x pass
+    static constexpr int WPC = 8;          // blocks (warps) per CTA
+};
+
+template <int P>
+__global__ void __launch_bounds__(256, 5)
+k_schwarz_lattice3d_w(int n, int nbc, int q, int ox, int oy, int oz, int nbx, int nby, int nblocks,
+                      const float *__restrict__ Kb, const float *__restrict__ Mb, const float *__restrict__ binv,
+                      const float *__restrict__ binv_lo, int interior, const int *__restrict__ bcls,
+                      float *__restrict__ u, const float *__restrict__ b)
+{
+    using G = Warp3dGeom<P>;
+    constexpr int S = G::S, R = G::R, W = G::W, SS = G::SS, PW = G::PW, NROW = G::NROW, WPC = G::WPC;
+    constexpr int PCI = 2 * P - 1;   // first interior row
+    __shared__ float sbi[SS * SS];             // interior inverse, transposed: [f][e]
+    __shared__ float2 tkm_s[WPC][NROW * S];    // x pass: [(z' PW + y') S + x]
+    __shared__ float2 smm_s[WPC][PW * S * S];  // y pass: [(z' S + y) S + x]
+    __shared__ float rs_s[WPC][SS + 1];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    for (int i = tid; i < SS * SS; i += 32 * WPC) sbi[i] = binv[(size_t)interior * SS * SS + i];   // constant table
+    const int blk = blockIdx.x * WPC + w;
+    const int cx = ox + q * (blk % nbx), cy = oy + q * ((blk / nbx) % nby), cz = oz + q * (blk / (nbx * nby));
+    const float h = 1.0f / (float)(n - P + 2), hinv = (float)(n - P + 2);
+    // are the block's rows along each axis all of the interior class?  is its patch inside?
+    const bool xint = cx - R >= PCI && cx + R <= n - 2 * P, yint = cy - R >= PCI && cy + R <= n - 2 * P,
+               zint = cz - R >= PCI && cz + R <= n - 2 * P;
+    const bool inside = cx - R - P >= 0 && cx + R + P < n && cy - R - P >= 0 && cy + R + P < n &&
+                        cz - R - P >= 0 && cz + R + P < n;
+    pdl_wait();   // the previous colour's writes of u
+    __syncthreads();
+    if (blk >= nblocks) return;   // whole warps: no CTA barrier follows
+    float2 *tkm = tkm_s[w], *smm = smm_s[w];
+    float *rs = rs_s[w];
+    // x pass
+    for (int row = lane; row < NROW; row += 32) {
+        const int zp = row / PW, yp = row - zp * PW;
+        const int gy = cy - R - P + yp, gz = cz - R - P + zp, gx0 = cx - R - P;
+        float v[PW];
+        if (inside) {
+            const float *src = u + ((size_t)gz * n + gy) * n + gx0;
+#pragma unroll
+            for (int k = 0; k < PW; ++k) v[k] = src[k];
+        } else {
+            const bool rin = gy >= 0 && gy < n && gz >= 0 && gz < n;
+#pragma unroll
+            for (int k = 0; k < PW; ++k) {
+                const int gx = gx0 + k;
+                v[k] = (rin && gx >= 0 && gx < n) ? u[((size_t)gz * n + gy) * n + gx] : 0.0f;
+            }
+        }
+#pragma unroll
+        for (int ex = 0; ex < S; ++ex) {
+            float2 o = make_float2(0.0f, 0.0f);
+            if (xint) {
+#pragma unroll
+                for (int a = 0; a < W; ++a) o = fma2_3d(c3_km[P][a], make_float2(v[ex + a], v[ex + a]), o);
+            } else {
+                const int gx = cx - R + ex;
+                if (gx >= 0 && gx < n) {
+#pragma unroll
+                    for (int a = 0; a < W; ++a) {
+                        const float2 km = make_float2(Kb[(size_t)gx * W + a] * h, Mb[(size_t)gx * W + a] * hinv);
+                        o = fma2_3d(km, make_float2(v[ex + a], v[ex + a]), o);
+                    }
+                }
+            }
+            tkm[row * S + ex] = o;
+        }
+    }
+    __syncwarp();
+    // y pass
+    for (int it = lane; it < PW * S; it += 32) {
+        const int zp = it / S, ex = it - zp * S;
+        float2 t[PW];
+#pragma unroll
+        for (int yp = 0; yp < PW; ++yp) t[yp] = tkm[(zp * PW + yp) * S + ex];
+#pragma unroll
+        for (int ey = 0; ey < S; ++ey) {
+            const int gy = cy - R + ey;
+            float2 acc = make_float2(0.0f, 0.0f);   // (sum m tK, sum m tM)
+            float ak = 0.0f;                         // sum k tM
+            if (yint) {
+#pragma unroll
+                for (int bb = 0; bb < W; ++bb) {
+                    const float2 c = c3_km[P][bb];
+                    acc = fma2_3d(make_float2(c.y, c.y), t[ey + bb], acc);
+                    ak = fmaf(c.x, t[ey + bb].y, ak);
+                }
+            } else if (gy >= 0 && gy < n) {
+#pragma unroll
+                for (int bb = 0; bb < W; ++bb) {
+                    const float k = Kb[(size_t)gy * W + bb] * h, m = Mb[(size_t)gy * W + bb] * hinv;
+                    acc = fma2_3d(make_float2(m, m), t[ey + bb], acc);
+                    ak = fmaf(k, t[ey + bb].y, ak);
+                }
+            }
+            smm[(zp * S + ey) * S + ex] = make_float2(acc.x + ak, acc.y);
+        }
+    }
+    __syncwarp();
+    // z pass and the block residual
+    if (lane < S * S) {
+        const int ey = lane / S, ex = lane - ey * S;
+        const int gx = cx - R + ex, gy = cy - R + ey;
+        float2 t[PW];
+#pragma unroll
+        for (int zp = 0; zp < PW; ++zp) t[zp] = smm[(zp * S + ey) * S + ex];
+#pragma unroll
+        for (int ez = 0; ez < S; ++ez) {
+            const int gz = cz - R + ez;
+            float rv = 0.0f;
+            if (gx >= 0 && gx < n && gy >= 0 && gy < n && gz >= 0 && gz < n) {
+                float2 acc = make_float2(0.0f, 0.0f);   // (sum m S1, sum k MM)
+                if (zint) {
+#pragma unroll
+                    for (int c = 0; c < W; ++c) {
+                        const float2 km = c3_km[P][c];
+                        acc = fma2_3d(make_float2(km.y, km.x), t[ez + c], acc);
+                    }
+                } else {
+#pragma unroll
+                    for (int c = 0; c < W; ++c) {
+                        const float2 mk = make_float2(Mb[(size_t)gz * W + c] * hinv, Kb[(size_t)gz * W + c] * h);
+                        acc = fma2_3d(mk, t[ez + c], acc);
+                    }
+                }
+                rv = b[((size_t)gz * n + gy) * n + gx] - h * (acc.x + acc.y);
+            }
+            rs[(ez * S + ey) * S + ex] = rv;
+        }
+    }
+    __syncwarp();
+    // block solve and update
+    if (lane < SS) {
+        const int e = lane, ex = e % S, ey = (e / S) % S, ez = e / (S * S);
+        const int gx = cx - R + ex, gy = cy - R + ey, gz = cz - R + ez;
+        if (gx >= 0 && gx < n && gy >= 0 && gy < n && gz >= 0 && gz < n) {
+            const int cls = (bcls[cz] * nbc + bcls[cy]) * nbc + bcls[cx];
+            const size_t k = ((size_t)gz * n + gy) * n + gx;
+            if (cls == interior) {
+                float e0 = 0.0f, e1 = 0.0f;
+#pragma unroll
+                for (int f = 0; f < SS; ++f) {
+                    float &acc = (f & 1) ? e1 : e0;
+                    acc = fmaf(sbi[f * SS + e], rs[f], acc);
+                }
+                u[k] += e0 + e1;
+            } else if (!binv_lo) {
+                const float *Bi = binv + (size_t)cls * SS * SS + e;
+                float ev = 0.0f;
+#pragma unroll
+                for (int f = 0; f < SS; ++f) ev = fmaf(__ldg(&Bi[(size_t)f * SS]), rs[f], ev);
+                u[k] += ev;
+            } else {
+                const size_t col = (size_t)cls * SS * SS + e;
+                u[k] += dot2_row<SS, SS>(binv + col, binv_lo + col, rs);
+            }
         }
     }
 }
@@ -838,8 +923,9 @@ cudaError_t schwarz3d_p(const Solver &S, const T *Kb, const T *Mb, const T *binv
         const int ox = ((c % q) * S.g) % q, oy = (((c / q) % q) * S.g) % q, oz = ((c / (q * q)) * S.g) % q;
         const int nbx = (S.n - ox + q - 1) / q, nby = (S.n - oy + q - 1) / q, nbz = (S.n - oz + q - 1) / q;
         if (nbx <= 0 || nby <= 0 || nbz <= 0) continue;
-        // FP64: several blocks per CTA (175 against 180 ms for the 128^3 p=3 solve); FP32: one
-        // block per CTA (the multi-block form was slower, 65.5 against 57.5 ms)
+        // FP64: several blocks per CTA, every pass over all threads (bound by the FP64 pipe;
+        // 175 against 180 ms for the 128^3 p=3 solve with one block per CTA); FP32: one block
+        // per warp (the one-block-per-CTA form spent ~3.3k warp instructions per block, ncu)
         const int nblocks = nbx * nby * nbz;
         cudaError_t err;
         if constexpr (sizeof(T) == sizeof(double)) {
@@ -848,8 +934,10 @@ cudaError_t schwarz3d_p(const Solver &S, const T *Kb, const T *Mb, const T *binv
                              ox, oy, oz, nbx, nby, nblocks, Kb, Mb, binv, S.boundary64_t(), interior,
                              (const int *)S.bcls, u, b);
         } else {
-            err = launch_pdl(k_schwarz_lattice3d<P, T>, dim3(nblocks), dim3(128), st, S.n, nbc, q, ox, oy, oz, nbx,
-                             nby, Kb, Mb, binv, S.boundary64_t(), interior, (const int *)S.bcls, u, b);
+            constexpr int WPC = Warp3dGeom<P>::WPC;
+            err = launch_pdl(k_schwarz_lattice3d_w<P>, dim3((nblocks + WPC - 1) / WPC), dim3(32 * WPC), st, S.n, nbc,
+                             q, ox, oy, oz, nbx, nby, nblocks, Kb, Mb, binv, S.boundary_lo_t(), interior,
+                             (const int *)S.bcls, u, b);
         }
         count_launches(1);
         if (err != cudaSuccess) return err;
@@ -972,6 +1060,23 @@ cudaError_t launch3d_inner_update(const Solver &S, double *u, cudaStream_t st)
 {
     const MixedState &X = S.mx;
     return prolong3d<float, double>(S, X.Cb, X.ec, X.t, X.t2, X.delta, u, st);
+}
+
+cudaError_t upload_rows3d(int p, const double *k1, const double *m1)
+{
+    static std::mutex mu;
+    static bool done[64][5] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev < 0 || dev >= 64 || p < 2 || p > 4) return cudaErrorInvalidValue;
+    if (done[dev][p]) return cudaSuccess;
+    float2 km[9] = {};
+    for (int i = 0; i < 2 * p + 1; ++i) km[i] = make_float2((float)k1[i], (float)m1[i]);
+    e = cudaMemcpyToSymbol(c3_km, km, sizeof(km), sizeof(km) * p);
+    if (e == cudaSuccess) done[dev][p] = true;
+    return e;
 }
 
 }  // namespace iga2l
