@@ -321,13 +321,29 @@ k_schwarz_lattice3d_w(int n, int nbc, int q, int ox, int oy, int oz, int nbx, in
                zint = cz - R >= PCI && cz + R <= n - 2 * P;
     const bool inside = cx - R - P >= 0 && cx + R + P < n && cy - R - P >= 0 && cy + R + P < n &&
                         cz - R - P >= 0 && cz + R + P < n;
-    pdl_wait();   // the previous colour's writes of u
+    pdl_wait();   // the previous colour's writes of u (and the outer cycle's of b)
     __syncthreads();
     if (blk >= nblocks) return;   // whole warps: no CTA barrier follows
     float2 *tkm = tkm_s[w], *smm = smm_s[w];
     float *rs = rs_s[w];
-    // x pass
-    for (int row = lane; row < NROW; row += 32) {
+    // the z pass's values of b, loaded now so that their latency overlaps the x pass
+    float bz[S];
+    {
+        const int ey = lane / S, ex = lane - ey * S;
+        const int gx = cx - R + ex, gy = cy - R + ey;
+#pragma unroll
+        for (int ez = 0; ez < S; ++ez) {
+            const int gz = cz - R + ez;
+            bz[ez] = (lane < S * S && gx >= 0 && gx < n && gy >= 0 && gy < n && gz >= 0 && gz < n)
+                         ? b[((size_t)gz * n + gy) * n + gx] : 0.0f;
+        }
+    }
+    // x pass (a compile-time number of rounds, so that a round's loads may be issued early)
+    constexpr int NR = (NROW + 31) / 32;
+#pragma unroll
+    for (int rr = 0; rr < NR; ++rr) {
+        const int row = lane + 32 * rr;
+        if (row >= NROW) break;
         const int zp = row / PW, yp = row - zp * PW;
         const int gy = cy - R - P + yp, gz = cz - R - P + zp, gx0 = cx - R - P;
         float v[PW];
@@ -419,7 +435,7 @@ k_schwarz_lattice3d_w(int n, int nbc, int q, int ox, int oy, int oz, int nbx, in
                         acc = fma2_3d(mk, t[ez + c], acc);
                     }
                 }
-                rv = b[((size_t)gz * n + gy) * n + gx] - h * (acc.x + acc.y);
+                rv = bz[ez] - h * (acc.x + acc.y);
             }
             rs[(ez * S + ey) * S + ex] = rv;
         }
