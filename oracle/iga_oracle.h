@@ -158,8 +158,10 @@ long long or_ndofs(const or_problem *P); /* n^d */
 /* Pinned by (problem level): or_residual = b - (explicit Kronecker A) u; or_smooth =
  * the product formula above for the problem's schedule; or_restrict / or_prolong_add =
  * Kronecker products of or_restriction_1d and their adjointness; or_coarse_solve =
- * the dense Cholesky solve (exact kind) or a V(1,1) that is symmetric and contracts
- * (V-cycle kind); or_cycle = the dense (I - R^T A_c^{-1} R A) S_E on tiny grids;
+ * the dense Cholesky solve (exact kind) or, V-cycle kind, a V(1,1) whose whole
+ * approximate inverse equals the dense product of its steps built independently (the
+ * sub-lattice Gauss-Seidel sweeps, the level restriction and embedding, the coarsest
+ * solve), and which is symmetric and contracts; or_cycle = the dense (I - R^T A_c^{-1} R A) S_E on tiny grids;
  * or_cycle_adjoint = <C x, y> = <x, C^T y> and the dense C^T; or_solve = the stopping
  * rule and the Section 5.1 manufactured solution reached to 1e-8.  In 3D (the paper is
  * 2D only) these are pinned by the same mathematics and parity is unpinned by the
