@@ -103,10 +103,21 @@ def test_library_bands_match_oracle(oracle_mod, p, m):
             assert abs(Mb[i, a] - ref_m) <= 1e-13 / m
 
 
-@pytest.mark.parametrize("p", [2, 3, 4, 5])
-@pytest.mark.parametrize("m", [24, 40])
+@pytest.mark.parametrize("p,m", [(p, m) for p in (2, 3, 4, 5) for m in (24, 40)] +
+                         # the smallest grids of each degree (every block a boundary block)
+                         [(2, 4), (3, 4), (4, 6), (5, 6), (6, 8), (7, 8), (8, 10), (8, 16)])
 def test_library_restriction_matches_oracle(oracle_mod, p, m):
     R = oracle_mod.restriction_1d(p, m, aggressive=True)
     Rl = iga2l.host_restriction(p, m)
     assert np.array_equal(Rl == 0, R == 0)              # same band
     assert np.allclose(Rl, R, atol=1e-14, rtol=0)        # rounding-level agreement
+
+
+def test_host_tables_refuse_grids_below_the_class_minimum():
+    """n = m + p - 2 must be at least 2p - 1 (every boundary row class a row of the grid)."""
+    lib = iga2l.load()
+    R = np.zeros(64 * 64)
+    for p, m in [(8, 8), (6, 6), (4, 4)]:
+        assert m + p - 2 < 2 * p - 1
+        rc = lib.iga2l_host_restriction(p, m, R.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        assert rc == iga2l.ERR_INVALID_ARG, (p, m)
