@@ -297,8 +297,12 @@ struct Warp3dGeom {
     static constexpr int WPC = 8;          // blocks (warps) per CTA
 };
 
+// resident CTAs per SM the register allocation must allow: 6 (40 registers) puts a 128^3
+// colour (up to 858 CTAs) in one wave; p = 4 would spill there and keeps 5
+constexpr int lattice3d_w_minb(int p) { return p == 4 ? 5 : 6; }
+
 template <int P>
-__global__ void __launch_bounds__(256, 5)
+__global__ void __launch_bounds__(256, lattice3d_w_minb(P))
 k_schwarz_lattice3d_w(int n, int nbc, int q, int ox, int oy, int oz, int nbx, int nby, int nblocks,
                       const float *__restrict__ Kb, const float *__restrict__ Mb, const float *__restrict__ binv,
                       const float *__restrict__ binv_lo, int interior, const int *__restrict__ bcls,
