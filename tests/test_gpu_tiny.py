@@ -1,6 +1,6 @@
 """GPU parity on tiny 2D grids, down to every Schwarz block and every stencil row being a
-boundary one (SURVEY's stand-in for a memory checker: the boundary paths of every kernel
-on their own).
+boundary one: in place of a memory checker, the boundary paths of every kernel on their
+own.
 
 The library accepts even m >= max(4, p + 1), i.e. n = m + p - 2 >= 2p - 1 DOFs per axis:
   * with n < 2L + 1 (L = p - 1 + r) no block centre is interior;
