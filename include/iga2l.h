@@ -47,7 +47,9 @@ extern "C" {
 /* precision */
 #define IGA2L_FP64 0
 /* FP64 outer residual, norm and update around an FP32 inner cycle (FP32 storage
- * and FMA; FP64 boundary-block inverses and coarsest solve): iterative refinement */
+ * and FMA; FP64 boundary-block inverses, applied in the FP32 colour kernels as FP32
+ * pairs by compensated (Dot2) arithmetic, and an FP64 coarsest solve): iterative
+ * refinement */
 #define IGA2L_MIXED_FP32 1
 /* The same with the boundary-block inverses also applied in FP32 (the Schwarz blocks
  * of p <= 5 have condition numbers below 5e2, so this costs the inner cycle ~3e-5
